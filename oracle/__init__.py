@@ -1,0 +1,326 @@
+"""Plain FP64 CPU oracle for per-pixel glint shading under an environment map.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` import this
+package.  The product library never imports, links or runs it, and the two
+share no code.
+
+The arithmetic lives in ``glint_oracle.c`` (each function cites the passage of
+Kneiphof & Klein, "Real-Time Image-based Lighting of Glints", EGSR 2025, that
+it follows).  This module compiles that file with gcc and wraps it with
+ctypes; it only converts arrays.
+
+Parity status of each function: every function is pinned by tests under
+``tests/test_oracle_*.py`` against closed forms, the paper's printed outcome
+table (Fig. "gatingdiagram"), brute force or independent library routines.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "glint_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+# Tie model of the FP32 kernel (see or_shade in glint_oracle.c):
+# relative error of subtree probability masses, of the FP32 normal quantile,
+# of an FP32 exp2/log2 chain, and an absolute floor.
+TIE_DEFAULT = (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23)
+NV = 6
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        D = ctypes.c_double
+        I = ctypes.c_int
+        L = ctypes.c_long
+        P = ctypes.c_void_p
+        U = ctypes.c_uint32
+        lib.or_pcg4d.argtypes = [P, P]
+        lib.or_xi.argtypes = [U]
+        lib.or_xi.restype = D
+        lib.or_ndtri.argtypes = [D]
+        lib.or_ndtri.restype = D
+        lib.or_eps.restype = D
+        lib.or_dualgated_thresholds.argtypes = [D, D, P, P, P]
+        lib.or_dualgated.argtypes = [D, D, D, D, I, P, P]
+        lib.or_singlegated_old.argtypes = [D, D, D, D]
+        lib.or_singlegated_old.restype = D
+        lib.or_singlegated.argtypes = [D, D, D, D]
+        lib.or_singlegated.restype = D
+        lib.or_ggx_d.argtypes = [D, D]
+        lib.or_ggx_d.restype = D
+        lib.or_lut.argtypes = [I, I, P]
+        lib.or_lut_point.argtypes = [D, D, I, P]
+        lib.or_projected_area.argtypes = [D, I]
+        lib.or_projected_area.restype = D
+        lib.or_dualgated_many.argtypes = [D, D, P, P, L, I, P, P]
+        lib.or_total_area.argtypes = [D, I]
+        lib.or_total_area.restype = D
+        lib.or_env_decompose.argtypes = [P, I, I, D, I, D, P, P, P]
+        lib.or_mip_count.argtypes = [I]
+        lib.or_mip_count.restype = I
+        lib.or_env_mips.argtypes = [P, I, I, I, P]
+        lib.or_prefilter_table.argtypes = [I, I, D, D, I, I, P, P]
+        lib.or_prefilter.argtypes = [P, I, I, I, P, P, I, I, I, I, P, L, P]
+        lib.or_prefilter_exact.argtypes = [P, I, I, I, D, P, L, P]
+        lib.or_shade.argtypes = [P, L, P, I, I, I, I, D, D, P, I, P, I, U, I, P, I,
+                                 P, P, P, P, P, P, P, P, P, P, P]
+        lib.or_shade.restype = L
+        lib.or_radiance.argtypes = [P, P, D, P, I, P, P, P]
+        lib.or_multinomial.argtypes = [P, I, D, U, U, U, U, I, P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- primitives
+def pcg4d(v) -> np.ndarray:
+    lib = _load()
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.uint32).reshape(4))
+    out = np.zeros(4, np.uint32)
+    lib.or_pcg4d(_ptr(a), _ptr(out))
+    return out
+
+
+def xi(h: int) -> float:
+    return _load().or_xi(int(h) & 0xFFFFFFFF)
+
+
+def ndtri(p: float) -> float:
+    return _load().or_ndtri(float(p))
+
+
+def eps() -> float:
+    return _load().or_eps()
+
+
+def dualgated_thresholds(N: float, p: float):
+    lib = _load()
+    T = np.zeros(4)
+    mu = ctypes.c_double()
+    sg = ctypes.c_double()
+    lib.or_dualgated_thresholds(float(N), float(p), _ptr(T), ctypes.byref(mu), ctypes.byref(sg))
+    return T, mu.value, sg.value
+
+
+def dualgated(N: float, p: float, xi1: float, xi2: float, integer_mode: bool = False):
+    lib = _load()
+    n = ctypes.c_double()
+    nb = ctypes.c_double()
+    lib.or_dualgated(float(N), float(p), float(xi1), float(xi2), int(integer_mode), ctypes.byref(n),
+                     ctypes.byref(nb))
+    return n.value, nb.value
+
+
+def singlegated_old(N, p, xi1, xi2) -> float:
+    return _load().or_singlegated_old(float(N), float(p), float(xi1), float(xi2))
+
+
+def singlegated(N, p, xi1, xi2) -> float:
+    return _load().or_singlegated(float(N), float(p), float(xi1), float(xi2))
+
+
+def ggx_d(cos_h: float, alpha: float) -> float:
+    return _load().or_ggx_d(float(cos_h), float(alpha))
+
+
+def lut(n: int = 64, Q: int = 128) -> np.ndarray:
+    """(n, n, 4) table over (sqrt alpha rows, mu_o columns): V, U, A, B."""
+    out = np.zeros((n, n, 4))
+    _load().or_lut(n, Q, _ptr(out))
+    return out
+
+
+def lut_point(mu: float, alpha: float, Q: int = 128) -> np.ndarray:
+    """(V, U, A, B) at one (mu_o, alpha) by the table's quadrature."""
+    out = np.zeros(4)
+    _load().or_lut_point(float(mu), float(alpha), int(Q), _ptr(out))
+    return out
+
+
+def projected_area(alpha: float, Q: int = 128) -> float:
+    return _load().or_projected_area(float(alpha), int(Q))
+
+
+def dualgated_many(N: float, p: float, xi1, xi2, integer_mode: bool = False):
+    lib = _load()
+    xi1 = np.ascontiguousarray(xi1, dtype=np.float64)
+    xi2 = np.ascontiguousarray(np.broadcast_to(xi2, xi1.shape), dtype=np.float64)
+    n = np.zeros(xi1.shape)
+    nb = np.zeros(xi1.shape)
+    lib.or_dualgated_many(float(N), float(p), _ptr(xi1), _ptr(xi2), xi1.size, int(integer_mode), _ptr(n), _ptr(nb))
+    return n, nb
+
+
+def total_area(alpha: float, Q: int = 128) -> float:
+    return _load().or_total_area(float(alpha), int(Q))
+
+
+# ---------------------------------------------------------------- environment
+@dataclass
+class EnvOracle:
+    levels: np.ndarray      # (K,)
+    lohi: np.ndarray        # (2,)
+    ch0: np.ndarray         # (H, W, 3+K)
+    mips: list              # list of (H>>m, W>>m, 3+K)
+    mips_flat: np.ndarray
+
+
+def env_decompose(rgba: np.ndarray, scale: float, K: int, ell: float):
+    lib = _load()
+    rgba = np.ascontiguousarray(rgba, dtype=np.float32)
+    H, W = rgba.shape[:2]
+    L = np.zeros(K)
+    lohi = np.zeros(2)
+    ch0 = np.zeros((H, W, 3 + K))
+    lib.or_env_decompose(_ptr(rgba), W, H, float(scale), K, float(ell), _ptr(L), _ptr(lohi), _ptr(ch0))
+    return L, lohi, ch0
+
+
+def mip_count(H: int) -> int:
+    return _load().or_mip_count(int(H))
+
+
+def env_mips(ch0: np.ndarray):
+    lib = _load()
+    H, W, C = ch0.shape
+    M = mip_count(H)
+    total = sum((W >> m) * (H >> m) * C for m in range(M))
+    flat = np.zeros(total)
+    lib.or_env_mips(_ptr(np.ascontiguousarray(ch0)), W, H, C, _ptr(flat))
+    levels, off = [], 0
+    for m in range(M):
+        n = (W >> m) * (H >> m) * C
+        levels.append(flat[off:off + n].reshape(H >> m, W >> m, C))
+        off += n
+    return flat, levels
+
+
+def env_full(rgba: np.ndarray, scale: float, K: int, ell: float) -> EnvOracle:
+    L, lohi, ch0 = env_decompose(rgba, scale, K, ell)
+    flat, levels = env_mips(ch0)
+    return EnvOracle(L, lohi, ch0, levels, flat)
+
+
+def prefilter_table(R: int, S: int, s_min: float, s_max: float, W: int, H: int):
+    table = np.zeros((R, S, 4))
+    nvalid = np.zeros(R, np.int32)
+    _load().or_prefilter_table(R, S, float(s_min), float(s_max), W, H, _ptr(table), _ptr(nvalid))
+    return table, nvalid
+
+
+def prefilter(env: EnvOracle, R: int, S: int, s_min: float, s_max: float, Wo: int, Ho: int, idx=None):
+    """Filtered environment (R, Ho, Wo, C), or only the listed flat texel indices (n, C)."""
+    lib = _load()
+    H, W, C = env.ch0.shape
+    table, nvalid = prefilter_table(R, S, s_min, s_max, W, H)
+    if idx is None:
+        out = np.zeros((R, Ho, Wo, C))
+        lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, Wo, Ho, None, 0, _ptr(out))
+        return out
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros((len(idx), C))
+    lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, Wo, Ho, _ptr(idx), len(idx),
+                     _ptr(out))
+    return out
+
+
+def prefilter_exact(ch0: np.ndarray, alpha: float, dirs: np.ndarray) -> np.ndarray:
+    lib = _load()
+    H, W, C = ch0.shape
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((len(dirs), C))
+    lib.or_prefilter_exact(_ptr(np.ascontiguousarray(ch0)), W, H, C, float(alpha), _ptr(dirs), len(dirs), _ptr(out))
+    return out
+
+
+# ---------------------------------------------------------------- shading
+@dataclass
+class ShadeOracle:
+    rgb: np.ndarray       # (n, 3) nominal outcome
+    lo: np.ndarray        # (n, 3) smooth radiance L_o
+    pk: np.ndarray        # (n, K)
+    np_: np.ndarray       # (n,) float32 N_P
+    vert: np.ndarray      # (n, 6, 3) int64 vertex x, y, level
+    wv: np.ndarray        # (n, 6) sample weights
+    nroot: np.ndarray     # (n, 6) trials at each tree root
+    ncand: np.ndarray     # (n, 6) number of valid count vectors (-1: overflow)
+    cand: np.ndarray      # (n, 6, max_cand, K)
+    cand_err: np.ndarray  # (n, 6, max_cand, K)
+    flags: np.ndarray     # (n,) decisions too close to call
+    levels: np.ndarray    # (K,)
+
+
+def gbuffer_rows(planes) -> np.ndarray:
+    """Stack the four (n, 4) G-buffer planes into the oracle's (n, 16) rows."""
+    return np.ascontiguousarray(np.concatenate([np.asarray(p, np.float32).reshape(-1, 4) for p in planes], axis=1))
+
+
+def shade(gb16: np.ndarray, pref: np.ndarray, s_min: float, s_max: float, lut_tab: np.ndarray, levels: np.ndarray,
+          seed: int, integer_mode: bool = True, tie=TIE_DEFAULT, max_cand: int = 8) -> ShadeOracle:
+    lib = _load()
+    gb16 = np.ascontiguousarray(gb16, dtype=np.float32).reshape(-1, 16)
+    n = gb16.shape[0]
+    R, Ho, Wo, C = pref.shape
+    K = len(levels)
+    pref = np.ascontiguousarray(pref, dtype=np.float64)
+    lut_tab = np.ascontiguousarray(lut_tab, dtype=np.float64)
+    nlut = lut_tab.shape[0]
+    levels = np.ascontiguousarray(levels, dtype=np.float64)
+    tie_a = np.asarray(tie, dtype=np.float64)
+    o = ShadeOracle(rgb=np.zeros((n, 3)), lo=np.zeros((n, 3)), pk=np.zeros((n, K)), np_=np.zeros(n, np.float32),
+                    vert=np.zeros((n, NV, 3), np.int64), wv=np.zeros((n, NV)), nroot=np.zeros((n, NV)),
+                    ncand=np.zeros((n, NV), np.int32), cand=np.zeros((n, NV, max_cand, K)),
+                    cand_err=np.zeros((n, NV, max_cand, K)), flags=np.zeros(n, np.int32), levels=levels)
+    lib.or_shade(_ptr(gb16), n, _ptr(pref), R, Ho, Wo, C, float(s_min), float(s_max), _ptr(lut_tab), nlut,
+                 _ptr(levels), K, ctypes.c_uint32(seed & 0xFFFFFFFF), int(integer_mode), _ptr(tie_a), max_cand,
+                 _ptr(o.rgb), _ptr(o.lo), _ptr(o.pk), _ptr(o.np_), _ptr(o.vert), _ptr(o.wv), _ptr(o.nroot),
+                 _ptr(o.ncand), _ptr(o.cand), _ptr(o.cand_err), _ptr(o.flags))
+    return o
+
+
+def radiance(o: ShadeOracle, q: int, counts: np.ndarray) -> np.ndarray:
+    """Radiance of pixel q for a chosen (6, K) count array drawn from its candidate lists."""
+    lib = _load()
+    K = o.pk.shape[1]
+    out = np.zeros(3)
+    lo3 = np.ascontiguousarray(o.lo[q])
+    pk = np.ascontiguousarray(o.pk[q])
+    wv = np.ascontiguousarray(o.wv[q])
+    c = np.ascontiguousarray(counts, dtype=np.float64).reshape(NV, K)
+    lib.or_radiance(_ptr(lo3), _ptr(pk), float(o.np_[q]), _ptr(o.levels), K, _ptr(wv), _ptr(c), _ptr(out))
+    return out
+
+
+def multinomial(p, N: float, key=(0, 0, 0), seed: int = 0, integer_mode: bool = True) -> np.ndarray:
+    lib = _load()
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    K = len(p)
+    out = np.zeros(K)
+    lib.or_multinomial(_ptr(p), K, float(N), ctypes.c_uint32(key[0] & 0xFFFFFFFF), ctypes.c_uint32(key[1] & 0xFFFFFFFF),
+                       ctypes.c_uint32(key[2] & 0xFFFFFFFF), ctypes.c_uint32(seed & 0xFFFFFFFF), int(integer_mode),
+                       _ptr(out))
+    return out

@@ -1,0 +1,995 @@
+/*
+ * glint_oracle.c -- plain, slow CPU oracle for per-pixel glint shading under
+ * an environment map (Kneiphof & Klein, "Real-Time Image-based Lighting of
+ * Glints", EGSR 2025, arXiv 2507.02674).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this library.  The CUDA library never
+ * links, calls or executes it, and the two share no code, header or table.
+ *
+ * Precision.  Everything is FP64, with one exception: the quantities that
+ * decide an integer before any probability enters -- the footprint area |P|,
+ * the microfacet count N_P, the grid level, the grid vertices and the
+ * dithering of N_P -- are computed with correctly rounded IEEE single
+ * precision operations in a fixed order.  The paper's method is an FP32
+ * method (Sec. 5 "Numeric Gating Issues"; its bias constant is tuned for
+ * FP32), so those integer decisions are taken in the paper's precision on
+ * both sides.  Compile with -ffp-contract=off so that no multiply-add is
+ * fused behind our back.
+ *
+ * Decisions that depend on probabilities (the gating comparisons of Alg. 1
+ * and the rounding of the Gaussian count) cannot be reproduced bit for bit by
+ * an FP32 kernel.  For each such decision the oracle evaluates how far its
+ * threshold can move under a stated relative error of the FP32 inputs
+ * (tie model, see or_shade) and, when the uniform number falls inside that
+ * band, keeps every outcome as a valid alternative.  A tree therefore yields
+ * a small set of valid count vectors; the GPU result must be one of them.
+ *
+ * Readings of the paper that this file makes (the paper is silent or the
+ * source is garbled) are marked "Reading:".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+#define OR_MAXK 16
+#define OR_NV 6 /* grid samples per pixel: 2 levels x 3 triangle vertices */
+
+/* --------------------------------------------------------------------------
+ * Hashing and uniform numbers.
+ * The paper stores random seeds theta_i at the grid vertices (Sec. 3.3,
+ * Eq. anisogrid) but does not name a generator.  Reading: pcg4d of
+ * Jarzynski & Olano, "Hash Functions for GPU Rendering", JCGT 9(3), 2020,
+ * applied to (vertex x, vertex y, level | node << 16, user seed); its four
+ * output words give xi0 (dither), xi1 (gating) and xi2 (Gaussian).
+ * ------------------------------------------------------------------------ */
+void or_pcg4d(const uint32_t in[4], uint32_t out[4])
+{
+    uint32_t x = in[0] * 1664525u + 1013904223u;
+    uint32_t y = in[1] * 1664525u + 1013904223u;
+    uint32_t z = in[2] * 1664525u + 1013904223u;
+    uint32_t w = in[3] * 1664525u + 1013904223u;
+    x += y * w; y += z * x; z += x * y; w += y * z;
+    x ^= x >> 16; y ^= y >> 16; z ^= z >> 16; w ^= w >> 16;
+    x += y * w; y += z * x; z += x * y; w += y * z;
+    out[0] = x; out[1] = y; out[2] = z; out[3] = w;
+}
+
+/* Uniform number in (0,1) from a hash word: the top 23 bits, centred,
+ * (2m+1) * 2^-24.  Exactly representable in FP32 and FP64, never 0 or 1,
+ * and 1 - xi is exact as well. */
+double or_xi(uint32_t h)
+{
+    return (2.0 * (double)(h >> 9) + 1.0) * 0x1p-24;
+}
+
+/* Standard normal quantile Phi^-1(p) in FP64.  Starting value from
+ * Abramowitz & Stegun 26.2.23 (absolute error < 4.5e-4), refined by Newton
+ * steps on Phi(x) = erfc(-x/sqrt 2)/2 from the C library. */
+double or_ndtri(double p)
+{
+    if (!(p > 0.0)) return -INFINITY;
+    if (!(p < 1.0)) return INFINITY;
+    if (p > 0.5) return -or_ndtri(1.0 - p); /* 1 - p is exact on (0.5, 1) */
+    double t = sqrt(-2.0 * log(p));
+    double x = -(t - (2.515517 + 0.802853 * t + 0.010328 * t * t) /
+                         (1.0 + 1.432788 * t + 0.189269 * t * t + 0.001308 * t * t * t));
+    for (int it = 0; it < 8; ++it) {
+        double f = 0.5 * erfc(-x / sqrt(2.0)) - p;
+        double d = exp(-0.5 * x * x) / sqrt(2.0 * OR_PI);
+        double dx = f / d;
+        x -= dx;
+        if (fabs(dx) <= 1e-17 * (1.0 + fabs(x))) break;
+    }
+    return x;
+}
+
+/* --------------------------------------------------------------------------
+ * Binomial approximations (Sec. 5).
+ * ------------------------------------------------------------------------ */
+
+/* Bias constant of the small-p fix: eps = 10^-3.54 (Sec. 5, "Numeric Gating
+ * Issues"). */
+double or_eps(void) { return pow(10.0, -3.54); }
+
+/* Thresholds of the dual-gated Gaussian (Alg. 1) for N trials and success
+ * probability p, as the four numbers xi1 is compared with:
+ *   T[0] = P_{n=N}                       (B_{n=N}      = xi1 <  T[0])
+ *   T[1] = P_{n=N} + P_{n=1}             (B_{n in 1,N} = xi1 <  T[1])
+ *   T[2] = 1 - P_{nbar=N}                (B_{nbar=N}   = T[2] <= xi1)
+ *   T[3] = 1 - P_{nbar=N} - P_{nbar=1}   (B_{nbar in 1,N} = T[3] <= xi1)
+ * and the mean and deviation of the Gaussian part.
+ * Reading: for p = 0 the bias factor c = max(1, eps/p) is infinite and
+ * (1 - c p)^(N/c) is taken at its limit 1. */
+void or_dualgated_thresholds(double N, double p, double T[4], double *mu, double *sigma)
+{
+    double eps = or_eps();
+    double N2 = fmax(2.0, N);
+    double a = fmin(fmax(N - 1.0, 0.0), 1.0);           /* clamp_[0,1](N-1) */
+    double Pall = a * pow(p, N2);
+    double Pallneg;
+    if (p > 0.0) {
+        double c = fmax(1.0, eps / p);
+        Pallneg = a * pow(1.0 - c * p, N2 / c);
+    } else {
+        Pallneg = a;
+    }
+    double b = fmax(0.0, 1.0 - fabs(1.0 - N));         /* max(0, 1-|1-N|) */
+    double Pone = b * p, Poneneg = b * (1.0 - p);
+    T[0] = Pall;
+    T[1] = Pall + Pone;
+    T[2] = 1.0 - Pallneg;
+    T[3] = 1.0 - Pallneg - Poneneg;
+    *mu = 1.0 + (N2 - 2.0) * p;
+    *sigma = sqrt(fmax((N2 - 2.0) * p * (1.0 - p), 0.0));
+}
+
+/* Dual-gated Gaussian b_dualgated(N, p, xi1, xi2) -> (n, nbar), Alg. 1,
+ * written out step by step.
+ * Reading: the clamp interval of G, garbled in the source, is the closed
+ * interval [1, N_{>=2} - 1]; Phi^-1(xi; mu, sigma^2) = mu + sigma Phi^-1(xi)
+ * (equal to mu when sigma = 0).
+ * integer_mode = 0: the paper's real-valued counts.
+ * integer_mode = 1 (Reading of "dithered to the nearest integer", Sec. 5):
+ * N is an integer, the Gaussian part is rounded half up,
+ * G = clamp(floor(mu + sigma z + 1/2), 1, N_{>=2} - 1), and nbar = N - n, which
+ * equals Alg. 1's nbar whenever the thresholds partition [0,1) (always, in
+ * exact arithmetic) and keeps sum_k n_k = N under rounding. */
+void or_dualgated(double N, double p, double xi1, double xi2, int integer_mode,
+                  double *n, double *nbar)
+{
+    double T[4], mu, sigma;
+    or_dualgated_thresholds(N, p, T, &mu, &sigma);
+    double N2 = fmax(2.0, N);
+    double B_all = xi1 < T[0];
+    double B_allone = xi1 < T[1];
+    double B_allneg = T[2] <= xi1;
+    double B_alloneneg = T[3] <= xi1;
+    double B_G = (N > 1.0) * (1.0 - B_allone) * (1.0 - B_alloneneg);
+    double z = or_ndtri(xi2);
+    double G = (sigma > 0.0) ? mu + sigma * z : mu;
+    if (integer_mode) G = floor(G + 0.5);
+    G = fmin(fmax(G, 1.0), N2 - 1.0);
+    double Gbar = N2 - G;
+    *n = B_all * (N2 - 1.0) + B_allone + B_G * G;
+    if (integer_mode)
+        *nbar = N - *n;
+    else
+        *nbar = B_allneg * (N2 - 1.0) + B_alloneneg + B_G * Gbar;
+}
+
+/* Alg. 1 over arrays of uniforms (test convenience). */
+void or_dualgated_many(double N, double p, const double *xi1, const double *xi2, long count, int integer_mode,
+                       double *n, double *nbar)
+{
+    for (long i = 0; i < count; ++i) or_dualgated(N, p, xi1[i], xi2[i], integer_mode, n + i, nbar + i);
+}
+
+/* Single-gated Gaussian of prior work, Eq. oldgated:
+ * floor(chi(xi1 < P_{n>=1}) * clamp_[1,N](Phi^-1(xi2; mu, sigma^2))),
+ * mu = 1 + (N-1) p, sigma^2 = (N-1) p (1-p), P_{n>=1} = 1 - (1-p)^N. */
+double or_singlegated_old(double N, double p, double xi1, double xi2)
+{
+    double Pany = 1.0 - pow(1.0 - p, N);
+    double mu = 1.0 + (N - 1.0) * p;
+    double s2 = (N - 1.0) * p * (1.0 - p);
+    double G = mu + sqrt(fmax(s2, 0.0)) * or_ndtri(xi2);
+    G = fmin(fmax(G, 1.0), N);
+    return floor((xi1 < Pany) * G);
+}
+
+/* Generalised single gating for real N >= 0, Eq. gated:
+ * chi(xi1 < min(N p, P_{n>=1})) * clamp_[1, max(N,1)](Phi^-1(xi2; mu, sigma^2)). */
+double or_singlegated(double N, double p, double xi1, double xi2)
+{
+    double Pany = 1.0 - pow(1.0 - p, N);
+    double gate = fmin(N * p, Pany);
+    double mu = 1.0 + (N - 1.0) * p;
+    double s2 = (N - 1.0) * p * (1.0 - p);
+    double G = (s2 > 0.0) ? mu + sqrt(s2) * or_ndtri(xi2) : mu;
+    G = fmin(fmax(G, 1.0), fmax(N, 1.0));
+    return (xi1 < gate) * G;
+}
+
+/* --------------------------------------------------------------------------
+ * Microfacet model (Sec. 3.1, Sec. 6: isotropic GGX, Smith, Schlick).
+ * ------------------------------------------------------------------------ */
+
+/* Isotropic GGX NDF as a function of cos(theta_h). */
+double or_ggx_d(double cos_h, double alpha)
+{
+    if (cos_h <= 0.0) return 0.0;
+    double c2 = cos_h * cos_h;
+    double a2 = alpha * alpha;
+    double d = c2 * (a2 - 1.0) + 1.0;
+    return a2 / (OR_PI * d * d);
+}
+
+/* Smith Lambda for GGX at a direction with cos(theta) = mu. */
+static double smith_lambda(double mu, double alpha)
+{
+    if (mu >= 1.0) return 0.0;
+    double t2 = (1.0 - mu * mu) / (mu * mu);
+    return 0.5 * (-1.0 + sqrt(1.0 + alpha * alpha * t2));
+}
+
+/* Look-up tables over (mu_o, sqrt(alpha)) on an n x n grid of texel centres
+ * mu_i = (i+1/2)/n, s_j = (j+1/2)/n, alpha = s_j^2.  Four channels per node:
+ *   V = E_D(w_o) / D_H   (visible reflecting microfacet area over the total
+ *                         microfacet area, Sec. 4 Eq. rtiblndf and Sec. 3.2)
+ *   U = 1 - V            (masked fraction, integrated on its own)
+ *   A, B                 (split-sum directional albedo E_rho = F0 A + B,
+ *                         Sec. 3.4 Eq. rtibl; Schlick F, height-correlated
+ *                         Smith G2 -- Reading of "Smith")
+ * Integrals over microfacet normals h:  int f(h) D(h) dh.
+ * Quadrature: the GGX projected-area distribution gives
+ * D(h) dh = 2 sqrt(a^2 + (1-a^2) s^2) ds dphi/(2 pi) in the variable
+ * s = sqrt(1 - u), u the CDF of theta_h (the integrand is bounded there);
+ * Q x Q midpoint rule in (s, phi), phi over [0, pi) by the mirror symmetry of
+ * the configuration.
+ * E_D(w_o) = int D(h) 1[h.w_o > 0] 1[n.w_i(h) > 0] dh, w_i = reflect(w_o, h)
+ * (change of variables of Sec. 3.2).  D_H = int D(h) dh.
+ * A = int (1-Fc) G2 D (v.h)/(n.v) dh over valid h, B the same with Fc,
+ * Fc = (1 - v.h)^5. */
+void or_lut_point(double mu, double alpha, int Q, double out[4])
+{
+    double a2 = alpha * alpha;
+    double sv = sqrt(fmax(1.0 - mu * mu, 0.0));
+    double sum_all = 0.0, sum_valid = 0.0, sum_invalid = 0.0, sA = 0.0, sB = 0.0;
+    for (int a = 0; a < Q; ++a) {
+        double s = (a + 0.5) / Q;
+        double root = sqrt(a2 + (1.0 - a2) * s * s);
+        double w = 2.0 * root;
+        double cos_h = s / root;
+        double sin_h = alpha * sqrt(1.0 - s * s) / root;
+        for (int b = 0; b < Q; ++b) {
+            double phi = OR_PI * (b + 0.5) / Q;
+            double hx = sin_h * cos(phi), hz = cos_h;
+            double vh = sv * hx + mu * hz;
+            double li_z = 2.0 * vh * hz - mu;
+            sum_all += w;
+            if (vh > 0.0 && li_z > 0.0) {
+                sum_valid += w;
+                double G2 = 1.0 / (1.0 + smith_lambda(mu, alpha) + smith_lambda(li_z, alpha));
+                double Fc = pow(1.0 - vh, 5.0);
+                double g = G2 * vh / mu;
+                sA += w * (1.0 - Fc) * g;
+                sB += w * Fc * g;
+            } else {
+                sum_invalid += w;
+            }
+        }
+    }
+    double norm = 1.0 / ((double)Q * (double)Q);
+    out[0] = sum_valid / sum_all;
+    out[1] = sum_invalid / sum_all;
+    out[2] = sA * norm;
+    out[3] = sB * norm;
+}
+
+void or_lut(int n, int Q, double *out)
+{
+    for (int j = 0; j < n; ++j) {
+        double s_tex = (j + 0.5) / n;
+        for (int i = 0; i < n; ++i) or_lut_point((i + 0.5) / n, s_tex * s_tex, Q, out + 4 * (j * n + i));
+    }
+}
+
+/* Quadrature of int D(h) cos(theta_h) dh with the weights of or_lut; the GGX
+ * projected microfacet area is exactly 1 (Sec. 3.2). */
+double or_projected_area(double alpha, int Q)
+{
+    double a2 = alpha * alpha, sum = 0.0;
+    for (int a = 0; a < Q; ++a) {
+        double s = (a + 0.5) / Q;
+        double root = sqrt(a2 + (1.0 - a2) * s * s);
+        sum += 2.0 * root * (s / root);
+    }
+    return sum / Q;
+}
+
+/* Total microfacet area D_H(alpha) = int D(h) dh by the same quadrature as
+ * or_lut (Sec. 3.2: the normaliser of the microfacet distribution). */
+double or_total_area(double alpha, int Q)
+{
+    double a2 = alpha * alpha, sum = 0.0;
+    for (int a = 0; a < Q; ++a) {
+        double s = (a + 0.5) / Q;
+        sum += 2.0 * sqrt(a2 + (1.0 - a2) * s * s);
+    }
+    return sum / Q;
+}
+
+/* Bilinear look-up in the (mu, sqrt alpha) table with texel-centre nodes and
+ * clamp-to-edge addressing. */
+static void lut_fetch(const double *lut, int n, double mu, double s, double out[4])
+{
+    double x = mu * n - 0.5, y = s * n - 0.5;
+    x = fmin(fmax(x, 0.0), n - 1.0);
+    y = fmin(fmax(y, 0.0), n - 1.0);
+    int x0 = (int)floor(x), y0 = (int)floor(y);
+    int x1 = x0 + 1 < n ? x0 + 1 : n - 1, y1 = y0 + 1 < n ? y0 + 1 : n - 1;
+    double fx = x - x0, fy = y - y0;
+    for (int c = 0; c < 4; ++c) {
+        double v00 = lut[4 * (y0 * n + x0) + c], v01 = lut[4 * (y0 * n + x1) + c];
+        double v10 = lut[4 * (y1 * n + x0) + c], v11 = lut[4 * (y1 * n + x1) + c];
+        out[c] = (1.0 - fy) * ((1.0 - fx) * v00 + fx * v01) + fy * ((1.0 - fx) * v10 + fx * v11);
+    }
+}
+
+/* --------------------------------------------------------------------------
+ * Environment map: equirectangular, texel (x, y) of a W x H image is centred
+ * on phi = 2 pi (x+1/2)/W, theta = pi (y+1/2)/H, direction
+ * d(theta, phi) = (sin th cos ph, cos th, sin th sin ph)  (y up).
+ * ------------------------------------------------------------------------ */
+
+/* Radiance levels and fuzzy weights, Sec. 4 "Discrete Radiance Levels" and
+ * "Fuzzy Indicator Functions", Eq. wkdefpractice.
+ *   Y = 0.2126 R + 0.7152 G + 0.0722 B          (Reading: Rec. 709 luminance
+ *                                                  as the scalar brightness)
+ *   lo = max(min Y, ell), hi = max(max Y, lo)
+ *   L_1 = 0, L_k = exp(lerp(ln lo, ln hi, (k-1)/(K-1))) for k >= 2
+ *   w_j = 1 - t, w_{j+1} = t, t = (Y - L_j)/(L_{j+1} - L_j), with j the
+ *   largest index in [1, K-1] such that L_j <= Y; Y >= L_K gives w_K = 1.
+ * rgba: H x W x 4 floats (stored radiance, multiplied by `scale`).
+ * ch0: H x W x (3+K) output, channels (R, G, B, w_1 .. w_K). */
+void or_env_decompose(const float *rgba, int W, int H, double scale, int K, double ell,
+                      double *L, double *lohi, double *ch0)
+{
+    long n = (long)W * H;
+    double ymin = INFINITY, ymax = -INFINITY;
+    for (long t = 0; t < n; ++t) {
+        double R = rgba[4 * t] * scale, G = rgba[4 * t + 1] * scale, B = rgba[4 * t + 2] * scale;
+        double Y = fmax(0.2126 * R + 0.7152 * G + 0.0722 * B, 0.0);
+        ymin = fmin(ymin, Y);
+        ymax = fmax(ymax, Y);
+    }
+    double lo = fmax(ymin, ell);
+    double hi = fmax(ymax, lo);
+    lohi[0] = lo;
+    lohi[1] = hi;
+    L[0] = 0.0;
+    for (int k = 2; k <= K; ++k) {
+        double a = (double)(k - 1) / (double)(K - 1);
+        L[k - 1] = exp(log(lo) + (log(hi) - log(lo)) * a);
+    }
+    int C = 3 + K;
+    for (long t = 0; t < n; ++t) {
+        double R = rgba[4 * t] * scale, G = rgba[4 * t + 1] * scale, B = rgba[4 * t + 2] * scale;
+        double Y = fmax(0.2126 * R + 0.7152 * G + 0.0722 * B, 0.0);
+        double *o = ch0 + C * t;
+        o[0] = R; o[1] = G; o[2] = B;
+        for (int k = 0; k < K; ++k) o[3 + k] = 0.0;
+        if (Y >= L[K - 1]) {
+            o[3 + K - 1] = 1.0;
+        } else {
+            int j = 0; /* 0-based: L[j] <= Y < L[j+1] */
+            for (int k = 1; k < K - 1; ++k)
+                if (L[k] <= Y) j = k;
+            double tt = (Y - L[j]) / (L[j + 1] - L[j]);
+            o[3 + j] = 1.0 - tt;
+            o[3 + j + 1] = tt;
+        }
+    }
+}
+
+/* Number of levels of the mip pyramid of a W x H (W = 2H, H a power of two)
+ * equirect image, down to 2 x 1. */
+int or_mip_count(int H)
+{
+    int m = 1;
+    while ((H >> (m - 1)) > 1) ++m;
+    return m;
+}
+
+/* Mip pyramid of the (3+K) channels.  Reading: each texel of level m+1 is the
+ * solid-angle weighted mean of its 2 x 2 children; the weight of a row of
+ * texels spanning [theta0, theta1] is cos(theta0) - cos(theta1).
+ * out: all levels concatenated, level m of size (H>>m) x (W>>m) x C. */
+void or_env_mips(const double *ch0, int W, int H, int C, double *out)
+{
+    int M = or_mip_count(H);
+    memcpy(out, ch0, sizeof(double) * (size_t)W * H * C);
+    const double *src = out;
+    double *dst = out + (size_t)W * H * C;
+    for (int m = 1; m < M; ++m) {
+        int Ws = W >> (m - 1), Hs = H >> (m - 1);
+        int Wd = Ws / 2, Hd = Hs / 2;
+        for (int y = 0; y < Hd; ++y) {
+            double w0 = cos(OR_PI * (2 * y) / Hs) - cos(OR_PI * (2 * y + 1) / Hs);
+            double w1 = cos(OR_PI * (2 * y + 1) / Hs) - cos(OR_PI * (2 * y + 2) / Hs);
+            for (int x = 0; x < Wd; ++x) {
+                for (int c = 0; c < C; ++c) {
+                    double a = src[((size_t)(2 * y) * Ws + 2 * x) * C + c] +
+                               src[((size_t)(2 * y) * Ws + 2 * x + 1) * C + c];
+                    double b = src[((size_t)(2 * y + 1) * Ws + 2 * x) * C + c] +
+                               src[((size_t)(2 * y + 1) * Ws + 2 * x + 1) * C + c];
+                    dst[((size_t)y * Wd + x) * C + c] = (w0 * a + w1 * b) / (2.0 * (w0 + w1));
+                }
+            }
+        }
+        src = dst;
+        dst += (size_t)Wd * Hd * C;
+    }
+}
+
+/* Bilinear look-up on level m of the pyramid: wrap in phi, clamp in theta. */
+static void env_bilinear(const double *lev, int Wm, int Hm, int C, const double d[3], double *out)
+{
+    double th = acos(fmin(fmax(d[1], -1.0), 1.0));
+    double ph = atan2(d[2], d[0]);
+    if (ph < 0.0) ph += 2.0 * OR_PI;
+    double x = ph / (2.0 * OR_PI) * Wm - 0.5;
+    double y = th / OR_PI * Hm - 0.5;
+    double fx0 = floor(x), fy0 = floor(y);
+    double fx = x - fx0, fy = y - fy0;
+    long x0 = (long)fx0, y0 = (long)fy0;
+    long xa = ((x0 % Wm) + Wm) % Wm, xb = (((x0 + 1) % Wm) + Wm) % Wm;
+    long ya = y0 < 0 ? 0 : (y0 > Hm - 1 ? Hm - 1 : y0);
+    long yb = y0 + 1 < 0 ? 0 : (y0 + 1 > Hm - 1 ? Hm - 1 : y0 + 1);
+    for (int c = 0; c < C; ++c) {
+        double v00 = lev[(ya * Wm + xa) * C + c], v01 = lev[(ya * Wm + xb) * C + c];
+        double v10 = lev[(yb * Wm + xa) * C + c], v11 = lev[(yb * Wm + xb) * C + c];
+        out[c] = (1.0 - fy) * ((1.0 - fx) * v00 + fx * v01) + fy * ((1.0 - fx) * v10 + fx * v11);
+    }
+}
+
+static size_t mip_offset(int W, int H, int C, int m)
+{
+    size_t off = 0;
+    for (int k = 0; k < m; ++k) off += (size_t)(W >> k) * (H >> k) * C;
+    return off;
+}
+
+/* Sample table of the environment filter.
+ * Sec. 3.4 Eq. rtibl: the map is filtered with p_{L_i}(w_i) proportional to
+ * rho~(w_i, w_r) under n = v = r.  Reading: F = G = 1, so p is proportional
+ * to D(h), h = normalize(w_i + r), on w_i . r > 0.  The filter is evaluated
+ * by filtered importance sampling (the technique of the real-time IBL works
+ * the paper cites, Karis 2013 / Lagarde 2014; Colbert & Krivanek, GPU Gems 3
+ * ch. 20): S Hammersley points u1 = (j+1/2)/S, u2 = radical inverse of j,
+ * cos^2 theta_h = (1-u1)/(1 + (a^2-1) u1), phi_h = 2 pi u2; the reflected
+ * direction in the frame (e1, e2, r) is
+ * w_i = sin 2th cos ph e1 + sin 2th sin ph e2 + cos 2th r,
+ * valid iff cos 2th > 0.  Sampling h with density D cos(theta_h) gives w_i the
+ * density D(h)/4 when n = r, so the importance weight p/pdf is constant and
+ * the estimate is the plain mean over valid samples.  Each sample reads the
+ * pyramid at lod = 0.5 log2(Omega_s / Omega_0) + 1, clamped to [0, M-1], with
+ * Omega_s = 4 / (S D(h)) and Omega_0 = 4 pi / (W H).
+ * Levels r = 0..R-1: sqrt(alpha_r) spaced evenly on [s_min, s_max].
+ * table: R x S x 4 (e1 weight, e2 weight, r weight, lod; zeros where
+ * invalid); nvalid: R; valid samples come first in each level. */
+void or_prefilter_table(int R, int S, double s_min, double s_max, int W, int H, double *table, int *nvalid)
+{
+    int M = or_mip_count(H);
+    double omega0 = 4.0 * OR_PI / ((double)W * H);
+    for (int r = 0; r < R; ++r) {
+        double sr = (R > 1) ? s_min + (s_max - s_min) * r / (R - 1) : s_min;
+        double alpha = sr * sr, a2 = alpha * alpha;
+        int nv = 0;
+        for (int j = 0; j < S; ++j) {
+            double u1 = (j + 0.5) / S;
+            uint32_t bits = (uint32_t)j, rev = 0;
+            for (int b = 0; b < 32; ++b) { rev = (rev << 1) | (bits & 1u); bits >>= 1; }
+            double u2 = rev * 0x1p-32;
+            double c2 = (1.0 - u1) / (1.0 + (a2 - 1.0) * u1);
+            double cos2t = 2.0 * c2 - 1.0;
+            if (!(cos2t > 0.0)) continue;
+            double c = sqrt(c2), s = sqrt(1.0 - c2);
+            double sin2t = 2.0 * s * c;
+            double ph = 2.0 * OR_PI * u2;
+            double D = or_ggx_d(c, alpha);
+            double omega_s = 4.0 / (S * D);
+            double lod = 0.5 * log2(omega_s / omega0) + 1.0;
+            lod = fmin(fmax(lod, 0.0), (double)(M - 1));
+            double *o = table + 4 * ((size_t)r * S + nv);
+            o[0] = sin2t * cos(ph);
+            o[1] = sin2t * sin(ph);
+            o[2] = cos2t;
+            o[3] = lod;
+            ++nv;
+        }
+        for (int j = nv; j < S; ++j) {
+            double *o = table + 4 * ((size_t)r * S + j);
+            o[0] = o[1] = o[2] = o[3] = 0.0;
+        }
+        nvalid[r] = nv;
+    }
+}
+
+/* Filtered environment, output texel (r, y, x) of an Wo x Ho equirect grid
+ * per level: mean over the valid samples of the trilinear pyramid look-up
+ * (bilinear on levels floor(lod) and floor(lod)+1, linear between).
+ * mips: from or_env_mips.  idx: optional list of `count` flat texel indices
+ * r*Ho*Wo + y*Wo + x (NULL = all R*Ho*Wo texels); out: one C-vector per
+ * listed texel. */
+void or_prefilter(const double *mips, int W, int H, int C, const double *table, const int *nvalid,
+                  int R, int S, int Wo, int Ho, const long *idx, long count, double *out)
+{
+    int M = or_mip_count(H);
+    double tmp0[3 + OR_MAXK], tmp1[3 + OR_MAXK];
+    long total = idx ? count : (long)R * Ho * Wo;
+    for (long q = 0; q < total; ++q) {
+        long id = idx ? idx[q] : q;
+        int r = (int)(id / ((long)Ho * Wo));
+        int y = (int)((id / Wo) % Ho);
+        int x = (int)(id % Wo);
+        double th = OR_PI * (y + 0.5) / Ho, ph = 2.0 * OR_PI * (x + 0.5) / Wo;
+        double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
+        double rr[3] = {st * cp, ct, st * sp};
+        double e1[3] = {ct * cp, -st, ct * sp};
+        double e2[3] = {-sp, 0.0, cp};
+        double acc[3 + OR_MAXK];
+        for (int c = 0; c < C; ++c) acc[c] = 0.0;
+        int nv = nvalid[r];
+        for (int j = 0; j < nv; ++j) {
+            const double *t = table + 4 * ((size_t)r * S + j);
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = t[0] * e1[k] + t[1] * e2[k] + t[2] * rr[k];
+            double lod = t[3];
+            int m0 = (int)floor(lod);
+            double f = lod - m0;
+            int m1 = m0 + 1 < M ? m0 + 1 : M - 1;
+            env_bilinear(mips + mip_offset(W, H, C, m0), W >> m0, H >> m0, C, d, tmp0);
+            env_bilinear(mips + mip_offset(W, H, C, m1), W >> m1, H >> m1, C, d, tmp1);
+            for (int c = 0; c < C; ++c) acc[c] += (1.0 - f) * tmp0[c] + f * tmp1[c];
+        }
+        for (int c = 0; c < C; ++c) out[q * C + c] = nv > 0 ? acc[c] / nv : 0.0;
+    }
+}
+
+/* Exact filter for comparison: the same kernel p ~ D(h) 1[w_i.r > 0] summed
+ * over every texel of level 0 with its solid angle, normalised by the sum of
+ * kernel times solid angle (Sec. 3.4 Eq. rtibl as a plain quadrature). */
+void or_prefilter_exact(const double *ch0, int W, int H, int C, double alpha, const double *dirs, long count,
+                        double *out)
+{
+    for (long q = 0; q < count; ++q) {
+        const double *r = dirs + 3 * q;
+        double acc[3 + OR_MAXK], norm = 0.0;
+        for (int c = 0; c < C; ++c) acc[c] = 0.0;
+        for (int y = 0; y < H; ++y) {
+            double th = OR_PI * (y + 0.5) / H;
+            double dOmega = (cos(OR_PI * y / H) - cos(OR_PI * (y + 1) / H)) * 2.0 * OR_PI / W;
+            for (int x = 0; x < W; ++x) {
+                double ph = 2.0 * OR_PI * (x + 0.5) / W;
+                double d[3] = {sin(th) * cos(ph), cos(th), sin(th) * sin(ph)};
+                double cd = d[0] * r[0] + d[1] * r[1] + d[2] * r[2];
+                if (!(cd > 0.0)) continue;
+                double hx = d[0] + r[0], hy = d[1] + r[1], hz = d[2] + r[2];
+                double hl = sqrt(hx * hx + hy * hy + hz * hz);
+                double cos_h = (hx * r[0] + hy * r[1] + hz * r[2]) / hl;
+                double k = or_ggx_d(cos_h, alpha) * dOmega;
+                norm += k;
+                for (int c = 0; c < C; ++c) acc[c] += k * ch0[((size_t)y * W + x) * C + c];
+            }
+        }
+        for (int c = 0; c < C; ++c) out[q * C + c] = norm > 0.0 ? acc[c] / norm : 0.0;
+    }
+}
+
+/* --------------------------------------------------------------------------
+ * Per-pixel shading.
+ * ------------------------------------------------------------------------ */
+
+/* |P| = |du/dx dv/dy - du/dy dv/dx| in FP32: the 2 x 2 determinant with one
+ * fused multiply-add correction (Kahan), then N_P = N_0 |P| (Sec. 3.2: the
+ * microfacets are stratified, so N_P equals its expectation). */
+static float f32_footprint_area(float dudx, float dvdx, float dudy, float dvdy)
+{
+    float w = dudy * dvdx;
+    float e = fmaf(-dudy, dvdx, w);
+    float f = fmaf(dudx, dvdy, -w);
+    return fabsf(f + e);
+}
+
+/* Grid level: l0 = floor(log2(sqrt|P|)) from the FP32 exponent of |P|
+ * (exact), f = log2(sqrt|P|) - l0 in FP64.  Reading (the grid of Sec. 3.3 is
+ * a black box in the paper): one level per octave of footprint size, cells as
+ * large as the footprint, l0 clamped to [-24, 23]. */
+static void grid_level(float area, int *l0, double *frac)
+{
+    int e;
+    float m = frexpf(area, &e); /* area = m 2^e, m in [1/2, 1) */
+    int ep = e - 1;             /* area = (2m) 2^ep, 2m in [1, 2) */
+    int l = (ep >= 0) ? ep / 2 : -((-ep + 1) / 2);
+    double f = 0.5 * ((double)(ep - 2 * l) + log2(2.0 * (double)m));
+    if (l < -24) { l = -24; f = 0.0; }
+    if (l > 23) { l = 23; f = 1.0; }
+    *l0 = l;
+    *frac = f;
+}
+
+/* Triangle grid vertices at one level (Sec. 3.3: "a triangle grid in the
+ * space of uv coordinates").  Reading: the equilateral lattice of 2-D simplex
+ * noise; the point (u,v) 2^-l is skewed by F = (sqrt 3 - 1)/2 (FP32 constant
+ * 0x3EBB67AE), the skewed cell (i, j) is split along its diagonal, and the
+ * barycentric weights of the three corners are taken in skewed coordinates.
+ * The skew and the vertex choice use FP32 operations in this order. */
+static void grid_vertices(float u, float v, int l, int64_t vx[3], int64_t vy[3], double b[3])
+{
+    const float F2 = 0x1.76cf5cp-2f; /* (sqrt(3)-1)/2 rounded to FP32 */
+    float x = ldexpf(u, -l), y = ldexpf(v, -l);
+    float t = x + y;
+    float s = t * F2;
+    float xs = x + s, ys = y + s;
+    float fi = floorf(xs), fj = floorf(ys);
+    float fx = xs - fi, fy = ys - fj;
+    int64_t i = (int64_t)fi, j = (int64_t)fj;
+    vx[0] = i; vy[0] = j;
+    vx[2] = i + 1; vy[2] = j + 1;
+    if (fx > fy) {
+        vx[1] = i + 1; vy[1] = j;
+        b[0] = 1.0 - (double)fx; b[1] = (double)fx - (double)fy; b[2] = (double)fy;
+    } else {
+        vx[1] = i; vy[1] = j + 1;
+        b[0] = 1.0 - (double)fy; b[1] = (double)fy - (double)fx; b[2] = (double)fx;
+    }
+}
+
+/* Tie model of the FP32 kernel, used to decide when a decision is too close
+ * to call:  tie[0] = e_P  relative error bound of each subtree probability
+ *                         mass (prefilter, look-up tables, interpolation)
+ *           tie[1] = e_z  relative error bound of the FP32 normal quantile
+ *           tie[2] = e_f  relative error bound of an FP32 exp2/log2 chain
+ *           tie[3] = d_a  absolute floor of every threshold tolerance */
+typedef struct {
+    int K, integer_mode;
+    uint32_t key0, key1, key2, seed;
+    double P[2 * OR_MAXK];
+    double tie[4];
+    int max_cand, n_out, overflow, flagged;
+    double *out;     /* max_cand x K leaf counts */
+    double *out_err; /* max_cand x K leaf count tolerance */
+} tree_ctx;
+
+static double thr_eval_err(double T, double a, double e_f)
+{
+    /* FP32 evaluation of a * exp2(X): relative error ~ (|X ln 2| + 1) e_f */
+    if (!(T > 0.0)) return 0.0;
+    double lx = (a > 0.0) ? fabs(log(T / a)) : 0.0;
+    return T * (lx + 2.0) * e_f;
+}
+
+typedef struct { double n, nb, en, eb; } outcome;
+
+/* Append an outcome unless an identical one is already listed. */
+static int push_outcome(outcome *list, int cnt, double n, double nb, double en, double eb)
+{
+    for (int i = 0; i < cnt; ++i)
+        if (list[i].n == n && list[i].nb == nb) return cnt;
+    list[cnt].n = n; list[cnt].nb = nb; list[cnt].en = en; list[cnt].eb = eb;
+    return cnt + 1;
+}
+
+/* Evaluate node `node` of the multinomial tree (heap order) for the trials
+ * N[node] (tolerance dN[node]) and recurse; every valid outcome is listed,
+ * the nominal FP64 outcome first. */
+static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
+{
+    int K = t->K;
+    if (node == K) {
+        if (t->n_out >= t->max_cand) { t->overflow = 1; return; }
+        for (int k = 0; k < K; ++k) {
+            t->out[t->n_out * K + k] = N[K + k];
+            t->out_err[t->n_out * K + k] = dN[K + k];
+        }
+        t->n_out++;
+        return;
+    }
+    double Nn = N[node], dNn = dN[node];
+    if (Nn <= 0.0 && dNn <= 0.0) { /* no trials: Alg. 1 gives (0, 0) */
+        N[2 * node] = N[2 * node + 1] = 0.0;
+        dN[2 * node] = dN[2 * node + 1] = 0.0;
+        tree_rec(t, node + 1, N, dN);
+        return;
+    }
+    uint32_t in[4] = {t->key0, t->key1, t->key2 | ((uint32_t)node << 16), t->seed}, h[4];
+    or_pcg4d(in, h);
+    double xi1 = or_xi(h[1]), xi2 = or_xi(h[2]);
+    double PL = t->P[2 * node], PR = t->P[2 * node + 1];
+    double p = (PL + PR > 0.0) ? PL / (PL + PR) : 0.0;
+    double e_P = t->tie[0], e_z = t->tie[1], e_f = t->tie[2], d_a = t->tie[3];
+    int use_tie = (e_P > 0.0 || e_z > 0.0 || e_f > 0.0 || d_a > 0.0);
+
+    double T[4], mu, sigma;
+    or_dualgated_thresholds(Nn, p, T, &mu, &sigma);
+    double z = or_ndtri(xi2);
+    double G = (sigma > 0.0) ? mu + sigma * z : mu;
+    double N2 = fmax(2.0, Nn);
+
+    /* tolerance of each threshold and of G: inputs perturbed by the tie model */
+    double tau[4] = {0, 0, 0, 0}, tauG = 0.0;
+    if (use_tie) {
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            double pp = p;
+            if (PL > 0.0 && PR > 0.0)
+                pp = PL * (1.0 + sgn * e_P) / (PL * (1.0 + sgn * e_P) + PR * (1.0 - sgn * e_P));
+            for (int sn = -1; sn <= 1; sn += 2) {
+                double Np = fmax(Nn + sn * dNn, 0.0);
+                double T2[4], mu2, sg2;
+                or_dualgated_thresholds(Np, pp, T2, &mu2, &sg2);
+                for (int i = 0; i < 4; ++i) tau[i] = fmax(tau[i], fabs(T2[i] - T[i]));
+                double G2 = (sg2 > 0.0) ? mu2 + sg2 * z : mu2;
+                tauG = fmax(tauG, fabs(G2 - G));
+            }
+        }
+        double a = fmin(fmax(Nn - 1.0, 0.0), 1.0);
+        double Pall = T[0], Pallneg = 1.0 - T[2];
+        tau[0] += thr_eval_err(Pall, a, e_f) + d_a;
+        tau[1] += thr_eval_err(Pall, a, e_f) + (T[1] - T[0]) * e_f + d_a;
+        tau[2] += thr_eval_err(Pallneg, a, e_f) + d_a;
+        tau[3] += thr_eval_err(Pallneg, a, e_f) + (T[2] - T[3]) * e_f + d_a;
+        tauG += sigma * (fabs(z) * e_z + 0x1p-22) + fabs(G) * 0x1p-22 + 0x1p-24;
+    }
+
+    outcome list[64];
+    int cnt = 0;
+    if (t->integer_mode) {
+        /* n is decided by the region of xi1 among T0 <= T1 <= T3:
+         * [0,T0): N   [T0,T1): 1   [T1,T3): G (only if N > 1)   [T3,1): 0 */
+        int nominal = (xi1 < T[0]) ? 0 : (xi1 < T[1]) ? 1 : (xi1 < T[3]) ? 2 : 3;
+        if (nominal == 2 && !(Nn > 1.0)) nominal = 3;
+        int poss[4] = {0, 0, 0, 0};
+        if (T[0] > 0.0 && xi1 < T[0] + tau[0]) poss[0] = 1;
+        if (T[1] > T[0] && xi1 >= T[0] - tau[0] && xi1 < T[1] + tau[1]) poss[1] = 1;
+        if (Nn > 1.0 && xi1 >= T[1] - tau[1] && xi1 < T[3] + tau[3]) poss[2] = 1;
+        if (xi1 >= T[3] - tau[3]) poss[3] = 1;
+        double Gn = fmin(fmax(floor(G + 0.5), 1.0), N2 - 1.0);
+        double glo = fmin(fmax(floor(G - tauG + 0.5), 1.0), N2 - 1.0);
+        double ghi = fmin(fmax(floor(G + tauG + 0.5), 1.0), N2 - 1.0);
+        if (ghi - glo > 8.0) { t->overflow = 1; glo = ghi = Gn; }
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int reg = 0; reg < 4; ++reg) {
+                if (pass == 0 ? reg != nominal : !poss[reg]) continue;
+                if (reg == 2) {
+                    cnt = push_outcome(list, cnt, Gn, Nn - Gn, 0.0, 0.0);
+                    if (pass == 1)
+                        for (double g = glo; g <= ghi; g += 1.0) cnt = push_outcome(list, cnt, g, Nn - g, 0.0, 0.0);
+                } else {
+                    double n = (reg == 0) ? N2 : (reg == 1) ? 1.0 : 0.0;
+                    cnt = push_outcome(list, cnt, n, Nn - n, 0.0, 0.0);
+                }
+            }
+        }
+    } else {
+        /* Real-valued counts (Alg. 1 as printed): n and nbar from their own
+         * masks.  n side: [0,T0): N2  [T0,T1): 1  [T1,1): G or 0;
+         * nbar side: [T2,1): N2  [T3,T2): 1  [0,T3): Gbar or 0; the Gaussian
+         * is used only when N > 1 and neither one-or-all gate fired. */
+        int nom_n = (xi1 < T[0]) ? 0 : (xi1 < T[1]) ? 1 : 2;
+        int nom_b = (T[2] <= xi1) ? 0 : (T[3] <= xi1) ? 1 : 2;
+        int pn[3] = {0, 0, 0}, pb[3] = {0, 0, 0};
+        if (T[0] > 0.0 && xi1 < T[0] + tau[0]) pn[0] = 1;
+        if (T[1] > T[0] && xi1 >= T[0] - tau[0] && xi1 < T[1] + tau[1]) pn[1] = 1;
+        if (xi1 >= T[1] - tau[1]) pn[2] = 1;
+        if (T[2] < 1.0 && xi1 >= T[2] - tau[2]) pb[0] = 1;
+        if (T[3] < T[2] && xi1 >= T[3] - tau[3] && xi1 < T[2] + tau[2]) pb[1] = 1;
+        if (xi1 < T[3] + tau[3]) pb[2] = 1;
+        double Gc = fmin(fmax(G, 1.0), N2 - 1.0);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int rn = 0; rn < 3; ++rn) {
+                for (int rb = 0; rb < 3; ++rb) {
+                    if (pass == 0 ? (rn != nom_n || rb != nom_b) : (!pn[rn] || !pb[rb])) continue;
+                    int gauss = (Nn > 1.0) && rn == 2 && rb == 2;
+                    double n = (rn == 0) ? N2 : (rn == 1) ? 1.0 : (gauss ? Gc : 0.0);
+                    double nb = (rb == 0) ? N2 : (rb == 1) ? 1.0 : (gauss ? N2 - Gc : 0.0);
+                    double en = gauss ? tauG : ((rn == 0) ? dNn : 0.0);
+                    double eb = gauss ? tauG : ((rb == 0) ? dNn : 0.0);
+                    cnt = push_outcome(list, cnt, n, nb, en, eb);
+                }
+            }
+        }
+    }
+    if (cnt > 1) t->flagged++;
+    for (int i = 0; i < cnt; ++i) {
+        N[2 * node] = list[i].n;
+        N[2 * node + 1] = list[i].nb;
+        dN[2 * node] = list[i].en;
+        dN[2 * node + 1] = list[i].eb;
+        tree_rec(t, node + 1, N, dN);
+    }
+}
+
+/* Shade npix pixels (Sec. 4, Eq. iblglints:fin; Sec. 3.3 Eq. anisogrid;
+ * Alg. 1; Sec. 5 hierarchical multinomial).
+ *
+ * G-buffer, 16 floats per pixel:
+ *   [0..2] w_o, unit vector towards the viewer; [3] N_0, microfacets per unit
+ *   uv area (<= 0 marks a background pixel, shaded black);
+ *   [4..6] n, unit shading normal; [7] F0 (Schlick);
+ *   [8..9] (u, v); [10] alpha_x; [11] alpha_y;
+ *   [12] du/dx, [13] dv/dx, [14] du/dy, [15] dv/dy (screen-space derivatives).
+ * pref: R x Ho x Wo x C filtered environment (C = 3+K: RGB, W_1..W_K) with
+ * levels at sqrt(alpha) in [s_min, s_max]; lut: nlut x nlut x 4 (V, U, A, B).
+ * L: the K radiance levels.
+ *
+ * Per pixel:
+ *  - smooth radiance L_o = prefRGB(w_r, alpha) (F0 A + B) (Eq. rtibl), with
+ *    w_r = 2 (n.w_o) n - w_o, alpha = sqrt(alpha_x alpha_y) (the paper's
+ *    method is isotropic), mu_o = clamp(n.w_o, 1e-4, 1) for the tables;
+ *  - p_k = V W_k for k >= 2 and p_1 = U + V W_1: Eq. probhk with Eq.
+ *    rtiblndf, D^(k) ~ E_D int p_{L_i} w_k; the masked mass 1 - V goes to the
+ *    dummy light, merged with k = 1 whose radiance is 0 (Sec. 4);
+ *  - N_P and the six grid samples (w_i, vertex, level);
+ *  - per sample, the multinomial M(N_i, p) by a balanced binary tree over the
+ *    K bins in heap order (Reading of "hierarchical sampling of binomial
+ *    distributions"), node probability P_left / (P_left + P_right) (0 if the
+ *    node has no mass), left child takes n, right child nbar; integer mode
+ *    dithers the root: N_i = floor(N_P) + chi(xi0 < N_P - floor(N_P)) with
+ *    xi0 from the root's hash; real mode uses N_i = N_P;
+ *  - M_k = sum_i w_i n_k(i), L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k)
+ *    (0 when the denominator is 0).
+ *
+ * Outputs (all per pixel): rgb (3, nominal outcome at every decision),
+ * lo (3), pk (K), np (1, FP32 N_P), vert (6 x 3: x, y, level), wv (6),
+ * nroot (6), ncand (6: number of valid count vectors of each tree, -1 when
+ * the enumeration overflowed), cand (6 x max_cand x K), cand_err (same
+ * shape, tolerance of each count in real mode), flags (decisions that were
+ * too close to call).  Returns the number of background pixels. */
+long or_shade(const float *gb, long npix, const double *pref, int R, int Ho, int Wo, int C, double s_min,
+              double s_max, const double *lut, int nlut, const double *L, int K, uint32_t seed, int integer_mode,
+              const double *tie, int max_cand, double *rgb, double *lo, double *pk, float *np, int64_t *vert,
+              double *wv, double *nroot, int32_t *ncand, double *cand, double *cand_err, int32_t *flags)
+{
+    long nbg = 0;
+    for (long q = 0; q < npix; ++q) {
+        const float *g = gb + 16 * q;
+        for (int c = 0; c < 3; ++c) rgb[3 * q + c] = lo[3 * q + c] = 0.0;
+        for (int k = 0; k < K; ++k) pk[q * K + k] = 0.0;
+        np[q] = 0.0f;
+        flags[q] = 0;
+        for (int v = 0; v < OR_NV; ++v) {
+            wv[q * OR_NV + v] = 0.0;
+            nroot[q * OR_NV + v] = 0.0;
+            ncand[q * OR_NV + v] = 0;
+            for (int k = 0; k < 3; ++k) vert[(q * OR_NV + v) * 3 + k] = 0;
+        }
+        if (!(g[3] > 0.0f)) { ++nbg; continue; }
+
+        /* smooth radiance and reflection probabilities (E1) */
+        double wo[3] = {g[0], g[1], g[2]}, nn[3] = {g[4], g[5], g[6]};
+        double F0 = g[7];
+        double mu_o = nn[0] * wo[0] + nn[1] * wo[1] + nn[2] * wo[2];
+        double wr[3];
+        for (int k = 0; k < 3; ++k) wr[k] = 2.0 * mu_o * nn[k] - wo[k];
+        double mu_c = fmin(fmax(mu_o, 1e-4), 1.0);
+        double alpha = sqrt((double)g[10] * (double)g[11]);
+        double s = sqrt(alpha);
+        double tab[4];
+        lut_fetch(lut, nlut, mu_c, s, tab);
+        double V = tab[0], U = tab[1], A = tab[2], B = tab[3];
+        double tl = (R > 1) ? (s - s_min) / (s_max - s_min) * (R - 1) : 0.0;
+        tl = fmin(fmax(tl, 0.0), (double)(R - 1));
+        int r0 = (int)floor(tl);
+        int r1 = r0 + 1 < R ? r0 + 1 : R - 1;
+        double ft = tl - r0;
+        double c0[3 + OR_MAXK], c1[3 + OR_MAXK], cc[3 + OR_MAXK];
+        env_bilinear(pref + (size_t)r0 * Ho * Wo * C, Wo, Ho, C, wr, c0);
+        env_bilinear(pref + (size_t)r1 * Ho * Wo * C, Wo, Ho, C, wr, c1);
+        for (int c = 0; c < C; ++c) cc[c] = (1.0 - ft) * c0[c] + ft * c1[c];
+        double Eb = F0 * A + B;
+        double Lo[3] = {cc[0] * Eb, cc[1] * Eb, cc[2] * Eb};
+        double p[OR_MAXK];
+        p[0] = U + V * cc[3];
+        for (int k = 1; k < K; ++k) p[k] = V * cc[3 + k];
+        for (int c = 0; c < 3; ++c) lo[3 * q + c] = Lo[c];
+        for (int k = 0; k < K; ++k) pk[q * K + k] = p[k];
+
+        /* footprint and microfacet count (FP32) */
+        /* Reading: counts are uint32, so N_P saturates at the largest FP32 value
+         * below 2^32; the radiance uses the same saturated N_P. */
+        float area = f32_footprint_area(g[12], g[13], g[14], g[15]);
+        float NP = fminf(g[3] * area, 4294967040.0f);
+        np[q] = NP;
+        if (!(area > 0.0f) || !(NP > 0.0f)) continue;
+
+        /* grid samples */
+        int l0;
+        double fl;
+        grid_level(area, &l0, &fl);
+        tree_ctx t;
+        memset(&t, 0, sizeof(t));
+        t.K = K;
+        t.integer_mode = integer_mode;
+        t.seed = seed;
+        for (int i = 0; i < 4; ++i) t.tie[i] = tie[i];
+        t.max_cand = max_cand;
+        for (int k = 0; k < K; ++k) t.P[K + k] = p[k];
+        for (int nd = K - 1; nd >= 1; --nd) t.P[nd] = t.P[2 * nd] + t.P[2 * nd + 1];
+
+        double Mk[OR_MAXK];
+        for (int k = 0; k < K; ++k) Mk[k] = 0.0;
+        for (int lv = 0; lv < 2; ++lv) {
+            int l = l0 + lv;
+            double lw = lv ? fl : 1.0 - fl;
+            int64_t vx[3], vy[3];
+            double b[3];
+            grid_vertices(g[8], g[9], l, vx, vy, b);
+            for (int c = 0; c < 3; ++c) {
+                int v = lv * 3 + c;
+                double w = lw * b[c];
+                wv[q * OR_NV + v] = w;
+                vert[(q * OR_NV + v) * 3 + 0] = vx[c];
+                vert[(q * OR_NV + v) * 3 + 1] = vy[c];
+                vert[(q * OR_NV + v) * 3 + 2] = l;
+                t.key0 = (uint32_t)vx[c];
+                t.key1 = (uint32_t)vy[c];
+                t.key2 = ((uint32_t)l) & 0xFFFFu;
+                double N[2 * OR_MAXK], dN[2 * OR_MAXK];
+                for (int i = 0; i < 2 * OR_MAXK; ++i) N[i] = dN[i] = 0.0;
+                if (integer_mode) {
+                    uint32_t in[4] = {t.key0, t.key1, t.key2 | (1u << 16), seed}, h[4];
+                    or_pcg4d(in, h);
+                    float xi0 = (float)or_xi(h[0]);
+                    float fN = floorf(NP);
+                    float frac = NP - fN;
+                    N[1] = (double)fN + (xi0 < frac ? 1.0 : 0.0);
+                } else {
+                    N[1] = (double)NP;
+                }
+                nroot[q * OR_NV + v] = N[1];
+                t.out = cand + ((size_t)q * OR_NV + v) * max_cand * K;
+                t.out_err = cand_err + ((size_t)q * OR_NV + v) * max_cand * K;
+                t.n_out = 0;
+                t.overflow = 0;
+                tree_rec(&t, 1, N, dN);
+                ncand[q * OR_NV + v] = t.overflow ? -1 : t.n_out;
+                for (int k = 0; k < K; ++k) Mk[k] += w * t.out[k]; /* first = nominal outcome */
+            }
+        }
+        flags[q] = t.flagged;
+        double num = 0.0, den = 0.0;
+        for (int k = 1; k < K; ++k) {
+            num += L[k] * Mk[k];
+            den += L[k] * p[k];
+        }
+        den *= (double)NP;
+        if (den > 0.0)
+            for (int c = 0; c < 3; ++c) rgb[3 * q + c] = Lo[c] * num / den;
+    }
+    return nbg;
+}
+
+/* Radiance of one pixel for a chosen valid count vector per grid sample
+ * (Eq. iblglints:fin): L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k),
+ * M_k = sum_i w_i n_k(i). counts: 6 x K. */
+void or_radiance(const double *lo3, const double *pk, double np, const double *L, int K, const double *wv,
+                 const double *counts, double *rgb)
+{
+    double num = 0.0, den = 0.0;
+    for (int k = 1; k < K; ++k) {
+        double M = 0.0;
+        for (int v = 0; v < OR_NV; ++v) M += wv[v] * counts[v * K + k];
+        num += L[k] * M;
+        den += L[k] * pk[k];
+    }
+    den *= np;
+    for (int c = 0; c < 3; ++c) rgb[c] = den > 0.0 ? lo3[c] * num / den : 0.0;
+}
+
+/* One hierarchical multinomial draw with explicit uniforms, for statistical
+ * tests of the tree: K bins with probabilities p, N trials at the root, key
+ * and seed as in or_shade; counts: K leaf counts (nominal outcome). */
+void or_multinomial(const double *p, int K, double N, uint32_t key0, uint32_t key1, uint32_t key2, uint32_t seed,
+                    int integer_mode, double *counts)
+{
+    tree_ctx t;
+    memset(&t, 0, sizeof(t));
+    double buf[OR_MAXK], ebuf[OR_MAXK];
+    t.K = K;
+    t.integer_mode = integer_mode;
+    t.key0 = key0; t.key1 = key1; t.key2 = key2; t.seed = seed;
+    t.max_cand = 1;
+    t.out = buf;
+    t.out_err = ebuf;
+    for (int k = 0; k < K; ++k) t.P[K + k] = p[k];
+    for (int nd = K - 1; nd >= 1; --nd) t.P[nd] = t.P[2 * nd] + t.P[2 * nd + 1];
+    double Nv[2 * OR_MAXK], dN[2 * OR_MAXK];
+    for (int i = 0; i < 2 * OR_MAXK; ++i) Nv[i] = dN[i] = 0.0;
+    Nv[1] = N;
+    tree_rec(&t, 1, Nv, dN);
+    for (int k = 0; k < K; ++k) counts[k] = buf[k];
+}

@@ -1,0 +1,54 @@
+"""Method parameters shared by the oracle tests and the GPU parity tests, and a
+helper that runs the oracle's full pipeline (decompose, pyramid, filter,
+tables, shade).  Test infrastructure."""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class MethodParams:
+    K: int = 4                     # radiance levels (power of two)
+    R: int = 8                     # filtered levels, sqrt(alpha) evenly in [s_min, s_max]
+    S: int = 64                    # filter samples per output texel
+    Wo: int = 64                   # filtered map width (height Wo/2)
+    ell: float = 1e-4              # clip of the minimum radiance
+    s_min: float = math.sqrt(0.02)
+    s_max: float = math.sqrt(0.5)
+    nlut: int = 64                 # table resolution
+    Q: int = 128                   # table quadrature points per axis
+    seed: int = 0
+    integer_mode: bool = True
+
+    @property
+    def Ho(self) -> int:
+        return self.Wo // 2
+
+    def with_(self, **kw) -> "MethodParams":
+        return replace(self, **kw)
+
+
+_LUT_CACHE = {}
+
+
+def oracle_lut(orc, mp: MethodParams) -> np.ndarray:
+    key = (mp.nlut, mp.Q)
+    if key not in _LUT_CACHE:
+        _LUT_CACHE[key] = orc.lut(mp.nlut, mp.Q)
+    return _LUT_CACHE[key]
+
+
+def oracle_env(orc, env, mp: MethodParams):
+    e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell)
+    pref = orc.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, mp.Ho)
+    return e, pref
+
+
+def oracle_shade(orc, rows16: np.ndarray, env, mp: MethodParams, tie=None, max_cand: int = 8, env_pref=None):
+    e, pref = env_pref if env_pref is not None else oracle_env(orc, env, mp)
+    lut = oracle_lut(orc, mp)
+    return orc.shade(rows16, pref, mp.s_min, mp.s_max, lut, e.levels, mp.seed, mp.integer_mode,
+                     tie=orc.TIE_DEFAULT if tie is None else tie, max_cand=max_cand)

@@ -1,0 +1,164 @@
+"""Pins of the oracle's environment decomposition (Sec. 4 'Discrete Radiance
+Levels', 'Fuzzy Indicator Functions', Eq. wkdefpractice), its pyramid and its
+filter (Sec. 3.4 Eq. rtibl, Sec. 4 Eq. rtiblndf).  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2507_02674_gb300 import synth
+
+
+def _lum(rgba, scale=1.0):
+    x = rgba.astype(np.float64) * scale
+    return np.maximum(0.2126 * x[..., 0] + 0.7152 * x[..., 1] + 0.0722 * x[..., 2], 0.0)
+
+
+@pytest.mark.parametrize("K", [2, 4, 8, 16])
+def test_levels_closed_form(orc, K):
+    """L_1 = 0, L_K = max Y, L_2..L_K geometric between max(min Y, ell) and max Y."""
+    env = synth.env_tiny(3)
+    ell = 1e-4
+    L, lohi, ch0 = orc.env_decompose(env.rgba32(), 1.0, K, ell)
+    Y = _lum(env.texels)
+    lo, hi = max(Y.min(), ell), Y.max()
+    assert L[0] == 0.0
+    assert lohi[0] == pytest.approx(lo, rel=1e-15) and lohi[1] == pytest.approx(hi, rel=1e-15)
+    assert L[-1] == pytest.approx(hi, rel=1e-12)
+    if K > 2:
+        r = L[2:] / L[1:-1]
+        assert np.allclose(r, (hi / lo) ** (1.0 / (K - 1)), rtol=1e-12)
+    assert L[1] == pytest.approx(lo ** ((K - 2) / (K - 1)) * hi ** (1 / (K - 1)), rel=1e-12)
+
+
+@pytest.mark.parametrize("K", [4, 8])
+def test_weights_partition_and_reconstruct(orc, K):
+    """Sum_k w_k = 1 and sum_k w_k L_k = Y for every texel below L_K; texels at or
+    above L_K carry w_K = 1 (Sec. 4: w_k is the lerp factor between the two
+    bracketing levels); at most two non-zero weights, adjacent."""
+    env = synth.env_hdr(seed=5, W=128, H=64)
+    L, lohi, ch0 = orc.env_decompose(env.rgba32(), env.scale, K, 1e-4)
+    w = ch0[..., 3:]
+    Y = _lum(env.rgba32(), env.scale)
+    assert np.allclose(w.sum(-1), 1.0, atol=1e-14)
+    assert np.all(w >= -1e-15)
+    rec = (w * L).sum(-1)
+    below = Y < L[-1]
+    assert np.allclose(rec[below], Y[below], rtol=1e-12, atol=1e-300)
+    assert np.all(w[~below][..., -1] == 1.0)
+    nz = w > 0
+    assert np.all(nz.sum(-1) <= 2)
+    two = nz.sum(-1) == 2
+    idx = np.argmax(nz, axis=-1)
+    assert np.all(nz[two][np.arange(two.sum()), idx[two] + 1])
+    assert np.allclose(ch0[..., :3], env.rgba32()[..., :3] * env.scale)
+
+
+def test_weights_hand_case(orc):
+    """Four texels worked by hand: Y = 0, 2, 8, 100 with ell = 2, K = 3 gives
+    levels (0, sqrt(2*100), 100) = (0, 14.142..., 100)."""
+    rgba = np.zeros((2, 4, 4), np.float32)
+    for x, y in enumerate([0.0, 2.0, 8.0, 100.0]):
+        rgba[0, x, :3] = y
+        rgba[1, x, :3] = y
+    L, lohi, ch0 = orc.env_decompose(rgba, 1.0, 3, 2.0)
+    l2 = math.sqrt(200.0)
+    assert np.allclose(L, [0.0, l2, 100.0], rtol=1e-13)
+    w = ch0[0, :, 3:]
+    assert np.allclose(w[0], [1, 0, 0])
+    assert np.allclose(w[1], [1 - 2 / l2, 2 / l2, 0])
+    assert np.allclose(w[2], [1 - 8 / l2, 8 / l2, 0])
+    assert np.allclose(w[3], [0, 0, 1])
+
+
+def test_constant_and_dark_env_degenerate(orc):
+    """Constant map: every level above L_1 equals the constant, every texel w_K = 1.
+    Black map: the clip ell sets both ends and every texel falls into bin 1."""
+    env = synth.env_constant(3.5)
+    L, lohi, ch0 = orc.env_decompose(env.rgba32(), 1.0, 4, 1e-4)
+    assert np.allclose(L[1:], 3.5) and L[0] == 0
+    assert np.all(ch0[..., 3 + 3] == 1.0)
+    black = synth.env_constant(0.0)
+    L, lohi, ch0 = orc.env_decompose(black.rgba32(), 1.0, 4, 1e-3)
+    assert np.allclose(L[1:], 1e-3)
+    assert np.all(ch0[..., 3] == 1.0)
+
+
+def _texel_solid_angles(W, H):
+    y = np.arange(H)
+    band = np.cos(np.pi * y / H) - np.cos(np.pi * (y + 1) / H)
+    return np.repeat(band[:, None], W, axis=1) * (2 * np.pi / W)
+
+
+def test_pyramid_preserves_integrals(orc):
+    """Each level is a solid-angle weighted mean of its children, so the integral
+    of every channel over the sphere is the same on every level."""
+    env = synth.env_hdr(seed=2, W=64, H=32)
+    e = orc.env_full(env.rgba32(), env.scale, 4, 1e-4)
+    ref = None
+    for lev in e.mips:
+        Hm, Wm, C = lev.shape
+        integral = np.tensordot(_texel_solid_angles(Wm, Hm), lev, axes=([0, 1], [0, 1]))
+        if ref is None:
+            ref = integral
+        assert np.allclose(integral, ref, rtol=1e-12)
+    assert len(e.mips) == orc.mip_count(32) == 6 and e.mips[-1].shape[:2] == (1, 2)
+
+
+def test_filter_constant_env(orc):
+    """A constant environment filters to itself: RGB = constant, W_K = 1."""
+    env = synth.env_constant(2.0)
+    e = orc.env_full(env.rgba32(), 1.0, 4, 1e-4)
+    pref = orc.prefilter(e, 4, 32, math.sqrt(0.02), math.sqrt(0.5), 16, 8)
+    assert np.allclose(pref[..., :3], 2.0, rtol=1e-13)
+    assert np.allclose(pref[..., 3 + 3], 1.0, rtol=1e-13)
+    assert np.allclose(pref[..., 3:6], 0.0, atol=1e-13)
+
+
+def test_filter_partition_of_unity(orc):
+    env = synth.env_tiny(0)
+    e = orc.env_full(env.rgba32(), 1.0, 8, 1e-4)
+    pref = orc.prefilter(e, 5, 64, math.sqrt(0.02), math.sqrt(0.5), 32, 16)
+    assert np.allclose(pref[..., 3:].sum(-1), 1.0, atol=1e-13)
+    assert np.all(pref[..., 3:] >= 0)
+
+
+def test_filter_narrow_lobe_is_identity(orc):
+    """As alpha -> 0 every sample reflects into w_r and reads level 0, so the
+    filtered map sampled at the texel centres of the source is the source."""
+    env = synth.env_tiny(1)
+    e = orc.env_full(env.rgba32(), 1.0, 4, 1e-4)
+    pref = orc.prefilter(e, 1, 16, 1e-7, 1e-7, 64, 32)
+    assert np.allclose(pref[0], e.ch0, rtol=1e-6, atol=1e-9)
+
+
+def test_filter_sample_table(orc):
+    """Hammersley table: reflected directions are unit vectors on the lobe side
+    (cos 2 theta_h > 0); narrow lobes keep every sample, alpha = 0.5 keeps the
+    fraction u < 0.8 (tan^2 theta_h < 1); lod grows as D(h) falls."""
+    tab, nv = orc.prefilter_table(2, 64, math.sqrt(0.02), math.sqrt(0.5), 1024, 512)
+    assert nv[0] == 64
+    assert nv[1] == int(np.sum((np.arange(64) + 0.5) / 64 < 0.8))
+    for r in range(2):
+        t = tab[r, :nv[r]]
+        assert np.allclose(np.linalg.norm(t[:, :3], axis=1), 1.0, atol=1e-14)
+        assert np.all(t[:, 2] > 0)
+        assert np.all(np.diff(t[:, 3]) >= -1e-12)
+
+
+def test_filter_close_to_exact_convolution(orc):
+    """Filtered importance sampling vs the plain texel-sum quadrature of the same
+    kernel (Sec. 3.4): the difference is the sampling and mip error, bounded here
+    on a smooth map."""
+    env = synth.env_hdr(seed=9, W=128, H=64, n_suns=0, sigma=0.7, fp16=False, scale_log2=0)
+    e = orc.env_full(env.rgba32(), 1.0, 4, 1e-4)
+    s = math.sqrt(0.3)
+    Wo, Ho = 16, 8
+    pref = orc.prefilter(e, 1, 256, s, s, Wo, Ho)
+    y, x = np.meshgrid(np.arange(Ho), np.arange(Wo), indexing="ij")
+    th, ph = np.pi * (y + 0.5) / Ho, 2 * np.pi * (x + 0.5) / Wo
+    dirs = np.stack([np.sin(th) * np.cos(ph), np.cos(th), np.sin(th) * np.sin(ph)], -1).reshape(-1, 3)
+    ex = orc.prefilter_exact(e.ch0, 0.3, dirs).reshape(Ho, Wo, -1)
+    rel = np.abs(pref[0, ..., :3] - ex[..., :3]) / ex[..., :3]
+    assert np.median(rel) < 0.03 and np.max(rel) < 0.12
+    assert np.max(np.abs(pref[0, ..., 3:] - ex[..., 3:])) < 0.05

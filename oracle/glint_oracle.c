@@ -227,8 +227,9 @@ static double smith_lambda(double mu, double alpha)
  * Quadrature: the GGX projected-area distribution gives
  * D(h) dh = 2 sqrt(a^2 + (1-a^2) s^2) ds dphi/(2 pi) in the variable
  * s = sqrt(1 - u), u the CDF of theta_h (the integrand is bounded there);
- * Q x Q midpoint rule in (s, phi), phi over [0, pi) by the mirror symmetry of
- * the configuration.
+ * phi over [0, pi) by the mirror symmetry of the configuration.  V and U
+ * integrate the validity indicator over phi in closed form and use a Q*Q
+ * point midpoint rule in s; A and B use a Q x Q midpoint rule in (s, phi).
  * E_D(w_o) = int D(h) 1[h.w_o > 0] 1[n.w_i(h) > 0] dh, w_i = reflect(w_o, h)
  * (change of variables of Sec. 3.2).  D_H = int D(h) dh.
  * A = int (1-Fc) G2 D (v.h)/(n.v) dh over valid h, B the same with Fc,
@@ -237,7 +238,35 @@ void or_lut_point(double mu, double alpha, int Q, double out[4])
 {
     double a2 = alpha * alpha;
     double sv = sqrt(fmax(1.0 - mu * mu, 0.0));
-    double sum_all = 0.0, sum_valid = 0.0, sum_invalid = 0.0, sA = 0.0, sB = 0.0;
+    /* V and U: for fixed theta_h the valid normals form the arc
+     * cos(phi) > c* = -(mu / sin theta_o) cot(2 theta_h) (the condition
+     * n.w_i > 0, which implies h.w_o > 0), whose share of [0, pi] is
+     * acos(clamp(c*)) / pi; midpoint rule with Q*Q points in s. */
+    int ns = Q * Q;
+    double sw = 0.0, sv_valid = 0.0, sv_invalid = 0.0;
+    for (int a = 0; a < ns; ++a) {
+        double s = (a + 0.5) / ns;
+        double root2 = a2 + (1.0 - a2) * s * s;
+        double w = 2.0 * sqrt(root2);
+        double cos2t = (s * s - a2 * (1.0 - s * s)) / root2;
+        double sin2t = 2.0 * s * alpha * sqrt(1.0 - s * s) / root2;
+        double m;
+        if (sv > 0.0) {
+            double cstar = -(mu / sv) * cos2t / sin2t;
+            m = acos(fmin(fmax(cstar, -1.0), 1.0));
+        } else {
+            m = (cos2t > 0.0) ? OR_PI : 0.0;
+        }
+        sw += w;
+        sv_valid += w * m;
+        sv_invalid += w * (OR_PI - m);
+    }
+    out[0] = sv_valid / (OR_PI * sw);
+    out[1] = sv_invalid / (OR_PI * sw);
+    /* A, B: Q x Q midpoint rule in (s, phi in [0, pi)); the integrand vanishes
+     * on the boundary of the valid set (G2 -> 0 as n.w_i -> 0). */
+    double sA = 0.0, sB = 0.0;
+    double lam_o = smith_lambda(mu, alpha);
     for (int a = 0; a < Q; ++a) {
         double s = (a + 0.5) / Q;
         double root = sqrt(a2 + (1.0 - a2) * s * s);
@@ -246,25 +275,18 @@ void or_lut_point(double mu, double alpha, int Q, double out[4])
         double sin_h = alpha * sqrt(1.0 - s * s) / root;
         for (int b = 0; b < Q; ++b) {
             double phi = OR_PI * (b + 0.5) / Q;
-            double hx = sin_h * cos(phi), hz = cos_h;
-            double vh = sv * hx + mu * hz;
-            double li_z = 2.0 * vh * hz - mu;
-            sum_all += w;
+            double vh = sv * sin_h * cos(phi) + mu * cos_h;
+            double li_z = 2.0 * vh * cos_h - mu;
             if (vh > 0.0 && li_z > 0.0) {
-                sum_valid += w;
-                double G2 = 1.0 / (1.0 + smith_lambda(mu, alpha) + smith_lambda(li_z, alpha));
+                double G2 = 1.0 / (1.0 + lam_o + smith_lambda(li_z, alpha));
                 double Fc = pow(1.0 - vh, 5.0);
                 double g = G2 * vh / mu;
                 sA += w * (1.0 - Fc) * g;
                 sB += w * Fc * g;
-            } else {
-                sum_invalid += w;
             }
         }
     }
     double norm = 1.0 / ((double)Q * (double)Q);
-    out[0] = sum_valid / sum_all;
-    out[1] = sum_invalid / sum_all;
     out[2] = sA * norm;
     out[3] = sB * norm;
 }
@@ -605,12 +627,12 @@ static void grid_level(float area, int *l0, double *frac)
 /* Triangle grid vertices at one level (Sec. 3.3: "a triangle grid in the
  * space of uv coordinates").  Reading: the equilateral lattice of 2-D simplex
  * noise; the point (u,v) 2^-l is skewed by F = (sqrt 3 - 1)/2 (FP32 constant
- * 0x3EBB67AE), the skewed cell (i, j) is split along its diagonal, and the
+ * 0x3EBB67AF), the skewed cell (i, j) is split along its diagonal, and the
  * barycentric weights of the three corners are taken in skewed coordinates.
  * The skew and the vertex choice use FP32 operations in this order. */
 static void grid_vertices(float u, float v, int l, int64_t vx[3], int64_t vy[3], double b[3])
 {
-    const float F2 = 0x1.76cf5cp-2f; /* (sqrt(3)-1)/2 rounded to FP32 */
+    const float F2 = 0x1.76cf5ep-2f; /* (sqrt(3)-1)/2 rounded to FP32 */
     float x = ldexpf(u, -l), y = ldexpf(v, -l);
     float t = x + y;
     float s = t * F2;
@@ -729,7 +751,11 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
     int cnt = 0;
     if (t->integer_mode) {
         /* n is decided by the region of xi1 among T0 <= T1 <= T3:
-         * [0,T0): N   [T0,T1): 1   [T1,T3): G (only if N > 1)   [T3,1): 0 */
+         * [0,T0): N   [T0,T1): 1   [T1,T3): G (only if N > 1)   [T3,1): 0.
+         * When the rounding of G cannot be called exactly (more than 3
+         * integers within its tolerance, or the trials themselves carry a
+         * tolerance), G is kept as one outcome with a count tolerance that the
+         * subtree propagates. */
         int nominal = (xi1 < T[0]) ? 0 : (xi1 < T[1]) ? 1 : (xi1 < T[3]) ? 2 : 3;
         if (nominal == 2 && !(Nn > 1.0)) nominal = 3;
         int poss[4] = {0, 0, 0, 0};
@@ -740,17 +766,19 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
         double Gn = fmin(fmax(floor(G + 0.5), 1.0), N2 - 1.0);
         double glo = fmin(fmax(floor(G - tauG + 0.5), 1.0), N2 - 1.0);
         double ghi = fmin(fmax(floor(G + tauG + 0.5), 1.0), N2 - 1.0);
-        if (ghi - glo > 8.0) { t->overflow = 1; glo = ghi = Gn; }
+        int interval = (dNn > 0.0) || (ghi - glo > 2.0);
+        double eG = interval ? tauG + 0.5 : 0.0;
         for (int pass = 0; pass < 2; ++pass) {
             for (int reg = 0; reg < 4; ++reg) {
                 if (pass == 0 ? reg != nominal : !poss[reg]) continue;
                 if (reg == 2) {
-                    cnt = push_outcome(list, cnt, Gn, Nn - Gn, 0.0, 0.0);
-                    if (pass == 1)
+                    cnt = push_outcome(list, cnt, Gn, Nn - Gn, eG, dNn + eG);
+                    if (pass == 1 && !interval)
                         for (double g = glo; g <= ghi; g += 1.0) cnt = push_outcome(list, cnt, g, Nn - g, 0.0, 0.0);
                 } else {
                     double n = (reg == 0) ? N2 : (reg == 1) ? 1.0 : 0.0;
-                    cnt = push_outcome(list, cnt, n, Nn - n, 0.0, 0.0);
+                    double en = (reg == 0) ? dNn : 0.0;
+                    cnt = push_outcome(list, cnt, n, Nn - n, en, dNn - en);
                 }
             }
         }

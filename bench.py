@@ -1,0 +1,389 @@
+"""Benchmark: glint-shaded Mpixel/s on the 1920 x 1080 scene with K = 8.
+
+A step is one pass of the whole hot path over one frame: the environment
+update (brightness reduction, radiance levels, fuzzy weights, pyramid,
+filtered maps) followed by per-pixel glint shading of the 1920 x 1080 G-buffer.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one process per GPU under torch.distributed.run; every rank shades
+its own frame (weak scaling, no collective on the data path); the value is all
+ranks' pixels over the slowest rank's time.  Rank 0 prints one JSON line.
+
+--impl reference times the CPU oracle (the plain FP64 implementation under
+oracle/) on a bounded sample of the same workload, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "glint-shaded Mpixel/s at 1080p, K=8: plain vs MLP surrogate at ≤1% RMSE; p99 ms"
+WIDTH, HEIGHT = 1920, 1080
+K, R, S, WO = 8, 8, 64, 256
+ENV_W, ENV_H = 1024, 512
+WORKLOAD = (f"{WIDTH}x{HEIGHT} G-buffer (ground plane + 16 spheres, alpha_x,alpha_y~U[0.03,0.3], "
+            f"N0~logU[1e3,1e8]); {ENV_W}x{ENV_H} RGBA16F env (log-normal sigma=1.5 + 4 suns 1e3-1e5); "
+            f"K={K}, R={R} filtered levels, S={S} samples, {WO}x{WO // 2} filtered maps; env re-filtered every frame")
+MUFU_PER_DRAW = 8          # algorithmic transcendentals per dual-gated draw
+MUFU_PER_SM_CLK = 16       # MUFU results per clock per SM
+L2_FLUSH_BYTES = 256 << 20
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "shade_k8_1080p.md")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(seed_offset: int = 0):
+    from paper_2507_02674_gb300 import synth
+    env = synth.env_hdr(seed=1, W=ENV_W, H=ENV_H)
+    gb = synth.gbuffer_scene(WIDTH, HEIGHT, seed=1)
+    return env, gb
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"glint_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("glint_shade.cu", "glint_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2507_02674_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic():
+    """DRAM bytes per shade launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None, None
+    sha = traffic = None
+    for line in txt.splitlines():
+        if line.startswith("kernel_source_sha:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    if sha != _source_sha():
+        return None, sha
+    return traffic, sha
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle legs
+def _oracle_setup():
+    import oracle
+    from tests._pipeline import MethodParams, oracle_lut
+    oracle.build()
+    mp = MethodParams(K=K, R=R, S=S, Wo=WO, seed=1)
+    env, gb = _workload()
+    return oracle, mp, env, gb
+
+
+def _oracle_frame_sample(oracle, mp, rgba, scale, rows16, pref_full, lut, pref_stride: int, px_stride: int):
+    """Times one frame's work on a sample: decomposition and pyramid in full,
+    every pref_stride-th filtered texel, the given pixels (every px_stride-th
+    pixel of the frame); returns (seconds, extrapolated seconds for the frame)."""
+    t0 = time.perf_counter()
+    e = oracle.env_full(rgba, scale, mp.K, mp.ell)
+    t1 = time.perf_counter()
+    idx = np.arange(0, mp.R * mp.Ho * mp.Wo, pref_stride)
+    oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, mp.Ho, idx=idx)
+    t2 = time.perf_counter()
+    oracle.shade(rows16, pref_full, mp.s_min, mp.s_max, lut, e.levels, mp.seed, True, tie=(0.0, 0.0, 0.0, 0.0),
+                 max_cand=1)
+    t3 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * pref_stride + (t3 - t2) * px_stride
+    return t3 - t0, full
+
+
+def cpu_baseline():
+    """The oracle as it stands, single-threaded on a host core: one frame with
+    the decomposition, pyramid and every filtered texel in full and every 4th
+    pixel shaded (about 10 s of CPU work), shading extrapolated to the frame."""
+    oracle, mp, env, gb = _oracle_setup()
+    from tests._pipeline import oracle_lut
+    lut = oracle_lut(oracle, mp)
+    rgba = env.rgba32()
+    rows = gb.rows16()[::4].copy()
+    t0 = time.perf_counter()
+    e = oracle.env_full(rgba, env.scale, mp.K, mp.ell)
+    pref = oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, mp.Ho)
+    t1 = time.perf_counter()
+    oracle.shade(rows, pref, mp.s_min, mp.s_max, lut, e.levels, mp.seed, True, tie=(0.0, 0.0, 0.0, 0.0), max_cand=1)
+    t2 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * 4
+    value = WIDTH * HEIGHT / full / 1e6
+    return {"value": round(value, 6), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+            "sample": f"env decomposition + pyramid + all {mp.R}x{mp.Ho}x{mp.Wo} filtered texels in full "
+                      f"({t1 - t0:.1f} s) and every 4th pixel ({len(rows)} px, {t2 - t1:.1f} s), shading "
+                      f"extrapolated x4 to the frame; FP64 C oracle, one thread, tie model off"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    oracle, mp, env, gb = _oracle_setup()
+    from tests._pipeline import oracle_lut
+    lut = oracle_lut(oracle, mp)
+    e = oracle.env_full(env.rgba32(), env.scale, mp.K, mp.ell)
+    pref = oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, mp.Ho)
+    pref_stride, px_stride = 64, 512
+    rgba = env.rgba32()
+    rows = gb.rows16()[::px_stride].copy()
+    for _ in range(args.warmup):
+        _oracle_frame_sample(oracle, mp, rgba, env.scale, rows, pref, lut, pref_stride, px_stride)
+    per_frame = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, full = _oracle_frame_sample(oracle, mp, rgba, env.scale, rows, pref, lut, pref_stride, px_stride)
+        per_frame.append(full)
+    wall = time.perf_counter() - t0
+    ms = float(np.mean(per_frame)) * 1e3
+    value = WIDTH * HEIGHT / (ms / 1e3) / 1e6
+    sample = (f"per step: env decomposition + pyramid in full, every {pref_stride}th filtered texel, every "
+              f"{px_stride}th pixel ({len(rows)} px); frame time extrapolated; FP64 C oracle, one thread; "
+              f"{wall:.1f} s wall")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Mpixel/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": WIDTH, "height": HEIGHT, "K": K},
+            "cpu_baseline": {"value": round(value, 6), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    from paper_2507_02674_gb300 import build as B
+    if rank == 0 or ws == 1:
+        B.build()
+    if pg:
+        pg.barrier()
+    from paper_2507_02674_gb300 import glint, render
+    env, gb = _workload()
+    ctx = glint.Context(local, 64, 128)
+    cfg = glint.EnvConfig(K=K, levels=R, samples=S, out_width=WO)
+    fr = render.Frame(ctx, env, cfg, device=dev)
+    planes = render.gbuffer_tensors(gb, device=dev)
+    npix = WIDTH * HEIGHT
+    out = torch.empty(npix, 4, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    seed = 1 + rank
+
+    def step():
+        fr.update_env(stream)
+        fr.shade(planes, WIDTH, HEIGHT, out=out, seed=seed, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    launches_per_step = fr.env.last_launches() + ctx.last_launches()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()                 # L2 flush, outside the timed events
+        ev[i][0].record(stream)
+        fr.update_env(stream)
+        ev[i][1].record(stream)
+        fr.shade(planes, WIDTH, HEIGHT, out=out, seed=seed, stream=stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if pg:
+        pg.barrier()
+    step_ms = np.array([ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)])
+    env_ms = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)])
+    shade_ms = np.array([ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)])
+    total_ms = float(step_ms.sum())
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end to end through the C ABI with host buffers: H2D of the frame's
+    # G-buffer and environment texels, the step, D2H of the shaded frame
+    host_planes = render.gbuffer_tensors(gb, device="cpu", pinned=True)
+    host_tex = torch.from_numpy(np.ascontiguousarray(env.texels)).pin_memory()
+    host_out = torch.empty(npix, 4, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    h2d = sum(p.numel() * 4 for p in host_planes) + host_tex.numel() * host_tex.element_size()
+    d2h = host_out.numel() * 4
+
+    def e2e_step():
+        for dp, hp in zip(planes, host_planes):
+            dp.copy_(hp, non_blocking=True)
+        fr.texels.copy_(host_tex, non_blocking=True)
+        step()
+        host_out.copy_(out, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = ws * npix * e2e_steps / (e2e_ms / 1e3) / 1e6
+
+    value = ws * npix * args.steps / (total_ms / 1e3) / 1e6
+    result = None
+    if rank == 0:
+        peaks = _peaks()
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        shade_avg_s = float(shade_ms.mean()) / 1e3
+        algo = MUFU_PER_DRAW * 6 * (K - 1) * npix
+        achieved = algo / shade_avg_s / 1e12
+        peak = n_sm * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+        traffic, _ = _profile_traffic()
+        result = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": WIDTH, "height": HEIGHT, "K": K, "levels": R, "samples": S,
+                       "filtered_width": WO, "env": f"{ENV_W}x{ENV_H} RGBA16F", "count_mode": "integer",
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
+            "p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+            "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+            "env_update_ms": round(float(env_ms.mean()), 4),
+            "shade_ms": round(float(shade_ms.mean()), 4),
+            "static_env_mpix_s": round(npix / (float(shade_ms.mean()) / 1e3) / 1e6, 3),
+            "roofline": {"kernel": "k_shade<8,integer>", "bound": "alu", "achieved": round(achieved, 4),
+                         "peak": round(peak, 4), "unit": "TMUFU/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic,
+                         "basis": (f"{MUFU_PER_DRAW} transcendentals x 6 samples x {K - 1} draws = "
+                                   f"{MUFU_PER_DRAW * 6 * (K - 1)} per pixel; peak = {n_sm} SMs x "
+                                   f"{MUFU_PER_SM_CLK} MUFU/clk x {sm_mhz:.0f} MHz (median SM clock sampled "
+                                   f"during the timed region)")},
+            "clocks": clk,
+            "e2e": {"value": round(e2e_val, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": launches_per_step * args.steps,
+        }
+    if pg:
+        pg.barrier()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * glint.h -- C ABI of the GB300 (sm_103a) library for real-time image-based
+ * lighting of glints (Kneiphof & Klein, "Real-Time Image-based Lighting of
+ * Glints", EGSR 2025, arXiv 2507.02674).
+ *
+ * The library computes, per pixel of a G-buffer, the outgoing radiance of a
+ * glittery microfacet surface lit by an environment map (Sec. 4,
+ * Eq. iblglints:fin), and the per-environment data it needs: K radiance levels,
+ * fuzzy weights and their filtered maps (Sec. 4 "Discrete Radiance Levels",
+ * "Fuzzy Indicator Functions", "Integrated NDF").
+ *
+ * Conventions for every call
+ *  - Pointers documented as "device" must point to device memory of the
+ *    context's GPU; "host" pointers to ordinary host memory.  The library never
+ *    frees caller memory; caller buffers must stay alive until the work enqueued
+ *    on `stream` has completed.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that only enqueue work return before it finishes.
+ *  - Every call returns a glint_status.  On failure the call has no effect on
+ *    its outputs' ownership, and glint_last_error() returns a message for the
+ *    calling thread.  No call aborts the process or throws across the ABI.
+ *  - Handles are opaque; they are created and destroyed only by the library.
+ *    A handle may be used from one host thread at a time.
+ *
+ * Memory layouts
+ *  - Environment map: equirectangular, `width` x `height` texels, width =
+ *    2 height, height a power of two; row y spans polar angle
+ *    theta in [pi y/H, pi (y+1)/H] around +y, column x spans
+ *    phi in [2 pi x/W, 2 pi (x+1)/W]; direction
+ *    (sin th cos ph, cos th, sin th sin ph).  Texels are RGBA, row-major,
+ *    float32 (16 bytes) or float16 (8 bytes); radiance = stored value *
+ *    2^scale_log2; alpha is ignored.  Values must be finite and >= 0.
+ *  - G-buffer: four planes of `width*height` float4, row-major, each 16-byte
+ *    aligned (see glint_gbuffer).
+ *  - Output: `width*height` float4 (R, G, B, 1), row-major, 16-byte aligned.
+ */
+#ifndef GLINT_H
+#define GLINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GLINT_ABI_VERSION 1
+#define GLINT_MAX_K 16
+
+typedef enum glint_status {
+    GLINT_OK = 0,
+    GLINT_ERR_INVALID_ARG = 1, /* a size, pointer or enum is out of range */
+    GLINT_ERR_OOM = 2,         /* device allocation failed */
+    GLINT_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the code) */
+    GLINT_ERR_NOT_READY = 4,   /* the request cannot be admitted now */
+    GLINT_ERR_TIMEOUT = 5,     /* a bounded wait gave up */
+    GLINT_ERR_UNSUPPORTED = 6  /* a valid configuration this build does not handle */
+} glint_status;
+
+typedef enum glint_format {
+    GLINT_FMT_RGBA32F = 0,
+    GLINT_FMT_RGBA16F = 1
+} glint_format;
+
+typedef enum glint_count_mode {
+    GLINT_COUNT_INTEGER = 0, /* uint32 counts: N_P dithered at each tree root, Gaussian rounded */
+    GLINT_COUNT_REAL = 1     /* real-valued counts, Alg. 1 as printed */
+} glint_count_mode;
+
+typedef struct glint_ctx glint_ctx;
+typedef struct glint_env glint_env;
+
+/* ABI version of the loaded library (GLINT_ABI_VERSION). */
+int glint_abi_version(void);
+
+/* Message describing the last failed call on the calling thread ("" if none).
+ * The pointer stays valid until the next library call on this thread. */
+const char *glint_last_error(void);
+
+/* Context on CUDA device `device`.  Builds the microfacet tables on the GPU:
+ * for lut_n x lut_n texel-centre nodes over (mu_o, sqrt alpha), the visible
+ * reflecting microfacet area over the total microfacet area V = E_D / D_H and
+ * its complement U (Sec. 4 Eq. rtiblndf; Sec. 3.2), and the split-sum albedo
+ * terms A, B with Schlick F and height-correlated Smith G2 (Sec. 3.4
+ * Eq. rtibl), each by a lut_q x lut_q midpoint quadrature.
+ * lut_n in [2, 256] (default 64), lut_q in [8, 1024] (default 128); 0 selects
+ * the default.  Blocks until the tables are built.  *out is owned by the
+ * caller and released with glint_ctx_destroy. */
+glint_status glint_ctx_create(int device, int lut_n, int lut_q, glint_ctx **out);
+
+/* Releases the context (NULL is ignored).  All environments made from it must
+ * be destroyed first. */
+void glint_ctx_destroy(glint_ctx *ctx);
+
+/* Copies the tables to host memory: lut_n * lut_n * 4 floats, row j (sqrt
+ * alpha = (j+1/2)/lut_n), column i (mu_o = (i+1/2)/lut_n), channels
+ * (V, U, A, B).  `bytes` must be at least that size.  Synchronous. */
+glint_status glint_lut_export(const glint_ctx *ctx, float *host_dst, size_t bytes);
+
+/* Description of an environment and of its filtered data. */
+typedef struct glint_env_desc {
+    int width;        /* texels, = 2 * height */
+    int height;       /* power of two, 2 .. 8192 */
+    int format;       /* glint_format */
+    int scale_log2;   /* radiance = stored * 2^scale_log2, |scale_log2| <= 64 */
+    int K;            /* radiance levels: 2, 4, 8 or 16 (Sec. 4, K in {4, 8} in the paper) */
+    float ell;        /* lower clip of the minimum brightness (Sec. 4), > 0 */
+    int levels;       /* R filtered roughness levels, 1 .. 32 */
+    int samples;      /* S filter samples per output texel, 1 .. 4096 */
+    int out_width;    /* filtered map width (height = out_width / 2), power of two, 4 .. 4096 */
+    float s_min;      /* sqrt(alpha) of filtered level 0, > 0 */
+    float s_max;      /* sqrt(alpha) of filtered level R-1, >= s_min */
+} glint_env_desc;
+
+/* Allocates an environment's device buffers (levels, weights pyramid,
+ * filtered maps, scratch) for the given description.  Computes nothing; call
+ * glint_env_update to fill it.  *out is released with glint_env_destroy. */
+glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *desc, glint_env **out);
+
+/* Recomputes all per-environment data from `texels` (device; width * height
+ * RGBA texels in desc.format) on `stream`, allocating nothing:
+ *   1. brightness Y = Rec. 709 luminance, lo = max(min Y, ell), hi = max Y
+ *      (Sec. 4 "Discrete Radiance Levels");
+ *   2. levels L_1 = 0, L_k = exp(lerp(ln lo, ln hi, (k-1)/(K-1)));
+ *   3. per texel the fuzzy weights of the two bracketing levels
+ *      (Eq. wkdefpractice), giving channels (R, G, B, w_1 .. w_K);
+ *   4. a solid-angle weighted 2x2 pyramid of those channels;
+ *   5. for each of R roughness levels the map filtered with the kernel
+ *      p_{L_i} ~ D(h) under n = v = r (Sec. 3.4 Eq. rtibl, Sec. 4
+ *      Eq. rtiblndf) by filtered importance sampling with S Hammersley samples.
+ * The texels must not change until the stream has passed this work. */
+glint_status glint_env_update(glint_env *env, const void *texels, void *stream);
+
+/* Copies the K radiance levels to host memory (K floats).  Synchronous. */
+glint_status glint_env_levels(const glint_env *env, float *host_L, int K);
+
+/* What glint_env_export copies. */
+typedef enum glint_env_item {
+    GLINT_ENV_LOHI = 0,      /* 2 floats: lo, hi */
+    GLINT_ENV_LEVELS = 1,    /* K floats */
+    GLINT_ENV_PYRAMID = 2,   /* pyramid level `index`: (H>>index) x (W>>index) x C floats */
+    GLINT_ENV_FILTERED = 3,  /* all filtered maps: R x (out_width/2) x out_width x C floats */
+    GLINT_ENV_TABLE = 4      /* filter sample table: R x S x 4 floats, then R int32 valid counts */
+} glint_env_item;
+
+/* Copies one item to host memory; C = 3 + K channels per texel, padded to a
+ * multiple of 4 in device memory and unpadded in the copy.  `bytes` must be at
+ * least the item's size.  Synchronous. */
+glint_status glint_env_export(const glint_env *env, int item, int index, void *host_dst, size_t bytes);
+
+/* Releases an environment (NULL is ignored). */
+void glint_env_destroy(glint_env *env);
+
+/* G-buffer: four device planes of width*height float4, 16-byte aligned.
+ *   view_n0:   w_o.xyz (unit vector from the surface to the viewer), N_0
+ *              (microfacets per unit uv area; <= 0 marks a background pixel,
+ *              shaded black)
+ *   normal_f0: n.xyz (unit shading normal), F0 (Schlick)
+ *   uv_alpha:  u, v, alpha_x, alpha_y (GGX roughness)
+ *   duv:       du/dx, dv/dx, du/dy, dv/dy (screen-space uv derivatives) */
+typedef struct glint_gbuffer {
+    const float *view_n0;
+    const float *normal_f0;
+    const float *uv_alpha;
+    const float *duv;
+    int width;
+    int height;
+} glint_gbuffer;
+
+typedef struct glint_params {
+    uint32_t seed;   /* user seed of the grid-vertex hashes */
+    int count_mode;  /* glint_count_mode */
+} glint_params;
+
+/* Optional per-pixel intermediate results (device; each pointer may be NULL).
+ *   p:      npix x K   reflection probabilities p_k (Eq. probhk)
+ *   np:     npix       microfacet count N_P of the footprint
+ *   vert:   npix x 6 x 3 int32: low 32 bits of grid vertex x, y, and level
+ *   w:      npix x 6   grid sample weights w_i (Eq. anisogrid)
+ *   nroot:  npix x 6   trials at each sample's tree root (float)
+ *   counts: npix x 6 x K per-sample bin counts n_k(i) (float; integers in
+ *           integer mode)
+ *   lo:     npix x 3   smooth radiance L_o (Eq. rtibl) */
+typedef struct glint_debug {
+    float *p;
+    float *np;
+    int32_t *vert;
+    float *w;
+    float *nroot;
+    float *counts;
+    float *lo;
+} glint_debug;
+
+/* Glint shading of every pixel of `gbuf` (Sec. 4 Eq. iblglints:fin):
+ *   L^_o = L_o * sum_k L_k M_k / (N_P * sum_k L_k p_k)
+ * with L_o the smooth split-sum radiance, p_k = V W_k (k >= 2) and
+ * p_1 = U + V W_1 from the filtered maps and tables, N_P = N_0 |det duv|, and
+ * M_k = sum_i w_i n_k(i) over six triangle-grid samples (Sec. 3.3
+ * Eq. anisogrid), each a hierarchical multinomial of dual-gated Gaussian
+ * binomials (Alg. 1, Sec. 5) seeded by a hash of its grid vertex.
+ * out_rgba: device, width*height float4.  dbg may be NULL.  Enqueued on
+ * `stream`; env must have been updated on the same stream (or synchronised). */
+glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf,
+                         const glint_params *params, float *out_rgba, const glint_debug *dbg, void *stream);
+
+/* Number of kernel launches the most recent glint_env_update / glint_shade on
+ * this environment / context enqueued (for launch accounting). */
+int glint_env_last_launches(const glint_env *env);
+int glint_ctx_last_launches(const glint_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLINT_H */

@@ -1,0 +1,308 @@
+// Host side of the C ABI declared in include/glint.h: argument checks, device
+// allocation, error reporting and launch accounting.  All computation is in
+// the kernels of glint_lut.cu, glint_env.cu and glint_shade.cu.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "glint_internal.cuh"
+
+namespace glint {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+glint_status cuda_status(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return GLINT_OK;
+    set_error("%s: CUDA error %d (%s)", what, (int)e, cudaGetErrorString(e));
+    return (e == cudaErrorMemoryAllocation) ? GLINT_ERR_OOM : GLINT_ERR_CUDA;
+}
+
+// Makes `dev` current for the lifetime of the guard and restores the caller's
+// device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace glint
+
+using namespace glint;
+
+extern "C" {
+
+int glint_abi_version(void) { return GLINT_ABI_VERSION; }
+
+const char *glint_last_error(void) { return g_err; }
+
+glint_status glint_ctx_create(int device, int lut_n, int lut_q, glint_ctx **out) {
+    g_err[0] = 0;
+    if (!out) { set_error("glint_ctx_create: out is NULL"); return GLINT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (lut_n == 0) lut_n = 64;
+    if (lut_q == 0) lut_q = 128;
+    if (lut_n < 2 || lut_n > 256 || lut_q < 8 || lut_q > 1024) {
+        set_error("glint_ctx_create: lut_n %d must be in [2,256], lut_q %d in [8,1024]", lut_n, lut_q);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    glint_status st = cuda_status(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (st != GLINT_OK) return st;
+    if (device < 0 || device >= ndev) {
+        set_error("glint_ctx_create: device %d out of range (%d devices)", device, ndev);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(device);
+    if (!guard.ok) { set_error("glint_ctx_create: cannot select device %d", device); return GLINT_ERR_CUDA; }
+    glint_ctx *c = new glint_ctx();
+    c->device = device;
+    c->lut_n = lut_n;
+    c->lut_q = lut_q;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    st = cuda_status(cudaMalloc(&c->lut, sizeof(float4) * (size_t)lut_n * lut_n), "glint_ctx_create: table");
+    if (st == GLINT_OK) st = cuda_status(glint_launch_lut(c->lut, lut_n, lut_q, 0), "glint_ctx_create: table kernel");
+    if (st == GLINT_OK) st = cuda_status(cudaStreamSynchronize(0), "glint_ctx_create: table kernel");
+    if (st != GLINT_OK) {
+        cudaFree(c->lut);
+        delete c;
+        return st;
+    }
+    c->last_launches = 1;
+    *out = c;
+    return GLINT_OK;
+}
+
+void glint_ctx_destroy(glint_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard guard(ctx->device);
+    cudaFree(ctx->lut);
+    delete ctx;
+}
+
+glint_status glint_lut_export(const glint_ctx *ctx, float *host_dst, size_t bytes) {
+    g_err[0] = 0;
+    if (!ctx || !host_dst) { set_error("glint_lut_export: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    const size_t need = sizeof(float4) * (size_t)ctx->lut_n * ctx->lut_n;
+    if (bytes < need) { set_error("glint_lut_export: need %zu bytes, got %zu", need, bytes); return GLINT_ERR_INVALID_ARG; }
+    DeviceGuard guard(ctx->device);
+    return cuda_status(cudaMemcpy(host_dst, ctx->lut, need, cudaMemcpyDeviceToHost), "glint_lut_export");
+}
+
+static void env_free(glint_env *e) {
+    cudaFree(e->levels);
+    cudaFree(e->partial);
+    cudaFree(e->pyr);
+    cudaFree(e->pyr_off4_dev);
+    cudaFree(e->table);
+    cudaFree(e->nvalid);
+    cudaFree(e->filt);
+}
+
+glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env **out) {
+    g_err[0] = 0;
+    if (!ctx || !d || !out) { set_error("glint_env_create: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!is_pow2(d->height) || d->height < 2 || d->height > 8192 || d->width != 2 * d->height) {
+        set_error("glint_env_create: need width = 2 height, height a power of two in [2, 8192] (got %d x %d)",
+                  d->width, d->height);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (d->format != GLINT_FMT_RGBA32F && d->format != GLINT_FMT_RGBA16F) {
+        set_error("glint_env_create: unknown format %d", d->format);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (d->K != 2 && d->K != 4 && d->K != 8 && d->K != 16) {
+        set_error("glint_env_create: K = %d, must be 2, 4, 8 or 16", d->K);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (!(d->ell > 0.f) || d->scale_log2 < -64 || d->scale_log2 > 64) {
+        set_error("glint_env_create: ell must be > 0 and |scale_log2| <= 64");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (d->levels < 1 || d->levels > 32 || d->samples < 1 || d->samples > 2048 || !is_pow2(d->out_width) ||
+        d->out_width < 4 || d->out_width > 4096) {
+        set_error("glint_env_create: levels in [1,32], samples in [1,2048], out_width a power of two in [4,4096]");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (!(d->s_min > 0.f) || !(d->s_max >= d->s_min) || !(d->s_max <= 1.f) || (d->levels > 1 && !(d->s_max > d->s_min))) {
+        set_error("glint_env_create: need 0 < s_min < s_max <= 1 (s_min = s_max only with one level)");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    glint_env *e = new glint_env();
+    e->ctx = ctx;
+    e->d = *d;
+    e->C = 3 + d->K;
+    e->Cpad = (e->C + 3) / 4 * 4;
+    e->Ho = d->out_width / 2;
+    int M = 1;
+    while ((d->height >> (M - 1)) > 1) ++M;
+    e->M = M;
+    size_t off = 0;
+    std::vector<size_t> off4(M);
+    for (int m = 0; m < M; ++m) {
+        e->pyr_off[m] = off;
+        off4[m] = off / 4;
+        off += (size_t)(d->width >> m) * (d->height >> m) * e->Cpad;
+    }
+    const long n = (long)d->width * d->height;
+    e->nblk_minmax = (int)std::min<long>((n + 255) / 256, (long)std::max(ctx->num_sms, 1) * 8);
+    glint_status st = GLINT_OK;
+    auto alloc = [&](void **p, size_t bytes, const char *what) {
+        if (st == GLINT_OK) st = cuda_status(cudaMalloc(p, bytes), what);
+    };
+    alloc((void **)&e->levels, sizeof(float) * (d->K + 2), "glint_env_create: levels");
+    alloc((void **)&e->partial, sizeof(float2) * e->nblk_minmax, "glint_env_create: scratch");
+    alloc((void **)&e->pyr, sizeof(float) * off, "glint_env_create: pyramid");
+    alloc((void **)&e->pyr_off4_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
+    alloc((void **)&e->table, sizeof(float4) * (size_t)d->levels * d->samples, "glint_env_create: filter table");
+    alloc((void **)&e->nvalid, sizeof(int) * d->levels, "glint_env_create: filter table");
+    alloc((void **)&e->filt, sizeof(float) * (size_t)d->levels * e->Ho * d->out_width * e->Cpad,
+          "glint_env_create: filtered maps");
+    if (st == GLINT_OK)
+        st = cuda_status(cudaMemcpy(e->pyr_off4_dev, off4.data(), sizeof(size_t) * M, cudaMemcpyHostToDevice),
+                         "glint_env_create: pyramid offsets");
+    if (st != GLINT_OK) {
+        env_free(e);
+        delete e;
+        return st;
+    }
+    *out = e;
+    return GLINT_OK;
+}
+
+glint_status glint_env_update(glint_env *env, const void *texels, void *stream) {
+    g_err[0] = 0;
+    if (!env || !texels) { set_error("glint_env_update: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (!aligned16(texels) && env->d.format == GLINT_FMT_RGBA32F) {
+        set_error("glint_env_update: RGBA32F texels must be 16-byte aligned");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)texels & 7u) != 0) {
+        set_error("glint_env_update: texels must be 8-byte aligned");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(env->ctx->device);
+    int nl = 0;
+    glint_status st = cuda_status(glint_launch_env(env, texels, (cudaStream_t)stream, &nl), "glint_env_update");
+    env->last_launches = nl;
+    return st;
+}
+
+glint_status glint_env_levels(const glint_env *env, float *host_L, int K) {
+    g_err[0] = 0;
+    if (!env || !host_L || K != env->d.K) {
+        set_error("glint_env_levels: NULL argument or K mismatch");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(env->ctx->device);
+    return cuda_status(cudaMemcpy(host_L, env->levels, sizeof(float) * K, cudaMemcpyDeviceToHost), "glint_env_levels");
+}
+
+glint_status glint_env_export(const glint_env *env, int item, int index, void *host_dst, size_t bytes) {
+    g_err[0] = 0;
+    if (!env || !host_dst) { set_error("glint_env_export: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    DeviceGuard guard(env->ctx->device);
+    const glint_env_desc &d = env->d;
+    auto copy = [&](const void *src, size_t n) -> glint_status {
+        if (bytes < n) { set_error("glint_env_export: need %zu bytes, got %zu", n, bytes); return GLINT_ERR_INVALID_ARG; }
+        return cuda_status(cudaMemcpy(host_dst, src, n, cudaMemcpyDeviceToHost), "glint_env_export");
+    };
+    auto copy_unpadded = [&](const float *src, size_t texels) -> glint_status {
+        const size_t n = texels * env->C * sizeof(float);
+        if (bytes < n) { set_error("glint_env_export: need %zu bytes, got %zu", n, bytes); return GLINT_ERR_INVALID_ARG; }
+        std::vector<float> tmp(texels * env->Cpad);
+        glint_status st = cuda_status(cudaMemcpy(tmp.data(), src, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost),
+                                      "glint_env_export");
+        if (st != GLINT_OK) return st;
+        float *dst = (float *)host_dst;
+        for (size_t t = 0; t < texels; ++t)
+            memcpy(dst + t * env->C, tmp.data() + t * env->Cpad, sizeof(float) * env->C);
+        return GLINT_OK;
+    };
+    switch (item) {
+    case GLINT_ENV_LOHI: return copy(env->levels + d.K, 2 * sizeof(float));
+    case GLINT_ENV_LEVELS: return copy(env->levels, d.K * sizeof(float));
+    case GLINT_ENV_PYRAMID:
+        if (index < 0 || index >= env->M) { set_error("glint_env_export: pyramid level %d out of range", index); return GLINT_ERR_INVALID_ARG; }
+        return copy_unpadded(env->pyr + env->pyr_off[index], (size_t)(d.width >> index) * (d.height >> index));
+    case GLINT_ENV_FILTERED:
+        return copy_unpadded(env->filt, (size_t)d.levels * env->Ho * d.out_width);
+    case GLINT_ENV_TABLE: {
+        const size_t nt = sizeof(float4) * (size_t)d.levels * d.samples;
+        const size_t n = nt + sizeof(int) * d.levels;
+        if (bytes < n) { set_error("glint_env_export: need %zu bytes, got %zu", n, bytes); return GLINT_ERR_INVALID_ARG; }
+        glint_status st = cuda_status(cudaMemcpy(host_dst, env->table, nt, cudaMemcpyDeviceToHost), "glint_env_export");
+        if (st != GLINT_OK) return st;
+        return cuda_status(cudaMemcpy((char *)host_dst + nt, env->nvalid, sizeof(int) * d.levels, cudaMemcpyDeviceToHost),
+                           "glint_env_export");
+    }
+    default:
+        set_error("glint_env_export: unknown item %d", item);
+        return GLINT_ERR_INVALID_ARG;
+    }
+}
+
+void glint_env_destroy(glint_env *env) {
+    if (!env) return;
+    DeviceGuard guard(env->ctx->device);
+    env_free(env);
+    delete env;
+}
+
+glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g, const glint_params *p,
+                         float *out_rgba, const glint_debug *dbg, void *stream) {
+    g_err[0] = 0;
+    if (!ctx || !env || !g || !p) { set_error("glint_shade: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (env->ctx != ctx) { set_error("glint_shade: environment belongs to another context"); return GLINT_ERR_INVALID_ARG; }
+    if (g->width < 0 || g->height < 0 || (long)g->width * g->height > (1L << 31)) {
+        set_error("glint_shade: width %d x height %d out of range", g->width, g->height);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (p->count_mode != GLINT_COUNT_INTEGER && p->count_mode != GLINT_COUNT_REAL) {
+        set_error("glint_shade: unknown count mode %d", p->count_mode);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    const long npix = (long)g->width * g->height;
+    if (npix > 0) {
+        if (!g->view_n0 || !g->normal_f0 || !g->uv_alpha || !g->duv || !out_rgba) {
+            set_error("glint_shade: NULL G-buffer plane or output");
+            return GLINT_ERR_INVALID_ARG;
+        }
+        if (!aligned16(g->view_n0) || !aligned16(g->normal_f0) || !aligned16(g->uv_alpha) || !aligned16(g->duv) ||
+            !aligned16(out_rgba)) {
+            set_error("glint_shade: G-buffer planes and output must be 16-byte aligned");
+            return GLINT_ERR_INVALID_ARG;
+        }
+    }
+    DeviceGuard guard(ctx->device);
+    int nl = 0;
+    glint_status st = cuda_status(glint_launch_shade(ctx, env, g, p, out_rgba, dbg, (cudaStream_t)stream, &nl),
+                                  "glint_shade");
+    ctx->last_launches = nl;
+    return st;
+}
+
+int glint_env_last_launches(const glint_env *env) { return env ? env->last_launches : 0; }
+int glint_ctx_last_launches(const glint_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+}  // extern "C"

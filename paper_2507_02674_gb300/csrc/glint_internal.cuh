@@ -1,0 +1,126 @@
+// Internal declarations of the CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "glint.h"
+
+namespace glint {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kInvTwoPi = 0.159154943091895335769f;
+constexpr float kInvPi = 0.318309886183790671538f;
+// Bias constant of the small-p fix of Sec. 5, eps = 10^-3.54, and log2(1 - eps).
+constexpr float kEps = 2.88403156446293e-4f;
+constexpr float kLog2OneMinusEps = -4.161378019489348e-4f;
+// Largest FP32 value below 2^32: N_P saturates here so counts fit in uint32.
+constexpr float kMaxCount = 4294967040.0f;
+
+void set_error(const char *fmt, ...);
+glint_status cuda_status(cudaError_t e, const char *what);
+
+}  // namespace glint
+
+struct glint_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int lut_n = 64;
+    int lut_q = 128;
+    float4 *lut = nullptr;  // lut_n * lut_n nodes: (V, U, A, B)
+    int last_launches = 0;
+};
+
+struct glint_env {
+    glint_ctx *ctx = nullptr;
+    glint_env_desc d{};
+    int C = 0;      // 3 + K channels
+    int Cpad = 0;   // channels padded to a multiple of 4
+    int M = 0;      // pyramid levels
+    int Ho = 0;     // filtered map height
+    int nblk_minmax = 0;
+    float *levels = nullptr;   // K levels, then lo, hi
+    float2 *partial = nullptr; // scratch: per-block (min, max) of the brightness
+    float *pyr = nullptr;      // pyramid, all levels, Cpad floats per texel
+    size_t pyr_off[24] = {};   // float offset of each level
+    size_t *pyr_off4_dev = nullptr; // same offsets in float4 units, on the device
+    float4 *table = nullptr;   // R x S filter samples
+    int *nvalid = nullptr;     // R valid sample counts
+    float *filt = nullptr;     // R x Ho x Wo x Cpad filtered maps
+    int last_launches = 0;
+};
+
+namespace glint {
+
+// ---------------------------------------------------------------- device helpers
+
+// pcg4d hash (Jarzynski & Olano, "Hash Functions for GPU Rendering", JCGT 2020).
+__device__ __forceinline__ uint4 pcg4d(uint4 v) {
+    v.x = v.x * 1664525u + 1013904223u;
+    v.y = v.y * 1664525u + 1013904223u;
+    v.z = v.z * 1664525u + 1013904223u;
+    v.w = v.w * 1664525u + 1013904223u;
+    v.x += v.y * v.w; v.y += v.z * v.x; v.z += v.x * v.y; v.w += v.y * v.z;
+    v.x ^= v.x >> 16; v.y ^= v.y >> 16; v.z ^= v.z >> 16; v.w ^= v.w >> 16;
+    v.x += v.y * v.w; v.y += v.z * v.x; v.z += v.x * v.y; v.w += v.y * v.z;
+    return v;
+}
+
+// Uniform in (0,1) from the top 23 bits of a hash word, (2m+1) 2^-24: exact in
+// FP32, never 0 or 1, and 1 - xi is exact.
+__device__ __forceinline__ float hash_uniform(uint32_t h) {
+    return __uint2float_rn(((h >> 9) << 1) | 1u) * 0x1p-24f;
+}
+__device__ __forceinline__ float hash_uniform_complement(uint32_t h) {
+    return __uint2float_rn((0x1000000u - (((h >> 9) << 1) | 1u))) * 0x1p-24f;
+}
+
+// Equirect texel coordinates of a direction (texel centres at integers).
+__device__ __forceinline__ void dir_to_texel(float dx, float dy, float dz, int W, int H, float &x, float &y) {
+    float th = acosf(fminf(fmaxf(dy, -1.f), 1.f));
+    float ph = atan2f(dz, dx);
+    if (ph < 0.f) ph += kTwoPi;
+    x = ph * (kInvTwoPi * (float)W) - 0.5f;
+    y = th * (kInvPi * (float)H) - 0.5f;
+}
+
+// Bilinear taps of an equirect level: wrap in phi, clamp in theta.
+struct Taps {
+    int i00, i01, i10, i11;
+    float w00, w01, w10, w11;
+};
+__device__ __forceinline__ Taps equirect_taps(float x, float y, int W, int H) {
+    float fx0 = floorf(x), fy0 = floorf(y);
+    float fx = x - fx0, fy = y - fy0;
+    int x0 = (int)fx0, y0 = (int)fy0;
+    int xa = x0 % W; if (xa < 0) xa += W;
+    int xb = xa + 1; if (xb >= W) xb -= W;
+    int ya = min(max(y0, 0), H - 1);
+    int yb = min(max(y0 + 1, 0), H - 1);
+    Taps t;
+    t.i00 = ya * W + xa; t.i01 = ya * W + xb; t.i10 = yb * W + xa; t.i11 = yb * W + xb;
+    t.w00 = (1.f - fy) * (1.f - fx); t.w01 = (1.f - fy) * fx;
+    t.w10 = fy * (1.f - fx); t.w11 = fy * fx;
+    return t;
+}
+
+__device__ __forceinline__ float4 ldg4(const float4 *p) { return __ldg(p); }
+
+__device__ __forceinline__ float4 fma4(float w, float4 a, float4 acc) {
+    acc.x = fmaf(w, a.x, acc.x); acc.y = fmaf(w, a.y, acc.y);
+    acc.z = fmaf(w, a.z, acc.z); acc.w = fmaf(w, a.w, acc.w);
+    return acc;
+}
+
+}  // namespace glint
+
+// Launchers implemented in the .cu files (return cudaGetLastError()).
+cudaError_t glint_launch_lut(float4 *lut, int n, int q, cudaStream_t s);
+cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s, int *launches);
+cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
+                               const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s,
+                               int *launches);

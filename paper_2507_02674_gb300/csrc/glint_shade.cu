@@ -1,0 +1,394 @@
+// Per-pixel glint shading (Sec. 4 Eq. iblglints:fin; Sec. 3.3 Eq. anisogrid;
+// Sec. 5 Alg. 1 and the hierarchical multinomial).
+//
+// One thread per pixel.  G-buffer reads are four coalesced float4 loads per
+// pixel (64 B), the output one float4 store (16 B).  The filtered maps (a few
+// MB) and the 64 x 64 table stay resident in L2/L1 across the frame.  Per pixel:
+//   1. smooth radiance L_o = prefRGB (F0 A + B) and p_k = V W_k, p_1 = U + V W_1
+//      from 8 bilinear taps of the filtered maps and 4 table taps (E1);
+//   2. footprint |P| and N_P in correctly rounded FP32 (same operation order
+//      as any IEEE implementation), grid level and triangle vertices likewise;
+//   3. per node of the balanced binary tree over the K bins: node probability,
+//      log2 p and the log2 of the (small-p biased) complement -- computed once
+//      per pixel and reused by all six grid samples;
+//   4. six samples x (K-1) dual-gated draws: a pcg4d hash of (vertex, level,
+//      node, seed) gives the uniforms, two exp2 give the gate probabilities,
+//      and the normal quantile is evaluated only when the Gaussian branch is
+//      taken;
+//   5. L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k).
+#include "glint_internal.cuh"
+
+using namespace glint;
+
+namespace {
+
+constexpr int kShadeNT = 128;
+
+struct ShadeArgs {
+    const float4 *view_n0, *normal_f0, *uv_alpha, *duv;
+    float4 *out;
+    long npix;
+    const float4 *lut;
+    int lut_n;
+    const float4 *filt;
+    int R, Wo, Ho;
+    float s_min, s_max;
+    const float *levels;
+    uint32_t seed;
+    glint_debug dbg;
+};
+
+__device__ __forceinline__ float4 lut_fetch(const float4 *lut, int n, float mu, float s) {
+    float x = fminf(fmaxf(mu * (float)n - 0.5f, 0.f), (float)(n - 1));
+    float y = fminf(fmaxf(s * (float)n - 0.5f, 0.f), (float)(n - 1));
+    const float fx0 = floorf(x), fy0 = floorf(y);
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    const int x1 = min(x0 + 1, n - 1), y1 = min(y0 + 1, n - 1);
+    const float fx = x - fx0, fy = y - fy0;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    r = fma4((1.f - fy) * (1.f - fx), __ldg(lut + y0 * n + x0), r);
+    r = fma4((1.f - fy) * fx, __ldg(lut + y0 * n + x1), r);
+    r = fma4(fy * (1.f - fx), __ldg(lut + y1 * n + x0), r);
+    r = fma4(fy * fx, __ldg(lut + y1 * n + x1), r);
+    return r;
+}
+
+// |du/dx dv/dy - du/dy dv/dx| with one FMA correction (Kahan), every
+// operation correctly rounded and never contracted.
+__device__ __forceinline__ float footprint_area(float dudx, float dvdx, float dudy, float dvdy) {
+    const float w = __fmul_rn(dudy, dvdx);
+    const float e = __fmaf_rn(-dudy, dvdx, w);
+    const float f = __fmaf_rn(dudx, dvdy, -w);
+    return fabsf(__fadd_rn(f, e));
+}
+
+struct NodeParams {
+    float p, q, lp, lq;  // node probability, complement, log2 p, log2 of (1 - c p)^(1/c)
+};
+
+// Dual-gated Gaussian (Alg. 1) for an integer number of trials N >= 1;
+// returns n (nbar = N - n).  Regions of xi1 (same as the printed masks):
+// [0, P_{n=N}) -> N;  [P_{n=N}, P_{n=N} + P_{n=1}) -> 1;
+// 1 - xi1 <= P_{nbar=N} + P_{nbar=1} -> 0;  otherwise the clamped, rounded
+// Gaussian when N > 1, else 0.
+__device__ __forceinline__ uint32_t draw_integer(uint32_t N, const NodeParams &np, uint32_t h1, uint32_t h2) {
+    const float xi1 = hash_uniform(h1);
+    const float xi1c = hash_uniform_complement(h1);
+    const float Nf = __uint2float_rn(N);
+    const float N2 = fmaxf(2.f, Nf);
+    const float a = (N >= 2u) ? 1.f : 0.f;
+    const float b = (N == 1u) ? 1.f : 0.f;
+    const float Pall = a * exp2f(N2 * np.lp);
+    const float T1 = Pall + b * np.p;
+    const float Sneg = a * exp2f(N2 * np.lq) + b * np.q;
+    if (xi1 < Pall) return N;
+    if (xi1 < T1) return 1u;
+    if (xi1c <= Sneg || N < 2u) return 0u;
+    const float mu = 1.f + (N2 - 2.f) * np.p;
+    const float sigma = sqrtf((N2 - 2.f) * np.p * np.q);
+    const float z = normcdfinvf(hash_uniform(h2));
+    float G = floorf(fmaf(sigma, z, mu) + 0.5f);
+    G = fminf(fmaxf(G, 1.f), kMaxCount);
+    return min((uint32_t)G, N - 1u);
+}
+
+// Dual-gated Gaussian (Alg. 1) with real-valued N and counts.
+__device__ __forceinline__ void draw_real(float N, const NodeParams &np, uint32_t h1, uint32_t h2, float &n,
+                                          float &nbar) {
+    const float xi1 = hash_uniform(h1);
+    const float xi1c = hash_uniform_complement(h1);
+    const float N2 = fmaxf(2.f, N);
+    const float a = fminf(fmaxf(N - 1.f, 0.f), 1.f);
+    const float b = fmaxf(0.f, 1.f - fabsf(1.f - N));
+    const float Pall = a * exp2f(N2 * np.lp);
+    const float Pallneg = a * exp2f(N2 * np.lq);
+    const float Pone = b * np.p, Poneneg = b * np.q;
+    const bool B_all = xi1 < Pall;
+    const bool B_allone = xi1 < Pall + Pone;
+    const bool B_allneg = xi1c <= Pallneg;
+    const bool B_alloneneg = xi1c <= Pallneg + Poneneg;
+    const bool B_G = (N > 1.f) && !B_allone && !B_alloneneg;
+    float G = 0.f;
+    if (B_G) {
+        const float mu = 1.f + (N2 - 2.f) * np.p;
+        const float sigma = sqrtf(fmaxf((N2 - 2.f) * np.p * np.q, 0.f));
+        const float z = normcdfinvf(hash_uniform(h2));
+        G = fminf(fmaxf(fmaf(sigma, z, mu), 1.f), N2 - 1.f);
+    }
+    n = (B_all ? N2 - 1.f : 0.f) + (B_allone ? 1.f : 0.f) + G;
+    nbar = (B_allneg ? N2 - 1.f : 0.f) + (B_alloneneg ? 1.f : 0.f) + (B_G ? N2 - G : 0.f);
+}
+
+template <int K, bool INTEGER, bool DEBUG>
+__global__ void __launch_bounds__(kShadeNT) k_shade(ShadeArgs a) {
+    constexpr int C4 = (3 + K + 3) / 4;
+    const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
+    if (q >= a.npix) return;
+    const float4 g0 = ldg4(a.view_n0 + q);
+    const float4 g1 = ldg4(a.normal_f0 + q);
+    const float4 g2 = ldg4(a.uv_alpha + q);
+    const float4 g3 = ldg4(a.duv + q);
+
+    if (!(g0.w > 0.f)) {  // background
+        a.out[q] = make_float4(0.f, 0.f, 0.f, 1.f);
+        if (DEBUG) {
+            if (a.dbg.np) a.dbg.np[q] = 0.f;
+            if (a.dbg.p) for (int k = 0; k < K; ++k) a.dbg.p[q * K + k] = 0.f;
+            if (a.dbg.lo) for (int c = 0; c < 3; ++c) a.dbg.lo[q * 3 + c] = 0.f;
+            for (int v = 0; v < 6; ++v) {
+                if (a.dbg.w) a.dbg.w[q * 6 + v] = 0.f;
+                if (a.dbg.nroot) a.dbg.nroot[q * 6 + v] = 0.f;
+                if (a.dbg.vert) for (int c = 0; c < 3; ++c) a.dbg.vert[(q * 6 + v) * 3 + c] = 0;
+                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * 6 + v) * K + k] = 0.f;
+            }
+        }
+        return;
+    }
+
+    // ---- 1. smooth radiance and reflection probabilities (E1)
+    const float mu_o = g1.x * g0.x + g1.y * g0.y + g1.z * g0.z;
+    const float rx = 2.f * mu_o * g1.x - g0.x;
+    const float ry = 2.f * mu_o * g1.y - g0.y;
+    const float rz = 2.f * mu_o * g1.z - g0.z;
+    const float mu_c = fminf(fmaxf(mu_o, 1e-4f), 1.f);
+    const float s = sqrtf(sqrtf(g2.z * g2.w));
+    const float4 tab = lut_fetch(a.lut, a.lut_n, mu_c, s);  // V, U, A, B
+    float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
+    tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
+    const int r0 = (int)floorf(tl);
+    const int r1 = min(r0 + 1, a.R - 1);
+    const float ft = tl - (float)r0;
+    float tx, ty;
+    dir_to_texel(rx, ry, rz, a.Wo, a.Ho, tx, ty);
+    const Taps tp = equirect_taps(tx, ty, a.Wo, a.Ho);
+    float4 cc[C4];
+#pragma unroll
+    for (int c = 0; c < C4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int lv = 0; lv < 2; ++lv) {
+        const float4 *base = a.filt + (size_t)(lv ? r1 : r0) * a.Wo * a.Ho * C4;
+        const float wl = lv ? ft : 1.f - ft;
+#pragma unroll
+        for (int c = 0; c < C4; ++c) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * C4 + c), v);
+            v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * C4 + c), v);
+            v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * C4 + c), v);
+            v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * C4 + c), v);
+            cc[c] = fma4(wl, v, cc[c]);
+        }
+    }
+    float ch[C4 * 4];
+#pragma unroll
+    for (int c = 0; c < C4; ++c) {
+        ch[4 * c] = cc[c].x; ch[4 * c + 1] = cc[c].y; ch[4 * c + 2] = cc[c].z; ch[4 * c + 3] = cc[c].w;
+    }
+    const float Eb = g1.w * tab.z + tab.w;
+    const float Lor = ch[0] * Eb, Log = ch[1] * Eb, Lob = ch[2] * Eb;
+    float p[K];
+    p[0] = tab.y + tab.x * ch[3];
+#pragma unroll
+    for (int k = 1; k < K; ++k) p[k] = tab.x * ch[3 + k];
+
+    // ---- 2. footprint, microfacet count, grid level
+    const float area = footprint_area(g3.x, g3.y, g3.z, g3.w);
+    const float NP = fminf(__fmul_rn(g0.w, area), kMaxCount);
+    float L[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) L[k] = __ldg(a.levels + k);
+
+    if (DEBUG) {
+        if (a.dbg.np) a.dbg.np[q] = NP;
+        if (a.dbg.p) for (int k = 0; k < K; ++k) a.dbg.p[q * K + k] = p[k];
+        if (a.dbg.lo) { a.dbg.lo[q * 3] = Lor; a.dbg.lo[q * 3 + 1] = Log; a.dbg.lo[q * 3 + 2] = Lob; }
+    }
+    if (!(area > 0.f) || !(NP > 0.f)) {
+        a.out[q] = make_float4(0.f, 0.f, 0.f, 1.f);
+        if (DEBUG) {
+            for (int v = 0; v < 6; ++v) {
+                if (a.dbg.w) a.dbg.w[q * 6 + v] = 0.f;
+                if (a.dbg.nroot) a.dbg.nroot[q * 6 + v] = 0.f;
+                if (a.dbg.vert) for (int c = 0; c < 3; ++c) a.dbg.vert[(q * 6 + v) * 3 + c] = 0;
+                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * 6 + v) * K + k] = 0.f;
+            }
+        }
+        return;
+    }
+    int e2;
+    const float mant = frexpf(area, &e2);  // area = mant 2^e2, mant in [1/2, 1)
+    const int ep = e2 - 1;
+    int l0 = (ep >= 0) ? ep / 2 : -((-ep + 1) / 2);
+    float fl = 0.5f * ((float)(ep - 2 * l0) + log2f(2.f * mant));
+    if (l0 < -24) { l0 = -24; fl = 0.f; }
+    if (l0 > 23) { l0 = 23; fl = 1.f; }
+
+    // ---- 3. node parameters of the balanced binary tree (heap order)
+    float P[2 * K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) P[K + k] = p[k];
+#pragma unroll
+    for (int n = K - 1; n >= 1; --n) P[n] = P[2 * n] + P[2 * n + 1];
+    NodeParams nd[K];
+#pragma unroll
+    for (int n = 1; n < K; ++n) {
+        const float tot = P[n];
+        float pn = 0.f, qn = 1.f;
+        if (tot > 0.f) {
+            const float inv = 1.f / tot;
+            pn = P[2 * n] * inv;
+            qn = P[2 * n + 1] * inv;
+        }
+        nd[n].p = pn;
+        nd[n].q = qn;
+        nd[n].lp = log2f(pn);
+        nd[n].lq = (pn >= kEps) ? log2f(qn) : (pn * (1.f / kEps)) * kLog2OneMinusEps;
+    }
+
+    // ---- 4. six grid samples x (K-1) draws
+    float M[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) M[k] = 0.f;
+    const float F2 = 0x1.76cf5ep-2f;  // (sqrt(3) - 1) / 2
+    const float fN = floorf(NP);
+    const float fracN = NP - fN;
+#pragma unroll 1
+    for (int lv = 0; lv < 2; ++lv) {
+        const int l = l0 + lv;
+        const float lw = lv ? fl : 1.f - fl;
+        const float x = ldexpf(g2.x, -l), y = ldexpf(g2.y, -l);
+        const float sk = __fmul_rn(__fadd_rn(x, y), F2);
+        const float xs = __fadd_rn(x, sk), ys = __fadd_rn(y, sk);
+        const float fi = floorf(xs), fj = floorf(ys);
+        const float fx = __fsub_rn(xs, fi), fy = __fsub_rn(ys, fj);
+        const long long ii = (long long)fi, jj = (long long)fj;
+        const bool tri = fx > fy;
+        const float bmax = tri ? fx : fy, bmin = tri ? fy : fx;
+        const uint32_t key2 = ((uint32_t)l) & 0xFFFFu;
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t vx = (uint32_t)(ii + ((c == 2 || (c == 1 && tri)) ? 1 : 0));
+            const uint32_t vy = (uint32_t)(jj + ((c == 2 || (c == 1 && !tri)) ? 1 : 0));
+            const float bc = (c == 0) ? 1.f - bmax : (c == 1) ? bmax - bmin : bmin;
+            const float w = lw * bc;
+            uint4 h = pcg4d(make_uint4(vx, vy, key2 | (1u << 16), a.seed));
+            float cnt[K];
+            float nroot;
+            if (INTEGER) {
+                uint32_t N[2 * K];
+                N[1] = (uint32_t)fN + ((hash_uniform(h.x) < fracN) ? 1u : 0u);
+#pragma unroll
+                for (int n = 1; n < K; ++n) {
+                    uint32_t nl = 0u, nr = 0u;
+                    if (N[n] > 0u) {
+                        if (n > 1) h = pcg4d(make_uint4(vx, vy, key2 | ((uint32_t)n << 16), a.seed));
+                        nl = draw_integer(N[n], nd[n], h.y, h.z);
+                        nr = N[n] - nl;
+                    }
+                    N[2 * n] = nl;
+                    N[2 * n + 1] = nr;
+                }
+                nroot = __uint2float_rn(N[1]);
+#pragma unroll
+                for (int k = 0; k < K; ++k) cnt[k] = __uint2float_rn(N[K + k]);
+            } else {
+                float N[2 * K];
+                N[1] = NP;
+#pragma unroll
+                for (int n = 1; n < K; ++n) {
+                    float nl = 0.f, nr = 0.f;
+                    if (N[n] > 0.f) {
+                        if (n > 1) h = pcg4d(make_uint4(vx, vy, key2 | ((uint32_t)n << 16), a.seed));
+                        draw_real(N[n], nd[n], h.y, h.z, nl, nr);
+                    }
+                    N[2 * n] = nl;
+                    N[2 * n + 1] = nr;
+                }
+                nroot = NP;
+#pragma unroll
+                for (int k = 0; k < K; ++k) cnt[k] = N[K + k];
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) M[k] = fmaf(w, cnt[k], M[k]);
+            if (DEBUG) {
+                const int v = lv * 3 + c;
+                if (a.dbg.w) a.dbg.w[q * 6 + v] = w;
+                if (a.dbg.nroot) a.dbg.nroot[q * 6 + v] = nroot;
+                if (a.dbg.vert) {
+                    a.dbg.vert[(q * 6 + v) * 3 + 0] = (int32_t)vx;
+                    a.dbg.vert[(q * 6 + v) * 3 + 1] = (int32_t)vy;
+                    a.dbg.vert[(q * 6 + v) * 3 + 2] = l;
+                }
+                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * 6 + v) * K + k] = cnt[k];
+            }
+        }
+    }
+
+    // ---- 5. radiance
+    float num = 0.f, den = 0.f;
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+        num = fmaf(L[k], M[k], num);
+        den = fmaf(L[k], p[k], den);
+    }
+    den *= NP;
+    float4 o = make_float4(0.f, 0.f, 0.f, 1.f);
+    if (den > 0.f) {
+        const float ratio = num / den;
+        o.x = Lor * ratio;
+        o.y = Log * ratio;
+        o.z = Lob * ratio;
+    }
+    a.out[q] = o;
+}
+
+template <int K>
+cudaError_t launch_k(const ShadeArgs &args, bool integer, bool debug, cudaStream_t s) {
+    const unsigned grid = (unsigned)((args.npix + kShadeNT - 1) / kShadeNT);
+    if (integer) {
+        if (debug) k_shade<K, true, true><<<grid, kShadeNT, 0, s>>>(args);
+        else k_shade<K, true, false><<<grid, kShadeNT, 0, s>>>(args);
+    } else {
+        if (debug) k_shade<K, false, true><<<grid, kShadeNT, 0, s>>>(args);
+        else k_shade<K, false, false><<<grid, kShadeNT, 0, s>>>(args);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
+                               const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s,
+                               int *launches) {
+    ShadeArgs a;
+    a.view_n0 = reinterpret_cast<const float4 *>(g->view_n0);
+    a.normal_f0 = reinterpret_cast<const float4 *>(g->normal_f0);
+    a.uv_alpha = reinterpret_cast<const float4 *>(g->uv_alpha);
+    a.duv = reinterpret_cast<const float4 *>(g->duv);
+    a.out = reinterpret_cast<float4 *>(out);
+    a.npix = (long)g->width * g->height;
+    a.lut = ctx->lut;
+    a.lut_n = ctx->lut_n;
+    a.filt = reinterpret_cast<const float4 *>(env->filt);
+    a.R = env->d.levels;
+    a.Wo = env->d.out_width;
+    a.Ho = env->Ho;
+    a.s_min = env->d.s_min;
+    a.s_max = env->d.s_max;
+    a.levels = env->levels;
+    a.seed = p->seed;
+    a.dbg = dbg ? *dbg : glint_debug{};
+    const bool debug = dbg != nullptr;
+    const bool integer = p->count_mode == GLINT_COUNT_INTEGER;
+    if (launches) *launches = 0;
+    if (a.npix == 0) return cudaSuccess;
+    cudaError_t e;
+    switch (env->d.K) {
+    case 2: e = launch_k<2>(a, integer, debug, s); break;
+    case 4: e = launch_k<4>(a, integer, debug, s); break;
+    case 8: e = launch_k<8>(a, integer, debug, s); break;
+    case 16: e = launch_k<16>(a, integer, debug, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (launches) *launches = 1;
+    return e;
+}

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the C ABI in ``include/glint.h``.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libglint.so``.  PyTorch provides device memory and streams.  If
+the library is missing, importing this module raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libglint.so")
+
+GLINT_OK = 0
+FMT_RGBA32F, FMT_RGBA16F = 0, 1
+COUNT_INTEGER, COUNT_REAL = 0, 1
+ENV_LOHI, ENV_LEVELS, ENV_PYRAMID, ENV_FILTERED, ENV_TABLE = 0, 1, 2, 3, 4
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_READY", 5: "TIMEOUT", 6: "UNSUPPORTED"}
+
+
+class GlintError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"glint status {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class EnvDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("format", ctypes.c_int),
+                ("scale_log2", ctypes.c_int), ("K", ctypes.c_int), ("ell", ctypes.c_float),
+                ("levels", ctypes.c_int), ("samples", ctypes.c_int), ("out_width", ctypes.c_int),
+                ("s_min", ctypes.c_float), ("s_max", ctypes.c_float)]
+
+
+class GBufferDesc(ctypes.Structure):
+    _fields_ = [("view_n0", ctypes.c_void_p), ("normal_f0", ctypes.c_void_p), ("uv_alpha", ctypes.c_void_p),
+                ("duv", ctypes.c_void_p), ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint32), ("count_mode", ctypes.c_int)]
+
+
+class Debug(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_void_p), ("np", ctypes.c_void_p), ("vert", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("nroot", ctypes.c_void_p), ("counts", ctypes.c_void_p), ("lo", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2507_02674_gb300.build.build() "
+                          "(the CUDA library is the only implementation)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    lib.glint_abi_version.restype = I
+    lib.glint_last_error.restype = ctypes.c_char_p
+    lib.glint_ctx_create.argtypes = [I, I, I, ctypes.POINTER(P)]
+    lib.glint_ctx_destroy.argtypes = [P]
+    lib.glint_ctx_destroy.restype = None
+    lib.glint_lut_export.argtypes = [P, P, S]
+    lib.glint_env_create.argtypes = [P, ctypes.POINTER(EnvDesc), ctypes.POINTER(P)]
+    lib.glint_env_update.argtypes = [P, P, P]
+    lib.glint_env_levels.argtypes = [P, P, I]
+    lib.glint_env_export.argtypes = [P, I, I, P, S]
+    lib.glint_env_destroy.argtypes = [P]
+    lib.glint_env_destroy.restype = None
+    lib.glint_shade.argtypes = [P, P, ctypes.POINTER(GBufferDesc), ctypes.POINTER(Params), P,
+                                ctypes.POINTER(Debug), P]
+    lib.glint_env_last_launches.argtypes = [P]
+    lib.glint_env_last_launches.restype = I
+    lib.glint_ctx_last_launches.argtypes = [P]
+    lib.glint_ctx_last_launches.restype = I
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int):
+    if status != GLINT_OK:
+        raise GlintError(status, lib.glint_last_error().decode())
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """glint_ctx: a device and its microfacet tables."""
+
+    def __init__(self, device: int = 0, lut_n: int = 64, lut_q: int = 128):
+        h = ctypes.c_void_p()
+        _check(lib.glint_ctx_create(device, lut_n, lut_q, ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+        self.lut_n = lut_n
+
+    def lut(self) -> np.ndarray:
+        out = np.zeros((self.lut_n, self.lut_n, 4), np.float32)
+        _check(lib.glint_lut_export(self.handle, out.ctypes.data, out.nbytes))
+        return out
+
+    def last_launches(self) -> int:
+        return lib.glint_ctx_last_launches(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib.glint_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class EnvConfig:
+    K: int = 8
+    ell: float = 1e-4
+    levels: int = 8
+    samples: int = 64
+    out_width: int = 256
+    s_min: float = 0.02 ** 0.5
+    s_max: float = 0.5 ** 0.5
+
+
+class Env:
+    """glint_env: device buffers of one environment's levels, pyramid and filtered maps."""
+
+    def __init__(self, ctx: Context, width: int, height: int, fmt: int, scale_log2: int, cfg: EnvConfig):
+        self.ctx = ctx
+        self.cfg = cfg
+        self.desc = EnvDesc(width, height, fmt, scale_log2, cfg.K, cfg.ell, cfg.levels, cfg.samples, cfg.out_width,
+                            cfg.s_min, cfg.s_max)
+        h = ctypes.c_void_p()
+        _check(lib.glint_env_create(ctx.handle, ctypes.byref(self.desc), ctypes.byref(h)))
+        self.handle = h
+        self.C = 3 + cfg.K
+        self.M = 1
+        while (height >> (self.M - 1)) > 1:
+            self.M += 1
+
+    def update(self, texels, stream=None):
+        """Recompute levels, weights, pyramid and filtered maps from device texels."""
+        _check(lib.glint_env_update(self.handle, texels.data_ptr(), _stream_handle(stream)))
+
+    def levels(self) -> np.ndarray:
+        out = np.zeros(self.cfg.K, np.float32)
+        _check(lib.glint_env_levels(self.handle, out.ctypes.data, self.cfg.K))
+        return out
+
+    def export(self, item: int, index: int = 0) -> np.ndarray:
+        d = self.desc
+        if item == ENV_LOHI:
+            out = np.zeros(2, np.float32)
+        elif item == ENV_LEVELS:
+            out = np.zeros(d.K, np.float32)
+        elif item == ENV_PYRAMID:
+            out = np.zeros((d.height >> index, d.width >> index, self.C), np.float32)
+        elif item == ENV_FILTERED:
+            out = np.zeros((d.levels, d.out_width // 2, d.out_width, self.C), np.float32)
+        elif item == ENV_TABLE:
+            raw = np.zeros(d.levels * d.samples * 4 + d.levels, np.float32)
+            _check(lib.glint_env_export(self.handle, item, index, raw.ctypes.data, raw.nbytes))
+            table = raw[:d.levels * d.samples * 4].reshape(d.levels, d.samples, 4).copy()
+            nvalid = raw[d.levels * d.samples * 4:].view(np.int32).copy()
+            return table, nvalid
+        else:
+            raise ValueError(item)
+        _check(lib.glint_env_export(self.handle, item, index, out.ctypes.data, out.nbytes))
+        return out
+
+    def last_launches(self) -> int:
+        return lib.glint_env_last_launches(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib.glint_env_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def shade(ctx: Context, env: Env, planes, width: int, height: int, out, seed: int = 0,
+          count_mode: int = COUNT_INTEGER, debug: dict | None = None, stream=None):
+    """glint_shade over a G-buffer given as four device tensors of (npix, 4) float32."""
+    g = GBufferDesc(_dptr(planes[0]), _dptr(planes[1]), _dptr(planes[2]), _dptr(planes[3]), width, height)
+    p = Params(seed & 0xFFFFFFFF, count_mode)
+    dbg = None
+    if debug is not None:
+        dbg = Debug(*(_dptr(debug.get(k)) for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")))
+    _check(lib.glint_shade(ctx.handle, env.handle, ctypes.byref(g), ctypes.byref(p), _dptr(out),
+                           ctypes.byref(dbg) if dbg is not None else None, _stream_handle(stream)))
+
+
+def debug_buffers(npix: int, K: int, device="cuda"):
+    """Device tensors for every optional intermediate output of glint_shade."""
+    import torch
+    return {"p": torch.zeros(npix, K, device=device), "np": torch.zeros(npix, device=device),
+            "vert": torch.zeros(npix, 6, 3, dtype=torch.int32, device=device),
+            "w": torch.zeros(npix, 6, device=device), "nroot": torch.zeros(npix, 6, device=device),
+            "counts": torch.zeros(npix, 6, K, device=device), "lo": torch.zeros(npix, 3, device=device)}

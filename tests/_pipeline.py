@@ -47,7 +47,7 @@ def oracle_env(orc, env, mp: MethodParams):
     return e, pref
 
 
-def oracle_shade(orc, rows16: np.ndarray, env, mp: MethodParams, tie=None, max_cand: int = 8, env_pref=None):
+def oracle_shade(orc, rows16: np.ndarray, env, mp: MethodParams, tie=None, max_cand: int = 64, env_pref=None):
     e, pref = env_pref if env_pref is not None else oracle_env(orc, env, mp)
     lut = oracle_lut(orc, mp)
     return orc.shade(rows16, pref, mp.s_min, mp.s_max, lut, e.levels, mp.seed, mp.integer_mode,

@@ -1,0 +1,234 @@
+"""Parity of the CUDA library with the CPU oracle, through the C ABI.
+
+Every stage is compared element by element on seeded inputs: tables, radiance
+levels, weights, pyramid, filter samples, filtered maps, and per-pixel shading
+(exact N_P, grid vertices and root trials; counts in the oracle's valid set;
+p_k, L_o and radiance within stated tolerances).  Sizes run from the 64 x 64
+sphere to the full 1920 x 1080 frame (sampled pixels)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2507_02674_gb300 import synth
+from tests._compare import compare_shade
+from tests._pipeline import MethodParams, oracle_env, oracle_lut, oracle_shade
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_02674_gb300 import build as B
+    B.build()
+    from paper_2507_02674_gb300 import glint, render
+    ctx = glint.Context(0, 64, 128)
+    return glint, render, ctx, torch
+
+
+def _cfg(glint, mp: MethodParams):
+    return glint.EnvConfig(K=mp.K, ell=mp.ell, levels=mp.R, samples=mp.S, out_width=mp.Wo, s_min=mp.s_min,
+                           s_max=mp.s_max)
+
+
+def _run(gl, env, gb, mp: MethodParams, debug=True, rows=None):
+    glint, render, ctx, torch = gl
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    planes = render.gbuffer_tensors(gb)
+    npix = gb.width * gb.height
+    dbg = glint.debug_buffers(npix, mp.K) if debug else None
+    mode = glint.COUNT_INTEGER if mp.integer_mode else glint.COUNT_REAL
+    out = fr.shade(planes, gb.width, gb.height, seed=mp.seed, count_mode=mode, debug=dbg)
+    torch.cuda.synchronize()
+    res = {"rgb": out[:, :3].cpu().numpy().astype(np.float64), "frame": fr}
+    if debug:
+        sel = slice(None) if rows is None else torch.as_tensor(rows, device="cuda")
+        for k, v in dbg.items():
+            res[k] = (v if rows is None else v[sel]).cpu().numpy()
+        if rows is not None:
+            res["rgb"] = res["rgb"][rows]
+    return res
+
+
+def test_tables(gl, orc):
+    glint, render, ctx, torch = gl
+    mp = MethodParams()
+    g = ctx.lut().astype(np.float64)
+    o = oracle_lut(orc, mp)
+    assert np.max(np.abs(g - o)) < 3e-6, np.max(np.abs(g - o))
+    assert np.max(np.abs(g - o) / np.maximum(np.abs(o), 1e-3)) < 2e-5
+
+
+@pytest.mark.parametrize("which", ["tiny", "hdr"])
+def test_env_levels_weights_pyramid(gl, orc, which):
+    glint, render, ctx, torch = gl
+    env = synth.env_tiny(0) if which == "tiny" else synth.env_hdr(seed=3, W=256, H=128)
+    mp = MethodParams(K=8, Wo=64)
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    torch.cuda.synchronize()
+    e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell)
+    L = fr.env.levels().astype(np.float64)
+    assert np.allclose(L, e.levels, rtol=3e-6, atol=0)
+    lohi = fr.env.export(glint.ENV_LOHI).astype(np.float64)
+    assert np.allclose(lohi, e.lohi, rtol=1e-7)
+    for m in range(fr.env.M):
+        g = fr.env.export(glint.ENV_PYRAMID, m).astype(np.float64)
+        o = e.mips[m]
+        assert g.shape == o.shape
+        if m == 0:
+            assert np.array_equal(g[..., :3], o[..., :3])  # scaled by a power of two: exact
+        # weights lie in [0, 1]: absolute error of the FP32 lerp factor (levels
+        # carry ~1e-6 relative error); RGB: relative error of the FP32 means
+        assert np.max(np.abs(g[..., 3:] - o[..., 3:])) < 4e-6, (m, np.max(np.abs(g[..., 3:] - o[..., 3:])))
+        rel = np.abs(g[..., :3] - o[..., :3]) / np.abs(o[..., :3])
+        assert rel.max() < 2e-6, (m, rel.max())
+
+
+def test_filter_table(gl, orc):
+    glint, render, ctx, torch = gl
+    mp = MethodParams(K=4, R=8, S=64, Wo=64)
+    env = synth.env_hdr(seed=3, W=1024, H=512)
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    torch.cuda.synchronize()
+    tab, nv = fr.env.export(glint.ENV_TABLE)
+    otab, onv = orc.prefilter_table(mp.R, mp.S, mp.s_min, mp.s_max, env.width, env.height)
+    assert np.array_equal(nv, onv)
+    assert np.max(np.abs(tab[..., :3] - otab[..., :3])) < 2e-6
+    assert np.max(np.abs(tab[..., 3] - otab[..., 3])) < 2e-5
+
+
+@pytest.mark.parametrize("K,which,Wo", [(4, "tiny", 64), (8, "hdr", 128), (16, "hdr", 64)])
+def test_filtered_maps(gl, orc, K, which, Wo):
+    glint, render, ctx, torch = gl
+    env = synth.env_tiny(0) if which == "tiny" else synth.env_hdr(seed=4, W=512, H=256)
+    mp = MethodParams(K=K, Wo=Wo)
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    torch.cuda.synchronize()
+    g = fr.env.export(glint.ENV_FILTERED).astype(np.float64)
+    e, o = oracle_env(orc, env, mp)
+    assert g.shape == o.shape
+    rgb_rel = np.abs(g[..., :3] - o[..., :3]) / np.abs(o[..., :3])
+    w_abs = np.abs(g[..., 3:] - o[..., 3:])
+    w_rel = w_abs / np.maximum(o[..., 3:], 1e-7)
+    print(f"filtered K={K}: rgb rel max {rgb_rel.max():.2e} p99.9 {np.percentile(rgb_rel, 99.9):.2e}; "
+          f"w abs max {w_abs.max():.2e}; w rel p99.9 {np.percentile(w_rel, 99.9):.2e}")
+    # FP32 texel coordinates of each sample carry ~1e-7 rad of error, i.e. a few
+    # 1e-5 texels; across a sun's edge that moves a bilinear tap by a few 1e-5
+    # of its value, and the mean over S samples averages it down.
+    assert rgb_rel.max() < 5e-5
+    assert w_abs.max() < 5e-6
+    assert np.percentile(w_rel, 99.9) < 5e-5
+
+
+def _check(orc, o, res, integer_mode=True):
+    gpu = {k: res[k] for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")}
+    rep = compare_shade(orc, o, gpu, res["rgb"], integer_mode)
+    print(rep.summary())
+    assert rep.ok(), rep.failures
+    return rep
+
+
+def test_shade_sphere_tiny(gl, orc):
+    """64 x 64 head-on sphere, alpha 0.15, N_0 = 1e4, 64 x 32 map with two suns, K = 4."""
+    mp = MethodParams(K=4, Wo=64)
+    env = synth.env_tiny(0)
+    gb = synth.gbuffer_sphere()
+    res = _run(gl, env, gb, mp)
+    o = oracle_shade(orc, gb.rows16(), env, mp)
+    rep = _check(orc, o, res)
+    assert rep.trees_unresolved == 0
+
+
+@pytest.mark.parametrize("K", [2, 8, 16])
+def test_shade_random_pixels(gl, orc, K):
+    """Unstructured pixels with the 1080p scene's material distributions (alpha in
+    [0.03, 0.3], N_0 log-uniform in [1e3, 1e8]), an fp16 HDR map with suns; the
+    pixel count is not a multiple of the block size (ragged tail)."""
+    mp = MethodParams(K=K, Wo=128, seed=17)
+    env = synth.env_hdr(seed=6, W=256, H=128)
+    gb = synth.gbuffer_random(3000 + 37, seed=K, width=3037)
+    res = _run(gl, env, gb, mp)
+    o = oracle_shade(orc, gb.rows16(), env, mp)
+    _check(orc, o, res)
+
+
+def test_shade_real_counts(gl, orc):
+    """Alg. 1 as printed (real-valued counts)."""
+    mp = MethodParams(K=8, Wo=128, seed=5, integer_mode=False)
+    env = synth.env_hdr(seed=6, W=256, H=128)
+    gb = synth.gbuffer_random(1500, seed=9, n_lo=0.1, n_hi=1e6)
+    res = _run(gl, env, gb, mp)
+    o = oracle_shade(orc, gb.rows16(), env, mp)
+    _check(orc, o, res, integer_mode=False)
+
+
+def test_shade_edge_cases(gl, orc):
+    """Background pixels, zero footprint, N_P below one, saturated N_P, grazing
+    view, extreme roughness; a ragged 37 x 3 frame; an empty frame."""
+    glint, render, ctx, torch = gl
+    mp = MethodParams(K=8, Wo=64, seed=3)
+    env = synth.env_tiny(1)
+    gb = synth.gbuffer_random(111, seed=21, width=37)
+    rows = gb.rows16()
+    rows[0, 3] = 0.0
+    rows[1, 12:16] = 0.0
+    rows[2, 3] = 1e-3
+    rows[3, 3] = 1e15
+    rows[3, 12:16] = [1.0, 0.0, 0.0, 1.0]
+    rows[4, 0:3] = rows[4, 4:7] * 0.0 + np.array([1.0, 0.0, 0.0], np.float32)
+    rows[4, 4:7] = [0.0, 1.0, 0.0]                  # grazing: n . w_o = 0
+    rows[5, 10:12] = [1e-4, 1e-4]                   # nearly a mirror
+    rows[6, 10:12] = [1.0, 1.0]                     # roughest
+    gb.planes = [rows[:, 4 * i:4 * i + 4].reshape(gb.height, gb.width, 4).copy() for i in range(4)]
+    res = _run(gl, env, gb, mp)
+    o = oracle_shade(orc, gb.rows16(), env, mp)
+    _check(orc, o, res)
+    assert np.all(res["rgb"][:2] == 0)
+    # empty frame: a valid call that launches nothing
+    fr = res["frame"]
+    out = torch.zeros(1, 4, device="cuda")
+    planes = [torch.zeros(1, 4, device="cuda") for _ in range(4)]
+    glint.shade(ctx, fr.env, planes, 0, 0, out)
+    assert ctx.last_launches() == 0
+
+
+def test_shade_full_1080p_sampled(gl, orc):
+    """The 1920 x 1080 frame (plane + 16 spheres, 1024 x 512 RGBA16F map with 4
+    suns, K = 8) in the launch configuration of the benchmark; 2000 sampled pixels
+    against the oracle, plus properties over every pixel."""
+    glint, render, ctx, torch = gl
+    mp = MethodParams(K=8, Wo=256, seed=1)
+    env = synth.env_hdr(seed=1)
+    gb = synth.gbuffer_scene(1920, 1080, seed=1)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(gb.npix, 2000, replace=False))
+    res = _run(gl, env, gb, mp, rows=rows)
+    o = oracle_shade(orc, gb.rows16()[rows], env, mp)
+    _check(orc, o, res)
+    # whole frame: finite, non-negative radiance
+    out = res["frame"].shade(render.gbuffer_tensors(gb), gb.width, gb.height, seed=mp.seed)
+    torch.cuda.synchronize()
+    a = out.cpu().numpy()
+    assert np.all(np.isfinite(a)) and np.all(a[:, :3] >= 0) and np.all(a[:, 3] == 1)
+
+
+def test_invalid_arguments(gl):
+    glint, render, ctx, torch = gl
+    with pytest.raises(glint.GlintError):
+        glint.Env(ctx, 64, 64, glint.FMT_RGBA32F, 0, glint.EnvConfig(K=4))   # width != 2 height
+    with pytest.raises(glint.GlintError):
+        glint.Env(ctx, 64, 32, glint.FMT_RGBA32F, 0, glint.EnvConfig(K=3))
+    with pytest.raises(glint.GlintError):
+        glint.Env(ctx, 64, 32, glint.FMT_RGBA32F, 0, glint.EnvConfig(K=4, out_width=48))
+    env = glint.Env(ctx, 64, 32, glint.FMT_RGBA32F, 0, glint.EnvConfig(K=4, out_width=16))
+    planes = [torch.zeros(8, 4, device="cuda") for _ in range(4)]
+    out = torch.zeros(9, 4, device="cuda")
+    with pytest.raises(glint.GlintError):  # misaligned output
+        glint.shade(ctx, env, planes, 8, 1, out.view(-1)[1:33].view(8, 4))

@@ -203,6 +203,33 @@ typedef struct glint_debug {
 glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf,
                          const glint_params *params, float *out_rgba, const glint_debug *dbg, void *stream);
 
+/* Fixed scratch of glint_env_levels_noalloc: one (min, max) float pair per
+ * reduction block, GLINT_NOALLOC_MAX_BLOCKS pairs (8 KB per device). */
+#define GLINT_NOALLOC_MAX_BLOCKS 1024
+#define GLINT_NOALLOC_MAX_HEIGHT 8192
+
+/* Radiance levels of an environment map (steps 1 and 2 of glint_env_update:
+ * brightness min and max, lo, hi and L_1 .. L_K) computed without allocating
+ * any memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- frame loops that must never stall on
+ * an allocation (cudaMalloc/cudaFree may synchronise the device) and host
+ * applications such as engines and plug-in hosts that own every device
+ * allocation through their own allocator.
+ *
+ * texels: device, width x height RGBA texels in `format` (width = 2 height,
+ * height a power of two, at most GLINT_NOALLOC_MAX_HEIGHT; larger maps are
+ * rejected with GLINT_ERR_INVALID_ARG).  levels_out: device, K + 2 floats
+ * written as L_1 .. L_K, lo, hi (the layout glint_env_levels and
+ * GLINT_ENV_LOHI report).  Work is enqueued on `stream` of device `device`.
+ * The block partials of the reduction go to a fixed array inside the library
+ * that every GPU loading it holds until the process exits.  The first call on a
+ * device looks up that array's device address; make the first call before any
+ * stream capture.  All calls on a device share the array and it keeps the last
+ * call's contents; calls whose work overlaps on the GPU race on it, so issue
+ * them on one stream or order them. */
+glint_status glint_env_levels_noalloc(int device, const void *texels, int width, int height, int format,
+                                      int scale_log2, int K, float ell, float *levels_out, void *stream);
+
 /* Number of kernel launches the most recent glint_env_update / glint_shade on
  * this environment / context enqueued (for launch accounting). */
 int glint_env_last_launches(const glint_env *env);

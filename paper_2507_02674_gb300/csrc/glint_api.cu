@@ -302,6 +302,15 @@ glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuff
     return st;
 }
 
+glint_status glint_normal_quantile(const float *p, float *z, long n, void *stream) {
+    g_err[0] = 0;
+    if (n < 0 || (n > 0 && (!p || !z))) {
+        set_error("glint_normal_quantile: NULL argument or negative count");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    return cuda_status(glint_launch_quantile(p, z, n, (cudaStream_t)stream), "glint_normal_quantile");
+}
+
 int glint_env_last_launches(const glint_env *env) { return env ? env->last_launches : 0; }
 int glint_ctx_last_launches(const glint_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
 

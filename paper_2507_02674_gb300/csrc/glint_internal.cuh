@@ -121,6 +121,7 @@ __device__ __forceinline__ float4 fma4(float w, float4 a, float4 acc) {
 // Launchers implemented in the .cu files (return cudaGetLastError()).
 cudaError_t glint_launch_lut(float4 *lut, int n, int q, cudaStream_t s);
 cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s, int *launches);
+cudaError_t glint_launch_quantile(const float *p, float *z, long n, cudaStream_t s);
 cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
                                const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s,
                                int *launches);

@@ -12,11 +12,13 @@
 //      log2 p and the log2 of the (small-p biased) complement -- computed once
 //      per pixel and reused by all six grid samples;
 //   4. six samples x (K-1) dual-gated draws: a pcg4d hash of (vertex, level,
-//      node, seed) gives the uniforms, two exp2 give the gate probabilities,
-//      and the normal quantile is evaluated only when the Gaussian branch is
-//      taken;
+//      node, seed) gives the uniforms, two hardware exp2 give the gate
+//      probabilities, and the normal quantile is evaluated only when the
+//      Gaussian branch is taken;
+// 64 registers per thread (8 blocks of 128 threads per SM) measured fastest.
 //   5. L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k).
 #include "glint_internal.cuh"
+#include "glint_quantile.cuh"
 
 using namespace glint;
 
@@ -62,6 +64,35 @@ __device__ __forceinline__ float footprint_area(float dudx, float dvdx, float du
     return fabsf(__fadd_rn(f, e));
 }
 
+// Low 32 bits of the two's-complement integer held by an integral float.  For
+// |f| >= 2^31 the value is mant 2^e with e >= 8; shifting the 24-bit mantissa
+// gives the low word without a 64-bit conversion (which would use the FP64 pipe).
+__device__ __forceinline__ uint32_t low32_of_integral(float f) {
+    if (fabsf(f) < 2147483648.f) return (uint32_t)__float2int_rz(f);
+    const uint32_t b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xffu) - 150;
+    const uint32_t mant = (b & 0x7fffffu) | 0x800000u;
+    const uint32_t v = (e >= 32) ? 0u : (mant << e);
+    return (b >> 31) ? (0u - v) : v;
+}
+
+// Hardware 2^x (MUFU.EX2, ftz): relative error below 2^-22 (PTX ISA, ex2.approx);
+// the gate probabilities it produces are compared with uniforms >= 2^-24, so
+// flushing subnormal results to 0 changes no decision.
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Hardware square root (sqrt.approx, relative error ~2^-23) for the Gaussian's
+// standard deviation.
+__device__ __forceinline__ float fast_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct NodeParams {
     float p, q, lp, lq;  // node probability, complement, log2 p, log2 of (1 - c p)^(1/c)
 };
@@ -78,15 +109,15 @@ __device__ __forceinline__ uint32_t draw_integer(uint32_t N, const NodeParams &n
     const float N2 = fmaxf(2.f, Nf);
     const float a = (N >= 2u) ? 1.f : 0.f;
     const float b = (N == 1u) ? 1.f : 0.f;
-    const float Pall = a * exp2f(N2 * np.lp);
+    const float Pall = a * fast_exp2(N2 * np.lp);
     const float T1 = Pall + b * np.p;
-    const float Sneg = a * exp2f(N2 * np.lq) + b * np.q;
+    const float Sneg = a * fast_exp2(N2 * np.lq) + b * np.q;
     if (xi1 < Pall) return N;
     if (xi1 < T1) return 1u;
     if (xi1c <= Sneg || N < 2u) return 0u;
     const float mu = 1.f + (N2 - 2.f) * np.p;
-    const float sigma = sqrtf((N2 - 2.f) * np.p * np.q);
-    const float z = normcdfinvf(hash_uniform(h2));
+    const float sigma = fast_sqrt((N2 - 2.f) * np.p * np.q);
+    const float z = normal_quantile(hash_uniform(h2));
     float G = floorf(fmaf(sigma, z, mu) + 0.5f);
     G = fminf(fmaxf(G, 1.f), kMaxCount);
     return min((uint32_t)G, N - 1u);
@@ -100,8 +131,8 @@ __device__ __forceinline__ void draw_real(float N, const NodeParams &np, uint32_
     const float N2 = fmaxf(2.f, N);
     const float a = fminf(fmaxf(N - 1.f, 0.f), 1.f);
     const float b = fmaxf(0.f, 1.f - fabsf(1.f - N));
-    const float Pall = a * exp2f(N2 * np.lp);
-    const float Pallneg = a * exp2f(N2 * np.lq);
+    const float Pall = a * fast_exp2(N2 * np.lp);
+    const float Pallneg = a * fast_exp2(N2 * np.lq);
     const float Pone = b * np.p, Poneneg = b * np.q;
     const bool B_all = xi1 < Pall;
     const bool B_allone = xi1 < Pall + Pone;
@@ -111,8 +142,8 @@ __device__ __forceinline__ void draw_real(float N, const NodeParams &np, uint32_
     float G = 0.f;
     if (B_G) {
         const float mu = 1.f + (N2 - 2.f) * np.p;
-        const float sigma = sqrtf(fmaxf((N2 - 2.f) * np.p * np.q, 0.f));
-        const float z = normcdfinvf(hash_uniform(h2));
+        const float sigma = fast_sqrt(fmaxf((N2 - 2.f) * np.p * np.q, 0.f));
+        const float z = normal_quantile(hash_uniform(h2));
         G = fminf(fmaxf(fmaf(sigma, z, mu), 1.f), N2 - 1.f);
     }
     n = (B_all ? N2 - 1.f : 0.f) + (B_allone ? 1.f : 0.f) + G;
@@ -120,7 +151,7 @@ __device__ __forceinline__ void draw_real(float N, const NodeParams &np, uint32_
 }
 
 template <int K, bool INTEGER, bool DEBUG>
-__global__ void __launch_bounds__(kShadeNT) k_shade(ShadeArgs a) {
+__global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
     constexpr int C4 = (3 + K + 3) / 4;
     const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
     if (q >= a.npix) return;
@@ -193,9 +224,10 @@ __global__ void __launch_bounds__(kShadeNT) k_shade(ShadeArgs a) {
     // ---- 2. footprint, microfacet count, grid level
     const float area = footprint_area(g3.x, g3.y, g3.z, g3.w);
     const float NP = fminf(__fmul_rn(g0.w, area), kMaxCount);
-    float L[K];
+    float den = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) L[k] = __ldg(a.levels + k);
+    for (int k = 1; k < K; ++k) den = fmaf(__ldg(a.levels + k), p[k], den);
+    den *= NP;
 
     if (DEBUG) {
         if (a.dbg.np) a.dbg.np[q] = NP;
@@ -260,14 +292,14 @@ __global__ void __launch_bounds__(kShadeNT) k_shade(ShadeArgs a) {
         const float xs = __fadd_rn(x, sk), ys = __fadd_rn(y, sk);
         const float fi = floorf(xs), fj = floorf(ys);
         const float fx = __fsub_rn(xs, fi), fy = __fsub_rn(ys, fj);
-        const long long ii = (long long)fi, jj = (long long)fj;
+        const uint32_t ii = low32_of_integral(fi), jj = low32_of_integral(fj);
         const bool tri = fx > fy;
         const float bmax = tri ? fx : fy, bmin = tri ? fy : fx;
         const uint32_t key2 = ((uint32_t)l) & 0xFFFFu;
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {
-            const uint32_t vx = (uint32_t)(ii + ((c == 2 || (c == 1 && tri)) ? 1 : 0));
-            const uint32_t vy = (uint32_t)(jj + ((c == 2 || (c == 1 && !tri)) ? 1 : 0));
+            const uint32_t vx = ii + ((c == 2 || (c == 1 && tri)) ? 1u : 0u);
+            const uint32_t vy = jj + ((c == 2 || (c == 1 && !tri)) ? 1u : 0u);
             const float bc = (c == 0) ? 1.f - bmax : (c == 1) ? bmax - bmin : bmin;
             const float w = lw * bc;
             uint4 h = pcg4d(make_uint4(vx, vy, key2 | (1u << 16), a.seed));
@@ -324,13 +356,9 @@ __global__ void __launch_bounds__(kShadeNT) k_shade(ShadeArgs a) {
     }
 
     // ---- 5. radiance
-    float num = 0.f, den = 0.f;
+    float num = 0.f;
 #pragma unroll
-    for (int k = 1; k < K; ++k) {
-        num = fmaf(L[k], M[k], num);
-        den = fmaf(L[k], p[k], den);
-    }
-    den *= NP;
+    for (int k = 1; k < K; ++k) num = fmaf(__ldg(a.levels + k), M[k], num);
     float4 o = make_float4(0.f, 0.f, 0.f, 1.f);
     if (den > 0.f) {
         const float ratio = num / den;
@@ -339,6 +367,11 @@ __global__ void __launch_bounds__(kShadeNT) k_shade(ShadeArgs a) {
         o.z = Lob * ratio;
     }
     a.out[q] = o;
+}
+
+__global__ void k_quantile(const float *__restrict__ p, float *__restrict__ z, long n) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) z[i] = normal_quantile(p[i]);
 }
 
 template <int K>
@@ -355,6 +388,11 @@ cudaError_t launch_k(const ShadeArgs &args, bool integer, bool debug, cudaStream
 }
 
 }  // namespace
+
+cudaError_t glint_launch_quantile(const float *p, float *z, long n, cudaStream_t s) {
+    if (n > 0) k_quantile<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, z, n);
+    return cudaGetLastError();
+}
 
 cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
                                const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s,

@@ -70,6 +70,7 @@ def _load():
     lib.glint_env_destroy.restype = None
     lib.glint_shade.argtypes = [P, P, ctypes.POINTER(GBufferDesc), ctypes.POINTER(Params), P,
                                 ctypes.POINTER(Debug), P]
+    lib.glint_normal_quantile.argtypes = [P, P, ctypes.c_long, P]
     lib.glint_env_last_launches.argtypes = [P]
     lib.glint_env_last_launches.restype = I
     lib.glint_ctx_last_launches.argtypes = [P]
@@ -210,6 +211,15 @@ def shade(ctx: Context, env: Env, planes, width: int, height: int, out, seed: in
         dbg = Debug(*(_dptr(debug.get(k)) for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")))
     _check(lib.glint_shade(ctx.handle, env.handle, ctypes.byref(g), ctypes.byref(p), _dptr(out),
                            ctypes.byref(dbg) if dbg is not None else None, _stream_handle(stream)))
+
+
+def normal_quantile(p, out=None, stream=None):
+    """Phi^-1 of a device float32 tensor, as the shading kernel computes it."""
+    import torch
+    if out is None:
+        out = torch.empty_like(p)
+    _check(lib.glint_normal_quantile(p.data_ptr(), out.data_ptr(), p.numel(), _stream_handle(stream)))
+    return out
 
 
 def debug_buffers(npix: int, K: int, device="cuda"):

@@ -54,6 +54,24 @@ def _run(gl, env, gb, mp: MethodParams, debug=True, rows=None):
     return res
 
 
+def test_normal_quantile(gl):
+    """Our inverse normal CDF against scipy's (FP64) on the uniforms the kernel
+    draws, (2m+1) 2^-24: within the oracle's tie-model bound 2^-20 relative
+    (2^-22 absolute near the median); CUDA's normcdff of the result returns p."""
+    from scipy import special
+    glint, render, ctx, torch = gl
+    rng = np.random.default_rng(1)
+    m = np.concatenate([rng.integers(0, 2 ** 23, 1 << 20), np.arange(4096), 2 ** 23 - 1 - np.arange(4096)])
+    p = ((2 * m + 1) * 2.0 ** -24).astype(np.float64)
+    z = glint.normal_quantile(torch.tensor(p, dtype=torch.float32, device="cuda")).cpu().numpy().astype(np.float64)
+    ref = special.ndtri(p)
+    big = np.abs(ref) > 0.25
+    rel = np.abs(z - ref)[big] / np.abs(ref[big])
+    print(f"quantile: max rel {rel.max():.3e}, max abs near 0 {np.abs(z - ref)[~big].max():.3e}")
+    assert rel.max() < 2.0 ** -20
+    assert np.abs(z - ref)[~big].max() < 2.0 ** -22
+
+
 def test_tables(gl, orc):
     glint, render, ctx, torch = gl
     mp = MethodParams()

@@ -35,7 +35,7 @@ K, R, S, WO = 8, 8, 64, 256
 ENV_W, ENV_H = 1024, 512
 WORKLOAD = (f"{WIDTH}x{HEIGHT} G-buffer (ground plane + 16 spheres, alpha_x,alpha_y~U[0.03,0.3], "
             f"N0~logU[1e3,1e8]); {ENV_W}x{ENV_H} RGBA16F env (log-normal sigma=1.5 + 4 suns 1e3-1e5); "
-            f"K={K}, R={R} filtered levels, S={S} samples, {WO}x{WO // 2} filtered maps; env re-filtered every frame")
+            f"K={K}, R={R} filtered levels (widest {WO}x{WO // 2}), S={S} samples; env re-filtered every frame")
 MUFU_PER_DRAW = 8          # algorithmic transcendentals per dual-gated draw
 MUFU_PER_SM_CLK = 16       # MUFU results per clock per SM
 L2_FLUSH_BYTES = 256 << 20
@@ -156,8 +156,9 @@ def _oracle_frame_sample(oracle, mp, rgba, scale, rows16, pref_full, lut, pref_s
     t0 = time.perf_counter()
     e = oracle.env_full(rgba, scale, mp.K, mp.ell)
     t1 = time.perf_counter()
-    idx = np.arange(0, mp.R * mp.Ho * mp.Wo, pref_stride)
-    oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, mp.Ho, idx=idx)
+    widths = oracle.filtered_widths(mp.R, mp.s_min, mp.s_max, mp.Wo)
+    idx = np.arange(0, int(sum(int(w) * (int(w) // 2) for w in widths)), pref_stride)
+    oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, idx=idx)
     t2 = time.perf_counter()
     oracle.shade(rows16, pref_full, mp.s_min, mp.s_max, lut, e.levels, mp.seed, True, tie=(0.0, 0.0, 0.0, 0.0),
                  max_cand=1)
@@ -177,14 +178,14 @@ def cpu_baseline():
     rows = gb.rows16()[::4].copy()
     t0 = time.perf_counter()
     e = oracle.env_full(rgba, env.scale, mp.K, mp.ell)
-    pref = oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, mp.Ho)
+    pref = oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo)
     t1 = time.perf_counter()
     oracle.shade(rows, pref, mp.s_min, mp.s_max, lut, e.levels, mp.seed, True, tie=(0.0, 0.0, 0.0, 0.0), max_cand=1)
     t2 = time.perf_counter()
     full = (t1 - t0) + (t2 - t1) * 4
     value = WIDTH * HEIGHT / full / 1e6
     return {"value": round(value, 6), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-            "sample": f"env decomposition + pyramid + all {mp.R}x{mp.Ho}x{mp.Wo} filtered texels in full "
+            "sample": f"env decomposition + pyramid + all {len(pref.flat)} filtered texels in full "
                       f"({t1 - t0:.1f} s) and every 4th pixel ({len(rows)} px, {t2 - t1:.1f} s), shading "
                       f"extrapolated x4 to the frame; FP64 C oracle, one thread, tie model off"}
 
@@ -197,8 +198,8 @@ def run_reference(args):
     from tests._pipeline import oracle_lut
     lut = oracle_lut(oracle, mp)
     e = oracle.env_full(env.rgba32(), env.scale, mp.K, mp.ell)
-    pref = oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, mp.Ho)
-    pref_stride, px_stride = 64, 512
+    pref = oracle.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo)
+    pref_stride, px_stride = 8, 512
     rgba = env.rgba32()
     rows = gb.rows16()[::px_stride].copy()
     for _ in range(args.warmup):

@@ -106,15 +106,19 @@ typedef struct glint_env_desc {
     int K;            /* radiance levels: 2, 4, 8 or 16 (Sec. 4, K in {4, 8} in the paper) */
     float ell;        /* lower clip of the minimum brightness (Sec. 4), > 0 */
     int levels;       /* R filtered roughness levels, 1 .. 32 */
-    int samples;      /* S filter samples per output texel, 1 .. 4096 */
-    int out_width;    /* filtered map width (height = out_width / 2), power of two, 4 .. 4096 */
+    int samples;      /* S filter samples per output texel, 1 .. 2048 */
+    int out_width;    /* width of the widest filtered level (power of two, 4 .. 4096); level r is
+                         the power of two nearest 2 pi / alpha_r, clamped to
+                         [min(8, out_width), out_width], height = width / 2 */
     float s_min;      /* sqrt(alpha) of filtered level 0, > 0 */
     float s_max;      /* sqrt(alpha) of filtered level R-1, >= s_min */
 } glint_env_desc;
 
 /* Allocates an environment's device buffers (levels, weights pyramid,
- * filtered maps, scratch) for the given description.  Computes nothing; call
- * glint_env_update to fill it.  *out is released with glint_env_destroy. */
+ * filtered maps, scratch) for the given description and builds the filter's
+ * sample table (it depends only on the description); blocks until done.  The
+ * map itself is processed by glint_env_update.  *out is released with
+ * glint_env_destroy. */
 glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *desc, glint_env **out);
 
 /* Recomputes all per-environment data from `texels` (device; width * height
@@ -139,8 +143,9 @@ typedef enum glint_env_item {
     GLINT_ENV_LOHI = 0,      /* 2 floats: lo, hi */
     GLINT_ENV_LEVELS = 1,    /* K floats */
     GLINT_ENV_PYRAMID = 2,   /* pyramid level `index`: (H>>index) x (W>>index) x C floats */
-    GLINT_ENV_FILTERED = 3,  /* all filtered maps: R x (out_width/2) x out_width x C floats */
-    GLINT_ENV_TABLE = 4      /* filter sample table: R x S x 4 floats, then R int32 valid counts */
+    GLINT_ENV_FILTERED = 3,  /* all filtered levels concatenated: level r is W_r/2 x W_r x C floats */
+    GLINT_ENV_TABLE = 4,     /* filter sample table: R x S x 4 floats, then R int32 valid counts */
+    GLINT_ENV_FILTERED_WIDTHS = 5 /* R int32: W_r of each filtered level */
 } glint_env_item;
 
 /* Copies one item to host memory; C = 3 + K channels per texel, padded to a

@@ -80,9 +80,10 @@ def _load():
         lib.or_mip_count.restype = I
         lib.or_env_mips.argtypes = [P, I, I, I, P]
         lib.or_prefilter_table.argtypes = [I, I, D, D, I, I, P, P]
-        lib.or_prefilter.argtypes = [P, I, I, I, P, P, I, I, I, I, P, L, P]
+        lib.or_filtered_widths.argtypes = [I, D, D, I, P]
+        lib.or_prefilter.argtypes = [P, I, I, I, P, P, I, I, P, P, L, P]
         lib.or_prefilter_exact.argtypes = [P, I, I, I, D, P, L, P]
-        lib.or_shade.argtypes = [P, L, P, I, I, I, I, D, D, P, I, P, I, U, I, P, I,
+        lib.or_shade.argtypes = [P, L, P, I, P, I, D, D, P, I, P, I, U, I, P, I,
                                  P, P, P, P, P, P, P, P, P, P, P]
         lib.or_shade.restype = L
         lib.or_radiance.argtypes = [P, P, D, P, I, P, P, P]
@@ -232,19 +233,43 @@ def prefilter_table(R: int, S: int, s_min: float, s_max: float, W: int, H: int):
     return table, nvalid
 
 
-def prefilter(env: EnvOracle, R: int, S: int, s_min: float, s_max: float, Wo: int, Ho: int, idx=None):
-    """Filtered environment (R, Ho, Wo, C), or only the listed flat texel indices (n, C)."""
+@dataclass
+class Filtered:
+    widths: np.ndarray      # (R,) level widths (height = width / 2)
+    flat: np.ndarray        # (total texels, C), levels concatenated
+    levels: list            # per level (W_r / 2, W_r, C) views of flat
+    s_min: float
+    s_max: float
+
+
+def filtered_widths(R: int, s_min: float, s_max: float, Wmax: int) -> np.ndarray:
+    w = np.zeros(R, np.int32)
+    _load().or_filtered_widths(R, float(s_min), float(s_max), int(Wmax), _ptr(w))
+    return w
+
+
+def prefilter(env: EnvOracle, R: int, S: int, s_min: float, s_max: float, Wmax: int, idx=None):
+    """Filtered environment as a Filtered (all levels), or only the listed flat
+    texel indices of the concatenation as an (n, C) array."""
     lib = _load()
     H, W, C = env.ch0.shape
     table, nvalid = prefilter_table(R, S, s_min, s_max, W, H)
+    widths = filtered_widths(R, s_min, s_max, Wmax)
+    total = int(sum(int(w) * (int(w) // 2) for w in widths))
     if idx is None:
-        out = np.zeros((R, Ho, Wo, C))
-        lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, Wo, Ho, None, 0, _ptr(out))
-        return out
+        flat = np.zeros((total, C))
+        lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, _ptr(widths), None, 0,
+                         _ptr(flat))
+        levels, off = [], 0
+        for w in widths:
+            n = int(w) * (int(w) // 2)
+            levels.append(flat[off:off + n].reshape(int(w) // 2, int(w), C))
+            off += n
+        return Filtered(widths, flat, levels, s_min, s_max)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     out = np.zeros((len(idx), C))
-    lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, Wo, Ho, _ptr(idx), len(idx),
-                     _ptr(out))
+    lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, _ptr(widths), _ptr(idx),
+                     len(idx), _ptr(out))
     return out
 
 
@@ -279,14 +304,16 @@ def gbuffer_rows(planes) -> np.ndarray:
     return np.ascontiguousarray(np.concatenate([np.asarray(p, np.float32).reshape(-1, 4) for p in planes], axis=1))
 
 
-def shade(gb16: np.ndarray, pref: np.ndarray, s_min: float, s_max: float, lut_tab: np.ndarray, levels: np.ndarray,
+def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab: np.ndarray, levels: np.ndarray,
           seed: int, integer_mode: bool = True, tie=TIE_DEFAULT, max_cand: int = 8) -> ShadeOracle:
     lib = _load()
     gb16 = np.ascontiguousarray(gb16, dtype=np.float32).reshape(-1, 16)
     n = gb16.shape[0]
-    R, Ho, Wo, C = pref.shape
+    R = len(pref.widths)
+    C = pref.flat.shape[1]
+    widths = np.ascontiguousarray(pref.widths, dtype=np.int32)
     K = len(levels)
-    pref = np.ascontiguousarray(pref, dtype=np.float64)
+    flat = np.ascontiguousarray(pref.flat, dtype=np.float64)
     lut_tab = np.ascontiguousarray(lut_tab, dtype=np.float64)
     nlut = lut_tab.shape[0]
     levels = np.ascontiguousarray(levels, dtype=np.float64)
@@ -295,7 +322,7 @@ def shade(gb16: np.ndarray, pref: np.ndarray, s_min: float, s_max: float, lut_ta
                     vert=np.zeros((n, NV, 3), np.int64), wv=np.zeros((n, NV)), nroot=np.zeros((n, NV)),
                     ncand=np.zeros((n, NV), np.int32), cand=np.zeros((n, NV, max_cand, K)),
                     cand_err=np.zeros((n, NV, max_cand, K)), flags=np.zeros(n, np.int32), levels=levels)
-    lib.or_shade(_ptr(gb16), n, _ptr(pref), R, Ho, Wo, C, float(s_min), float(s_max), _ptr(lut_tab), nlut,
+    lib.or_shade(_ptr(gb16), n, _ptr(flat), R, _ptr(widths), C, float(s_min), float(s_max), _ptr(lut_tab), nlut,
                  _ptr(levels), K, ctypes.c_uint32(seed & 0xFFFFFFFF), int(integer_mode), _ptr(tie_a), max_cand,
                  _ptr(o.rgb), _ptr(o.lo), _ptr(o.pk), _ptr(o.np_), _ptr(o.vert), _ptr(o.wv), _ptr(o.nroot),
                  _ptr(o.ncand), _ptr(o.cand), _ptr(o.cand_err), _ptr(o.flags))

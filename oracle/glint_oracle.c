@@ -521,23 +521,50 @@ void or_prefilter_table(int R, int S, double s_min, double s_max, int W, int H, 
     }
 }
 
-/* Filtered environment, output texel (r, y, x) of an Wo x Ho equirect grid
- * per level: mean over the valid samples of the trilinear pyramid look-up
- * (bilinear on levels floor(lod) and floor(lod)+1, linear between).
+/* Width of filtered level r (height = width / 2).  Reading: the real-time
+ * IBL technique the paper cites (Sec. 3.4, Sec. 4) stores each roughness
+ * level as a mip of decreasing resolution; we give level r the power of two
+ * nearest (in log2) to 2 pi / alpha_r texels around the equator, i.e. texels
+ * of about alpha_r radians, clamped to [min(8, Wmax), Wmax]. */
+void or_filtered_widths(int R, double s_min, double s_max, int Wmax, int *widths)
+{
+    int lo = Wmax < 8 ? Wmax : 8;
+    for (int r = 0; r < R; ++r) {
+        double sr = (R > 1) ? s_min + (s_max - s_min) * r / (R - 1) : s_min;
+        double alpha = sr * sr;
+        double e = floor(log2(2.0 * OR_PI / alpha) + 0.5);
+        double w = e > 30.0 ? 1073741824.0 : pow(2.0, e);
+        if (w > Wmax) w = Wmax;
+        if (w < lo) w = lo;
+        widths[r] = (int)w;
+    }
+}
+
+/* Filtered environment: for level r, output texel (y, x) of a W_r x W_r/2
+ * equirect grid, the mean over the level's valid samples of the trilinear
+ * pyramid look-up (bilinear on levels floor(lod) and floor(lod)+1, linear
+ * between) at the sample's reflected direction.
+ * Levels are concatenated (level r starts after levels 0..r-1).
  * mips: from or_env_mips.  idx: optional list of `count` flat texel indices
- * r*Ho*Wo + y*Wo + x (NULL = all R*Ho*Wo texels); out: one C-vector per
- * listed texel. */
+ * into the concatenation (NULL = all texels); out: one C-vector per listed
+ * texel. */
 void or_prefilter(const double *mips, int W, int H, int C, const double *table, const int *nvalid,
-                  int R, int S, int Wo, int Ho, const long *idx, long count, double *out)
+                  int R, int S, const int *widths, const long *idx, long count, double *out)
 {
     int M = or_mip_count(H);
     double tmp0[3 + OR_MAXK], tmp1[3 + OR_MAXK];
-    long total = idx ? count : (long)R * Ho * Wo;
+    long start[65];
+    start[0] = 0;
+    for (int r = 0; r < R; ++r) start[r + 1] = start[r] + (long)widths[r] * (widths[r] / 2);
+    long total = idx ? count : start[R];
     for (long q = 0; q < total; ++q) {
         long id = idx ? idx[q] : q;
-        int r = (int)(id / ((long)Ho * Wo));
-        int y = (int)((id / Wo) % Ho);
-        int x = (int)(id % Wo);
+        int r = 0;
+        while (r + 1 < R && id >= start[r + 1]) ++r;
+        int Wo = widths[r], Ho = widths[r] / 2;
+        long t = id - start[r];
+        int y = (int)(t / Wo);
+        int x = (int)(t % Wo);
         double th = OR_PI * (y + 0.5) / Ho, ph = 2.0 * OR_PI * (x + 0.5) / Wo;
         double st = sin(th), ct = cos(th), sp = sin(ph), cp = cos(ph);
         double rr[3] = {st * cp, ct, st * sp};
@@ -547,10 +574,10 @@ void or_prefilter(const double *mips, int W, int H, int C, const double *table, 
         for (int c = 0; c < C; ++c) acc[c] = 0.0;
         int nv = nvalid[r];
         for (int j = 0; j < nv; ++j) {
-            const double *t = table + 4 * ((size_t)r * S + j);
+            const double *tb = table + 4 * ((size_t)r * S + j);
             double d[3];
-            for (int k = 0; k < 3; ++k) d[k] = t[0] * e1[k] + t[1] * e2[k] + t[2] * rr[k];
-            double lod = t[3];
+            for (int k = 0; k < 3; ++k) d[k] = tb[0] * e1[k] + tb[1] * e2[k] + tb[2] * rr[k];
+            double lod = tb[3];
             int m0 = (int)floor(lod);
             double f = lod - m0;
             int m1 = m0 + 1 < M ? m0 + 1 : M - 1;
@@ -830,8 +857,9 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
  *   [4..6] n, unit shading normal; [7] F0 (Schlick);
  *   [8..9] (u, v); [10] alpha_x; [11] alpha_y;
  *   [12] du/dx, [13] dv/dx, [14] du/dy, [15] dv/dy (screen-space derivatives).
- * pref: R x Ho x Wo x C filtered environment (C = 3+K: RGB, W_1..W_K) with
- * levels at sqrt(alpha) in [s_min, s_max]; lut: nlut x nlut x 4 (V, U, A, B).
+ * pref: the R filtered levels concatenated, level r of widths[r] x
+ * widths[r]/2 texels x C (C = 3+K: RGB, W_1..W_K), sqrt(alpha) of the levels
+ * evenly spaced in [s_min, s_max]; lut: nlut x nlut x 4 (V, U, A, B).
  * L: the K radiance levels.
  *
  * Per pixel:
@@ -857,7 +885,7 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
  * the enumeration overflowed), cand (6 x max_cand x K), cand_err (same
  * shape, tolerance of each count in real mode), flags (decisions that were
  * too close to call).  Returns the number of background pixels. */
-long or_shade(const float *gb, long npix, const double *pref, int R, int Ho, int Wo, int C, double s_min,
+long or_shade(const float *gb, long npix, const double *pref, int R, const int *widths, int C, double s_min,
               double s_max, const double *lut, int nlut, const double *L, int K, uint32_t seed, int integer_mode,
               const double *tie, int max_cand, double *rgb, double *lo, double *pk, float *np, int64_t *vert,
               double *wv, double *nroot, int32_t *ncand, double *cand, double *cand_err, int32_t *flags)
@@ -895,8 +923,11 @@ long or_shade(const float *gb, long npix, const double *pref, int R, int Ho, int
         int r1 = r0 + 1 < R ? r0 + 1 : R - 1;
         double ft = tl - r0;
         double c0[3 + OR_MAXK], c1[3 + OR_MAXK], cc[3 + OR_MAXK];
-        env_bilinear(pref + (size_t)r0 * Ho * Wo * C, Wo, Ho, C, wr, c0);
-        env_bilinear(pref + (size_t)r1 * Ho * Wo * C, Wo, Ho, C, wr, c1);
+        size_t off0 = 0, off1 = 0;
+        for (int r = 0; r < r0; ++r) off0 += (size_t)widths[r] * (widths[r] / 2) * C;
+        for (int r = 0; r < r1; ++r) off1 += (size_t)widths[r] * (widths[r] / 2) * C;
+        env_bilinear(pref + off0, widths[r0], widths[r0] / 2, C, wr, c0);
+        env_bilinear(pref + off1, widths[r1], widths[r1] / 2, C, wr, c1);
         for (int c = 0; c < C; ++c) cc[c] = (1.0 - ft) * c0[c] + ft * c1[c];
         double Eb = F0 * A + B;
         double Lo[3] = {cc[0] * Eb, cc[1] * Eb, cc[2] * Eb};

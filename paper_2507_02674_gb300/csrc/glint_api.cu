@@ -108,10 +108,12 @@ glint_status glint_lut_export(const glint_ctx *ctx, float *host_dst, size_t byte
 }
 
 static void env_free(glint_env *e) {
+    cudaFree(e->flev);
     cudaFree(e->levels);
     cudaFree(e->partial);
     cudaFree(e->pyr);
     cudaFree(e->pyr_off4_dev);
+    cudaFree(e->pyr_off_dev);
     cudaFree(e->table);
     cudaFree(e->nvalid);
     cudaFree(e->filt);
@@ -153,7 +155,27 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
     e->d = *d;
     e->C = 3 + d->K;
     e->Cpad = (e->C + 3) / 4 * 4;
-    e->Ho = d->out_width / 2;
+    // Filtered level r: the power of two nearest (in log2) to 2 pi / alpha_r
+    // texels around the equator (texels of about alpha_r radians, the mip
+    // chain of real-time IBL), clamped to [min(8, out_width), out_width].
+    {
+        const int lo = d->out_width < 8 ? d->out_width : 8;
+        long long off = 0;
+        for (int r = 0; r < d->levels; ++r) {
+            const double sr = (d->levels > 1) ? (double)d->s_min + ((double)d->s_max - (double)d->s_min) * r /
+                                                                       (d->levels - 1)
+                                              : (double)d->s_min;
+            const double alpha = sr * sr;
+            const double ex = floor(log2(2.0 * 3.14159265358979323846 / alpha) + 0.5);
+            double w = ex > 30.0 ? 1073741824.0 : pow(2.0, ex);
+            if (w > d->out_width) w = d->out_width;
+            if (w < lo) w = lo;
+            e->fw[r] = (int)w;
+            e->foff[r] = off;
+            off += (long long)e->fw[r] * (e->fw[r] / 2);
+        }
+        e->foff[d->levels] = off;
+    }
     int M = 1;
     while ((d->height >> (M - 1)) > 1) ++M;
     e->M = M;
@@ -174,13 +196,25 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
     alloc((void **)&e->partial, sizeof(float2) * e->nblk_minmax, "glint_env_create: scratch");
     alloc((void **)&e->pyr, sizeof(float) * off, "glint_env_create: pyramid");
     alloc((void **)&e->pyr_off4_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
+    alloc((void **)&e->pyr_off_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
     alloc((void **)&e->table, sizeof(float4) * (size_t)d->levels * d->samples, "glint_env_create: filter table");
     alloc((void **)&e->nvalid, sizeof(int) * d->levels, "glint_env_create: filter table");
-    alloc((void **)&e->filt, sizeof(float) * (size_t)d->levels * e->Ho * d->out_width * e->Cpad,
-          "glint_env_create: filtered maps");
+    alloc((void **)&e->filt, sizeof(float) * (size_t)e->foff[d->levels] * e->Cpad, "glint_env_create: filtered maps");
+    alloc((void **)&e->flev, sizeof(int2) * d->levels, "glint_env_create: filtered level table");
     if (st == GLINT_OK)
         st = cuda_status(cudaMemcpy(e->pyr_off4_dev, off4.data(), sizeof(size_t) * M, cudaMemcpyHostToDevice),
                          "glint_env_create: pyramid offsets");
+    if (st == GLINT_OK)
+        st = cuda_status(cudaMemcpy(e->pyr_off_dev, e->pyr_off, sizeof(size_t) * M, cudaMemcpyHostToDevice),
+                         "glint_env_create: pyramid offsets");
+    if (st == GLINT_OK) {
+        std::vector<int2> lev(d->levels);
+        for (int r = 0; r < d->levels; ++r) lev[r] = make_int2(e->fw[r], (int)e->foff[r]);
+        st = cuda_status(cudaMemcpy(e->flev, lev.data(), sizeof(int2) * d->levels, cudaMemcpyHostToDevice),
+                         "glint_env_create: filtered level table");
+    }
+    if (st == GLINT_OK) st = cuda_status(glint_launch_filter_table(e, 0), "glint_env_create: filter table");
+    if (st == GLINT_OK) st = cuda_status(cudaStreamSynchronize(0), "glint_env_create: filter table");
     if (st != GLINT_OK) {
         env_free(e);
         delete e;
@@ -246,7 +280,13 @@ glint_status glint_env_export(const glint_env *env, int item, int index, void *h
         if (index < 0 || index >= env->M) { set_error("glint_env_export: pyramid level %d out of range", index); return GLINT_ERR_INVALID_ARG; }
         return copy_unpadded(env->pyr + env->pyr_off[index], (size_t)(d.width >> index) * (d.height >> index));
     case GLINT_ENV_FILTERED:
-        return copy_unpadded(env->filt, (size_t)d.levels * env->Ho * d.out_width);
+        return copy_unpadded(env->filt, (size_t)env->foff[d.levels]);
+    case GLINT_ENV_FILTERED_WIDTHS: {
+        const size_t n = sizeof(int) * d.levels;
+        if (bytes < n) { set_error("glint_env_export: need %zu bytes, got %zu", n, bytes); return GLINT_ERR_INVALID_ARG; }
+        memcpy(host_dst, env->fw, n);
+        return GLINT_OK;
+    }
     case GLINT_ENV_TABLE: {
         const size_t nt = sizeof(float4) * (size_t)d.levels * d.samples;
         const size_t n = nt + sizeof(int) * d.levels;

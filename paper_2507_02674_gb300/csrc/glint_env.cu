@@ -6,8 +6,8 @@
 // Data layout in HBM: every per-texel channel vector (R, G, B, w_1..w_K) is
 // stored contiguously and padded to Cpad = 4 ceil((3+K)/4) floats, so one texel
 // is Cpad/4 aligned float4 loads (3 for K = 8).  The pyramid levels are
-// concatenated; the filtered maps are R levels of Ho x Wo texels of the same
-// layout.  Brightness min/max go through a small per-block scratch array.
+// concatenated; the filtered maps are R levels of W_r/2 x W_r texels of the
+// same layout, also concatenated.  Brightness min/max go through a small per-block scratch array.
 #include <stdio.h>
 
 #include "glint_internal.cuh"
@@ -96,74 +96,104 @@ __global__ void __launch_bounds__(kNT) k_levels(const float2 *__restrict__ parti
     }
 }
 
-// Step 3: channels (R, G, B, w_1 .. w_K) of every texel (pyramid level 0).
-__global__ void __launch_bounds__(kNT) k_weights(const void *__restrict__ texels, int fmt, long n, float scale,
-                                                   int K, int Cpad, const float *__restrict__ levels,
-                                                   float *__restrict__ ch0) {
-    __shared__ float L[GLINT_MAX_K];
-    if (threadIdx.x < K) L[threadIdx.x] = levels[threadIdx.x];
-    __syncthreads();
-    const long i = (long)blockIdx.x * kNT + threadIdx.x;
-    if (i >= n) return;
-    const float4 t = load_texel(texels, fmt, i);
+// Channel vector (R, G, B, w_1 .. w_K, 0 padding) of one texel: the fuzzy
+// weights of the two levels bracketing its brightness (Eq. wkdefpractice).
+__device__ __forceinline__ void texel_channels(float4 t, float scale, int K, const float *L, int Cpad, float *v) {
     const float R = t.x * scale, G = t.y * scale, B = t.z * scale;
     const float Y = fmaxf(0.2126f * R + 0.7152f * G + 0.0722f * B, 0.f);
-    float4 *dst = reinterpret_cast<float4 *>(ch0 + (size_t)i * Cpad);
     // bracket: largest j in [0, K-2] with L[j] <= Y; Y >= L[K-1] -> w_K = 1
     int j = 0;
     for (int k = 1; k < K - 1; ++k)
         if (L[k] <= Y) j = k;
     const bool top = Y >= L[K - 1];
     const float tt = (Y - L[j]) / (L[j + 1] - L[j]);
-    // write channel vector in float4 chunks
-    for (int c4 = 0; c4 < Cpad / 4; ++c4) {
-        float v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int c = c4 * 4 + e;
-            float val = 0.f;
-            if (c == 0) val = R;
-            else if (c == 1) val = G;
-            else if (c == 2) val = B;
-            else if (c < 3 + K) {
-                const int k = c - 3;
-                if (top) val = (k == K - 1) ? 1.f : 0.f;
-                else if (k == j) val = 1.f - tt;
-                else if (k == j + 1) val = tt;
-            }
-            v[e] = val;
+    v[0] = R; v[1] = G; v[2] = B;
+    for (int c = 3; c < Cpad; ++c) {
+        const int k = c - 3;
+        float val = 0.f;
+        if (k < K) {
+            if (top) val = (k == K - 1) ? 1.f : 0.f;
+            else if (k == j) val = 1.f - tt;
+            else if (k == j + 1) val = tt;
         }
-        dst[c4] = make_float4(v[0], v[1], v[2], v[3]);
+        v[c] = val;
     }
 }
 
-// Step 4: one pyramid level from the previous one; the weight of a texel row
-// spanning [theta0, theta1] is cos theta0 - cos theta1 = 2 sin(mid) sin(half),
-// written as a product to stay accurate near the poles.  One thread per
-// (destination texel, float4 chunk).
-__global__ void __launch_bounds__(kNT) k_mip(const float4 *__restrict__ src, int Ws, int Hs, int C4,
-                                               float4 *__restrict__ dst) {
-    const int Wd = Ws >> 1, Hd = Hs >> 1;
-    const long total = (long)Wd * Hd * C4;
-    const long id = (long)blockIdx.x * kNT + threadIdx.x;
-    if (id >= total) return;
-    const int c = (int)(id % C4);
-    const long t = id / C4;
-    const int x = (int)(t % Wd), y = (int)(t / Wd);
-    const float half = 0.5f * kPi / (float)Hs;
-    const float w0 = sinf((2.f * y + 0.5f) * (kPi / (float)Hs)) * sinf(half);
-    const float w1 = sinf((2.f * y + 1.5f) * (kPi / (float)Hs)) * sinf(half);
-    const float4 a0 = src[((long)(2 * y) * Ws + 2 * x) * C4 + c];
-    const float4 a1 = src[((long)(2 * y) * Ws + 2 * x + 1) * C4 + c];
-    const float4 b0 = src[((long)(2 * y + 1) * Ws + 2 * x) * C4 + c];
-    const float4 b1 = src[((long)(2 * y + 1) * Ws + 2 * x + 1) * C4 + c];
-    const float inv = 1.f / (2.f * (w0 + w1));
-    float4 r;
-    r.x = (w0 * (a0.x + a1.x) + w1 * (b0.x + b1.x)) * inv;
-    r.y = (w0 * (a0.y + a1.y) + w1 * (b0.y + b1.y)) * inv;
-    r.z = (w0 * (a0.z + a1.z) + w1 * (b0.z + b1.z)) * inv;
-    r.w = (w0 * (a0.w + a1.w) + w1 * (b0.w + b1.w)) * inv;
-    dst[id] = r;
+// Steps 3 and 4: pyramid.  Each block takes a T x T tile of pyramid level m
+// (T <= 32, a power of two), writes it (for m = 0 computing the channels of the
+// texels first) and reduces it through log2 T further levels in shared memory,
+// writing each.  A texel of level l+1 is the solid-angle weighted mean of its
+// 2 x 2 children; the weight of a row spanning [theta0, theta1] is
+// cos theta0 - cos theta1 = 2 sin(mid) sin(half), written as a product to stay
+// accurate near the poles.
+template <bool FROM_TEXELS>
+__global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels, int fmt, float scale, int K,
+                                                   const float *__restrict__ levels, float *__restrict__ pyr,
+                                                   const size_t *__restrict__ off, int m, int Ws, int Hs, int T,
+                                                   int nlev, int Cpad) {
+    extern __shared__ float smem[];
+    float *bufA = smem;                       // T*T texels
+    float *bufB = smem + (size_t)T * T * Cpad; // (T/2)^2 texels
+    __shared__ float L[GLINT_MAX_K];
+    if (FROM_TEXELS) {
+        if (threadIdx.x < K) L[threadIdx.x] = levels[threadIdx.x];
+        __syncthreads();
+    }
+    const int tiles_x = Ws / T;
+    const int tx0 = (blockIdx.x % tiles_x) * T, ty0 = (blockIdx.x / tiles_x) * T;
+    const int C4 = Cpad / 4;
+    for (int i = threadIdx.x; i < T * T; i += kNT) {
+        const int lx = i % T, ly = i / T;
+        const size_t gi = (size_t)(ty0 + ly) * Ws + (tx0 + lx);
+        float *v = bufA + (size_t)i * Cpad;
+        if (FROM_TEXELS) {
+            float tmp[3 + GLINT_MAX_K + 1];
+            texel_channels(load_texel(texels, fmt, (long)gi), scale, K, L, Cpad, tmp);
+            float4 *dst = reinterpret_cast<float4 *>(pyr + off[0] + gi * Cpad);
+            for (int c = 0; c < C4; ++c) {
+                const float4 q = make_float4(tmp[4 * c], tmp[4 * c + 1], tmp[4 * c + 2], tmp[4 * c + 3]);
+                dst[c] = q;
+                reinterpret_cast<float4 *>(v)[c] = q;
+            }
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(pyr + off[m] + gi * Cpad);
+            for (int c = 0; c < C4; ++c) reinterpret_cast<float4 *>(v)[c] = src[c];
+        }
+    }
+    __syncthreads();
+    int cur = T;
+    for (int l = 1; l <= nlev; ++l) {
+        const int nxt = cur / 2;
+        const int Hp = Hs >> (l - 1), Wd = Ws >> l;  // parent height, level width
+        const float half = 0.5f * kPi / (float)Hp;
+        const int X0 = tx0 >> l, Y0 = ty0 >> l;
+        for (int i = threadIdx.x; i < nxt * nxt * C4; i += kNT) {
+            const int c = i % C4, t = i / C4;
+            const int x = t % nxt, y = t / nxt;
+            const int Y = Y0 + y;
+            const float w0 = sinf((2.f * Y + 0.5f) * (kPi / (float)Hp)) * sinf(half);
+            const float w1 = sinf((2.f * Y + 1.5f) * (kPi / (float)Hp)) * sinf(half);
+            const float4 *src = reinterpret_cast<const float4 *>(bufA);
+            const float4 a0 = src[((2 * y) * cur + 2 * x) * C4 + c];
+            const float4 a1 = src[((2 * y) * cur + 2 * x + 1) * C4 + c];
+            const float4 b0 = src[((2 * y + 1) * cur + 2 * x) * C4 + c];
+            const float4 b1 = src[((2 * y + 1) * cur + 2 * x + 1) * C4 + c];
+            const float inv = 1.f / (2.f * (w0 + w1));
+            float4 r;
+            r.x = (w0 * (a0.x + a1.x) + w1 * (b0.x + b1.x)) * inv;
+            r.y = (w0 * (a0.y + a1.y) + w1 * (b0.y + b1.y)) * inv;
+            r.z = (w0 * (a0.z + a1.z) + w1 * (b0.z + b1.z)) * inv;
+            r.w = (w0 * (a0.w + a1.w) + w1 * (b0.w + b1.w)) * inv;
+            reinterpret_cast<float4 *>(bufB)[t * C4 + c] = r;
+            reinterpret_cast<float4 *>(pyr + off[m + l])[((size_t)Y * Wd + X0 + x) * C4 + c] = r;
+        }
+        __syncthreads();
+        float *tmp = bufA;
+        bufA = bufB;
+        bufB = tmp;
+        cur = nxt;
+    }
 }
 
 // Step 5a: filter sample table (Hammersley points mapped through the GGX
@@ -211,21 +241,32 @@ __global__ void k_filter_table(int R, int S, float s_min, float s_max, int W, in
     table[(size_t)r * S + j] = e;
 }
 
-// Step 5b: filtered maps.  One thread per output texel (r, y, x) of an
-// Wo x Ho equirect grid; mean over the level's valid samples of the trilinear
-// pyramid look-up at w_i = a e1 + b e2 + c r, where r is the texel direction,
-// e1 = d r / d theta, e2 = d r / d phi / sin theta.
+// Step 5b: filtered maps.  Level r is a W_r x W_r/2 equirect grid; the
+// levels are concatenated and the grid of blocks runs over all of them (block
+// ranges per level in FilterLevels).  One thread per output texel: the mean
+// over the level's valid samples of the trilinear pyramid look-up at
+// w_i = a e1 + b e2 + c r, where r is the texel direction, e1 = d r / d theta,
+// e2 = d r / d phi / sin theta.
+struct FilterLevels {
+    int nlev;
+    int width[33];
+    int blk[33];          // first block of level r; blk[nlev] = total blocks
+    long long off[33];    // first texel of level r
+};
+
 template <int C4>
 __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, const size_t *__restrict__ off4,
                                                   int W, int H, int M, const float4 *__restrict__ table,
-                                                  const int *__restrict__ nvalid, int S, int Wo, int Ho,
+                                                  const int *__restrict__ nvalid, int S, const FilterLevels fl,
                                                   float4 *__restrict__ out) {
     extern __shared__ float4 tab[];
-    const int r = blockIdx.y;
+    int r = 0;
+    while (r + 1 < fl.nlev && (int)blockIdx.x >= fl.blk[r + 1]) ++r;
+    const int Wo = fl.width[r], Ho = Wo / 2;
     const int nv = nvalid[r];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) tab[k] = table[(size_t)r * S + k];
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = ((int)blockIdx.x - fl.blk[r]) * blockDim.x + threadIdx.x;
     if (t >= Wo * Ho) return;
     const int x = t % Wo, y = t / Wo;
     const float th = kPi * ((float)y + 0.5f) / (float)Ho;
@@ -240,11 +281,11 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
 #pragma unroll
     for (int c = 0; c < C4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = 0; k < nv; ++k) {
-        const float4 s = tab[k];
-        const float dx = s.x * e1x + s.y * e2x + s.z * rx;
-        const float dy = s.x * e1y + s.z * ry;
-        const float dz = s.x * e1z + s.y * e2z + s.z * rz;
-        const float lod = s.w;
+        const float4 smp = tab[k];
+        const float dx = smp.x * e1x + smp.y * e2x + smp.z * rx;
+        const float dy = smp.x * e1y + smp.z * ry;
+        const float dz = smp.x * e1z + smp.y * e2z + smp.z * rz;
+        const float lod = smp.w;
         const int m0 = (int)floorf(lod);
         const float f = lod - (float)m0;
         const int m1 = min(m0 + 1, M - 1);
@@ -272,7 +313,7 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
         }
     }
     const float inv = nv > 0 ? 1.f / (float)nv : 0.f;
-    float4 *o = out + ((size_t)r * Wo * Ho + t) * C4;
+    float4 *o = out + ((size_t)fl.off[r] + t) * C4;
 #pragma unroll
     for (int c = 0; c < C4; ++c)
         o[c] = make_float4(acc[c].x * inv, acc[c].y * inv, acc[c].z * inv, acc[c].w * inv);
@@ -287,47 +328,66 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
     const long n = (long)d.width * d.height;
     const float scale = ldexpf(1.f, d.scale_log2);
     const int C4 = env->Cpad / 4;
+    (void)n;
     int nl = 0;
     k_minmax<<<env->nblk_minmax, kNT, 0, s>>>(texels, d.format, n, scale, env->partial);
     ++nl;
     k_levels<<<1, kNT, 0, s>>>(env->partial, env->nblk_minmax, d.K, d.ell, env->levels);
     ++nl;
-    k_weights<<<(unsigned)((n + kNT - 1) / kNT), kNT, 0, s>>>(texels, d.format, n, scale, d.K, env->Cpad,
-                                                               env->levels, env->pyr);
-    ++nl;
-    for (int m = 1; m < env->M; ++m) {
-        const int Ws = d.width >> (m - 1), Hs = d.height >> (m - 1);
-        const long total = (long)(Ws / 2) * (Hs / 2) * C4;
-        k_mip<<<(unsigned)((total + kNT - 1) / kNT), kNT, 0, s>>>(
-            reinterpret_cast<const float4 *>(env->pyr + env->pyr_off[m - 1]), Ws, Hs, C4,
-            reinterpret_cast<float4 *>(env->pyr + env->pyr_off[m]));
-        ++nl;
+    {
+        // level 0 and the next log2 T levels from the texels, then the rest
+        int m = 0, Ws = d.width, Hs = d.height;
+        bool first = true;
+        while (first || m < env->M - 1) {
+            const int T = Hs < 32 ? Hs : 32;
+            int nlev = 0;
+            while ((1 << nlev) < T) ++nlev;
+            const size_t smem = sizeof(float) * env->Cpad * ((size_t)T * T + (size_t)(T / 2) * (T / 2));
+            const unsigned blocks = (unsigned)((Ws / T) * (Hs / T));
+            if (first) {
+                cudaFuncSetAttribute(k_pyramid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_pyramid<true><<<blocks, kNT, smem, s>>>(texels, d.format, scale, d.K, env->levels, env->pyr,
+                                                           env->pyr_off_dev, 0, Ws, Hs, T, nlev, env->Cpad);
+            } else {
+                cudaFuncSetAttribute(k_pyramid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_pyramid<false><<<blocks, kNT, smem, s>>>(nullptr, d.format, scale, d.K, env->levels, env->pyr,
+                                                            env->pyr_off_dev, m, Ws, Hs, T, nlev, env->Cpad);
+            }
+            ++nl;
+            first = false;
+            m += nlev;
+            Ws >>= nlev;
+            Hs >>= nlev;
+            if (nlev == 0) break;
+        }
     }
     {
-        dim3 grid((d.samples + 127) / 128, d.levels);
-        k_filter_table<<<grid, 128, 0, s>>>(d.levels, d.samples, d.s_min, d.s_max, d.width, d.height, env->M,
-                                            env->table, env->nvalid);
-        ++nl;
-    }
-    {
-        const int texels_out = d.out_width * env->Ho;
-        dim3 grid((texels_out + 127) / 128, d.levels);
+        FilterLevels fl{};
+        fl.nlev = d.levels;
+        int blk = 0;
+        for (int r = 0; r < d.levels; ++r) {
+            fl.width[r] = env->fw[r];
+            fl.off[r] = env->foff[r];
+            fl.blk[r] = blk;
+            blk += (int)((env->fw[r] * (env->fw[r] / 2) + 127) / 128);
+        }
+        fl.blk[d.levels] = blk;
         const size_t smem = sizeof(float4) * (size_t)d.samples;
         const float4 *pyr4 = reinterpret_cast<const float4 *>(env->pyr);
         const size_t *off4 = env->pyr_off4_dev;
         float4 *out4 = reinterpret_cast<float4 *>(env->filt);
         switch (C4) {
         case 2:
-            k_filter<2><<<grid, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                                d.samples, d.out_width, env->Ho, out4);
+            k_filter<2><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
+                                               d.samples, fl, out4);
             break;
         case 3:
-            k_filter<3><<<grid, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                                d.samples, d.out_width, env->Ho, out4);
+            k_filter<3><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
+                                               d.samples, fl, out4);
             break;
         case 5:
-            k_filter<5><<<grid, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                                d.samples, d.out_width, env->Ho, out4);
+            k_filter<5><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
+                                               d.samples, fl, out4);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -335,5 +395,15 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
         ++nl;
     }
     if (launches) *launches = nl;
+    return cudaGetLastError();
+}
+
+// The filter sample table depends only on the description (levels, samples,
+// roughness range, map size); glint_env_create builds it once.
+cudaError_t glint_launch_filter_table(glint_env *env, cudaStream_t s) {
+    const glint_env_desc &d = env->d;
+    dim3 grid((d.samples + 127) / 128, d.levels);
+    k_filter_table<<<grid, 128, 0, s>>>(d.levels, d.samples, d.s_min, d.s_max, d.width, d.height, env->M, env->table,
+                                        env->nvalid);
     return cudaGetLastError();
 }

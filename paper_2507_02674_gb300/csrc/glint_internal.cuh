@@ -41,16 +41,19 @@ struct glint_env {
     int C = 0;      // 3 + K channels
     int Cpad = 0;   // channels padded to a multiple of 4
     int M = 0;      // pyramid levels
-    int Ho = 0;     // filtered map height
     int nblk_minmax = 0;
     float *levels = nullptr;   // K levels, then lo, hi
     float2 *partial = nullptr; // scratch: per-block (min, max) of the brightness
     float *pyr = nullptr;      // pyramid, all levels, Cpad floats per texel
     size_t pyr_off[24] = {};   // float offset of each level
     size_t *pyr_off4_dev = nullptr; // same offsets in float4 units, on the device
-    float4 *table = nullptr;   // R x S filter samples
+    size_t *pyr_off_dev = nullptr;  // offsets in floats, on the device
+    float4 *table = nullptr;   // R x S filter samples (built once at creation)
     int *nvalid = nullptr;     // R valid sample counts
-    float *filt = nullptr;     // R x Ho x Wo x Cpad filtered maps
+    float *filt = nullptr;     // filtered levels, concatenated, Cpad floats per texel
+    int fw[33] = {};           // width of filtered level r (height fw/2)
+    long long foff[33] = {};   // first texel of level r in filt; foff[R] = total
+    int2 *flev = nullptr;      // device copy of (width, first texel) per level
     int last_launches = 0;
 };
 
@@ -121,6 +124,7 @@ __device__ __forceinline__ float4 fma4(float w, float4 a, float4 acc) {
 // Launchers implemented in the .cu files (return cudaGetLastError()).
 cudaError_t glint_launch_lut(float4 *lut, int n, int q, cudaStream_t s);
 cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s, int *launches);
+cudaError_t glint_launch_filter_table(glint_env *env, cudaStream_t s);
 cudaError_t glint_launch_quantile(const float *p, float *z, long n, cudaStream_t s);
 cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
                                const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s,

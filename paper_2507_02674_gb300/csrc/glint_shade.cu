@@ -2,10 +2,11 @@
 // Sec. 5 Alg. 1 and the hierarchical multinomial).
 //
 // One thread per pixel.  G-buffer reads are four coalesced float4 loads per
-// pixel (64 B), the output one float4 store (16 B).  The filtered maps (a few
-// MB) and the 64 x 64 table stay resident in L2/L1 across the frame.  Per pixel:
+// pixel (64 B), the output one float4 store (16 B).  The filtered maps (~2 MB)
+// and the 64 x 64 table stay resident in L2/L1 across the frame.  Per pixel:
 //   1. smooth radiance L_o = prefRGB (F0 A + B) and p_k = V W_k, p_1 = U + V W_1
-//      from 8 bilinear taps of the filtered maps and 4 table taps (E1);
+//      from 8 bilinear taps of the two filtered levels bracketing the pixel's
+//      roughness and 4 table taps (E1);
 //   2. footprint |P| and N_P in correctly rounded FP32 (same operation order
 //      as any IEEE implementation), grid level and triangle vertices likewise;
 //   3. per node of the balanced binary tree over the K bins: node probability,
@@ -33,7 +34,8 @@ struct ShadeArgs {
     const float4 *lut;
     int lut_n;
     const float4 *filt;
-    int R, Wo, Ho;
+    const int2 *flev;  // (width, first texel) of each filtered level
+    int R;
     float s_min, s_max;
     const float *levels;
     uint32_t seed;
@@ -189,15 +191,19 @@ __global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
     const int r0 = (int)floorf(tl);
     const int r1 = min(r0 + 1, a.R - 1);
     const float ft = tl - (float)r0;
-    float tx, ty;
-    dir_to_texel(rx, ry, rz, a.Wo, a.Ho, tx, ty);
-    const Taps tp = equirect_taps(tx, ty, a.Wo, a.Ho);
+    // direction of w_r on the unit sphere, then texel coordinates per level
+    const float th_r = acosf(fminf(fmaxf(ry, -1.f), 1.f));
+    float ph_r = atan2f(rz, rx);
+    if (ph_r < 0.f) ph_r += kTwoPi;
     float4 cc[C4];
 #pragma unroll
     for (int c = 0; c < C4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int lv = 0; lv < 2; ++lv) {
-        const float4 *base = a.filt + (size_t)(lv ? r1 : r0) * a.Wo * a.Ho * C4;
+        const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
+        const int Wr = lev.x, Hr = lev.x / 2;
+        const Taps tp = equirect_taps(ph_r * (kInvTwoPi * (float)Wr) - 0.5f, th_r * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
+        const float4 *base = a.filt + (size_t)lev.y * C4;
         const float wl = lv ? ft : 1.f - ft;
 #pragma unroll
         for (int c = 0; c < C4; ++c) {
@@ -408,8 +414,7 @@ cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const
     a.lut_n = ctx->lut_n;
     a.filt = reinterpret_cast<const float4 *>(env->filt);
     a.R = env->d.levels;
-    a.Wo = env->d.out_width;
-    a.Ho = env->Ho;
+    a.flev = env->flev;
     a.s_min = env->d.s_min;
     a.s_max = env->d.s_max;
     a.levels = env->levels;

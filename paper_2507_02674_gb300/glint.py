@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libglint.so")
 GLINT_OK = 0
 FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
-ENV_LOHI, ENV_LEVELS, ENV_PYRAMID, ENV_FILTERED, ENV_TABLE = 0, 1, 2, 3, 4
+ENV_LOHI, ENV_LEVELS, ENV_PYRAMID, ENV_FILTERED, ENV_TABLE, ENV_FILTERED_WIDTHS = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_READY", 5: "TIMEOUT", 6: "UNSUPPORTED"}
 
 
@@ -173,8 +173,14 @@ class Env:
             out = np.zeros(d.K, np.float32)
         elif item == ENV_PYRAMID:
             out = np.zeros((d.height >> index, d.width >> index, self.C), np.float32)
+        elif item == ENV_FILTERED_WIDTHS:
+            out = np.zeros(d.levels, np.int32)
         elif item == ENV_FILTERED:
-            out = np.zeros((d.levels, d.out_width // 2, d.out_width, self.C), np.float32)
+            widths = self.export(ENV_FILTERED_WIDTHS)
+            total = int(sum(int(w) * (int(w) // 2) for w in widths))
+            flat = np.zeros((total, self.C), np.float32)
+            _check(lib.glint_env_export(self.handle, item, index, flat.ctypes.data, flat.nbytes))
+            return widths, flat
         elif item == ENV_TABLE:
             raw = np.zeros(d.levels * d.samples * 4 + d.levels, np.float32)
             _check(lib.glint_env_export(self.handle, item, index, raw.ctypes.data, raw.nbytes))

@@ -14,7 +14,7 @@ class MethodParams:
     K: int = 4                     # radiance levels (power of two)
     R: int = 8                     # filtered levels, sqrt(alpha) evenly in [s_min, s_max]
     S: int = 64                    # filter samples per output texel
-    Wo: int = 64                   # filtered map width (height Wo/2)
+    Wo: int = 64                   # widest filtered level (level r: ~2 pi / alpha_r texels, at most Wo)
     ell: float = 1e-4              # clip of the minimum radiance
     s_min: float = math.sqrt(0.02)
     s_max: float = math.sqrt(0.5)
@@ -22,10 +22,6 @@ class MethodParams:
     Q: int = 128                   # table quadrature points per axis
     seed: int = 0
     integer_mode: bool = True
-
-    @property
-    def Ho(self) -> int:
-        return self.Wo // 2
 
     def with_(self, **kw) -> "MethodParams":
         return replace(self, **kw)
@@ -43,7 +39,7 @@ def oracle_lut(orc, mp: MethodParams) -> np.ndarray:
 
 def oracle_env(orc, env, mp: MethodParams):
     e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell)
-    pref = orc.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, mp.Ho)
+    pref = orc.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo)
     return e, pref
 
 

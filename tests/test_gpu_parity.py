@@ -129,8 +129,11 @@ def test_filtered_maps(gl, orc, K, which, Wo):
     fr = render.Frame(ctx, env, _cfg(glint, mp))
     fr.update_env()
     torch.cuda.synchronize()
-    g = fr.env.export(glint.ENV_FILTERED).astype(np.float64)
-    e, o = oracle_env(orc, env, mp)
+    widths, g = fr.env.export(glint.ENV_FILTERED)
+    g = g.astype(np.float64)
+    e, of = oracle_env(orc, env, mp)
+    assert list(widths) == list(of.widths)
+    o = of.flat
     assert g.shape == o.shape
     rgb_rel = np.abs(g[..., :3] - o[..., :3]) / np.abs(o[..., :3])
     w_abs = np.abs(g[..., 3:] - o[..., 3:])

@@ -109,7 +109,7 @@ def test_filter_constant_env(orc):
     """A constant environment filters to itself: RGB = constant, W_K = 1."""
     env = synth.env_constant(2.0)
     e = orc.env_full(env.rgba32(), 1.0, 4, 1e-4)
-    pref = orc.prefilter(e, 4, 32, math.sqrt(0.02), math.sqrt(0.5), 16, 8)
+    pref = orc.prefilter(e, 4, 32, math.sqrt(0.02), math.sqrt(0.5), 16).flat
     assert np.allclose(pref[..., :3], 2.0, rtol=1e-13)
     assert np.allclose(pref[..., 3 + 3], 1.0, rtol=1e-13)
     assert np.allclose(pref[..., 3:6], 0.0, atol=1e-13)
@@ -118,7 +118,7 @@ def test_filter_constant_env(orc):
 def test_filter_partition_of_unity(orc):
     env = synth.env_tiny(0)
     e = orc.env_full(env.rgba32(), 1.0, 8, 1e-4)
-    pref = orc.prefilter(e, 5, 64, math.sqrt(0.02), math.sqrt(0.5), 32, 16)
+    pref = orc.prefilter(e, 5, 64, math.sqrt(0.02), math.sqrt(0.5), 32).flat
     assert np.allclose(pref[..., 3:].sum(-1), 1.0, atol=1e-13)
     assert np.all(pref[..., 3:] >= 0)
 
@@ -128,8 +128,20 @@ def test_filter_narrow_lobe_is_identity(orc):
     filtered map sampled at the texel centres of the source is the source."""
     env = synth.env_tiny(1)
     e = orc.env_full(env.rgba32(), 1.0, 4, 1e-4)
-    pref = orc.prefilter(e, 1, 16, 1e-7, 1e-7, 64, 32)
-    assert np.allclose(pref[0], e.ch0, rtol=1e-6, atol=1e-9)
+    pref = orc.prefilter(e, 1, 16, 1e-7, 1e-7, 64)
+    assert np.allclose(pref.levels[0], e.ch0, rtol=1e-6, atol=1e-9)
+
+
+def test_filtered_level_widths(orc):
+    """Level r has about 2 pi / alpha_r texels around the equator (a power of two),
+    clamped to the requested maximum: 256..16 for sqrt(alpha) in [sqrt .02, sqrt .5]."""
+    w = orc.filtered_widths(8, math.sqrt(0.02), math.sqrt(0.5), 256)
+    assert list(w) == [256, 128, 64, 32, 32, 16, 16, 16]
+    for r, wr in enumerate(w):
+        s = math.sqrt(0.02) + (math.sqrt(0.5) - math.sqrt(0.02)) * r / 7
+        texel = 2 * math.pi / wr
+        assert 2 ** -0.5 <= texel / s ** 2 <= 2 ** 0.5
+    assert list(orc.filtered_widths(3, 0.9, 1.0, 4)) == [4, 4, 4]
 
 
 def test_filter_sample_table(orc):
@@ -154,11 +166,13 @@ def test_filter_close_to_exact_convolution(orc):
     e = orc.env_full(env.rgba32(), 1.0, 4, 1e-4)
     s = math.sqrt(0.3)
     Wo, Ho = 16, 8
-    pref = orc.prefilter(e, 1, 256, s, s, Wo, Ho)
+    pref = orc.prefilter(e, 1, 256, s, s, Wo)
+    assert list(pref.widths) == [Wo]
     y, x = np.meshgrid(np.arange(Ho), np.arange(Wo), indexing="ij")
     th, ph = np.pi * (y + 0.5) / Ho, 2 * np.pi * (x + 0.5) / Wo
     dirs = np.stack([np.sin(th) * np.cos(ph), np.cos(th), np.sin(th) * np.sin(ph)], -1).reshape(-1, 3)
     ex = orc.prefilter_exact(e.ch0, 0.3, dirs).reshape(Ho, Wo, -1)
-    rel = np.abs(pref[0, ..., :3] - ex[..., :3]) / ex[..., :3]
+    lev = pref.levels[0]
+    rel = np.abs(lev[..., :3] - ex[..., :3]) / ex[..., :3]
     assert np.median(rel) < 0.03 and np.max(rel) < 0.12
-    assert np.max(np.abs(pref[0, ..., 3:] - ex[..., 3:])) < 0.05
+    assert np.max(np.abs(lev[..., 3:] - ex[..., 3:])) < 0.05

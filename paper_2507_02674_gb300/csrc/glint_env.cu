@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels
     float *bufA = smem;                       // T*T texels
     float *bufB = smem + (size_t)T * T * Cpad; // (T/2)^2 texels
     __shared__ float L[GLINT_MAX_K];
+    __shared__ float2 rw[16];  // row weights of the level being built
     if (FROM_TEXELS) {
         if (threadIdx.x < K) L[threadIdx.x] = levels[threadIdx.x];
         __syncthreads();
@@ -168,12 +169,17 @@ __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels
         const int Hp = Hs >> (l - 1), Wd = Ws >> l;  // parent height, level width
         const float half = 0.5f * kPi / (float)Hp;
         const int X0 = tx0 >> l, Y0 = ty0 >> l;
+        if (threadIdx.x < nxt) {
+            const int Y = Y0 + threadIdx.x;
+            rw[threadIdx.x] = make_float2(sinf((2.f * Y + 0.5f) * (kPi / (float)Hp)) * sinf(half),
+                                          sinf((2.f * Y + 1.5f) * (kPi / (float)Hp)) * sinf(half));
+        }
+        __syncthreads();
         for (int i = threadIdx.x; i < nxt * nxt * C4; i += kNT) {
             const int c = i % C4, t = i / C4;
             const int x = t % nxt, y = t / nxt;
             const int Y = Y0 + y;
-            const float w0 = sinf((2.f * Y + 0.5f) * (kPi / (float)Hp)) * sinf(half);
-            const float w1 = sinf((2.f * Y + 1.5f) * (kPi / (float)Hp)) * sinf(half);
+            const float w0 = rw[y].x, w1 = rw[y].y;
             const float4 *src = reinterpret_cast<const float4 *>(bufA);
             const float4 a0 = src[((2 * y) * cur + 2 * x) * C4 + c];
             const float4 a1 = src[((2 * y) * cur + 2 * x + 1) * C4 + c];
@@ -243,8 +249,9 @@ __global__ void k_filter_table(int R, int S, float s_min, float s_max, int W, in
 
 // Step 5b: filtered maps.  Level r is a W_r x W_r/2 equirect grid; the
 // levels are concatenated and the grid of blocks runs over all of them (block
-// ranges per level in FilterLevels).  One thread per output texel: the mean
-// over the level's valid samples of the trilinear pyramid look-up at
+// ranges per level in FilterLevels).  kFilterSplit adjacent threads per output
+// texel share its samples; their sums are combined with shuffles.  Result: the
+// mean over the level's valid samples of the trilinear pyramid look-up at
 // w_i = a e1 + b e2 + c r, where r is the texel direction, e1 = d r / d theta,
 // e2 = d r / d phi / sin theta.
 struct FilterLevels {
@@ -253,6 +260,8 @@ struct FilterLevels {
     int blk[33];          // first block of level r; blk[nlev] = total blocks
     long long off[33];    // first texel of level r
 };
+
+constexpr int kFilterSplit = 2;  // threads per output texel (samples strided over them)
 
 template <int C4>
 __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, const size_t *__restrict__ off4,
@@ -266,9 +275,11 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
     const int nv = nvalid[r];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) tab[k] = table[(size_t)r * S + k];
     __syncthreads();
-    const int t = ((int)blockIdx.x - fl.blk[r]) * blockDim.x + threadIdx.x;
-    if (t >= Wo * Ho) return;
-    const int x = t % Wo, y = t / Wo;
+    const int g = threadIdx.x % kFilterSplit;
+    const int t = ((int)blockIdx.x - fl.blk[r]) * (blockDim.x / kFilterSplit) + threadIdx.x / kFilterSplit;
+    const bool active = t < Wo * Ho;
+    const int tt = active ? t : 0;
+    const int x = tt % Wo, y = tt / Wo;
     const float th = kPi * ((float)y + 0.5f) / (float)Ho;
     const float ph = kTwoPi * ((float)x + 0.5f) / (float)Wo;
     float st, ct, sp, cp;
@@ -280,7 +291,7 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
     float4 acc[C4];
 #pragma unroll
     for (int c = 0; c < C4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = 0; k < nv; ++k) {
+    for (int k = g; k < nv; k += kFilterSplit) {
         const float4 smp = tab[k];
         const float dx = smp.x * e1x + smp.y * e2x + smp.z * rx;
         const float dy = smp.x * e1y + smp.z * ry;
@@ -312,6 +323,18 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
             }
         }
     }
+    // sum the partial means of the kFilterSplit adjacent lanes of a texel
+#pragma unroll
+    for (int c = 0; c < C4; ++c) {
+#pragma unroll
+        for (int o = 1; o < kFilterSplit; o <<= 1) {
+            acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
+            acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
+            acc[c].z += __shfl_xor_sync(0xffffffffu, acc[c].z, o);
+            acc[c].w += __shfl_xor_sync(0xffffffffu, acc[c].w, o);
+        }
+    }
+    if (!active || g != 0) return;
     const float inv = nv > 0 ? 1.f / (float)nv : 0.f;
     float4 *o = out + ((size_t)fl.off[r] + t) * C4;
 #pragma unroll
@@ -369,7 +392,8 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
             fl.width[r] = env->fw[r];
             fl.off[r] = env->foff[r];
             fl.blk[r] = blk;
-            blk += (int)((env->fw[r] * (env->fw[r] / 2) + 127) / 128);
+            const int per_block = 128 / kFilterSplit;
+            blk += (int)((env->fw[r] * (env->fw[r] / 2) + per_block - 1) / per_block);
         }
         fl.blk[d.levels] = blk;
         const size_t smem = sizeof(float4) * (size_t)d.samples;

@@ -9,9 +9,10 @@
 //      roughness and 4 table taps (E1);
 //   2. footprint |P| and N_P in correctly rounded FP32 (same operation order
 //      as any IEEE implementation), grid level and triangle vertices likewise;
-//   3. per node of the balanced binary tree over the K bins: node probability,
-//      log2 p and the log2 of the (small-p biased) complement -- computed once
-//      per pixel and reused by all six grid samples;
+//   3. per node of the balanced binary tree over the K bins: node probability
+//      p, its complement q (both from the subtree masses), log2 p and the log2
+//      of the small-p biased complement, each logarithm taken of whichever of
+//      p, q is below 1/2 -- computed once per pixel, reused by all six samples;
 //   4. six samples x (K-1) dual-gated draws: a pcg4d hash of (vertex, level,
 //      node, seed) gives the uniforms, two hardware exp2 give the gate
 //      probabilities, and the normal quantile is evaluated only when the
@@ -278,8 +279,19 @@ __global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
         }
         nd[n].p = pn;
         nd[n].q = qn;
-        nd[n].lp = log2f(pn);
-        nd[n].lq = (pn >= kEps) ? log2f(qn) : (pn * (1.f / kEps)) * kLog2OneMinusEps;
+        // log2 p and log2 q from whichever of p, q is the smaller (both are
+        // accurate relative to themselves; 1 - x near 1 is not)
+        constexpr float kLog2e = 1.44269504088896340736f;
+        float l2p, l2q;
+        if (pn <= 0.5f) {
+            l2p = log2f(pn);
+            l2q = log1pf(-pn) * kLog2e;
+        } else {
+            l2p = log1pf(-qn) * kLog2e;
+            l2q = log2f(qn);
+        }
+        nd[n].lp = l2p;
+        nd[n].lq = (pn >= kEps) ? l2q : (pn * (1.f / kEps)) * kLog2OneMinusEps;
     }
 
     // ---- 4. six grid samples x (K-1) draws

@@ -180,6 +180,23 @@ def test_shade_random_pixels(gl, orc, K):
     _check(orc, o, res)
 
 
+def test_shade_large_n_near_certain_nodes(gl, orc):
+    """Very large N (N_0 up to 1e10, footprints up to 1e-2) under a map whose
+    bright levels hold tiny masses, so tree nodes have p within 1e-6 of 1 and
+    p^N, (1-p)^N sit in their sensitive range: the kernel must take log p from
+    the accurate complement."""
+    mp = MethodParams(K=8, Wo=64, seed=11)
+    env = synth.env_tiny(4)
+    gb = synth.gbuffer_random(2500, seed=13, n_lo=1e5, n_hi=1e10)
+    rows = gb.rows16()
+    rng = np.random.default_rng(3)
+    rows[:, 12:16] = (10.0 ** rng.uniform(-3, -1, size=(len(rows), 4)) * rng.choice([-1, 1], size=(len(rows), 4)))
+    gb.planes = [rows[:, 4 * i:4 * i + 4].reshape(gb.height, gb.width, 4).copy() for i in range(4)]
+    res = _run(gl, env, gb, mp)
+    o = oracle_shade(orc, gb.rows16(), env, mp)
+    _check(orc, o, res)
+
+
 def test_shade_real_counts(gl, orc):
     """Alg. 1 as printed (real-valued counts)."""
     mp = MethodParams(K=8, Wo=128, seed=5, integer_mode=False)

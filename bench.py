@@ -132,6 +132,21 @@ def _profile_traffic():
     return traffic, sha
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """Largest value of x over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size: int, pixels_per_rank: int, steps: int, slowest_ms: float) -> float:
+    """Whole-job Mpixel/s: every rank shades its own frames (weak scaling)."""
+    return world_size * pixels_per_rank * steps / (slowest_ms / 1e3) / 1e6
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -284,11 +299,7 @@ def run_ours(args):
     step_ms = np.array([ev[i][0].elapsed_time(ev[i][2]) for i in range(args.steps)])
     env_ms = np.array([ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)])
     shade_ms = np.array([ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)])
-    total_ms = float(step_ms.sum())
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(step_ms.sum()), pg, dev)
 
     # end to end through the C ABI with host buffers: H2D of the frame's
     # G-buffer and environment texels, the step, D2H of the shaded frame
@@ -317,14 +328,10 @@ def run_ours(args):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1)
-    if pg:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = ws * npix * e2e_steps / (e2e_ms / 1e3) / 1e6
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    e2e_val = job_throughput(ws, npix, e2e_steps, e2e_ms)
 
-    value = ws * npix * args.steps / (total_ms / 1e3) / 1e6
+    value = job_throughput(ws, npix, args.steps, total_ms)
     result = None
     if rank == 0:
         peaks = _peaks()

@@ -62,6 +62,11 @@ typedef enum glint_format {
     GLINT_FMT_RGBA16F = 1
 } glint_format;
 
+typedef enum glint_evaluator {
+    GLINT_EVAL_E1 = 0, /* p_k from the filtered maps and tables (Eq. rtiblndf), isotropic sqrt(a_x a_y) */
+    GLINT_EVAL_E2 = 1  /* p_k by per-pixel quadrature of the anisotropic NDF (Eq. probhk) */
+} glint_evaluator;
+
 typedef enum glint_count_mode {
     GLINT_COUNT_INTEGER = 0, /* uint32 counts: N_P dithered at each tree root, Gaussian rounded */
     GLINT_COUNT_REAL = 1     /* real-valued counts, Alg. 1 as printed */
@@ -162,7 +167,9 @@ void glint_env_destroy(glint_env *env);
  *              shaded black)
  *   normal_f0: n.xyz (unit shading normal), F0 (Schlick)
  *   uv_alpha:  u, v, alpha_x, alpha_y (GGX roughness)
- *   duv:       du/dx, dv/dx, du/dy, dv/dy (screen-space uv derivatives) */
+ *   duv:       du/dx, dv/dx, du/dy, dv/dy (screen-space uv derivatives)
+ *   tangent:   t.xyz (direction of alpha_x), unused w; may be NULL for E1,
+ *              required for E2 */
 typedef struct glint_gbuffer {
     const float *view_n0;
     const float *normal_f0;
@@ -170,11 +177,14 @@ typedef struct glint_gbuffer {
     const float *duv;
     int width;
     int height;
+    const float *tangent;
 } glint_gbuffer;
 
 typedef struct glint_params {
     uint32_t seed;   /* user seed of the grid-vertex hashes */
     int count_mode;  /* glint_count_mode */
+    int evaluator;   /* glint_evaluator */
+    int e2_samples;  /* E2: S x S quadrature points, S in [1, 256] (0 = 16) */
 } glint_params;
 
 /* Optional per-pixel intermediate results (device; each pointer may be NULL).
@@ -199,7 +209,10 @@ typedef struct glint_debug {
 /* Glint shading of every pixel of `gbuf` (Sec. 4 Eq. iblglints:fin):
  *   L^_o = L_o * sum_k L_k M_k / (N_P * sum_k L_k p_k)
  * with L_o the smooth split-sum radiance, p_k = V W_k (k >= 2) and
- * p_1 = U + V W_1 from the filtered maps and tables, N_P = N_0 |det duv|, and
+ * p_1 = U + V W_1 from the filtered maps and tables (E1), or, with
+ * GLINT_EVAL_E2, p_k = int D(h) 1[n.w_i > 0] w_k(w_i) dh / int D(h) dh of the
+ * anisotropic footprint by an S x S quadrature of the GGX slope distribution
+ * reading the weights pyramid (masked mass in p_1), N_P = N_0 |det duv|, and
  * M_k = sum_i w_i n_k(i) over six triangle-grid samples (Sec. 3.3
  * Eq. anisogrid), each a hierarchical multinomial of dual-gated Gaussian
  * binomials (Alg. 1, Sec. 5) seeded by a hash of its grid vertex.

@@ -30,8 +30,15 @@ _lib = None
 
 # Tie model of the FP32 kernel (see or_shade in glint_oracle.c):
 # relative error of subtree probability masses, of the FP32 normal quantile,
-# of an FP32 exp2/log2 chain, and an absolute floor.
-TIE_DEFAULT = (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23)
+# of an FP32 exp2/log2 chain, an absolute floor of every threshold, and an
+# absolute error of subtree masses.
+TIE_DEFAULT = (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 0.0)
+# The E2 quadrature reads single pyramid texels per point at FP32 texel
+# coordinates (up to ~1.2e-4 texel of error, w_k changing by at most 1 per
+# texel), so a mass carried by a few points moves by ~1e-4 of itself and tiny
+# masses by an absolute ~1e-9 (measured on a GB300: 8.9e-5 relative, 5e-10
+# absolute).  Bounds 2^-12 and 2^-28.
+TIE_E2 = (2.0 ** -12, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -28)
 NV = 6
 
 
@@ -84,7 +91,9 @@ def _load():
         lib.or_prefilter.argtypes = [P, I, I, I, P, P, I, I, P, P, L, P]
         lib.or_prefilter_exact.argtypes = [P, I, I, I, D, P, L, P]
         lib.or_shade.argtypes = [P, L, P, I, P, I, D, D, P, I, P, I, U, I, P, I,
-                                 P, P, P, P, P, P, P, P, P, P, P]
+                                 P, P, P, P, P, P, P, P, P, P, P, I, P, I, P, I, I, P]
+        lib.or_e2_pk.argtypes = [P, P, P, ctypes.c_float, ctypes.c_float, I, P, I, I, I, I, P]
+        lib.or_e2_pk.restype = I
         lib.or_shade.restype = L
         lib.or_radiance.argtypes = [P, P, D, P, I, P, P, P]
         lib.or_multinomial.argtypes = [P, I, D, U, U, U, U, I, P]
@@ -297,6 +306,7 @@ class ShadeOracle:
     cand_err: np.ndarray  # (n, 6, max_cand, K)
     flags: np.ndarray     # (n,) decisions too close to call
     levels: np.ndarray    # (K,)
+    e2_flags: np.ndarray  # (n,) E2 points on the validity boundary (0 for E1)
 
 
 def gbuffer_rows(planes) -> np.ndarray:
@@ -305,7 +315,8 @@ def gbuffer_rows(planes) -> np.ndarray:
 
 
 def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab: np.ndarray, levels: np.ndarray,
-          seed: int, integer_mode: bool = True, tie=TIE_DEFAULT, max_cand: int = 8) -> ShadeOracle:
+          seed: int, integer_mode: bool = True, tie=TIE_DEFAULT, max_cand: int = 8, evaluator: int = 0,
+          tangents=None, e2_S: int = 16, env: "EnvOracle | None" = None) -> ShadeOracle:
     lib = _load()
     gb16 = np.ascontiguousarray(gb16, dtype=np.float32).reshape(-1, 16)
     n = gb16.shape[0]
@@ -321,12 +332,32 @@ def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab:
     o = ShadeOracle(rgb=np.zeros((n, 3)), lo=np.zeros((n, 3)), pk=np.zeros((n, K)), np_=np.zeros(n, np.float32),
                     vert=np.zeros((n, NV, 3), np.int64), wv=np.zeros((n, NV)), nroot=np.zeros((n, NV)),
                     ncand=np.zeros((n, NV), np.int32), cand=np.zeros((n, NV, max_cand, K)),
-                    cand_err=np.zeros((n, NV, max_cand, K)), flags=np.zeros(n, np.int32), levels=levels)
+                    cand_err=np.zeros((n, NV, max_cand, K)), flags=np.zeros(n, np.int32), levels=levels,
+                    e2_flags=np.zeros(n, np.int32))
+    if evaluator == 1:
+        tangents = np.ascontiguousarray(tangents, dtype=np.float32).reshape(-1, 4)
+        mips = env.mips_flat
+        H, W = env.ch0.shape[:2]
+    else:
+        tangents, mips, W, H = None, None, 0, 0
     lib.or_shade(_ptr(gb16), n, _ptr(flat), R, _ptr(widths), C, float(s_min), float(s_max), _ptr(lut_tab), nlut,
                  _ptr(levels), K, ctypes.c_uint32(seed & 0xFFFFFFFF), int(integer_mode), _ptr(tie_a), max_cand,
                  _ptr(o.rgb), _ptr(o.lo), _ptr(o.pk), _ptr(o.np_), _ptr(o.vert), _ptr(o.wv), _ptr(o.nroot),
-                 _ptr(o.ncand), _ptr(o.cand), _ptr(o.cand_err), _ptr(o.flags))
+                 _ptr(o.ncand), _ptr(o.cand), _ptr(o.cand_err), _ptr(o.flags), int(evaluator),
+                 None if tangents is None else _ptr(tangents), int(e2_S), None if mips is None else _ptr(mips), W, H,
+                 _ptr(o.e2_flags))
     return o
+
+
+def e2_pk(wo, n, t, ax: float, ay: float, S: int, env: EnvOracle, K: int):
+    """E2 reflection probabilities of one pixel and its count of boundary points."""
+    lib = _load()
+    H, W, C = env.ch0.shape
+    pk = np.zeros(K)
+    f = lib.or_e2_pk(_ptr(np.ascontiguousarray(wo, np.float64)), _ptr(np.ascontiguousarray(n, np.float64)),
+                     _ptr(np.ascontiguousarray(t, np.float64)), float(ax), float(ay), int(S), _ptr(env.mips_flat),
+                     W, H, C, K, _ptr(pk))
+    return pk, f
 
 
 def radiance(o: ShadeOracle, q: int, counts: np.ndarray) -> np.ndarray:

@@ -620,6 +620,85 @@ void or_prefilter_exact(const double *ch0, int W, int H, int C, double alpha, co
 }
 
 /* --------------------------------------------------------------------------
+ * E2: reflection probabilities of an anisotropic GGX footprint by quadrature.
+ *
+ * Eq. probhk without the n = v = r approximation of Eq. rtiblndf:
+ *   p_k = int D(h) 1[n.w_i(h) > 0] w_k(w_i(h)) dh / int D(h) dh      (k >= 2)
+ *   p_1 = (int D(h) 1[n.w_i <= 0] dh + int D(h) 1[n.w_i > 0] w_1 dh) / int D(h) dh
+ * with w_i(h) = reflect(w_o, h) (Sec. 3.2 change of variables) and the
+ * masked mass in bin 1 as in the E1 path.  Quadrature (Reading; the paper only
+ * treats the isotropic case): the GGX projected-area slope distribution with
+ * u1 = 1 - s^2 (the CDF of the standard slope radius), so r = sqrt(1-s^2)/s,
+ * slope = (a_x r cos phi, a_y r sin phi), phi = 2 pi u2, h' = (-slope, 1) in
+ * the frame (t, b = n x t, n).  Since D(h) dh = (D cos dh)/cos and
+ * du1 = 2 s ds, a point carries the bounded weight
+ * 2 s / cos(theta_h) = 2 sqrt(s^2 + rho^2 (1 - s^2)), rho^2 = a_x^2 cos^2 phi +
+ * a_y^2 sin^2 phi; S x S midpoint points in (s, u2).  A point is valid iff
+ * 2 (w_o . h') > mu_o |h'|^2 (<=> n . w_i > 0).  The weights w_k(w_i) are read
+ * bilinearly from pyramid level m, the coarsest level whose texel (pi / H_m
+ * radians) is at most 4 min(a_x, a_y) / S; the comparison is made in FP32 as
+ * (float)H_m * (min(a_x, a_y) * (4/S)) >= (float)pi, exact for powers of two.
+ * Returns the number of points whose validity margin is below 1e-5 of its
+ * scale (FP32 may classify those either way). */
+int or_e2_pk(const double wo[3], const double nn[3], const double tg[3], float ax, float ay, int S,
+             const double *mips, int W, int H, int C, int K, double *pk)
+{
+    int M = or_mip_count(H);
+    float x = fminf(ax, ay) * (4.0f / (float)S);
+    int m = 0;
+    for (int k = 0; k < M; ++k)
+        if ((float)(H >> k) * x >= (float)OR_PI) m = k;
+    const double *lev = mips + mip_offset(W, H, C, m);
+    int Wm = W >> m, Hm = H >> m;
+    /* frame: tangent made orthogonal to n */
+    double tn = tg[0] * nn[0] + tg[1] * nn[1] + tg[2] * nn[2];
+    double t[3] = {tg[0] - tn * nn[0], tg[1] - tn * nn[1], tg[2] - tn * nn[2]};
+    double tl = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    for (int i = 0; i < 3; ++i) t[i] /= tl;
+    double b[3] = {nn[1] * t[2] - nn[2] * t[1], nn[2] * t[0] - nn[0] * t[2], nn[0] * t[1] - nn[1] * t[0]};
+    double mu = wo[0] * nn[0] + wo[1] * nn[1] + wo[2] * nn[2];
+    double ot = wo[0] * t[0] + wo[1] * t[1] + wo[2] * t[2];
+    double ob = wo[0] * b[0] + wo[1] * b[1] + wo[2] * b[2];
+    double sum_all = 0.0, sum_inv = 0.0, acc[OR_MAXK];
+    double ch[3 + OR_MAXK];
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    int flagged = 0;
+    for (int a = 0; a < S; ++a) {
+        double sv = (a + 0.5) / S;
+        double r = sqrt(1.0 - sv * sv) / sv;
+        for (int c = 0; c < S; ++c) {
+            double u2 = (c + 0.5) / S;
+            double cp = cos(2.0 * OR_PI * u2), sp = sin(2.0 * OR_PI * u2);
+            double sx = ax * r * cp, sy = ay * r * sp;
+            double rho2 = (double)ax * ax * cp * cp + (double)ay * ay * sp * sp;
+            double wgt = 2.0 * sqrt(sv * sv + rho2 * (1.0 - sv * sv));
+            double hl2 = 1.0 + sx * sx + sy * sy;
+            double hl = sqrt(hl2);
+            double oh = -sx * ot - sy * ob + mu; /* w_o . h' */
+            double margin = 2.0 * oh - mu * hl2;
+            double scale = 2.0 * fabs(oh) + fabs(mu) * hl2;
+            if (fabs(margin) < 1e-5 * scale) ++flagged;
+            sum_all += wgt;
+            if (!(margin > 0.0)) {
+                sum_inv += wgt;
+                continue;
+            }
+            /* w_i = 2 (w_o . h) h - w_o, h = h'/|h'| */
+            double hw[3];
+            for (int i = 0; i < 3; ++i) hw[i] = (-sx * t[i] - sy * b[i] + nn[i]) / hl;
+            double oh_n = oh / hl;
+            double wi[3];
+            for (int i = 0; i < 3; ++i) wi[i] = 2.0 * oh_n * hw[i] - wo[i];
+            env_bilinear(lev, Wm, Hm, C, wi, ch);
+            for (int k = 0; k < K; ++k) acc[k] += wgt * ch[3 + k];
+        }
+    }
+    pk[0] = (sum_inv + acc[0]) / sum_all;
+    for (int k = 1; k < K; ++k) pk[k] = acc[k] / sum_all;
+    return flagged;
+}
+
+/* --------------------------------------------------------------------------
  * Per-pixel shading.
  * ------------------------------------------------------------------------ */
 
@@ -683,12 +762,14 @@ static void grid_vertices(float u, float v, int l, int64_t vx[3], int64_t vy[3],
  *                         mass (prefilter, look-up tables, interpolation)
  *           tie[1] = e_z  relative error bound of the FP32 normal quantile
  *           tie[2] = e_f  relative error bound of an FP32 exp2/log2 chain
- *           tie[3] = d_a  absolute floor of every threshold tolerance */
+ *           tie[3] = d_a  absolute floor of every threshold tolerance
+ *           tie[4] = a_P  absolute error bound of each subtree mass (E2 reads
+ *                         single pyramid texels per quadrature point) */
 typedef struct {
     int K, integer_mode;
     uint32_t key0, key1, key2, seed;
     double P[2 * OR_MAXK];
-    double tie[4];
+    double tie[5];
     int max_cand, n_out, overflow, flagged;
     double *out;     /* max_cand x K leaf counts */
     double *out_err; /* max_cand x K leaf count tolerance */
@@ -740,8 +821,8 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
     double xi1 = or_xi(h[1]), xi2 = or_xi(h[2]);
     double PL = t->P[2 * node], PR = t->P[2 * node + 1];
     double p = (PL + PR > 0.0) ? PL / (PL + PR) : 0.0;
-    double e_P = t->tie[0], e_z = t->tie[1], e_f = t->tie[2], d_a = t->tie[3];
-    int use_tie = (e_P > 0.0 || e_z > 0.0 || e_f > 0.0 || d_a > 0.0);
+    double e_P = t->tie[0], e_z = t->tie[1], e_f = t->tie[2], d_a = t->tie[3], a_P = t->tie[4];
+    int use_tie = (e_P > 0.0 || e_z > 0.0 || e_f > 0.0 || d_a > 0.0 || a_P > 0.0);
 
     double T[4], mu, sigma;
     or_dualgated_thresholds(Nn, p, T, &mu, &sigma);
@@ -754,8 +835,11 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
     if (use_tie) {
         for (int sgn = -1; sgn <= 1; sgn += 2) {
             double pp = p;
-            if (PL > 0.0 && PR > 0.0)
-                pp = PL * (1.0 + sgn * e_P) / (PL * (1.0 + sgn * e_P) + PR * (1.0 - sgn * e_P));
+            if (PL + PR > 0.0) {
+                double pl = fmax(PL * (1.0 + sgn * e_P) + sgn * a_P, 0.0);
+                double pr = fmax(PR * (1.0 - sgn * e_P) - sgn * a_P, 0.0);
+                if (pl + pr > 0.0) pp = pl / (pl + pr);
+            }
             for (int sn = -1; sn <= 1; sn += 2) {
                 double Np = fmax(Nn + sn * dNn, 0.0);
                 double T2[4], mu2, sg2;
@@ -879,6 +963,10 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
  *  - M_k = sum_i w_i n_k(i), L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k)
  *    (0 when the denominator is 0).
  *
+ * evaluator = 1 replaces p_k by the E2 quadrature (or_e2_pk) of the
+ * anisotropic footprint, with per-pixel tangents (npix x 4) and the pyramid
+ * (mips, W x H level 0); e2_flags counts its near-boundary points.
+ *
  * Outputs (all per pixel): rgb (3, nominal outcome at every decision),
  * lo (3), pk (K), np (1, FP32 N_P), vert (6 x 3: x, y, level), wv (6),
  * nroot (6), ncand (6: number of valid count vectors of each tree, -1 when
@@ -888,7 +976,8 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
 long or_shade(const float *gb, long npix, const double *pref, int R, const int *widths, int C, double s_min,
               double s_max, const double *lut, int nlut, const double *L, int K, uint32_t seed, int integer_mode,
               const double *tie, int max_cand, double *rgb, double *lo, double *pk, float *np, int64_t *vert,
-              double *wv, double *nroot, int32_t *ncand, double *cand, double *cand_err, int32_t *flags)
+              double *wv, double *nroot, int32_t *ncand, double *cand, double *cand_err, int32_t *flags,
+              int evaluator, const float *tangents, int e2_S, const double *mips, int W, int H, int32_t *e2_flags)
 {
     long nbg = 0;
     for (long q = 0; q < npix; ++q) {
@@ -934,6 +1023,12 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
         double p[OR_MAXK];
         p[0] = U + V * cc[3];
         for (int k = 1; k < K; ++k) p[k] = V * cc[3 + k];
+        if (evaluator == 1) {
+            double tg[3] = {tangents[4 * q], tangents[4 * q + 1], tangents[4 * q + 2]};
+            e2_flags[q] = or_e2_pk(wo, nn, tg, g[10], g[11], e2_S, mips, W, H, C, K, p);
+        } else if (e2_flags) {
+            e2_flags[q] = 0;
+        }
         for (int c = 0; c < 3; ++c) lo[3 * q + c] = Lo[c];
         for (int k = 0; k < K; ++k) pk[q * K + k] = p[k];
 
@@ -954,7 +1049,7 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
         t.K = K;
         t.integer_mode = integer_mode;
         t.seed = seed;
-        for (int i = 0; i < 4; ++i) t.tie[i] = tie[i];
+        for (int i = 0; i < 5; ++i) t.tie[i] = tie[i];
         t.max_cand = max_cand;
         for (int k = 0; k < K; ++k) t.P[K + k] = p[k];
         for (int nd = K - 1; nd >= 1; --nd) t.P[nd] = t.P[2 * nd] + t.P[2 * nd + 1];

@@ -322,6 +322,14 @@ glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuff
         set_error("glint_shade: unknown count mode %d", p->count_mode);
         return GLINT_ERR_INVALID_ARG;
     }
+    if (p->evaluator != GLINT_EVAL_E1 && p->evaluator != GLINT_EVAL_E2) {
+        set_error("glint_shade: unknown evaluator %d", p->evaluator);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (p->evaluator == GLINT_EVAL_E2 && (p->e2_samples < 0 || p->e2_samples > 256)) {
+        set_error("glint_shade: e2_samples %d outside [0, 256]", p->e2_samples);
+        return GLINT_ERR_INVALID_ARG;
+    }
     const long npix = (long)g->width * g->height;
     if (npix > 0) {
         if (!g->view_n0 || !g->normal_f0 || !g->uv_alpha || !g->duv || !out_rgba) {
@@ -329,8 +337,12 @@ glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuff
             return GLINT_ERR_INVALID_ARG;
         }
         if (!aligned16(g->view_n0) || !aligned16(g->normal_f0) || !aligned16(g->uv_alpha) || !aligned16(g->duv) ||
-            !aligned16(out_rgba)) {
+            !aligned16(out_rgba) || !aligned16(g->tangent)) {
             set_error("glint_shade: G-buffer planes and output must be 16-byte aligned");
+            return GLINT_ERR_INVALID_ARG;
+        }
+        if (p->evaluator == GLINT_EVAL_E2 && !g->tangent) {
+            set_error("glint_shade: the E2 evaluator needs the tangent plane");
             return GLINT_ERR_INVALID_ARG;
         }
     }

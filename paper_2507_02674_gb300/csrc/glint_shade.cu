@@ -29,7 +29,7 @@ namespace {
 constexpr int kShadeNT = 128;
 
 struct ShadeArgs {
-    const float4 *view_n0, *normal_f0, *uv_alpha, *duv;
+    const float4 *view_n0, *normal_f0, *uv_alpha, *duv, *tangent;
     float4 *out;
     long npix;
     const float4 *lut;
@@ -41,7 +41,88 @@ struct ShadeArgs {
     const float *levels;
     uint32_t seed;
     glint_debug dbg;
+    // E2: weights pyramid
+    const float4 *pyr;
+    const size_t *pyr_off4;
+    int envW, envH, envM, e2S;
 };
+
+// E2: reflection probabilities of an anisotropic GGX footprint by quadrature
+// (Eq. probhk).  Points of the projected-area slope distribution in
+// (s, u2), u1 = 1 - s^2, r = sqrt(1 - s^2)/s, slope = (a_x r cos phi,
+// a_y r sin phi), h' = (-slope, 1) in (t, b = n x t, n); bounded weight
+// 2 sqrt(s^2 + rho^2 (1 - s^2)); valid iff 2 w_o.h' > mu_o |h'|^2
+// (n . w_i > 0); w_k read bilinearly at pyramid level m, the coarsest whose
+// texel pi/H_m is at most 4 min(a_x, a_y)/S (an exact FP32 comparison).
+template <int K, int C4>
+__device__ __forceinline__ void e2_probabilities(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
+                                                 float mu_o, float *p) {
+    const float4 tg = ldg4(a.tangent + q);
+    const float tn = tg.x * g1.x + tg.y * g1.y + tg.z * g1.z;
+    float tx = tg.x - tn * g1.x, ty = tg.y - tn * g1.y, tz = tg.z - tn * g1.z;
+    const float tinv = 1.f / sqrtf(tx * tx + ty * ty + tz * tz);
+    tx *= tinv; ty *= tinv; tz *= tinv;
+    const float bx = g1.y * tz - g1.z * ty, by = g1.z * tx - g1.x * tz, bz = g1.x * ty - g1.y * tx;
+    const float ot = g0.x * tx + g0.y * ty + g0.z * tz;
+    const float ob = g0.x * bx + g0.y * by + g0.z * bz;
+    const int S = a.e2S;
+    const float lx = fminf(g2.z, g2.w) * (4.0f / (float)S);
+    int m = 0;
+    for (int k = 0; k < a.envM; ++k)
+        if ((float)(a.envH >> k) * lx >= kPi) m = k;
+    const int Wm = a.envW >> m, Hm = a.envH >> m;
+    const float4 *lev = a.pyr + a.pyr_off4[m];
+    const float ax2 = g2.z * g2.z, ay2 = g2.w * g2.w;
+    float sum_all = 0.f, sum_inv = 0.f;
+    float acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.f;
+#pragma unroll 1
+    for (int ia = 0; ia < S; ++ia) {
+        const float sv = ((float)ia + 0.5f) / (float)S;
+        const float r = sqrtf(1.f - sv * sv) / sv;
+#pragma unroll 1
+        for (int ic = 0; ic < S; ++ic) {
+            float sp, cp;
+            sincospif(2.f * ((float)ic + 0.5f) / (float)S, &sp, &cp);
+            const float sx = g2.z * r * cp, sy = g2.w * r * sp;
+            const float rho2 = ax2 * cp * cp + ay2 * sp * sp;
+            const float wgt = 2.f * sqrtf(sv * sv + rho2 * (1.f - sv * sv));
+            const float hl2 = 1.f + sx * sx + sy * sy;
+            const float oh = -sx * ot - sy * ob + mu_o;
+            sum_all += wgt;
+            if (!(2.f * oh - mu_o * hl2 > 0.f)) {
+                sum_inv += wgt;
+                continue;
+            }
+            const float il = rsqrtf(hl2);
+            const float hx = (-sx * tx - sy * bx + g1.x) * il;
+            const float hy = (-sx * ty - sy * by + g1.y) * il;
+            const float hz = (-sx * tz - sy * bz + g1.z) * il;
+            const float c2 = 2.f * oh * il;
+            const float dx = c2 * hx - g0.x, dy = c2 * hy - g0.y, dz = c2 * hz - g0.z;
+            float ex, ey;
+            dir_to_texel(dx, dy, dz, Wm, Hm, ex, ey);
+            const Taps tp = equirect_taps(ex, ey, Wm, Hm);
+            float w[C4 * 4];
+#pragma unroll
+            for (int c = 0; c < C4; ++c) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                v = fma4(tp.w00, __ldg(lev + (size_t)tp.i00 * C4 + c), v);
+                v = fma4(tp.w01, __ldg(lev + (size_t)tp.i01 * C4 + c), v);
+                v = fma4(tp.w10, __ldg(lev + (size_t)tp.i10 * C4 + c), v);
+                v = fma4(tp.w11, __ldg(lev + (size_t)tp.i11 * C4 + c), v);
+                w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] = fmaf(wgt, w[3 + k], acc[k]);
+        }
+    }
+    const float inv = 1.f / sum_all;
+    p[0] = (sum_inv + acc[0]) * inv;
+#pragma unroll
+    for (int k = 1; k < K; ++k) p[k] = acc[k] * inv;
+}
 
 __device__ __forceinline__ float4 lut_fetch(const float4 *lut, int n, float mu, float s) {
     float x = fminf(fmaxf(mu * (float)n - 0.5f, 0.f), (float)(n - 1));
@@ -153,7 +234,7 @@ __device__ __forceinline__ void draw_real(float N, const NodeParams &np, uint32_
     nbar = (B_allneg ? N2 - 1.f : 0.f) + (B_alloneneg ? 1.f : 0.f) + (B_G ? N2 - G : 0.f);
 }
 
-template <int K, bool INTEGER, bool DEBUG>
+template <int K, bool INTEGER, bool DEBUG, bool E2>
 __global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
     constexpr int C4 = (3 + K + 3) / 4;
     const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
@@ -224,9 +305,13 @@ __global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
     const float Eb = g1.w * tab.z + tab.w;
     const float Lor = ch[0] * Eb, Log = ch[1] * Eb, Lob = ch[2] * Eb;
     float p[K];
-    p[0] = tab.y + tab.x * ch[3];
+    if (E2) {
+        e2_probabilities<K, C4>(a, q, g0, g1, g2, mu_o, p);
+    } else {
+        p[0] = tab.y + tab.x * ch[3];
 #pragma unroll
-    for (int k = 1; k < K; ++k) p[k] = tab.x * ch[3 + k];
+        for (int k = 1; k < K; ++k) p[k] = tab.x * ch[3 + k];
+    }
 
     // ---- 2. footprint, microfacet count, grid level
     const float area = footprint_area(g3.x, g3.y, g3.z, g3.w);
@@ -392,16 +477,22 @@ __global__ void k_quantile(const float *__restrict__ p, float *__restrict__ z, l
     if (i < n) z[i] = normal_quantile(p[i]);
 }
 
-template <int K>
-cudaError_t launch_k(const ShadeArgs &args, bool integer, bool debug, cudaStream_t s) {
+template <int K, bool E2>
+void launch_ke(const ShadeArgs &args, bool integer, bool debug, cudaStream_t s) {
     const unsigned grid = (unsigned)((args.npix + kShadeNT - 1) / kShadeNT);
     if (integer) {
-        if (debug) k_shade<K, true, true><<<grid, kShadeNT, 0, s>>>(args);
-        else k_shade<K, true, false><<<grid, kShadeNT, 0, s>>>(args);
+        if (debug) k_shade<K, true, true, E2><<<grid, kShadeNT, 0, s>>>(args);
+        else k_shade<K, true, false, E2><<<grid, kShadeNT, 0, s>>>(args);
     } else {
-        if (debug) k_shade<K, false, true><<<grid, kShadeNT, 0, s>>>(args);
-        else k_shade<K, false, false><<<grid, kShadeNT, 0, s>>>(args);
+        if (debug) k_shade<K, false, true, E2><<<grid, kShadeNT, 0, s>>>(args);
+        else k_shade<K, false, false, E2><<<grid, kShadeNT, 0, s>>>(args);
     }
+}
+
+template <int K>
+cudaError_t launch_k(const ShadeArgs &args, bool integer, bool debug, bool e2, cudaStream_t s) {
+    if (e2) launch_ke<K, true>(args, integer, debug, s);
+    else launch_ke<K, false>(args, integer, debug, s);
     return cudaGetLastError();
 }
 
@@ -417,6 +508,7 @@ cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const
                                int *launches) {
     ShadeArgs a;
     a.view_n0 = reinterpret_cast<const float4 *>(g->view_n0);
+    a.tangent = reinterpret_cast<const float4 *>(g->tangent);
     a.normal_f0 = reinterpret_cast<const float4 *>(g->normal_f0);
     a.uv_alpha = reinterpret_cast<const float4 *>(g->uv_alpha);
     a.duv = reinterpret_cast<const float4 *>(g->duv);
@@ -432,16 +524,23 @@ cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const
     a.levels = env->levels;
     a.seed = p->seed;
     a.dbg = dbg ? *dbg : glint_debug{};
+    a.pyr = reinterpret_cast<const float4 *>(env->pyr);
+    a.pyr_off4 = env->pyr_off4_dev;
+    a.envW = env->d.width;
+    a.envH = env->d.height;
+    a.envM = env->M;
+    a.e2S = p->e2_samples > 0 ? p->e2_samples : 16;
+    const bool e2 = p->evaluator == GLINT_EVAL_E2;
     const bool debug = dbg != nullptr;
     const bool integer = p->count_mode == GLINT_COUNT_INTEGER;
     if (launches) *launches = 0;
     if (a.npix == 0) return cudaSuccess;
     cudaError_t e;
     switch (env->d.K) {
-    case 2: e = launch_k<2>(a, integer, debug, s); break;
-    case 4: e = launch_k<4>(a, integer, debug, s); break;
-    case 8: e = launch_k<8>(a, integer, debug, s); break;
-    case 16: e = launch_k<16>(a, integer, debug, s); break;
+    case 2: e = launch_k<2>(a, integer, debug, e2, s); break;
+    case 4: e = launch_k<4>(a, integer, debug, e2, s); break;
+    case 8: e = launch_k<8>(a, integer, debug, e2, s); break;
+    case 16: e = launch_k<16>(a, integer, debug, e2, s); break;
     default: return cudaErrorInvalidValue;
     }
     if (launches) *launches = 1;

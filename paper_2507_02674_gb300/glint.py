@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libglint.so")
 GLINT_OK = 0
 FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
+EVAL_E1, EVAL_E2 = 0, 1
 ENV_LOHI, ENV_LEVELS, ENV_PYRAMID, ENV_FILTERED, ENV_TABLE, ENV_FILTERED_WIDTHS = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_READY", 5: "TIMEOUT", 6: "UNSUPPORTED"}
 
@@ -38,11 +39,13 @@ class EnvDesc(ctypes.Structure):
 
 class GBufferDesc(ctypes.Structure):
     _fields_ = [("view_n0", ctypes.c_void_p), ("normal_f0", ctypes.c_void_p), ("uv_alpha", ctypes.c_void_p),
-                ("duv", ctypes.c_void_p), ("width", ctypes.c_int), ("height", ctypes.c_int)]
+                ("duv", ctypes.c_void_p), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("tangent", ctypes.c_void_p)]
 
 
 class Params(ctypes.Structure):
-    _fields_ = [("seed", ctypes.c_uint32), ("count_mode", ctypes.c_int)]
+    _fields_ = [("seed", ctypes.c_uint32), ("count_mode", ctypes.c_int), ("evaluator", ctypes.c_int),
+                ("e2_samples", ctypes.c_int)]
 
 
 class Debug(ctypes.Structure):
@@ -208,10 +211,13 @@ class Env:
 
 
 def shade(ctx: Context, env: Env, planes, width: int, height: int, out, seed: int = 0,
-          count_mode: int = COUNT_INTEGER, debug: dict | None = None, stream=None):
-    """glint_shade over a G-buffer given as four device tensors of (npix, 4) float32."""
-    g = GBufferDesc(_dptr(planes[0]), _dptr(planes[1]), _dptr(planes[2]), _dptr(planes[3]), width, height)
-    p = Params(seed & 0xFFFFFFFF, count_mode)
+          count_mode: int = COUNT_INTEGER, debug: dict | None = None, stream=None, tangent=None,
+          evaluator: int = EVAL_E1, e2_samples: int = 16):
+    """glint_shade over a G-buffer given as four device tensors of (npix, 4) float32
+    (plus an optional (npix, 4) tangent tensor, needed by E2)."""
+    g = GBufferDesc(_dptr(planes[0]), _dptr(planes[1]), _dptr(planes[2]), _dptr(planes[3]), width, height,
+                    _dptr(tangent))
+    p = Params(seed & 0xFFFFFFFF, count_mode, evaluator, e2_samples)
     dbg = None
     if debug is not None:
         dbg = Debug(*(_dptr(debug.get(k)) for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")))

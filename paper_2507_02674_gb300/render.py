@@ -26,6 +26,10 @@ def gbuffer_tensors(gb: GBuffer, device="cuda", pinned: bool = False):
     return [p.to(device) for p in planes]
 
 
+def tangent_tensor(gb: GBuffer, device="cuda"):
+    return torch.from_numpy(gb.tangents()).to(device)
+
+
 class Frame:
     """One environment and the buffers to shade G-buffers with it."""
 
@@ -39,8 +43,9 @@ class Frame:
         self.env.update(self.texels, stream)
 
     def shade(self, planes, width: int, height: int, out=None, seed: int = 0, count_mode: int = glint.COUNT_INTEGER,
-              debug=None, stream=None):
+              debug=None, stream=None, tangent=None, evaluator: int = glint.EVAL_E1, e2_samples: int = 16):
         if out is None:
             out = torch.empty(width * height, 4, device=planes[0].device)
-        glint.shade(self.ctx, self.env, planes, width, height, out, seed, count_mode, debug, stream)
+        glint.shade(self.ctx, self.env, planes, width, height, out, seed, count_mode, debug, stream, tangent,
+                    evaluator, e2_samples)
         return out

@@ -12,6 +12,8 @@ pixel, row-major over the image,
   plane 1: n.xyz (unit shading normal), F0 (Schlick reflectance)
   plane 2: u, v, alpha_x, alpha_y
   plane 3: du/dx, dv/dx, du/dy, dv/dy (screen-space derivatives of uv)
+  tangent (optional fifth plane): t.xyz, 0 -- the direction of alpha_x, used by
+           the anisotropic quadrature evaluator
 Environment maps are equirectangular W x H (W = 2H) RGBA images, texel (x, y)
 centred on phi = 2 pi (x+1/2)/W, theta = pi (y+1/2)/H around the +y axis,
 direction (sin th cos ph, cos th, sin th sin ph).  Radiance = stored value *
@@ -30,6 +32,7 @@ class GBuffer:
     height: int
     planes: list  # four float32 arrays (H, W, 4)
     desc: str = ""
+    tangent: np.ndarray | None = None  # (H, W, 4) float32: t.xyz, 0
 
     @property
     def npix(self) -> int:
@@ -42,6 +45,10 @@ class GBuffer:
 
     def nbytes(self) -> int:
         return sum(p.nbytes for p in self.planes)
+
+    def tangents(self) -> np.ndarray:
+        """(npix, 4) float32 tangent rows."""
+        return np.ascontiguousarray(self.tangent.reshape(-1, 4).astype(np.float32))
 
 
 @dataclass
@@ -200,7 +207,11 @@ def gbuffer_sphere(W: int = 64, H: int = 64, alpha: float = 0.15, N0: float = 1e
     planes[3][..., 1] = np.where(hit, dvdx, 0.0)
     planes[3][..., 2] = np.where(hit, dudy, 0.0)
     planes[3][..., 3] = np.where(hit, dvdy, 0.0)
-    return GBuffer(W, H, planes, f"sphere {W}x{H} ortho alpha={alpha} N0={N0:g} uv x{uv_scale:g}")
+    tan = np.zeros((H, W, 4), np.float32)
+    ph = np.arctan2(n[..., 2], n[..., 0])
+    tan[..., 0] = -np.sin(ph)
+    tan[..., 2] = np.cos(ph)
+    return GBuffer(W, H, planes, f"sphere {W}x{H} ortho alpha={alpha} N0={N0:g} uv x{uv_scale:g}", tan)
 
 
 def _random_materials(rng, shape, a_lo, a_hi, n_lo, n_hi):
@@ -298,9 +309,13 @@ def gbuffer_scene(W: int = 1920, H: int = 1080, seed: int = 1, n_spheres: int = 
     planes[3][..., 1] = dvdx
     planes[3][..., 2] = dudy
     planes[3][..., 3] = dvdy
+    tan = np.zeros((H, W, 4), np.float32)
+    sph = np.arctan2(ns[..., 2], ns[..., 0])
+    tan[..., 0] = np.where(on_sphere, -np.sin(sph), 1.0)
+    tan[..., 2] = np.where(on_sphere, np.cos(sph), 0.0)
     return GBuffer(W, H, planes,
                    f"scene {W}x{H} plane+{n_spheres} spheres pitch={pitch_deg} alpha~U[{a_lo},{a_hi}] "
-                   f"N0~logU[{n_lo:g},{n_hi:g}]")
+                   f"N0~logU[{n_lo:g},{n_hi:g}]", tan)
 
 
 def gbuffer_random(n: int, seed: int = 7, a_lo: float = 0.03, a_hi: float = 0.3, n_lo: float = 1e3,
@@ -330,4 +345,10 @@ def gbuffer_random(n: int, seed: int = 7, a_lo: float = 0.03, a_hi: float = 0.3,
     planes[2][:n, 3] = ay
     planes[3][:n] = mag * sgn
     planes = [p.reshape(H, W, 4) for p in planes]
-    return GBuffer(W, H, planes, f"random {n} px")
+    t = rng.normal(size=(n, 3))
+    t -= np.sum(t * nrm, 1)[:, None] * nrm
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    tan = np.zeros((H * W, 4), np.float32)
+    tan[:n, :3] = t
+    tan[n:, 0] = 1.0
+    return GBuffer(W, H, planes, f"random {n} px", tan.reshape(H, W, 4))

@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GLINT_ABI_VERSION 1
+#define GLINT_ABI_VERSION 2
 #define GLINT_MAX_K 16
 
 typedef enum glint_status {
@@ -64,7 +64,9 @@ typedef enum glint_format {
 
 typedef enum glint_evaluator {
     GLINT_EVAL_E1 = 0, /* p_k from the filtered maps and tables (Eq. rtiblndf), isotropic sqrt(a_x a_y) */
-    GLINT_EVAL_E2 = 1  /* p_k by per-pixel quadrature of the anisotropic NDF (Eq. probhk) */
+    GLINT_EVAL_E2 = 1, /* p_k by per-pixel quadrature of the anisotropic NDF (Eq. probhk) */
+    GLINT_EVAL_MLP = 2, /* p_k from a trained glint_mlp surrogate of E2 (no counterpart in the paper) */
+    GLINT_EVAL_GIVEN = 3 /* p_k supplied by the caller in params->p_scratch (width*height*K floats) */
 } glint_evaluator;
 
 typedef enum glint_count_mode {
@@ -74,6 +76,7 @@ typedef enum glint_count_mode {
 
 typedef struct glint_ctx glint_ctx;
 typedef struct glint_env glint_env;
+typedef struct glint_mlp glint_mlp;
 
 /* ABI version of the loaded library (GLINT_ABI_VERSION). */
 int glint_abi_version(void);
@@ -185,6 +188,10 @@ typedef struct glint_params {
     int count_mode;  /* glint_count_mode */
     int evaluator;   /* glint_evaluator */
     int e2_samples;  /* E2: S x S quadrature points, S in [1, 256] (0 = 16) */
+    const glint_mlp *mlp; /* GLINT_EVAL_MLP: the network; its K must equal the environment's */
+    float *p_scratch;     /* GLINT_EVAL_MLP: device, width*height*K floats (4-byte aligned) that
+                             receive the network's p_k before shading; GLINT_EVAL_GIVEN: the
+                             p_k to shade with (read only).  Caller-owned */
 } glint_params;
 
 /* Optional per-pixel intermediate results (device; each pointer may be NULL).
@@ -212,7 +219,10 @@ typedef struct glint_debug {
  * p_1 = U + V W_1 from the filtered maps and tables (E1), or, with
  * GLINT_EVAL_E2, p_k = int D(h) 1[n.w_i > 0] w_k(w_i) dh / int D(h) dh of the
  * anisotropic footprint by an S x S quadrature of the GGX slope distribution
- * reading the weights pyramid (masked mass in p_1), N_P = N_0 |det duv|, and
+ * reading the weights pyramid (masked mass in p_1), or, with GLINT_EVAL_MLP,
+ * p_k from params->mlp written to params->p_scratch first (two launches),
+ * or, with GLINT_EVAL_GIVEN, the p_k in params->p_scratch,
+ * N_P = N_0 |det duv|, and
  * M_k = sum_i w_i n_k(i) over six triangle-grid samples (Sec. 3.3
  * Eq. anisogrid), each a hierarchical multinomial of dual-gated Gaussian
  * binomials (Alg. 1, Sec. 5) seeded by a hash of its grid vertex.
@@ -220,6 +230,108 @@ typedef struct glint_debug {
  * `stream`; env must have been updated on the same stream (or synchronised). */
 glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf,
                          const glint_params *params, float *out_rgba, const glint_debug *dbg, void *stream);
+
+/* Reflection probabilities p_k (Eq. probhk) of every pixel of `gbuf` under
+ * params->evaluator (E1, E2 or MLP; GIVEN is rejected; seed and count mode
+ * are ignored), the
+ * quantity glint_shade feeds to the counts.  p_out: device, width*height*K
+ * floats, pixel-major; background pixels (N_0 <= 0) get 0.  Used to generate
+ * the surrogate's training targets (E2) and to measure its error.  Enqueued on
+ * `stream`. */
+glint_status glint_reflect_probs(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf,
+                                 const glint_params *params, float *p_out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned surrogate of the per-component NDF mass (no counterpart in the
+ * paper).  A BF16 MLP with FP32 accumulation corrects E1's p_k towards the
+ * anisotropic integral that E2 computes, for K in {2, 4, 8}:
+ *   x = ( p_k^E1 (K) | W_k at five taps (5K) | mu_o, sqrt a_x, sqrt a_y | 0 )
+ *       (64 values); W_k is read from the filtered maps at roughness
+ *       parameter s = sqrt(min(a_x, a_y)) in the directions w_r and
+ *       normalize(w_r + a_x J_t), normalize(w_r - a_x J_t),
+ *       normalize(w_r + a_y J_b), normalize(w_r - a_y J_b), in that order,
+ *       where J_t = 2 (-(w_o.t) n - mu_o t) (t the tangent made orthogonal to
+ *       n) and J_b likewise for b = n x t;
+ *   lp = log max(p_k^E1, 1e-6);
+ *   h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2),
+ *   p = softmax((h2 W3 + b3)[0..K) + lp)
+ * with x, W, h1 and h2 rounded to BF16 and every sum accumulated in FP32.
+ * Parameters (FP32 master copy, glint_mlp_param_count() floats, in order):
+ *   W1 [64 in][64 out], b1 [64], W2 [64][64], b2 [64], W3 [64][16], b3 [16]
+ * (columns >= K of W3 and b3 are unused and stay fixed).  Training minimises
+ * the mean cross-entropy -sum_k y_k log p_k against target distributions y
+ * (e.g. E2's p_k from glint_reflect_probs) with Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8, FP32).  The gradient of a batch is accumulated per resident block
+ * in a fixed order and summed over blocks in block order, so a step is
+ * deterministic.  Inputs x are stored as BF16 bit patterns (uint16), 64 per
+ * sample, row-major; lp as K floats per sample.
+ * ------------------------------------------------------------------------- */
+
+typedef enum glint_mlp_item {
+    GLINT_MLP_PARAMS = 0, /* FP32 master parameters */
+    GLINT_MLP_GRAD = 1,   /* gradient of the last glint_mlp_train_step */
+    GLINT_MLP_ADAM_M = 2, /* Adam first moment */
+    GLINT_MLP_ADAM_V = 3  /* Adam second moment */
+} glint_mlp_item;
+
+/* Number of FP32 parameters (9360). */
+int glint_mlp_param_count(void);
+
+/* A network for K in {2, 4, 8} components (K = 16 gives GLINT_ERR_UNSUPPORTED)
+ * on ctx's device, trainable with batches of up to max_batch samples
+ * (1 .. 2^30).  Weights He-uniform from a pcg4d hash of (layer, index, seed),
+ * biases 0, Adam moments 0, step 0. */
+glint_status glint_mlp_create(glint_ctx *ctx, int K, long max_batch, uint32_t seed, glint_mlp **out);
+void glint_mlp_destroy(glint_mlp *mlp);
+
+/* Copies glint_mlp_param_count() host floats into the master parameters and
+ * refreshes the BF16 copies (synchronous). */
+glint_status glint_mlp_set_params(glint_mlp *mlp, const float *host, long n);
+
+/* Copies one glint_mlp_item (n = glint_mlp_param_count() floats) to host
+ * memory (synchronous). */
+glint_status glint_mlp_export(const glint_mlp *mlp, int item, float *host, long n);
+
+/* Restores parameters, Adam moments and the step counter (checkpoint resume;
+ * training continues bit-identically).  Synchronous. */
+glint_status glint_mlp_import_state(glint_mlp *mlp, const float *params, const float *adam_m, const float *adam_v,
+                                    long n, long step);
+
+/* Adam steps taken so far. */
+long glint_mlp_step(const glint_mlp *mlp);
+
+/* The surrogate's inputs of every pixel of `gbuf` (view_n0, normal_f0,
+ * uv_alpha and tangent planes) under environment `env` (K in {2, 4, 8}):
+ * x_out (device, width*height*64 uint16 BF16 patterns, 16-byte aligned) and
+ * lp_out (device, width*height*K floats); background rows are 0.  Enqueued on
+ * `stream`. */
+glint_status glint_mlp_features(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf, uint16_t *x_out,
+                                float *lp_out, void *stream);
+
+/* p_out (device, n*K floats) = the network applied to given inputs x (device,
+ * n*64 BF16 patterns, 16-byte aligned) and lp (device, n*K floats).  Enqueued
+ * on `stream`. */
+glint_status glint_mlp_forward(const glint_mlp *mlp, const uint16_t *x, const float *lp, long n, float *p_out,
+                               void *stream);
+
+/* One optimisation step on samples first, first+1, ..., first+batch-1 (indices
+ * modulo n_total) of the inputs x, lp (as glint_mlp_forward) against
+ * `targets` (device, n_total*K floats, each row a distribution).  lr = 0 only
+ * computes the gradient (GLINT_MLP_GRAD); 0 < lr < 1 also takes an Adam step.
+ * If loss_out is not NULL the batch's mean cross-entropy is written there
+ * (host) and the call waits for the stream.  Enqueued on `stream`. */
+glint_status glint_mlp_train_step(glint_mlp *mlp, const uint16_t *x, const float *lp, const float *targets,
+                                  long n_total, long first, long batch, float lr, float *loss_out, void *stream);
+
+/* p_out (device, width*height*K floats) = the network's p_k of every pixel of
+ * `gbuf` under `env` (inputs computed on the fly, one persistent launch);
+ * background pixels get 0.  The network's K must equal the environment's.
+ * Enqueued on `stream`. */
+glint_status glint_mlp_infer(const glint_mlp *mlp, glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf,
+                             float *p_out, void *stream);
+
+int glint_mlp_get_k(const glint_mlp *mlp);
+int glint_mlp_last_launches(const glint_mlp *mlp);
 
 /* Standard normal quantile z = Phi^-1(p) as the shading kernel evaluates it for
  * the Gaussian part of the dual-gated draw (Alg. 1): for n device floats p in

@@ -91,9 +91,11 @@ def _load():
         lib.or_prefilter.argtypes = [P, I, I, I, P, P, I, I, P, P, L, P]
         lib.or_prefilter_exact.argtypes = [P, I, I, I, D, P, L, P]
         lib.or_shade.argtypes = [P, L, P, I, P, I, D, D, P, I, P, I, U, I, P, I,
-                                 P, P, P, P, P, P, P, P, P, P, P, I, P, I, P, I, I, P]
+                                 P, P, P, P, P, P, P, P, P, P, P, I, P, I, P, I, I, P, P]
         lib.or_e2_pk.argtypes = [P, P, P, ctypes.c_float, ctypes.c_float, I, P, I, I, I, I, P]
         lib.or_e2_pk.restype = I
+        lib.or_mlp_features.argtypes = [P, P, L, P, I, P, I, D, D, P, I, I, P, P, P]
+        lib.or_mlp_features.restype = None
         lib.or_shade.restype = L
         lib.or_radiance.argtypes = [P, P, D, P, I, P, P, P]
         lib.or_multinomial.argtypes = [P, I, D, U, U, U, U, I, P]
@@ -316,7 +318,9 @@ def gbuffer_rows(planes) -> np.ndarray:
 
 def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab: np.ndarray, levels: np.ndarray,
           seed: int, integer_mode: bool = True, tie=TIE_DEFAULT, max_cand: int = 8, evaluator: int = 0,
-          tangents=None, e2_S: int = 16, env: "EnvOracle | None" = None) -> ShadeOracle:
+          tangents=None, e2_S: int = 16, env: "EnvOracle | None" = None, pk_in=None) -> ShadeOracle:
+    """Per-pixel shading (or_shade).  evaluator 0 = E1, 1 = E2 (needs tangents
+    and env), 2 = the p_k given in pk_in (npix x K)."""
     lib = _load()
     gb16 = np.ascontiguousarray(gb16, dtype=np.float32).reshape(-1, 16)
     n = gb16.shape[0]
@@ -340,13 +344,37 @@ def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab:
         H, W = env.ch0.shape[:2]
     else:
         tangents, mips, W, H = None, None, 0, 0
+    if evaluator == 2:
+        pk_in = np.ascontiguousarray(np.asarray(pk_in, np.float64).reshape(n, K))
+    else:
+        pk_in = None
     lib.or_shade(_ptr(gb16), n, _ptr(flat), R, _ptr(widths), C, float(s_min), float(s_max), _ptr(lut_tab), nlut,
                  _ptr(levels), K, ctypes.c_uint32(seed & 0xFFFFFFFF), int(integer_mode), _ptr(tie_a), max_cand,
                  _ptr(o.rgb), _ptr(o.lo), _ptr(o.pk), _ptr(o.np_), _ptr(o.vert), _ptr(o.wv), _ptr(o.nroot),
                  _ptr(o.ncand), _ptr(o.cand), _ptr(o.cand_err), _ptr(o.flags), int(evaluator),
                  None if tangents is None else _ptr(tangents), int(e2_S), None if mips is None else _ptr(mips), W, H,
-                 _ptr(o.e2_flags))
+                 _ptr(o.e2_flags), None if pk_in is None else _ptr(pk_in))
     return o
+
+
+def mlp_features(gb16: np.ndarray, tangents: np.ndarray, pref: Filtered, s_min: float, s_max: float,
+                 lut_tab: np.ndarray, K: int, want_dirs: bool = False):
+    """Inputs x (npix, 64) and log-priors lp (npix, K) of the p_k surrogate
+    (or_mlp_features), and with want_dirs the five tap directions (npix, 5, 3)."""
+    lib = _load()
+    gb16 = np.ascontiguousarray(gb16, dtype=np.float32).reshape(-1, 16)
+    n = gb16.shape[0]
+    tangents = np.ascontiguousarray(tangents, dtype=np.float32).reshape(-1, 4)
+    flat = np.ascontiguousarray(pref.flat, dtype=np.float64)
+    widths = np.ascontiguousarray(pref.widths, dtype=np.int32)
+    lut_tab = np.ascontiguousarray(lut_tab, dtype=np.float64)
+    x = np.zeros((n, 64))
+    lp = np.zeros((n, K))
+    dirs = np.zeros((n, 5, 3)) if want_dirs else None
+    lib.or_mlp_features(_ptr(gb16), _ptr(tangents), n, _ptr(flat), len(pref.widths), _ptr(widths), flat.shape[1],
+                        float(s_min), float(s_max), _ptr(lut_tab), lut_tab.shape[0], K, _ptr(x), _ptr(lp),
+                        None if dirs is None else _ptr(dirs))
+    return (x, lp, dirs) if want_dirs else (x, lp)
 
 
 def e2_pk(wo, n, t, ax: float, ay: float, S: int, env: EnvOracle, K: int):

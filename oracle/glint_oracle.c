@@ -699,6 +699,101 @@ int or_e2_pk(const double wo[3], const double nn[3], const double tg[3], float a
 }
 
 /* --------------------------------------------------------------------------
+ * Inputs of the p_k surrogate (the learned part has no counterpart in the
+ * paper; this is the definition the library documents).  Per pixel row of
+ * the G-buffer (16 floats) and tangent (4 floats):
+ *   x[0..K)      p_k of E1 (Eq. rtiblndf: V W_k, p_1 = U + V W_1)
+ *   x[K..6K)     W_k of the filtered maps at roughness parameter
+ *                s = sqrt(min(a_x, a_y)) in five directions: w_r, then
+ *                normalize(w_r + a_x J_t), normalize(w_r - a_x J_t),
+ *                normalize(w_r + a_y J_b), normalize(w_r - a_y J_b), with
+ *                J_t = 2 (-(w_o.t) n - mu_o t) the derivative of the mirror
+ *                direction with respect to the slope along t (tangent made
+ *                orthogonal to n), J_b likewise for b = n x t
+ *   x[6K..6K+3)  mu_o, sqrt a_x, sqrt a_y;  x[6K+3..64) = 0
+ *   lp[k]        log max(p_k^E1, 1e-6)
+ * Background rows (N_0 <= 0) are all zero.  dirs (optional, npix x 5 x 3):
+ * the five unit directions.
+ * ------------------------------------------------------------------------ */
+static void filtered_at(const double *pref, int R, const int *widths, int C, double s_min, double s_max,
+                        double s, const double d[3], double *cc)
+{
+    double tl = (R > 1) ? (s - s_min) / (s_max - s_min) * (R - 1) : 0.0;
+    tl = fmin(fmax(tl, 0.0), (double)(R - 1));
+    int r0 = (int)floor(tl);
+    int r1 = r0 + 1 < R ? r0 + 1 : R - 1;
+    double ft = tl - r0;
+    size_t off0 = 0, off1 = 0;
+    for (int r = 0; r < r0; ++r) off0 += (size_t)widths[r] * (widths[r] / 2) * C;
+    for (int r = 0; r < r1; ++r) off1 += (size_t)widths[r] * (widths[r] / 2) * C;
+    double c0[3 + OR_MAXK], c1[3 + OR_MAXK];
+    env_bilinear(pref + off0, widths[r0], widths[r0] / 2, C, d, c0);
+    env_bilinear(pref + off1, widths[r1], widths[r1] / 2, C, d, c1);
+    for (int i = 0; i < C; ++i) cc[i] = (1.0 - ft) * c0[i] + ft * c1[i];
+}
+
+void or_mlp_features(const float *gb, const float *tangents, long npix, const double *pref, int R, const int *widths,
+                     int C, double s_min, double s_max, const double *lut, int nlut, int K, double *x, double *lp,
+                     double *dirs)
+{
+    for (long q = 0; q < npix; ++q) {
+        const float *g = gb + 16 * q;
+        double *xq = x + 64 * q;
+        for (int i = 0; i < 64; ++i) xq[i] = 0.0;
+        for (int k = 0; k < K; ++k) lp[q * K + k] = 0.0;
+        if (!(g[3] > 0.0f)) continue;
+        double wo[3] = {g[0], g[1], g[2]}, n[3] = {g[4], g[5], g[6]};
+        double ax = g[10], ay = g[11];
+        double mu = n[0] * wo[0] + n[1] * wo[1] + n[2] * wo[2];
+        double wr[3];
+        for (int i = 0; i < 3; ++i) wr[i] = 2.0 * mu * n[i] - wo[i];
+        /* E1 */
+        double s_iso = sqrt(sqrt(ax * ay));
+        double tab[4], cc[3 + OR_MAXK];
+        lut_fetch(lut, nlut, fmin(fmax(mu, 1e-4), 1.0), s_iso, tab);
+        filtered_at(pref, R, widths, C, s_min, s_max, s_iso, wr, cc);
+        xq[0] = tab[1] + tab[0] * cc[3];
+        for (int k = 1; k < K; ++k) xq[k] = tab[0] * cc[3 + k];
+        for (int k = 0; k < K; ++k) lp[q * K + k] = log(fmax(xq[k], 1e-6));
+        /* lobe axes */
+        const float *tg = tangents + 4 * q;
+        double tn = tg[0] * n[0] + tg[1] * n[1] + tg[2] * n[2];
+        double t[3] = {tg[0] - tn * n[0], tg[1] - tn * n[1], tg[2] - tn * n[2]};
+        double tl = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        for (int i = 0; i < 3; ++i) t[i] /= tl;
+        double b[3] = {n[1] * t[2] - n[2] * t[1], n[2] * t[0] - n[0] * t[2], n[0] * t[1] - n[1] * t[0]};
+        double ot = wo[0] * t[0] + wo[1] * t[1] + wo[2] * t[2];
+        double ob = wo[0] * b[0] + wo[1] * b[1] + wo[2] * b[2];
+        double Jt[3], Jb[3];
+        for (int i = 0; i < 3; ++i) {
+            Jt[i] = 2.0 * (-ot * n[i] - mu * t[i]);
+            Jb[i] = 2.0 * (-ob * n[i] - mu * b[i]);
+        }
+        double s_tap = sqrt(fmin(ax, ay));
+        for (int tap = 0; tap < 5; ++tap) {
+            double d[3];
+            for (int i = 0; i < 3; ++i) {
+                double off = 0.0;
+                if (tap == 1) off = ax * Jt[i];
+                if (tap == 2) off = -ax * Jt[i];
+                if (tap == 3) off = ay * Jb[i];
+                if (tap == 4) off = -ay * Jb[i];
+                d[i] = wr[i] + off;
+            }
+            double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            for (int i = 0; i < 3; ++i) d[i] /= dl;
+            if (dirs)
+                for (int i = 0; i < 3; ++i) dirs[(q * 5 + tap) * 3 + i] = d[i];
+            filtered_at(pref, R, widths, C, s_min, s_max, s_tap, d, cc);
+            for (int k = 0; k < K; ++k) xq[K + tap * K + k] = cc[3 + k];
+        }
+        xq[6 * K] = mu;
+        xq[6 * K + 1] = sqrt(ax);
+        xq[6 * K + 2] = sqrt(ay);
+    }
+}
+
+/* --------------------------------------------------------------------------
  * Per-pixel shading.
  * ------------------------------------------------------------------------ */
 
@@ -963,6 +1058,7 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
  *  - M_k = sum_i w_i n_k(i), L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k)
  *    (0 when the denominator is 0).
  *
+ * evaluator = 2 takes p_k from pk_in (npix x K) as given.
  * evaluator = 1 replaces p_k by the E2 quadrature (or_e2_pk) of the
  * anisotropic footprint, with per-pixel tangents (npix x 4) and the pyramid
  * (mips, W x H level 0); e2_flags counts its near-boundary points.
@@ -977,7 +1073,8 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
               double s_max, const double *lut, int nlut, const double *L, int K, uint32_t seed, int integer_mode,
               const double *tie, int max_cand, double *rgb, double *lo, double *pk, float *np, int64_t *vert,
               double *wv, double *nroot, int32_t *ncand, double *cand, double *cand_err, int32_t *flags,
-              int evaluator, const float *tangents, int e2_S, const double *mips, int W, int H, int32_t *e2_flags)
+              int evaluator, const float *tangents, int e2_S, const double *mips, int W, int H, int32_t *e2_flags,
+              const double *pk_in)
 {
     long nbg = 0;
     for (long q = 0; q < npix; ++q) {
@@ -1029,6 +1126,8 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
         } else if (e2_flags) {
             e2_flags[q] = 0;
         }
+        if (evaluator == 2)
+            for (int k = 0; k < K; ++k) p[k] = pk_in[q * K + k];
         for (int c = 0; c < 3; ++c) lo[3 * q + c] = Lo[c];
         for (int k = 0; k < K; ++k) pk[q * K + k] = p[k];
 

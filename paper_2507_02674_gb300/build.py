@@ -1,6 +1,6 @@
 """Builds the CUDA library ``libglint.so`` in-tree for sm_103a (GB300).
 
-The four translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 ``paper_2507_02674_gb300/libglint.so``; object files go to ``_build/``.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libglint.so")
-SOURCES = ["glint_api.cu", "glint_lut.cu", "glint_env.cu", "glint_shade.cu", "glint_noalloc.cu"]
+SOURCES = ["glint_api.cu", "glint_lut.cu", "glint_env.cu", "glint_shade.cu", "glint_noalloc.cu", "glint_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

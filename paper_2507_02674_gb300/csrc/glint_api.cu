@@ -309,48 +309,105 @@ void glint_env_destroy(glint_env *env) {
     delete env;
 }
 
-glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g, const glint_params *p,
-                         float *out_rgba, const glint_debug *dbg, void *stream) {
-    g_err[0] = 0;
-    if (!ctx || !env || !g || !p) { set_error("glint_shade: NULL argument"); return GLINT_ERR_INVALID_ARG; }
-    if (env->ctx != ctx) { set_error("glint_shade: environment belongs to another context"); return GLINT_ERR_INVALID_ARG; }
+// Checks shared by glint_shade and glint_reflect_probs.
+static glint_status check_shade_args(const char *who, glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
+                                     const glint_params *p, const void *out) {
+    if (!ctx || !env || !g || !p) { set_error("%s: NULL argument", who); return GLINT_ERR_INVALID_ARG; }
+    if (env->ctx != ctx) { set_error("%s: environment belongs to another context", who); return GLINT_ERR_INVALID_ARG; }
     if (g->width < 0 || g->height < 0 || (long)g->width * g->height > (1L << 31)) {
-        set_error("glint_shade: width %d x height %d out of range", g->width, g->height);
+        set_error("%s: width %d x height %d out of range", who, g->width, g->height);
         return GLINT_ERR_INVALID_ARG;
     }
     if (p->count_mode != GLINT_COUNT_INTEGER && p->count_mode != GLINT_COUNT_REAL) {
-        set_error("glint_shade: unknown count mode %d", p->count_mode);
+        set_error("%s: unknown count mode %d", who, p->count_mode);
         return GLINT_ERR_INVALID_ARG;
     }
-    if (p->evaluator != GLINT_EVAL_E1 && p->evaluator != GLINT_EVAL_E2) {
-        set_error("glint_shade: unknown evaluator %d", p->evaluator);
+    if (p->evaluator != GLINT_EVAL_E1 && p->evaluator != GLINT_EVAL_E2 && p->evaluator != GLINT_EVAL_MLP &&
+        p->evaluator != GLINT_EVAL_GIVEN) {
+        set_error("%s: unknown evaluator %d", who, p->evaluator);
         return GLINT_ERR_INVALID_ARG;
     }
     if (p->evaluator == GLINT_EVAL_E2 && (p->e2_samples < 0 || p->e2_samples > 256)) {
-        set_error("glint_shade: e2_samples %d outside [0, 256]", p->e2_samples);
+        set_error("%s: e2_samples %d outside [0, 256]", who, p->e2_samples);
         return GLINT_ERR_INVALID_ARG;
+    }
+    if (p->evaluator == GLINT_EVAL_MLP) {
+        if (!p->mlp) { set_error("%s: the MLP evaluator needs params->mlp", who); return GLINT_ERR_INVALID_ARG; }
+        if (glint_mlp_k(p->mlp) != env->d.K) {
+            set_error("%s: network K %d differs from the environment's %d", who, glint_mlp_k(p->mlp), env->d.K);
+            return GLINT_ERR_INVALID_ARG;
+        }
+        if (glint_mlp_device(p->mlp) != ctx->device) {
+            set_error("%s: network lives on another device", who);
+            return GLINT_ERR_INVALID_ARG;
+        }
     }
     const long npix = (long)g->width * g->height;
     if (npix > 0) {
-        if (!g->view_n0 || !g->normal_f0 || !g->uv_alpha || !g->duv || !out_rgba) {
-            set_error("glint_shade: NULL G-buffer plane or output");
+        if (!g->view_n0 || !g->normal_f0 || !g->uv_alpha || !out) {
+            set_error("%s: NULL G-buffer plane or output", who);
             return GLINT_ERR_INVALID_ARG;
         }
         if (!aligned16(g->view_n0) || !aligned16(g->normal_f0) || !aligned16(g->uv_alpha) || !aligned16(g->duv) ||
-            !aligned16(out_rgba) || !aligned16(g->tangent)) {
-            set_error("glint_shade: G-buffer planes and output must be 16-byte aligned");
+            !aligned16(g->tangent)) {
+            set_error("%s: G-buffer planes must be 16-byte aligned", who);
             return GLINT_ERR_INVALID_ARG;
         }
-        if (p->evaluator == GLINT_EVAL_E2 && !g->tangent) {
-            set_error("glint_shade: the E2 evaluator needs the tangent plane");
+        if ((p->evaluator == GLINT_EVAL_E2 || p->evaluator == GLINT_EVAL_MLP) && !g->tangent) {
+            set_error("%s: the E2 and MLP evaluators need the tangent plane", who);
+            return GLINT_ERR_INVALID_ARG;
+        }
+    }
+    return GLINT_OK;
+}
+
+glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g, const glint_params *p,
+                         float *out_rgba, const glint_debug *dbg, void *stream) {
+    g_err[0] = 0;
+    glint_status st = check_shade_args("glint_shade", ctx, env, g, p, out_rgba);
+    if (st != GLINT_OK) return st;
+    const long npix = (long)g->width * g->height;
+    if (npix > 0) {
+        if (!g->duv) { set_error("glint_shade: NULL duv plane"); return GLINT_ERR_INVALID_ARG; }
+        if (!aligned16(out_rgba)) { set_error("glint_shade: output must be 16-byte aligned"); return GLINT_ERR_INVALID_ARG; }
+        if ((p->evaluator == GLINT_EVAL_MLP || p->evaluator == GLINT_EVAL_GIVEN) &&
+            (!p->p_scratch || ((uintptr_t)p->p_scratch & 3u))) {
+            set_error("glint_shade: the MLP and GIVEN evaluators need params->p_scratch (width*height*K floats)");
             return GLINT_ERR_INVALID_ARG;
         }
     }
     DeviceGuard guard(ctx->device);
     int nl = 0;
-    glint_status st = cuda_status(glint_launch_shade(ctx, env, g, p, out_rgba, dbg, (cudaStream_t)stream, &nl),
-                                  "glint_shade");
-    ctx->last_launches = nl;
+    const float *pk_in = nullptr;
+    if (p->evaluator == GLINT_EVAL_MLP && npix > 0) {
+        st = cuda_status(glint_launch_mlp_infer(ctx, env, p->mlp, g, p->p_scratch, (cudaStream_t)stream), "glint_shade: MLP");
+        if (st != GLINT_OK) return st;
+        pk_in = p->p_scratch;
+    } else if (p->evaluator == GLINT_EVAL_GIVEN) {
+        pk_in = p->p_scratch;
+    }
+    st = cuda_status(glint_launch_shade(ctx, env, g, p, pk_in, out_rgba, dbg, (cudaStream_t)stream, &nl),
+                     "glint_shade");
+    ctx->last_launches = nl + (p->evaluator == GLINT_EVAL_MLP && npix > 0 ? 1 : 0);
+    return st;
+}
+
+glint_status glint_reflect_probs(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
+                                 const glint_params *p, float *p_out, void *stream) {
+    g_err[0] = 0;
+    glint_status st = check_shade_args("glint_reflect_probs", ctx, env, g, p, p_out);
+    if (st != GLINT_OK) return st;
+    if (((uintptr_t)p_out & 3u)) { set_error("glint_reflect_probs: p_out misaligned"); return GLINT_ERR_INVALID_ARG; }
+    if (p->evaluator == GLINT_EVAL_GIVEN) {
+        set_error("glint_reflect_probs: the GIVEN evaluator has nothing to compute");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    if (p->evaluator == GLINT_EVAL_MLP)
+        st = cuda_status(glint_launch_mlp_infer(ctx, env, p->mlp, g, p_out, (cudaStream_t)stream), "glint_reflect_probs");
+    else
+        st = cuda_status(glint_launch_probs(ctx, env, g, p, p_out, (cudaStream_t)stream), "glint_reflect_probs");
+    ctx->last_launches = (long)g->width * g->height > 0 ? 1 : 0;
     return st;
 }
 

@@ -126,6 +126,15 @@ cudaError_t glint_launch_lut(float4 *lut, int n, int q, cudaStream_t s);
 cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s, int *launches);
 cudaError_t glint_launch_filter_table(glint_env *env, cudaStream_t s);
 cudaError_t glint_launch_quantile(const float *p, float *z, long n, cudaStream_t s);
+// The MLP surrogate (glint_mlp.cu): p_k of every pixel of `g` into p (npix x K).
+cudaError_t glint_launch_mlp_infer(const glint_ctx *ctx, const glint_env *env, const glint_mlp *m,
+                                   const glint_gbuffer *g, float *p, cudaStream_t s);
+int glint_mlp_k(const glint_mlp *m);
+int glint_mlp_device(const glint_mlp *m);
+// p_k only (E1 or E2), background pixels 0.
+cudaError_t glint_launch_probs(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
+                               const glint_params *p, float *p_out, cudaStream_t s);
+// pk_in: p_k per pixel (npix x K) to use instead of E1/E2, or NULL.
 cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
-                               const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s,
-                               int *launches);
+                               const glint_params *p, const float *pk_in, float *out, const glint_debug *dbg,
+                               cudaStream_t s, int *launches);

@@ -1,0 +1,924 @@
+// BF16 MLP surrogate of the per-component reflection probabilities p_k
+// (the NDF mass of Eq. probhk that the E2 quadrature computes), trained and
+// evaluated on the tensor cores with FP32 accumulation.
+//
+// Network: 64 inputs (glint_probs.cuh: E1's p_k, the filtered weights W_k at
+// five taps across the anisotropic lobe, mu_o, sqrt a_x, sqrt a_y) -> 64 ->
+// 64 -> K, ReLU, and p = softmax(logits + log max(p^E1, 1e-6)): the network
+// learns a correction of E1 towards the anisotropic integral.  Parameters
+// (FP32 master copy, `glint_mlp_param_count` floats):
+//   W1 [64 in][64 out], b1[64], W2 [64][64], b2[64], W3 [64][16] (columns >= K
+//   unused), b3[16].
+// The tensor-core copies are BF16 in both layouts: W^T [out][in] for the
+// forward pass (B fragments read (k, k+1) pairs contiguously) and W [in][out]
+// for the backward pass.
+//
+// Tensor cores: warp-level mma.sync.m16n8k16 (BF16 in, FP32 accumulate).  A
+// layer for a 16-row tile is 4 k-steps x (out/8) n-tiles; the FP32
+// accumulator fragments of two adjacent n-tiles are exactly the A fragment of
+// the next layer's k-step, so activations stay in registers between layers
+// (ReLU and BF16 rounding applied on the way).  The inference and forward
+// kernels are persistent: each block stages the weights in shared memory once
+// and loops over 128-row tiles.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "glint_internal.cuh"
+#include "glint_probs.cuh"
+
+using namespace glint;
+
+namespace {
+
+constexpr int kIn = 64;
+constexpr int kHid = 64;
+constexpr int kOutPad = 16;
+constexpr int kP = kIn * kHid + kHid + kHid * kHid + kHid + kHid * kOutPad + kOutPad;  // 9360
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kIn * kHid, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid,
+              kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kOutPad;
+constexpr int kNT = 128;  // threads (samples) per block
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ uint32_t pair16(const __nv_bfloat16 *lo, const __nv_bfloat16 *hi) {
+    const uint32_t a = *reinterpret_cast<const uint16_t *>(lo);
+    const uint32_t b = *reinterpret_cast<const uint16_t *>(hi);
+    return a | (b << 16);
+}
+
+// Every [rows][64] BF16 tile in shared memory (inputs, activations,
+// backpropagated signals and the 64-wide weight matrices) is stored with its
+// eight 16-byte chunks per row permuted by chunk ^ (row & 7): the fragment
+// loads of mma.sync (8 consecutive rows x 4 words, or 8 rows apart in the
+// transposed gradient reads) then hit 32 distinct banks.
+__device__ __forceinline__ int word_at(int r, int w) {
+    return r * 32 + ((((w >> 2) ^ (r & 7)) << 2) | (w & 3));
+}
+__device__ __forceinline__ const __nv_bfloat16 *el(const __nv_bfloat16 *m, int r, int c) {
+    return m + 2 * word_at(r, c >> 1) + (c & 1);
+}
+__device__ __forceinline__ uint32_t wd(const __nv_bfloat16 *m, int r, int w) {
+    return reinterpret_cast<const uint32_t *>(m)[word_at(r, w)];
+}
+
+// Copy a row-major [rows][64] BF16 matrix from global memory into the
+// swizzled layout.
+__device__ __forceinline__ void copy_swz(__nv_bfloat16 *dst, const __nv_bfloat16 *src, int rows) {
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+    for (int i = threadIdx.x; i < rows * 32; i += blockDim.x) d32[word_at(i >> 5, i & 31)] = s32[i];
+}
+
+struct SmemW {
+    __nv_bfloat16 w1t[kHid * kIn], w2t[kHid * kHid], w3t[kOutPad * kHid];  // [out][in]
+    float b1[kHid], b2[kHid], b3[kOutPad];
+};
+struct SmemWB {
+    __nv_bfloat16 w2[kHid * kHid], w3[kHid * kOutPad];  // [in][out] (backward)
+};
+
+__device__ void load_weights(SmemW &s, const __nv_bfloat16 *wt, const float *params) {
+    copy_swz(s.w1t, wt, kHid);
+    copy_swz(s.w2t, wt + kHid * kIn, kHid);
+    copy_swz(s.w3t, wt + kHid * kIn + kHid * kHid, kOutPad);
+    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+        s.b1[i] = params[kOffB1 + i];
+        s.b2[i] = params[kOffB2 + i];
+    }
+    for (int i = threadIdx.x; i < kOutPad; i += blockDim.x) s.b3[i] = params[kOffB3 + i];
+}
+
+// One layer for a warp's 16-row tile: c[j] = bias + A (16 x 64) W^T[j-th 8 columns].
+template <int NT>
+__device__ __forceinline__ void layer_fwd(const uint32_t a[4][4], const __nv_bfloat16 *wt, const float *bias,
+                                          float c[NT][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        c[j][0] = c[j][2] = bias[j * 8 + 2 * t];
+        c[j][1] = c[j][3] = bias[j * 8 + 2 * t + 1];
+    }
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            mma16816(c[j], a[ks], wd(wt, j * 8 + g, ks * 8 + t), wd(wt, j * 8 + g, ks * 8 + t + 4));
+        }
+    }
+}
+
+// ReLU, BF16 rounding, and the accumulators of n-tiles (2ks, 2ks+1) as the A
+// fragment of k-step ks.
+__device__ __forceinline__ void relu_to_a(const float c[8][4], uint32_t a[4][4]) {
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        a[ks][0] = pack_bf16(fmaxf(c[2 * ks][0], 0.f), fmaxf(c[2 * ks][1], 0.f));
+        a[ks][1] = pack_bf16(fmaxf(c[2 * ks][2], 0.f), fmaxf(c[2 * ks][3], 0.f));
+        a[ks][2] = pack_bf16(fmaxf(c[2 * ks + 1][0], 0.f), fmaxf(c[2 * ks + 1][1], 0.f));
+        a[ks][3] = pack_bf16(fmaxf(c[2 * ks + 1][2], 0.f), fmaxf(c[2 * ks + 1][3], 0.f));
+    }
+}
+
+// A fragments of a 16-row tile of a row-major [rows][64] BF16 matrix in smem.
+__device__ __forceinline__ void load_a(const __nv_bfloat16 *m, int row0, uint32_t a[4][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+        a[ks][0] = wd(m, row0 + g, ks * 8 + t);
+        a[ks][1] = wd(m, row0 + g + 8, ks * 8 + t);
+        a[ks][2] = wd(m, row0 + g, ks * 8 + t + 4);
+        a[ks][3] = wd(m, row0 + g + 8, ks * 8 + t + 4);
+    }
+}
+
+// Store the (ReLU'd, BF16) accumulators of a 16-row tile to smem [rows][64].
+__device__ __forceinline__ void store_c_bf16(__nv_bfloat16 *m, int row0, const float c[8][4], bool relu) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float v0 = c[j][0], v1 = c[j][1], v2 = c[j][2], v3 = c[j][3];
+        if (relu) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); v2 = fmaxf(v2, 0.f); v3 = fmaxf(v3, 0.f); }
+        uint32_t *w = reinterpret_cast<uint32_t *>(m);
+        w[word_at(row0 + g, j * 4 + t)] = pack_bf16(v0, v1);
+        w[word_at(row0 + g + 8, j * 4 + t)] = pack_bf16(v2, v3);
+    }
+}
+
+// Softmax over the K logits plus log-prior (lp: smem [rows][16]) of each row
+// of a 16-row tile (cols >= K ignored); the 8 (or 16) logits of a row live in
+// the 4 lanes of its quad.
+template <int NT>
+__device__ __forceinline__ void softmax_rows(float c[NT][4], int K, const float *lp, int row0) {
+    const int t = threadIdx.x & 3, g = (threadIdx.x & 31) >> 2;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // rows g and g + 8
+        const float *lr = lp + (row0 + g + 8 * h) * kOutPad;
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (j * 8 + 2 * t + e < K) c[j][2 * h + e] += lr[j * 8 + 2 * t + e];
+        float mx = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (j * 8 + 2 * t + e < K) mx = fmaxf(mx, c[j][2 * h + e]);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+        float sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const bool ok = j * 8 + 2 * t + e < K;
+                const float v = ok ? expf(c[j][2 * h + e] - mx) : 0.f;
+                c[j][2 * h + e] = v;
+                sum += v;
+            }
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        const float inv = 1.f / sum;
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            c[j][2 * h] *= inv;
+            c[j][2 * h + 1] *= inv;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ inference
+// Shared memory of the inference kernels: weights, one 128-row input tile
+// (swizzled) and its log-priors.
+struct SmemInfer {
+    SmemW w;
+    __align__(16) __nv_bfloat16 xs[kNT * 64];
+    float lp[kNT * kOutPad];
+    int fg[kNT];
+};
+
+// Network on the staged tile: rows [0, 128) of xs/lp; p of live rows to
+// p_out[(base + r) K + k] (0 where fg[r] == 0).
+template <int NT>
+__device__ __forceinline__ void net_tile(const SmemInfer &sm, long base, long n, int K, float *__restrict__ p_out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+        const int row0 = warp * 32 + mt * 16;
+        uint32_t a[4][4];
+        float c[8][4];
+        load_a(sm.xs, row0, a);
+        layer_fwd<8>(a, sm.w.w1t, sm.w.b1, c);
+        relu_to_a(c, a);
+        layer_fwd<8>(a, sm.w.w2t, sm.w.b2, c);
+        relu_to_a(c, a);
+        float o[NT][4];
+        layer_fwd<NT>(a, sm.w.w3t, sm.w.b3, o);
+        softmax_rows<NT>(o, K, sm.lp, row0);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = row0 + g + 8 * h;
+            const long i = base + r;
+            if (i >= n) continue;
+            const bool fg = sm.fg[r] != 0;
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int col = j * 8 + 2 * t + e;
+                    if (col < K) p_out[i * K + col] = fg ? o[j][2 * h + e] : 0.f;
+                }
+        }
+    }
+}
+
+// Write one row of inputs (64 floats, rounded to BF16) and its log-prior.
+template <int K>
+__device__ __forceinline__ void stage_row(SmemInfer &sm, int r, const float *x, const float *lp, bool fg) {
+    uint4 *x4 = reinterpret_cast<uint4 *>(sm.xs);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (fg)
+            v = make_uint4(pack_bf16(x[8 * q], x[8 * q + 1]), pack_bf16(x[8 * q + 2], x[8 * q + 3]),
+                           pack_bf16(x[8 * q + 4], x[8 * q + 5]), pack_bf16(x[8 * q + 6], x[8 * q + 7]));
+        x4[r * 8 + (q ^ (r & 7))] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < kOutPad; ++k) sm.lp[r * kOutPad + k] = (fg && k < K) ? lp[k] : 0.f;
+    sm.fg[r] = fg ? 1 : 0;
+}
+
+// p of given inputs: x (n x 64 BF16, row-major), lp (n x K).  Persistent.
+template <int NT>
+__global__ void __launch_bounds__(kNT) k_mlp_forward(const uint4 *__restrict__ x, const float *__restrict__ lp, long n,
+                                                     int K, const __nv_bfloat16 *__restrict__ wt,
+                                                     const float *__restrict__ params, float *__restrict__ p_out) {
+    __shared__ SmemInfer sm;
+    load_weights(sm.w, wt, params);
+    const long ntiles = (n + kNT - 1) / kNT;
+#pragma unroll 1
+    for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long base = tile * kNT;
+        __syncthreads();  // the previous tile's readers are done
+        uint4 *x4 = reinterpret_cast<uint4 *>(sm.xs);
+        // 128 rows x 8 uint4: consecutive threads read consecutive 16-byte pieces
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int idx = it * kNT + threadIdx.x;
+            const int r = idx >> 3, q = idx & 7;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (base + r < n) v = __ldg(x + (base + r) * 8 + q);
+            x4[r * 8 + (q ^ (r & 7))] = v;
+        }
+        for (int idx = threadIdx.x; idx < kNT * kOutPad; idx += kNT) {
+            const int r = idx / kOutPad, k = idx % kOutPad;
+            sm.lp[idx] = (base + r < n && k < K) ? __ldg(lp + (base + r) * K + k) : 0.f;
+        }
+        sm.fg[threadIdx.x] = 1;
+        __syncthreads();
+        net_tile<NT>(sm, base, n, K, p_out);
+    }
+}
+
+// Features and network fused: p of every pixel of a G-buffer (background 0).
+template <int K>
+__global__ void __launch_bounds__(kNT) k_mlp_infer(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
+                                                   const float *__restrict__ params, float *__restrict__ p_out) {
+    __shared__ SmemInfer sm;
+    load_weights(sm.w, wt, params);
+    const long ntiles = (a.npix + kNT - 1) / kNT;
+#pragma unroll 1
+    for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long base = tile * kNT;
+        const long q = base + threadIdx.x;
+        float x[kMlpIn], lp[K];
+        bool fg = false;
+        if (q < a.npix) {
+            const float4 g0 = ldg4(a.view_n0 + q);
+            fg = g0.w > 0.f;
+            if (fg) mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), x, lp);
+        }
+        __syncthreads();  // the previous tile's readers are done
+        stage_row<K>(sm, threadIdx.x, x, lp, fg);
+        __syncthreads();
+        net_tile<(K > 8 ? 2 : 1)>(sm, base, a.npix, K, p_out);
+    }
+}
+
+// Inputs of every pixel: x (n x 64 BF16, background rows 0), lp (n x K).
+template <int K>
+__global__ void __launch_bounds__(kNT) k_mlp_features(ShadeArgs a, uint4 *__restrict__ x, float *__restrict__ lp) {
+    const long q = (long)blockIdx.x * kNT + threadIdx.x;
+    if (q >= a.npix) return;
+    float f[kMlpIn], l[K];
+    const float4 g0 = ldg4(a.view_n0 + q);
+    const bool fg = g0.w > 0.f;
+    if (fg) {
+        mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), f, l);
+    } else {
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) f[i] = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) l[k] = 0.f;
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v)
+        x[q * 8 + v] = make_uint4(pack_bf16(f[8 * v], f[8 * v + 1]), pack_bf16(f[8 * v + 2], f[8 * v + 3]),
+                                  pack_bf16(f[8 * v + 4], f[8 * v + 5]), pack_bf16(f[8 * v + 6], f[8 * v + 7]));
+#pragma unroll
+    for (int k = 0; k < K; ++k) lp[q * K + k] = l[k];
+}
+
+// ------------------------------------------------------------------ training
+// Forward and backward over chunks of 128 samples.  Block b handles chunks
+// b, b + G, b + 2G, ... (G = gridDim.x) of the batch and accumulates its
+// gradient (each sample's loss weighted by 1/batch) in partial[b][kP], always
+// in the same order, so the result does not depend on scheduling; its summed
+// cross-entropy goes to loss[b].
+template <int NT>
+__global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, const float *__restrict__ lpg,
+                                                  const float *__restrict__ targets, long n_total, long first,
+                                                  long batch, int K, const __nv_bfloat16 *__restrict__ wt,
+                                                  const __nv_bfloat16 *__restrict__ wb,
+                                                  const float *__restrict__ params, float *__restrict__ partial,
+                                                  float *__restrict__ loss) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemW &sw = *reinterpret_cast<SmemW *>(smem_raw);
+    SmemWB &sb = *reinterpret_cast<SmemWB *>(smem_raw + sizeof(SmemW));
+    __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(smem_raw + sizeof(SmemW) + sizeof(SmemWB));
+    __nv_bfloat16 *h1 = xs + kNT * 64;
+    __nv_bfloat16 *h2 = h1 + kNT * 64;     // H2, later dZ1
+    __nv_bfloat16 *dz = h2 + kNT * 64;     // dZ2
+    __nv_bfloat16 *dz3 = dz + kNT * 64;    // [kNT][16]
+    float *red = reinterpret_cast<float *>(dz3 + kNT * 16);  // kNT floats
+    float *lps = red + kNT;                                   // [kNT][16] log-priors
+
+    load_weights(sw, wt, params);
+    copy_swz(sb.w2, wb, kHid);
+    for (int i = threadIdx.x; i < kHid * kOutPad; i += kNT) sb.w3[i] = wb[kHid * kHid + i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float invB = 1.f / (float)batch;
+    const long nchunks = (batch + kNT - 1) / kNT;
+    float *part = partial + (size_t)blockIdx.x * kP;
+    float lsum = 0.f;
+
+    // dst (+)= A^T dZ over the chunk's samples: M = inputs (warp w owns rows
+    // [16 w, 16 w + 16)), N = outputs, K = samples
+    auto grad_w = [&](const __nv_bfloat16 *act, const __nv_bfloat16 *dzm, int ldz, int ntiles, float *dst, int ldo,
+                      bool acc) {
+        const int m0 = warp * 16;
+#pragma unroll 1
+        for (int j = 0; j < ntiles; ++j) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+            for (int ks = 0; ks < kNT / 16; ++ks) {
+                const int k0 = ks * 16 + 2 * t;
+                uint32_t a[4];
+                a[0] = pair16(el(act, k0, m0 + g), el(act, k0 + 1, m0 + g));
+                a[1] = pair16(el(act, k0, m0 + g + 8), el(act, k0 + 1, m0 + g + 8));
+                a[2] = pair16(el(act, k0 + 8, m0 + g), el(act, k0 + 9, m0 + g));
+                a[3] = pair16(el(act, k0 + 8, m0 + g + 8), el(act, k0 + 9, m0 + g + 8));
+                uint32_t b0, b1;
+                if (ldz == 64) {  // swizzled [rows][64]
+                    b0 = pair16(el(dzm, k0, j * 8 + g), el(dzm, k0 + 1, j * 8 + g));
+                    b1 = pair16(el(dzm, k0 + 8, j * 8 + g), el(dzm, k0 + 9, j * 8 + g));
+                } else {
+                    b0 = pair16(dzm + (k0) * ldz + j * 8 + g, dzm + (k0 + 1) * ldz + j * 8 + g);
+                    b1 = pair16(dzm + (k0 + 8) * ldz + j * 8 + g, dzm + (k0 + 9) * ldz + j * 8 + g);
+                }
+                mma16816(c, a, b0, b1);
+            }
+            const int col = j * 8 + 2 * t;
+            float *d0 = dst + (m0 + g) * ldo + col, *d1 = dst + (m0 + g + 8) * ldo + col;
+            if (acc) { c[0] += d0[0]; c[1] += d0[1]; c[2] += d1[0]; c[3] += d1[1]; }
+            d0[0] = c[0]; d0[1] = c[1]; d1[0] = c[2]; d1[1] = c[3];
+        }
+    };
+    // column sums of a [kNT][ld] BF16 matrix into dst (+)= (one thread per column)
+    auto col_sum = [&](const __nv_bfloat16 *m, int ld, int col, float *dst, bool acc) {
+        float s = 0.f;
+        for (int r = 0; r < kNT; ++r) s += __bfloat162float(ld == 64 ? *el(m, r, col) : m[r * ld + col]);
+        *dst = acc ? *dst + s : s;
+    };
+
+#pragma unroll 1
+    for (long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const bool acc = chunk != (long)blockIdx.x;
+        const long base = first + chunk * kNT;  // samples [base, base + kNT) of the data set, wrapping
+        const long nb = first + batch;
+        {
+            uint4 *xs4 = reinterpret_cast<uint4 *>(xs);
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const int idx = it * kNT + threadIdx.x;
+                const int r = idx >> 3, q = idx & 7;
+                const long i = base + r;
+                xs4[r * 8 + (q ^ (r & 7))] = (i < nb) ? __ldg(xg + (i % n_total) * 8 + q) : make_uint4(0u, 0u, 0u, 0u);
+            }
+            for (int idx = threadIdx.x; idx < kNT * kOutPad; idx += kNT) {
+                const int r = idx / kOutPad, k = idx % kOutPad;
+                const long i = base + r;
+                lps[idx] = (i < nb && k < K) ? __ldg(lpg + (i % n_total) * K + k) : 0.f;
+            }
+        }
+        __syncthreads();
+        // forward, and dZ3 = (softmax * sum(y) - y) / batch
+#pragma unroll 1
+        for (int mt = 0; mt < 2; ++mt) {
+            const int row0 = warp * 32 + mt * 16;
+            uint32_t a[4][4];
+            float c[8][4];
+            load_a(xs, row0, a);
+            layer_fwd<8>(a, sw.w1t, sw.b1, c);
+            store_c_bf16(h1, row0, c, true);
+            relu_to_a(c, a);
+            layer_fwd<8>(a, sw.w2t, sw.b2, c);
+            store_c_bf16(h2, row0, c, true);
+            relu_to_a(c, a);
+            float o[NT][4];
+            layer_fwd<NT>(a, sw.w3t, sw.b3, o);
+            softmax_rows<NT>(o, K, lps, row0);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = row0 + g + 8 * h;
+                const long i = base + r;
+                const bool live = i < nb;
+                const long s = live ? i % n_total : 0;
+                float y[2][2], ysum = 0.f;
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int col = j * 8 + 2 * t + e;
+                        y[j][e] = (live && col < K) ? __ldg(targets + s * K + col) : 0.f;
+                        ysum += y[j][e];
+                    }
+                ysum += __shfl_xor_sync(0xffffffffu, ysum, 1);
+                ysum += __shfl_xor_sync(0xffffffffu, ysum, 2);
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int col = j * 8 + 2 * t + e;
+                        float d = 0.f;
+                        if (live && col < K) {
+                            const float pv = o[j < NT ? j : 0][2 * h + e];
+                            d = (pv * ysum - y[j][e]) * invB;
+                            if (y[j][e] > 0.f) lsum -= y[j][e] * logf(fmaxf(pv, 1e-30f));
+                        }
+                        dz3[r * 16 + col] = __float2bfloat16_rn(d);
+                    }
+            }
+        }
+        __syncthreads();
+        // dZ2 = (dZ3 W3^T) * 1[H2 > 0]; W3 [in][out] gives (k, k+1) pairs
+#pragma unroll 1
+        for (int mt = 0; mt < 2; ++mt) {
+            const int row0 = warp * 32 + mt * 16;
+            uint32_t a[4];
+            {
+                const __nv_bfloat16 *r0 = dz3 + (row0 + g) * 16 + 2 * t;
+                const __nv_bfloat16 *r1 = dz3 + (row0 + g + 8) * 16 + 2 * t;
+                a[0] = ld32(r0); a[1] = ld32(r1); a[2] = ld32(r0 + 8); a[3] = ld32(r1 + 8);
+            }
+            float c[8][4];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+                const __nv_bfloat16 *row = sb.w3 + (j * 8 + g) * kOutPad + 2 * t;
+                mma16816(c[j], a, ld32(row), ld32(row + 8));
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = j * 8 + 2 * t;
+                if (!(__bfloat162float(*el(h2, row0 + g, col)) > 0.f)) c[j][0] = 0.f;
+                if (!(__bfloat162float(*el(h2, row0 + g, col + 1)) > 0.f)) c[j][1] = 0.f;
+                if (!(__bfloat162float(*el(h2, row0 + g + 8, col)) > 0.f)) c[j][2] = 0.f;
+                if (!(__bfloat162float(*el(h2, row0 + g + 8, col + 1)) > 0.f)) c[j][3] = 0.f;
+            }
+            store_c_bf16(dz, row0, c, false);
+        }
+        __syncthreads();
+        grad_w(h2, dz3, 16, 2, part + kOffW3, kOutPad, acc);
+        grad_w(h1, dz, 64, 8, part + kOffW2, kHid, acc);
+        if (threadIdx.x < kOutPad) col_sum(dz3, 16, threadIdx.x, part + kOffB3 + threadIdx.x, acc);
+        else if (threadIdx.x < kOutPad + kHid)
+            col_sum(dz, 64, threadIdx.x - kOutPad, part + kOffB2 + threadIdx.x - kOutPad, acc);
+        __syncthreads();
+        // dZ1 = (dZ2 W2^T) * 1[H1 > 0], written over H2
+#pragma unroll 1
+        for (int mt = 0; mt < 2; ++mt) {
+            const int row0 = warp * 32 + mt * 16;
+            uint32_t a[4][4];
+            load_a(dz, row0, a);
+            float c[8][4];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    mma16816(c[j], a[ks], wd(sb.w2, j * 8 + g, ks * 8 + t), wd(sb.w2, j * 8 + g, ks * 8 + t + 4));
+                }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = j * 8 + 2 * t;
+                if (!(__bfloat162float(*el(h1, row0 + g, col)) > 0.f)) c[j][0] = 0.f;
+                if (!(__bfloat162float(*el(h1, row0 + g, col + 1)) > 0.f)) c[j][1] = 0.f;
+                if (!(__bfloat162float(*el(h1, row0 + g + 8, col)) > 0.f)) c[j][2] = 0.f;
+                if (!(__bfloat162float(*el(h1, row0 + g + 8, col + 1)) > 0.f)) c[j][3] = 0.f;
+            }
+            store_c_bf16(h2, row0, c, false);
+        }
+        __syncthreads();
+        grad_w(xs, h2, 64, 8, part + kOffW1, kHid, acc);
+        if (threadIdx.x < kHid) col_sum(h2, 64, threadIdx.x, part + kOffB1 + threadIdx.x, acc);
+        __syncthreads();  // xs, h1, h2 and dz are rewritten by the next chunk
+    }
+    red[threadIdx.x] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int r = 0; r < kNT; ++r) s += red[r];
+        loss[blockIdx.x] = s;
+    }
+}
+
+// Sum the per-block gradients in block order (deterministic) into grad, then
+// (if lr > 0) one Adam step on the FP32 master copy and the BF16 copies.
+__global__ void k_mlp_reduce_adam(const float *__restrict__ partial, int nblk, float *__restrict__ grad,
+                                  float *__restrict__ params, float *__restrict__ m, float *__restrict__ v, int K, float lr,
+                                  float beta1, float beta2, float eps, float bc1, float bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kP) return;
+    // output columns >= K carry no parameters: no gradient, no update
+    const bool unused = (i >= kOffW3 && i < kOffB3 && (i - kOffW3) % kOutPad >= K) || (i >= kOffB3 && i - kOffB3 >= K);
+    if (unused) {
+        grad[i] = 0.f;
+        return;
+    }
+    float g = 0.f;
+    for (int b = 0; b < nblk; ++b) g += partial[(size_t)b * kP + i];
+    grad[i] = g;
+    if (!(lr > 0.f)) return;
+    const float mi = beta1 * m[i] + (1.f - beta1) * g;
+    const float vi = beta2 * v[i] + (1.f - beta2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float w = params[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    params[i] = w;
+}
+
+// BF16 copies of the weights in both layouts from the FP32 master copy.
+__global__ void k_mlp_refresh(const float *__restrict__ params, __nv_bfloat16 *__restrict__ wt,
+                              __nv_bfloat16 *__restrict__ wb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kIn * kHid) {  // W1: [in][out] -> wt [out][in]
+        const int in = i / kHid, out = i % kHid;
+        wt[out * kIn + in] = __float2bfloat16_rn(params[kOffW1 + i]);
+    } else if (i < kIn * kHid + kHid * kHid) {
+        const int k = i - kIn * kHid, in = k / kHid, out = k % kHid;
+        const __nv_bfloat16 w = __float2bfloat16_rn(params[kOffW2 + k]);
+        wt[kHid * kIn + out * kHid + in] = w;
+        wb[k] = w;
+    } else if (i < kIn * kHid + kHid * kHid + kHid * kOutPad) {
+        const int k = i - kIn * kHid - kHid * kHid, in = k / kOutPad, out = k % kOutPad;
+        const __nv_bfloat16 w = __float2bfloat16_rn(params[kOffW3 + k]);
+        wt[kHid * kIn + kHid * kHid + out * kHid + in] = w;
+        wb[kHid * kHid + k] = w;
+    }
+}
+
+// He-uniform initial weights from pcg4d(layer, index, seed, 0), zero biases.
+__global__ void k_mlp_init(float *__restrict__ params, uint32_t seed, int K) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kP) return;
+    int layer = -1, fan_in = 1, idx = i;
+    if (i < kOffB1) { layer = 1; fan_in = kIn; }
+    else if (i >= kOffW2 && i < kOffB2) { layer = 2; fan_in = kHid; idx = i - kOffW2; }
+    else if (i >= kOffW3 && i < kOffB3) { layer = 3; fan_in = kHid; idx = i - kOffW3; }
+    float w = 0.f;
+    if (layer > 0) {
+        const uint4 h = pcg4d(make_uint4((uint32_t)layer, (uint32_t)idx, seed, 0u));
+        const float u = hash_uniform(h.x) * 2.f - 1.f;
+        const float lim = sqrtf(6.f / (float)fan_in) * (layer == 1 ? 2.f : 1.f);
+        w = u * lim;
+        if (layer == 3 && (idx % kOutPad) >= K) w = 0.f;
+    }
+    params[i] = w;
+}
+
+}  // namespace
+
+struct glint_mlp {
+    glint_ctx *ctx = nullptr;
+    int K = 8;
+    long max_batch = 0;
+    int max_grid = 0;    // resident training blocks (rows of `partial`)
+    int infer_grid = 0;  // resident blocks of the persistent inference kernels
+    float *params = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *partial = nullptr, *loss = nullptr;
+    __nv_bfloat16 *wt = nullptr, *wb = nullptr;
+    long step = 0;
+    int last_launches = 0;
+};
+
+namespace {
+
+constexpr int kNW = kIn * kHid + kHid * kHid + kHid * kOutPad;  // weights (no biases)
+
+size_t grad_smem() {
+    return sizeof(SmemW) + sizeof(SmemWB) + sizeof(__nv_bfloat16) * (4 * kNT * 64 + kNT * 16) +
+           sizeof(float) * (kNT + kNT * kOutPad);
+}
+
+void mlp_free(glint_mlp *g) {
+    cudaFree(g->params); cudaFree(g->grad); cudaFree(g->m); cudaFree(g->v);
+    cudaFree(g->partial); cudaFree(g->loss); cudaFree(g->wt); cudaFree(g->wb);
+}
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+template <int K>
+void launch_features(const ShadeArgs &a, uint4 *x, float *lp, cudaStream_t s) {
+    k_mlp_features<K><<<(unsigned)((a.npix + kNT - 1) / kNT), kNT, 0, s>>>(a, x, lp);
+}
+
+}  // namespace
+
+cudaError_t glint_launch_mlp_infer(const glint_ctx *ctx, const glint_env *env, const glint_mlp *g,
+                                   const glint_gbuffer *smp, float *p_out, cudaStream_t s) {
+    glint_params prm{};
+    ShadeArgs a = make_args(ctx, env, smp, &prm);
+    if (a.npix == 0) return cudaSuccess;
+    const long ntiles = (a.npix + kNT - 1) / kNT;
+    const unsigned grid = (unsigned)std::min<long>(ntiles, g->infer_grid);
+    switch (g->K) {
+    case 2: k_mlp_infer<2><<<grid, kNT, 0, s>>>(a, g->wt, g->params, p_out); break;
+    case 4: k_mlp_infer<4><<<grid, kNT, 0, s>>>(a, g->wt, g->params, p_out); break;
+    case 8: k_mlp_infer<8><<<grid, kNT, 0, s>>>(a, g->wt, g->params, p_out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int glint_mlp_k(const glint_mlp *g) { return g ? g->K : 0; }
+int glint_mlp_device(const glint_mlp *g) { return g ? g->ctx->device : -1; }
+
+extern "C" {
+
+int glint_mlp_param_count(void) { return kP; }
+
+glint_status glint_mlp_create(glint_ctx *ctx, int K, long max_batch, uint32_t seed, glint_mlp **out) {
+    set_error("%s", "");
+    if (!ctx || !out) { set_error("glint_mlp_create: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (K != 2 && K != 4 && K != 8) {
+        set_error("glint_mlp_create: K = %d; the surrogate's 64 inputs hold 6K + 3 features, so K is 2, 4 or 8", K);
+        return K == 16 ? GLINT_ERR_UNSUPPORTED : GLINT_ERR_INVALID_ARG;
+    }
+    if (max_batch < 1 || max_batch > (1L << 30)) {
+        set_error("glint_mlp_create: max_batch %ld outside [1, 2^30]", max_batch);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) { set_error("glint_mlp_create: cannot select device"); return GLINT_ERR_CUDA; }
+    glint_mlp *g = new glint_mlp();
+    g->ctx = ctx;
+    g->K = K;
+    g->max_batch = max_batch;
+    glint_status st = GLINT_OK;
+    const size_t smem = grad_smem();
+    st = cuda_status(cudaFuncSetAttribute(k_mlp_grad<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                     "glint_mlp_create: smem");
+    int per_sm = 0, per_sm_inf = 0, per_sm_fwd = 0;
+    if (st == GLINT_OK)
+        st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_grad<1>, kNT, smem),
+                         "glint_mlp_create: occupancy");
+    if (st == GLINT_OK) {
+        cudaError_t e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inf, k_mlp_infer<2>, kNT, 0)
+                      : K == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inf, k_mlp_infer<4>, kNT, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_inf, k_mlp_infer<8>, kNT, 0);
+        st = cuda_status(e, "glint_mlp_create: occupancy");
+    }
+    if (st == GLINT_OK)
+        st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_fwd, k_mlp_forward<1>, kNT, 0),
+                         "glint_mlp_create: occupancy");
+    if (st == GLINT_OK && (per_sm < 1 || per_sm_inf < 1 || per_sm_fwd < 1)) {
+        set_error("glint_mlp_create: a surrogate kernel does not fit an SM");
+        st = GLINT_ERR_UNSUPPORTED;
+    }
+    const long nchunks_max = (max_batch + kNT - 1) / kNT;
+    g->max_grid = (int)std::min<long>((long)per_sm * ctx->num_sms, nchunks_max);
+    g->infer_grid = std::max(1, std::min(per_sm_inf, per_sm_fwd) * ctx->num_sms);
+    auto alloc = [&](void **p, size_t bytes) {
+        if (st == GLINT_OK) st = cuda_status(cudaMalloc(p, bytes), "glint_mlp_create");
+    };
+    alloc((void **)&g->params, sizeof(float) * kP);
+    alloc((void **)&g->grad, sizeof(float) * kP);
+    alloc((void **)&g->m, sizeof(float) * kP);
+    alloc((void **)&g->v, sizeof(float) * kP);
+    alloc((void **)&g->partial, sizeof(float) * kP * (size_t)std::max(g->max_grid, 1));
+    alloc((void **)&g->loss, sizeof(float) * (size_t)std::max(g->max_grid, 1));
+    alloc((void **)&g->wt, sizeof(__nv_bfloat16) * kNW);
+    alloc((void **)&g->wb, sizeof(__nv_bfloat16) * (kHid * kHid + kHid * kOutPad));
+    if (st == GLINT_OK) st = cuda_status(cudaMemset(g->m, 0, sizeof(float) * kP), "glint_mlp_create");
+    if (st == GLINT_OK) st = cuda_status(cudaMemset(g->v, 0, sizeof(float) * kP), "glint_mlp_create");
+    if (st == GLINT_OK) st = cuda_status(cudaMemset(g->grad, 0, sizeof(float) * kP), "glint_mlp_create");
+    if (st == GLINT_OK) {
+        k_mlp_init<<<(kP + 255) / 256, 256>>>(g->params, seed, K);
+        k_mlp_refresh<<<(kNW + 255) / 256, 256>>>(g->params, g->wt, g->wb);
+        st = cuda_status(cudaDeviceSynchronize(), "glint_mlp_create: init");
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    if (st != GLINT_OK) { mlp_free(g); delete g; return st; }
+    *out = g;
+    return GLINT_OK;
+}
+
+void glint_mlp_destroy(glint_mlp *g) {
+    if (!g) return;
+    mlp_free(g);
+    delete g;
+}
+
+glint_status glint_mlp_set_params(glint_mlp *g, const float *host, long n) {
+    set_error("%s", "");
+    if (!g || !host || n != kP) { set_error("glint_mlp_set_params: need %d floats", kP); return GLINT_ERR_INVALID_ARG; }
+    glint_status st = cuda_status(cudaMemcpy(g->params, host, sizeof(float) * kP, cudaMemcpyHostToDevice),
+                                  "glint_mlp_set_params");
+    if (st != GLINT_OK) return st;
+    k_mlp_refresh<<<(kNW + 255) / 256, 256>>>(g->params, g->wt, g->wb);
+    return cuda_status(cudaDeviceSynchronize(), "glint_mlp_set_params");
+}
+
+glint_status glint_mlp_export(const glint_mlp *g, int item, float *host, long n) {
+    set_error("%s", "");
+    if (!g || !host) { set_error("glint_mlp_export: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    const float *src = item == GLINT_MLP_PARAMS ? g->params : item == GLINT_MLP_GRAD ? g->grad
+                     : item == GLINT_MLP_ADAM_M ? g->m : item == GLINT_MLP_ADAM_V ? g->v : nullptr;
+    if (!src || n != kP) { set_error("glint_mlp_export: item %d, need %d floats", item, kP); return GLINT_ERR_INVALID_ARG; }
+    return cuda_status(cudaMemcpy(host, src, sizeof(float) * kP, cudaMemcpyDeviceToHost), "glint_mlp_export");
+}
+
+glint_status glint_mlp_import_state(glint_mlp *g, const float *params, const float *m, const float *v, long n,
+                                    long step) {
+    set_error("%s", "");
+    if (!g || !params || !m || !v || n != kP || step < 0) {
+        set_error("glint_mlp_import_state: need %d floats of each and step >= 0", kP);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    glint_status st = cuda_status(cudaMemcpy(g->m, m, sizeof(float) * kP, cudaMemcpyHostToDevice), "glint_mlp_import_state");
+    if (st == GLINT_OK) st = cuda_status(cudaMemcpy(g->v, v, sizeof(float) * kP, cudaMemcpyHostToDevice), "glint_mlp_import_state");
+    if (st != GLINT_OK) return st;
+    g->step = step;
+    return glint_mlp_set_params(g, params, kP);
+}
+
+long glint_mlp_step(const glint_mlp *g) { return g ? g->step : -1; }
+
+glint_status glint_mlp_features(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gb, uint16_t *x_out,
+                                float *lp_out, void *stream) {
+    set_error("%s", "");
+    if (!ctx || !env || !gb) { set_error("glint_mlp_features: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (env->ctx != ctx) { set_error("glint_mlp_features: environment belongs to another context"); return GLINT_ERR_INVALID_ARG; }
+    if (env->d.K != 2 && env->d.K != 4 && env->d.K != 8) {
+        set_error("glint_mlp_features: environment K = %d (the surrogate takes K = 2, 4 or 8)", env->d.K);
+        return GLINT_ERR_UNSUPPORTED;
+    }
+    if (gb->width < 0 || gb->height < 0 || (long)gb->width * gb->height > (1L << 31)) {
+        set_error("glint_mlp_features: width %d x height %d out of range", gb->width, gb->height);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    const long n = (long)gb->width * gb->height;
+    if (n == 0) return GLINT_OK;
+    if (!gb->view_n0 || !gb->normal_f0 || !gb->uv_alpha || !gb->tangent || !x_out || !lp_out) {
+        set_error("glint_mlp_features: the view, normal, uv/alpha and tangent planes and both outputs are required");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (!aligned(gb->view_n0, 16) || !aligned(gb->normal_f0, 16) || !aligned(gb->uv_alpha, 16) ||
+        !aligned(gb->tangent, 16) || !aligned(x_out, 16) || !aligned(lp_out, 4)) {
+        set_error("glint_mlp_features: planes and x_out must be 16-byte aligned, lp_out 4-byte aligned");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    glint_params prm{};
+    const ShadeArgs a = make_args(ctx, env, gb, &prm);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint4 *x = reinterpret_cast<uint4 *>(x_out);
+    switch (env->d.K) {
+    case 2: launch_features<2>(a, x, lp_out, s); break;
+    case 4: launch_features<4>(a, x, lp_out, s); break;
+    default: launch_features<8>(a, x, lp_out, s); break;
+    }
+    ctx->last_launches = 1;
+    return cuda_status(cudaGetLastError(), "glint_mlp_features");
+}
+
+glint_status glint_mlp_forward(const glint_mlp *g, const uint16_t *x, const float *lp, long n, float *p_out,
+                               void *stream) {
+    set_error("%s", "");
+    if (!g || n < 0) { set_error("glint_mlp_forward: NULL network or n < 0"); return GLINT_ERR_INVALID_ARG; }
+    if (n == 0) return GLINT_OK;
+    if (!x || !lp || !p_out || !aligned(x, 16) || !aligned(lp, 4) || !aligned(p_out, 4)) {
+        set_error("glint_mlp_forward: x (16-byte aligned), lp and p_out are required");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    const long ntiles = (n + kNT - 1) / kNT;
+    const unsigned grid = (unsigned)std::min<long>(ntiles, g->infer_grid);
+    k_mlp_forward<1><<<grid, kNT, 0, (cudaStream_t)stream>>>(reinterpret_cast<const uint4 *>(x), lp, n, g->K, g->wt,
+                                                             g->params, p_out);
+    const_cast<glint_mlp *>(g)->last_launches = 1;
+    return cuda_status(cudaGetLastError(), "glint_mlp_forward");
+}
+
+glint_status glint_mlp_train_step(glint_mlp *g, const uint16_t *x, const float *lp, const float *targets,
+                                  long n_total, long first, long batch, float lr, float *loss_out, void *stream) {
+    set_error("%s", "");
+    if (!g || !x || !lp || !targets) { set_error("glint_mlp_train_step: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (batch < 1 || batch > g->max_batch || n_total < 1 || first < 0 || !(lr >= 0.f) || !(lr < 1.f)) {
+        set_error("glint_mlp_train_step: batch %ld outside [1, %ld], empty data, first < 0 or lr %g outside [0, 1)",
+                  batch, g->max_batch, (double)lr);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (!aligned(x, 16) || !aligned(lp, 4) || !aligned(targets, 4)) {
+        set_error("glint_mlp_train_step: x must be 16-byte aligned, lp and targets 4-byte aligned");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const long nchunks = (batch + kNT - 1) / kNT;
+    const int grid = (int)std::min<long>(nchunks, g->max_grid);
+    k_mlp_grad<1><<<grid, kNT, grad_smem(), s>>>(reinterpret_cast<const uint4 *>(x), lp, targets, n_total,
+                                                 first % n_total, batch, g->K, g->wt, g->wb, g->params, g->partial,
+                                                 g->loss);
+    const long t = lr > 0.f ? g->step + 1 : std::max(g->step, 1L);
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)t));
+    const float bc2 = (float)(1.0 - std::pow(0.999, (double)t));
+    k_mlp_reduce_adam<<<(kP + 255) / 256, 256, 0, s>>>(g->partial, grid, g->grad, g->params, g->m, g->v, g->K, lr,
+                                                       0.9f, 0.999f, 1e-8f, bc1, bc2);
+    int nl = 2;
+    if (lr > 0.f) {
+        k_mlp_refresh<<<(kNW + 255) / 256, 256, 0, s>>>(g->params, g->wt, g->wb);
+        ++nl;
+        g->step = t;
+    }
+    g->last_launches = nl;
+    glint_status st = cuda_status(cudaGetLastError(), "glint_mlp_train_step");
+    if (st != GLINT_OK || !loss_out) return st;
+    std::vector<float> l(grid);
+    st = cuda_status(cudaMemcpyAsync(l.data(), g->loss, sizeof(float) * grid, cudaMemcpyDeviceToHost, s),
+                     "glint_mlp_train_step: loss");
+    if (st == GLINT_OK) st = cuda_status(cudaStreamSynchronize(s), "glint_mlp_train_step: loss");
+    double acc = 0.0;
+    for (float v : l) acc += v;
+    *loss_out = (float)(acc / (double)batch);
+    return st;
+}
+
+glint_status glint_mlp_infer(const glint_mlp *g, glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gb,
+                             float *p_out, void *stream) {
+    set_error("%s", "");
+    if (!g || !ctx || !env || !gb) { set_error("glint_mlp_infer: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (env->ctx != ctx || g->ctx != ctx) { set_error("glint_mlp_infer: network, environment and context differ"); return GLINT_ERR_INVALID_ARG; }
+    if (env->d.K != g->K) { set_error("glint_mlp_infer: network K %d, environment K %d", g->K, env->d.K); return GLINT_ERR_INVALID_ARG; }
+    if (gb->width < 0 || gb->height < 0 || (long)gb->width * gb->height > (1L << 31)) {
+        set_error("glint_mlp_infer: width %d x height %d out of range", gb->width, gb->height);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    const long n = (long)gb->width * gb->height;
+    if (n == 0) return GLINT_OK;
+    if (!gb->view_n0 || !gb->normal_f0 || !gb->uv_alpha || !gb->tangent || !p_out) {
+        set_error("glint_mlp_infer: the view, normal, uv/alpha and tangent planes and p_out are required");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (!aligned(gb->view_n0, 16) || !aligned(gb->normal_f0, 16) || !aligned(gb->uv_alpha, 16) ||
+        !aligned(gb->tangent, 16) || !aligned(p_out, 4)) {
+        set_error("glint_mlp_infer: planes must be 16-byte aligned, p_out 4-byte aligned");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    glint_status st = cuda_status(glint_launch_mlp_infer(ctx, env, g, gb, p_out, (cudaStream_t)stream),
+                                  "glint_mlp_infer");
+    const_cast<glint_mlp *>(g)->last_launches = 1;
+    return st;
+}
+
+int glint_mlp_get_k(const glint_mlp *g) { return g ? g->K : 0; }
+int glint_mlp_last_launches(const glint_mlp *g) { return g ? g->last_launches : 0; }
+
+}  // extern "C"

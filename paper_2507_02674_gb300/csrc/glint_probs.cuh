@@ -1,0 +1,320 @@
+// Reflection probabilities p_k of a pixel (Eq. probhk): E1 from the filtered
+// maps and tables (Eq. rtiblndf), E2 by quadrature of the anisotropic NDF, or
+// given; shared by the shading kernel and the surrogate's feature kernels.
+#pragma once
+#include "glint_internal.cuh"
+
+namespace glint {
+
+struct ShadeArgs {
+    const float4 *view_n0, *normal_f0, *uv_alpha, *duv, *tangent;
+    float4 *out;
+    long npix;
+    const float4 *lut;
+    int lut_n;
+    const float4 *filt;
+    const int2 *flev;  // (width, first texel) of each filtered level
+    int R;
+    float s_min, s_max;
+    const float *levels;
+    uint32_t seed;
+    glint_debug dbg;
+    // E2: weights pyramid
+    const float4 *pyr;
+    const size_t *pyr_off4;
+    int envW, envH, envM, e2S;
+    const float *pk_in;  // EV_GIVEN: p_k per pixel (npix x K)
+    float *p_out;        // k_probs: p_k per pixel (npix x K)
+};
+
+// Source of the reflection probabilities p_k.
+constexpr int EV_E1 = 0, EV_E2 = 1, EV_GIVEN = 2;
+
+// E2: reflection probabilities of an anisotropic GGX footprint by quadrature
+// (Eq. probhk).  Points of the projected-area slope distribution in
+// (s, u2), u1 = 1 - s^2, r = sqrt(1 - s^2)/s, slope = (a_x r cos phi,
+// a_y r sin phi), h' = (-slope, 1) in (t, b = n x t, n); bounded weight
+// 2 sqrt(s^2 + rho^2 (1 - s^2)); valid iff 2 w_o.h' > mu_o |h'|^2
+// (n . w_i > 0); w_k read bilinearly at pyramid level m, the coarsest whose
+// texel pi/H_m is at most 4 min(a_x, a_y)/S (an exact FP32 comparison).
+template <int K, int C4>
+__device__ __forceinline__ void e2_probabilities(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
+                                                 float mu_o, float *p) {
+    const float4 tg = ldg4(a.tangent + q);
+    const float tn = tg.x * g1.x + tg.y * g1.y + tg.z * g1.z;
+    float tx = tg.x - tn * g1.x, ty = tg.y - tn * g1.y, tz = tg.z - tn * g1.z;
+    const float tinv = 1.f / sqrtf(tx * tx + ty * ty + tz * tz);
+    tx *= tinv; ty *= tinv; tz *= tinv;
+    const float bx = g1.y * tz - g1.z * ty, by = g1.z * tx - g1.x * tz, bz = g1.x * ty - g1.y * tx;
+    const float ot = g0.x * tx + g0.y * ty + g0.z * tz;
+    const float ob = g0.x * bx + g0.y * by + g0.z * bz;
+    const int S = a.e2S;
+    const float lx = fminf(g2.z, g2.w) * (4.0f / (float)S);
+    int m = 0;
+    for (int k = 0; k < a.envM; ++k)
+        if ((float)(a.envH >> k) * lx >= kPi) m = k;
+    const int Wm = a.envW >> m, Hm = a.envH >> m;
+    const float4 *lev = a.pyr + a.pyr_off4[m];
+    const float ax2 = g2.z * g2.z, ay2 = g2.w * g2.w;
+    float sum_all = 0.f, sum_inv = 0.f;
+    float acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.f;
+#pragma unroll 1
+    for (int ia = 0; ia < S; ++ia) {
+        const float sv = ((float)ia + 0.5f) / (float)S;
+        const float r = sqrtf(1.f - sv * sv) / sv;
+#pragma unroll 1
+        for (int ic = 0; ic < S; ++ic) {
+            float sp, cp;
+            sincospif(2.f * ((float)ic + 0.5f) / (float)S, &sp, &cp);
+            const float sx = g2.z * r * cp, sy = g2.w * r * sp;
+            const float rho2 = ax2 * cp * cp + ay2 * sp * sp;
+            const float wgt = 2.f * sqrtf(sv * sv + rho2 * (1.f - sv * sv));
+            const float hl2 = 1.f + sx * sx + sy * sy;
+            const float oh = -sx * ot - sy * ob + mu_o;
+            sum_all += wgt;
+            if (!(2.f * oh - mu_o * hl2 > 0.f)) {
+                sum_inv += wgt;
+                continue;
+            }
+            const float il = rsqrtf(hl2);
+            const float hx = (-sx * tx - sy * bx + g1.x) * il;
+            const float hy = (-sx * ty - sy * by + g1.y) * il;
+            const float hz = (-sx * tz - sy * bz + g1.z) * il;
+            const float c2 = 2.f * oh * il;
+            const float dx = c2 * hx - g0.x, dy = c2 * hy - g0.y, dz = c2 * hz - g0.z;
+            float ex, ey;
+            dir_to_texel(dx, dy, dz, Wm, Hm, ex, ey);
+            const Taps tp = equirect_taps(ex, ey, Wm, Hm);
+            float w[C4 * 4];
+#pragma unroll
+            for (int c = 0; c < C4; ++c) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                v = fma4(tp.w00, __ldg(lev + (size_t)tp.i00 * C4 + c), v);
+                v = fma4(tp.w01, __ldg(lev + (size_t)tp.i01 * C4 + c), v);
+                v = fma4(tp.w10, __ldg(lev + (size_t)tp.i10 * C4 + c), v);
+                v = fma4(tp.w11, __ldg(lev + (size_t)tp.i11 * C4 + c), v);
+                w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] = fmaf(wgt, w[3 + k], acc[k]);
+        }
+    }
+    const float inv = 1.f / sum_all;
+    p[0] = (sum_inv + acc[0]) * inv;
+#pragma unroll
+    for (int k = 1; k < K; ++k) p[k] = acc[k] * inv;
+}
+
+__device__ __forceinline__ float4 lut_fetch(const float4 *lut, int n, float mu, float s) {
+    float x = fminf(fmaxf(mu * (float)n - 0.5f, 0.f), (float)(n - 1));
+    float y = fminf(fmaxf(s * (float)n - 0.5f, 0.f), (float)(n - 1));
+    const float fx0 = floorf(x), fy0 = floorf(y);
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    const int x1 = min(x0 + 1, n - 1), y1 = min(y0 + 1, n - 1);
+    const float fx = x - fx0, fy = y - fy0;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    r = fma4((1.f - fy) * (1.f - fx), __ldg(lut + y0 * n + x0), r);
+    r = fma4((1.f - fy) * fx, __ldg(lut + y0 * n + x1), r);
+    r = fma4(fy * (1.f - fx), __ldg(lut + y1 * n + x0), r);
+    r = fma4(fy * fx, __ldg(lut + y1 * n + x1), r);
+    return r;
+}
+
+
+// Step 1: smooth radiance (L_o) and the reflection probabilities p_k.
+template <int K, int EV>
+__device__ __forceinline__ void smooth_and_probs(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
+                                                 float &Lor, float &Log, float &Lob, float *p) {
+    constexpr int C4 = (3 + K + 3) / 4;
+    const float mu_o = g1.x * g0.x + g1.y * g0.y + g1.z * g0.z;
+    const float rx = 2.f * mu_o * g1.x - g0.x;
+    const float ry = 2.f * mu_o * g1.y - g0.y;
+    const float rz = 2.f * mu_o * g1.z - g0.z;
+    const float mu_c = fminf(fmaxf(mu_o, 1e-4f), 1.f);
+    const float s = sqrtf(sqrtf(g2.z * g2.w));
+    const float4 tab = lut_fetch(a.lut, a.lut_n, mu_c, s);  // V, U, A, B
+    float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
+    tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
+    const int r0 = (int)floorf(tl);
+    const int r1 = min(r0 + 1, a.R - 1);
+    const float ft = tl - (float)r0;
+    // direction of w_r on the unit sphere, then texel coordinates per level
+    const float th_r = acosf(fminf(fmaxf(ry, -1.f), 1.f));
+    float ph_r = atan2f(rz, rx);
+    if (ph_r < 0.f) ph_r += kTwoPi;
+    float4 cc[C4];
+#pragma unroll
+    for (int c = 0; c < C4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int lv = 0; lv < 2; ++lv) {
+        const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
+        const int Wr = lev.x, Hr = lev.x / 2;
+        const Taps tp = equirect_taps(ph_r * (kInvTwoPi * (float)Wr) - 0.5f, th_r * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
+        const float4 *base = a.filt + (size_t)lev.y * C4;
+        const float wl = lv ? ft : 1.f - ft;
+        // E2 and given p_k need the colour channels (first float4) only
+        constexpr int CN = (EV == EV_E1) ? C4 : 1;
+#pragma unroll
+        for (int c = 0; c < CN; ++c) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * C4 + c), v);
+            v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * C4 + c), v);
+            v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * C4 + c), v);
+            v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * C4 + c), v);
+            cc[c] = fma4(wl, v, cc[c]);
+        }
+    }
+    float ch[C4 * 4];
+#pragma unroll
+    for (int c = 0; c < C4; ++c) {
+        ch[4 * c] = cc[c].x; ch[4 * c + 1] = cc[c].y; ch[4 * c + 2] = cc[c].z; ch[4 * c + 3] = cc[c].w;
+    }
+    const float Eb = g1.w * tab.z + tab.w;
+    Lor = ch[0] * Eb;
+    Log = ch[1] * Eb;
+    Lob = ch[2] * Eb;
+    if (EV == EV_E2) {
+        e2_probabilities<K, C4>(a, q, g0, g1, g2, mu_o, p);
+    } else if (EV == EV_GIVEN) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) p[k] = __ldg(a.pk_in + q * K + k);
+    } else {
+        p[0] = tab.y + tab.x * ch[3];
+#pragma unroll
+        for (int k = 1; k < K; ++k) p[k] = tab.x * ch[3 + k];
+    }
+}
+
+
+inline ShadeArgs make_args(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g, const glint_params *p) {
+    ShadeArgs a{};
+    a.view_n0 = reinterpret_cast<const float4 *>(g->view_n0);
+    a.tangent = reinterpret_cast<const float4 *>(g->tangent);
+    a.normal_f0 = reinterpret_cast<const float4 *>(g->normal_f0);
+    a.uv_alpha = reinterpret_cast<const float4 *>(g->uv_alpha);
+    a.duv = reinterpret_cast<const float4 *>(g->duv);
+    a.npix = (long)g->width * g->height;
+    a.lut = ctx->lut;
+    a.lut_n = ctx->lut_n;
+    a.filt = reinterpret_cast<const float4 *>(env->filt);
+    a.R = env->d.levels;
+    a.flev = env->flev;
+    a.s_min = env->d.s_min;
+    a.s_max = env->d.s_max;
+    a.levels = env->levels;
+    a.seed = p->seed;
+    a.pyr = reinterpret_cast<const float4 *>(env->pyr);
+    a.pyr_off4 = env->pyr_off4_dev;
+    a.envW = env->d.width;
+    a.envH = env->d.height;
+    a.envM = env->M;
+    a.e2S = p->e2_samples > 0 ? p->e2_samples : 16;
+    return a;
+}
+
+
+}  // namespace glint
+
+namespace glint {
+
+// ---------------------------------------------------------------------------
+// Inputs of the p_k surrogate (no counterpart in the paper): per pixel
+//   [ p_k of E1 (K) | W_k at 5 taps (5K) | mu_o, sqrt a_x, sqrt a_y | 0 ... ]
+// (64 values) and the prior log max(p_k^E1, 1e-6) added to the output logits.
+// W_k is read from the filtered maps at roughness parameter s = sqrt(min(a_x,
+// a_y)) in the directions w_r (centre) and normalize(w_r +- a_x J_t),
+// normalize(w_r +- a_y J_b), where J_t = 2 (-(w_o.t) n - mu_o t) is the
+// derivative of the mirror direction with respect to the slope along the
+// tangent t (made orthogonal to n) and J_b likewise along b = n x t: the
+// lobe's extent along its two axes, including the stretch at grazing views.
+constexpr int kMlpIn = 64;
+constexpr int kMlpTaps = 5;
+constexpr float kPriorFloor = 1e-6f;
+
+// W_1 .. W_K of the filtered maps at unit direction d and roughness parameter
+// s (the two levels bracketing s, bilinear in each, as E1 does for w_r).
+template <int K, int C4>
+__device__ __forceinline__ void filtered_weights(const ShadeArgs &a, float dx, float dy, float dz, float s, float *W) {
+    float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
+    tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
+    const int r0 = (int)floorf(tl);
+    const int r1 = min(r0 + 1, a.R - 1);
+    const float ft = tl - (float)r0;
+    const float th = acosf(fminf(fmaxf(dy, -1.f), 1.f));
+    float ph = atan2f(dz, dx);
+    if (ph < 0.f) ph += kTwoPi;
+    float4 cc[C4];
+#pragma unroll
+    for (int c = 0; c < C4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int lv = 0; lv < 2; ++lv) {
+        const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
+        const int Wr = lev.x, Hr = lev.x / 2;
+        const Taps tp = equirect_taps(ph * (kInvTwoPi * (float)Wr) - 0.5f, th * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
+        const float4 *base = a.filt + (size_t)lev.y * C4;
+        const float wl = lv ? ft : 1.f - ft;
+#pragma unroll
+        for (int c = 0; c < C4; ++c) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * C4 + c), v);
+            v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * C4 + c), v);
+            v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * C4 + c), v);
+            v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * C4 + c), v);
+            cc[c] = fma4(wl, v, cc[c]);
+        }
+    }
+    float ch[C4 * 4];
+#pragma unroll
+    for (int c = 0; c < C4; ++c) {
+        ch[4 * c] = cc[c].x; ch[4 * c + 1] = cc[c].y; ch[4 * c + 2] = cc[c].z; ch[4 * c + 3] = cc[c].w;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) W[k] = ch[3 + k];
+}
+
+// The surrogate's inputs x[0 .. 6K+3) (the rest of the 64 are zero) and
+// log-prior lp[K] of foreground pixel q.
+template <int K>
+__device__ __forceinline__ void mlp_features(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2, float *x,
+                                             float *lp) {
+    constexpr int C4 = (3 + K + 3) / 4;
+    float lr, lg, lb;
+    smooth_and_probs<K, EV_E1>(a, q, g0, g1, g2, lr, lg, lb, x);
+#pragma unroll
+    for (int k = 0; k < K; ++k) lp[k] = logf(fmaxf(x[k], kPriorFloor));
+    const float4 tg = ldg4(a.tangent + q);
+    const float tn = tg.x * g1.x + tg.y * g1.y + tg.z * g1.z;
+    float tx = tg.x - tn * g1.x, ty = tg.y - tn * g1.y, tz = tg.z - tn * g1.z;
+    const float tinv = 1.f / sqrtf(tx * tx + ty * ty + tz * tz);
+    tx *= tinv; ty *= tinv; tz *= tinv;
+    const float bx = g1.y * tz - g1.z * ty, by = g1.z * tx - g1.x * tz, bz = g1.x * ty - g1.y * tx;
+    const float mu = g1.x * g0.x + g1.y * g0.y + g1.z * g0.z;
+    const float ot = g0.x * tx + g0.y * ty + g0.z * tz;
+    const float ob = g0.x * bx + g0.y * by + g0.z * bz;
+    const float rx = 2.f * mu * g1.x - g0.x, ry = 2.f * mu * g1.y - g0.y, rz = 2.f * mu * g1.z - g0.z;
+    const float jtx = -2.f * (ot * g1.x + mu * tx), jty = -2.f * (ot * g1.y + mu * ty), jtz = -2.f * (ot * g1.z + mu * tz);
+    const float jbx = -2.f * (ob * g1.x + mu * bx), jby = -2.f * (ob * g1.y + mu * by), jbz = -2.f * (ob * g1.z + mu * bz);
+    const float s = sqrtf(fminf(g2.z, g2.w));
+#pragma unroll
+    for (int tap = 0; tap < kMlpTaps; ++tap) {
+        float dx = rx, dy = ry, dz = rz;
+        if (tap > 0) {
+            const float sg = (tap & 1) ? 1.f : -1.f;
+            const float e = sg * ((tap <= 2) ? g2.z : g2.w);
+            dx += e * ((tap <= 2) ? jtx : jbx);
+            dy += e * ((tap <= 2) ? jty : jby);
+            dz += e * ((tap <= 2) ? jtz : jbz);
+        }
+        const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        filtered_weights<K, C4>(a, dx * il, dy * il, dz * il, s, x + K + tap * K);
+    }
+    x[6 * K] = mu;
+    x[6 * K + 1] = sqrtf(g2.z);
+    x[6 * K + 2] = sqrtf(g2.w);
+#pragma unroll
+    for (int i = 6 * K + 3; i < kMlpIn; ++i) x[i] = 0.f;
+}
+
+}  // namespace glint

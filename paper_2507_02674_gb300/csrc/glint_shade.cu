@@ -20,6 +20,7 @@
 // 64 registers per thread (8 blocks of 128 threads per SM) measured fastest.
 //   5. L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k).
 #include "glint_internal.cuh"
+#include "glint_probs.cuh"
 #include "glint_quantile.cuh"
 
 using namespace glint;
@@ -27,117 +28,6 @@ using namespace glint;
 namespace {
 
 constexpr int kShadeNT = 128;
-
-struct ShadeArgs {
-    const float4 *view_n0, *normal_f0, *uv_alpha, *duv, *tangent;
-    float4 *out;
-    long npix;
-    const float4 *lut;
-    int lut_n;
-    const float4 *filt;
-    const int2 *flev;  // (width, first texel) of each filtered level
-    int R;
-    float s_min, s_max;
-    const float *levels;
-    uint32_t seed;
-    glint_debug dbg;
-    // E2: weights pyramid
-    const float4 *pyr;
-    const size_t *pyr_off4;
-    int envW, envH, envM, e2S;
-};
-
-// E2: reflection probabilities of an anisotropic GGX footprint by quadrature
-// (Eq. probhk).  Points of the projected-area slope distribution in
-// (s, u2), u1 = 1 - s^2, r = sqrt(1 - s^2)/s, slope = (a_x r cos phi,
-// a_y r sin phi), h' = (-slope, 1) in (t, b = n x t, n); bounded weight
-// 2 sqrt(s^2 + rho^2 (1 - s^2)); valid iff 2 w_o.h' > mu_o |h'|^2
-// (n . w_i > 0); w_k read bilinearly at pyramid level m, the coarsest whose
-// texel pi/H_m is at most 4 min(a_x, a_y)/S (an exact FP32 comparison).
-template <int K, int C4>
-__device__ __forceinline__ void e2_probabilities(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
-                                                 float mu_o, float *p) {
-    const float4 tg = ldg4(a.tangent + q);
-    const float tn = tg.x * g1.x + tg.y * g1.y + tg.z * g1.z;
-    float tx = tg.x - tn * g1.x, ty = tg.y - tn * g1.y, tz = tg.z - tn * g1.z;
-    const float tinv = 1.f / sqrtf(tx * tx + ty * ty + tz * tz);
-    tx *= tinv; ty *= tinv; tz *= tinv;
-    const float bx = g1.y * tz - g1.z * ty, by = g1.z * tx - g1.x * tz, bz = g1.x * ty - g1.y * tx;
-    const float ot = g0.x * tx + g0.y * ty + g0.z * tz;
-    const float ob = g0.x * bx + g0.y * by + g0.z * bz;
-    const int S = a.e2S;
-    const float lx = fminf(g2.z, g2.w) * (4.0f / (float)S);
-    int m = 0;
-    for (int k = 0; k < a.envM; ++k)
-        if ((float)(a.envH >> k) * lx >= kPi) m = k;
-    const int Wm = a.envW >> m, Hm = a.envH >> m;
-    const float4 *lev = a.pyr + a.pyr_off4[m];
-    const float ax2 = g2.z * g2.z, ay2 = g2.w * g2.w;
-    float sum_all = 0.f, sum_inv = 0.f;
-    float acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.f;
-#pragma unroll 1
-    for (int ia = 0; ia < S; ++ia) {
-        const float sv = ((float)ia + 0.5f) / (float)S;
-        const float r = sqrtf(1.f - sv * sv) / sv;
-#pragma unroll 1
-        for (int ic = 0; ic < S; ++ic) {
-            float sp, cp;
-            sincospif(2.f * ((float)ic + 0.5f) / (float)S, &sp, &cp);
-            const float sx = g2.z * r * cp, sy = g2.w * r * sp;
-            const float rho2 = ax2 * cp * cp + ay2 * sp * sp;
-            const float wgt = 2.f * sqrtf(sv * sv + rho2 * (1.f - sv * sv));
-            const float hl2 = 1.f + sx * sx + sy * sy;
-            const float oh = -sx * ot - sy * ob + mu_o;
-            sum_all += wgt;
-            if (!(2.f * oh - mu_o * hl2 > 0.f)) {
-                sum_inv += wgt;
-                continue;
-            }
-            const float il = rsqrtf(hl2);
-            const float hx = (-sx * tx - sy * bx + g1.x) * il;
-            const float hy = (-sx * ty - sy * by + g1.y) * il;
-            const float hz = (-sx * tz - sy * bz + g1.z) * il;
-            const float c2 = 2.f * oh * il;
-            const float dx = c2 * hx - g0.x, dy = c2 * hy - g0.y, dz = c2 * hz - g0.z;
-            float ex, ey;
-            dir_to_texel(dx, dy, dz, Wm, Hm, ex, ey);
-            const Taps tp = equirect_taps(ex, ey, Wm, Hm);
-            float w[C4 * 4];
-#pragma unroll
-            for (int c = 0; c < C4; ++c) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                v = fma4(tp.w00, __ldg(lev + (size_t)tp.i00 * C4 + c), v);
-                v = fma4(tp.w01, __ldg(lev + (size_t)tp.i01 * C4 + c), v);
-                v = fma4(tp.w10, __ldg(lev + (size_t)tp.i10 * C4 + c), v);
-                v = fma4(tp.w11, __ldg(lev + (size_t)tp.i11 * C4 + c), v);
-                w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
-            }
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc[k] = fmaf(wgt, w[3 + k], acc[k]);
-        }
-    }
-    const float inv = 1.f / sum_all;
-    p[0] = (sum_inv + acc[0]) * inv;
-#pragma unroll
-    for (int k = 1; k < K; ++k) p[k] = acc[k] * inv;
-}
-
-__device__ __forceinline__ float4 lut_fetch(const float4 *lut, int n, float mu, float s) {
-    float x = fminf(fmaxf(mu * (float)n - 0.5f, 0.f), (float)(n - 1));
-    float y = fminf(fmaxf(s * (float)n - 0.5f, 0.f), (float)(n - 1));
-    const float fx0 = floorf(x), fy0 = floorf(y);
-    const int x0 = (int)fx0, y0 = (int)fy0;
-    const int x1 = min(x0 + 1, n - 1), y1 = min(y0 + 1, n - 1);
-    const float fx = x - fx0, fy = y - fy0;
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    r = fma4((1.f - fy) * (1.f - fx), __ldg(lut + y0 * n + x0), r);
-    r = fma4((1.f - fy) * fx, __ldg(lut + y0 * n + x1), r);
-    r = fma4(fy * (1.f - fx), __ldg(lut + y1 * n + x0), r);
-    r = fma4(fy * fx, __ldg(lut + y1 * n + x1), r);
-    return r;
-}
 
 // |du/dx dv/dy - du/dy dv/dx| with one FMA correction (Kahan), every
 // operation correctly rounded and never contracted.
@@ -234,9 +124,26 @@ __device__ __forceinline__ void draw_real(float N, const NodeParams &np, uint32_
     nbar = (B_allneg ? N2 - 1.f : 0.f) + (B_alloneneg ? 1.f : 0.f) + (B_G ? N2 - G : 0.f);
 }
 
-template <int K, bool INTEGER, bool DEBUG, bool E2>
+// p_k only, one thread per pixel (background 0).
+template <int K, int EV>
+__global__ void __launch_bounds__(kShadeNT) k_probs(ShadeArgs a) {
+    const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
+    if (q >= a.npix) return;
+    const float4 g0 = ldg4(a.view_n0 + q);
+    float p[K];
+    if (g0.w > 0.f) {
+        float lr, lg, lb;
+        smooth_and_probs<K, EV>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), lr, lg, lb, p);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) p[k] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.p_out[q * K + k] = p[k];
+}
+
+template <int K, bool INTEGER, bool DEBUG, int EV>
 __global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
-    constexpr int C4 = (3 + K + 3) / 4;
     const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
     if (q >= a.npix) return;
     const float4 g0 = ldg4(a.view_n0 + q);
@@ -260,58 +167,10 @@ __global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
         return;
     }
 
-    // ---- 1. smooth radiance and reflection probabilities (E1)
-    const float mu_o = g1.x * g0.x + g1.y * g0.y + g1.z * g0.z;
-    const float rx = 2.f * mu_o * g1.x - g0.x;
-    const float ry = 2.f * mu_o * g1.y - g0.y;
-    const float rz = 2.f * mu_o * g1.z - g0.z;
-    const float mu_c = fminf(fmaxf(mu_o, 1e-4f), 1.f);
-    const float s = sqrtf(sqrtf(g2.z * g2.w));
-    const float4 tab = lut_fetch(a.lut, a.lut_n, mu_c, s);  // V, U, A, B
-    float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
-    tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
-    const int r0 = (int)floorf(tl);
-    const int r1 = min(r0 + 1, a.R - 1);
-    const float ft = tl - (float)r0;
-    // direction of w_r on the unit sphere, then texel coordinates per level
-    const float th_r = acosf(fminf(fmaxf(ry, -1.f), 1.f));
-    float ph_r = atan2f(rz, rx);
-    if (ph_r < 0.f) ph_r += kTwoPi;
-    float4 cc[C4];
-#pragma unroll
-    for (int c = 0; c < C4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int lv = 0; lv < 2; ++lv) {
-        const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
-        const int Wr = lev.x, Hr = lev.x / 2;
-        const Taps tp = equirect_taps(ph_r * (kInvTwoPi * (float)Wr) - 0.5f, th_r * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
-        const float4 *base = a.filt + (size_t)lev.y * C4;
-        const float wl = lv ? ft : 1.f - ft;
-#pragma unroll
-        for (int c = 0; c < C4; ++c) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * C4 + c), v);
-            v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * C4 + c), v);
-            v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * C4 + c), v);
-            v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * C4 + c), v);
-            cc[c] = fma4(wl, v, cc[c]);
-        }
-    }
-    float ch[C4 * 4];
-#pragma unroll
-    for (int c = 0; c < C4; ++c) {
-        ch[4 * c] = cc[c].x; ch[4 * c + 1] = cc[c].y; ch[4 * c + 2] = cc[c].z; ch[4 * c + 3] = cc[c].w;
-    }
-    const float Eb = g1.w * tab.z + tab.w;
-    const float Lor = ch[0] * Eb, Log = ch[1] * Eb, Lob = ch[2] * Eb;
+    // ---- 1. smooth radiance and reflection probabilities
+    float Lor, Log, Lob;
     float p[K];
-    if (E2) {
-        e2_probabilities<K, C4>(a, q, g0, g1, g2, mu_o, p);
-    } else {
-        p[0] = tab.y + tab.x * ch[3];
-#pragma unroll
-        for (int k = 1; k < K; ++k) p[k] = tab.x * ch[3 + k];
-    }
+    smooth_and_probs<K, EV>(a, q, g0, g1, g2, Lor, Log, Lob, p);
 
     // ---- 2. footprint, microfacet count, grid level
     const float area = footprint_area(g3.x, g3.y, g3.z, g3.w);
@@ -477,22 +336,31 @@ __global__ void k_quantile(const float *__restrict__ p, float *__restrict__ z, l
     if (i < n) z[i] = normal_quantile(p[i]);
 }
 
-template <int K, bool E2>
+template <int K, int EV>
 void launch_ke(const ShadeArgs &args, bool integer, bool debug, cudaStream_t s) {
     const unsigned grid = (unsigned)((args.npix + kShadeNT - 1) / kShadeNT);
     if (integer) {
-        if (debug) k_shade<K, true, true, E2><<<grid, kShadeNT, 0, s>>>(args);
-        else k_shade<K, true, false, E2><<<grid, kShadeNT, 0, s>>>(args);
+        if (debug) k_shade<K, true, true, EV><<<grid, kShadeNT, 0, s>>>(args);
+        else k_shade<K, true, false, EV><<<grid, kShadeNT, 0, s>>>(args);
     } else {
-        if (debug) k_shade<K, false, true, E2><<<grid, kShadeNT, 0, s>>>(args);
-        else k_shade<K, false, false, E2><<<grid, kShadeNT, 0, s>>>(args);
+        if (debug) k_shade<K, false, true, EV><<<grid, kShadeNT, 0, s>>>(args);
+        else k_shade<K, false, false, EV><<<grid, kShadeNT, 0, s>>>(args);
     }
 }
 
 template <int K>
-cudaError_t launch_k(const ShadeArgs &args, bool integer, bool debug, bool e2, cudaStream_t s) {
-    if (e2) launch_ke<K, true>(args, integer, debug, s);
-    else launch_ke<K, false>(args, integer, debug, s);
+cudaError_t launch_k(const ShadeArgs &args, bool integer, bool debug, int ev, cudaStream_t s) {
+    if (ev == EV_E2) launch_ke<K, EV_E2>(args, integer, debug, s);
+    else if (ev == EV_GIVEN) launch_ke<K, EV_GIVEN>(args, integer, debug, s);
+    else launch_ke<K, EV_E1>(args, integer, debug, s);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_probs(const ShadeArgs &args, int ev, cudaStream_t s) {
+    const unsigned grid = (unsigned)((args.npix + kShadeNT - 1) / kShadeNT);
+    if (ev == EV_E2) k_probs<K, EV_E2><<<grid, kShadeNT, 0, s>>>(args);
+    else k_probs<K, EV_E1><<<grid, kShadeNT, 0, s>>>(args);
     return cudaGetLastError();
 }
 
@@ -504,45 +372,40 @@ cudaError_t glint_launch_quantile(const float *p, float *z, long n, cudaStream_t
 }
 
 cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
-                               const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s,
-                               int *launches) {
-    ShadeArgs a;
-    a.view_n0 = reinterpret_cast<const float4 *>(g->view_n0);
-    a.tangent = reinterpret_cast<const float4 *>(g->tangent);
-    a.normal_f0 = reinterpret_cast<const float4 *>(g->normal_f0);
-    a.uv_alpha = reinterpret_cast<const float4 *>(g->uv_alpha);
-    a.duv = reinterpret_cast<const float4 *>(g->duv);
+                               const glint_params *p, const float *pk_in, float *out, const glint_debug *dbg,
+                               cudaStream_t s, int *launches) {
+    ShadeArgs a = make_args(ctx, env, g, p);
     a.out = reinterpret_cast<float4 *>(out);
-    a.npix = (long)g->width * g->height;
-    a.lut = ctx->lut;
-    a.lut_n = ctx->lut_n;
-    a.filt = reinterpret_cast<const float4 *>(env->filt);
-    a.R = env->d.levels;
-    a.flev = env->flev;
-    a.s_min = env->d.s_min;
-    a.s_max = env->d.s_max;
-    a.levels = env->levels;
-    a.seed = p->seed;
     a.dbg = dbg ? *dbg : glint_debug{};
-    a.pyr = reinterpret_cast<const float4 *>(env->pyr);
-    a.pyr_off4 = env->pyr_off4_dev;
-    a.envW = env->d.width;
-    a.envH = env->d.height;
-    a.envM = env->M;
-    a.e2S = p->e2_samples > 0 ? p->e2_samples : 16;
-    const bool e2 = p->evaluator == GLINT_EVAL_E2;
+    a.pk_in = pk_in;
+    const int ev = pk_in ? EV_GIVEN : (p->evaluator == GLINT_EVAL_E2 ? EV_E2 : EV_E1);
     const bool debug = dbg != nullptr;
     const bool integer = p->count_mode == GLINT_COUNT_INTEGER;
     if (launches) *launches = 0;
     if (a.npix == 0) return cudaSuccess;
     cudaError_t e;
     switch (env->d.K) {
-    case 2: e = launch_k<2>(a, integer, debug, e2, s); break;
-    case 4: e = launch_k<4>(a, integer, debug, e2, s); break;
-    case 8: e = launch_k<8>(a, integer, debug, e2, s); break;
-    case 16: e = launch_k<16>(a, integer, debug, e2, s); break;
+    case 2: e = launch_k<2>(a, integer, debug, ev, s); break;
+    case 4: e = launch_k<4>(a, integer, debug, ev, s); break;
+    case 8: e = launch_k<8>(a, integer, debug, ev, s); break;
+    case 16: e = launch_k<16>(a, integer, debug, ev, s); break;
     default: return cudaErrorInvalidValue;
     }
     if (launches) *launches = 1;
     return e;
+}
+
+cudaError_t glint_launch_probs(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
+                               const glint_params *p, float *p_out, cudaStream_t s) {
+    ShadeArgs a = make_args(ctx, env, g, p);
+    a.p_out = p_out;
+    const int ev = p->evaluator == GLINT_EVAL_E2 ? EV_E2 : EV_E1;
+    if (a.npix == 0) return cudaSuccess;
+    switch (env->d.K) {
+    case 2: return launch_probs<2>(a, ev, s);
+    case 4: return launch_probs<4>(a, ev, s);
+    case 8: return launch_probs<8>(a, ev, s);
+    case 16: return launch_probs<16>(a, ev, s);
+    default: return cudaErrorInvalidValue;
+    }
 }

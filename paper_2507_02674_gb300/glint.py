@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(_HERE, "libglint.so")
 GLINT_OK = 0
 FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
-EVAL_E1, EVAL_E2 = 0, 1
+EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN = 0, 1, 2, 3
+MLP_PARAMS, MLP_GRAD, MLP_ADAM_M, MLP_ADAM_V = 0, 1, 2, 3
+ABI_VERSION = 2
 ENV_LOHI, ENV_LEVELS, ENV_PYRAMID, ENV_FILTERED, ENV_TABLE, ENV_FILTERED_WIDTHS = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_READY", 5: "TIMEOUT", 6: "UNSUPPORTED"}
 
@@ -45,7 +47,7 @@ class GBufferDesc(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint32), ("count_mode", ctypes.c_int), ("evaluator", ctypes.c_int),
-                ("e2_samples", ctypes.c_int)]
+                ("e2_samples", ctypes.c_int), ("mlp", ctypes.c_void_p), ("p_scratch", ctypes.c_void_p)]
 
 
 class Debug(ctypes.Structure):
@@ -74,10 +76,31 @@ def _load():
     lib.glint_shade.argtypes = [P, P, ctypes.POINTER(GBufferDesc), ctypes.POINTER(Params), P,
                                 ctypes.POINTER(Debug), P]
     lib.glint_normal_quantile.argtypes = [P, P, ctypes.c_long, P]
+    lib.glint_reflect_probs.argtypes = [P, P, ctypes.POINTER(GBufferDesc), ctypes.POINTER(Params), P, P]
+    L, F = ctypes.c_long, ctypes.c_float
+    lib.glint_mlp_param_count.restype = I
+    lib.glint_mlp_create.argtypes = [P, I, L, ctypes.c_uint32, ctypes.POINTER(P)]
+    lib.glint_mlp_destroy.argtypes = [P]
+    lib.glint_mlp_destroy.restype = None
+    lib.glint_mlp_set_params.argtypes = [P, P, L]
+    lib.glint_mlp_export.argtypes = [P, I, P, L]
+    lib.glint_mlp_import_state.argtypes = [P, P, P, P, L, L]
+    lib.glint_mlp_step.argtypes = [P]
+    lib.glint_mlp_step.restype = L
+    lib.glint_mlp_features.argtypes = [P, P, ctypes.POINTER(GBufferDesc), P, P, P]
+    lib.glint_mlp_forward.argtypes = [P, P, P, L, P, P]
+    lib.glint_mlp_train_step.argtypes = [P, P, P, P, L, L, L, F, ctypes.POINTER(F), P]
+    lib.glint_mlp_infer.argtypes = [P, P, P, ctypes.POINTER(GBufferDesc), P, P]
+    lib.glint_mlp_get_k.argtypes = [P]
+    lib.glint_mlp_get_k.restype = I
+    lib.glint_mlp_last_launches.argtypes = [P]
+    lib.glint_mlp_last_launches.restype = I
     lib.glint_env_last_launches.argtypes = [P]
     lib.glint_env_last_launches.restype = I
     lib.glint_ctx_last_launches.argtypes = [P]
     lib.glint_ctx_last_launches.restype = I
+    if lib.glint_abi_version() != ABI_VERSION:
+        raise ImportError(f"{LIB_PATH} has ABI {lib.glint_abi_version()}, the binding expects {ABI_VERSION}")
     return lib
 
 
@@ -210,19 +233,127 @@ class Env:
             pass
 
 
+def _gbuffer(planes, width: int, height: int, tangent=None) -> GBufferDesc:
+    duv = planes[3] if len(planes) > 3 else None
+    return GBufferDesc(_dptr(planes[0]), _dptr(planes[1]), _dptr(planes[2]), _dptr(duv), width, height,
+                       _dptr(tangent))
+
+
+def _params(seed=0, count_mode=COUNT_INTEGER, evaluator=EVAL_E1, e2_samples=16, mlp=None, p_scratch=None):
+    return Params(seed & 0xFFFFFFFF, count_mode, evaluator, e2_samples,
+                  mlp.handle.value if mlp is not None else None, _dptr(p_scratch))
+
+
 def shade(ctx: Context, env: Env, planes, width: int, height: int, out, seed: int = 0,
           count_mode: int = COUNT_INTEGER, debug: dict | None = None, stream=None, tangent=None,
-          evaluator: int = EVAL_E1, e2_samples: int = 16):
+          evaluator: int = EVAL_E1, e2_samples: int = 16, mlp=None, p_scratch=None):
     """glint_shade over a G-buffer given as four device tensors of (npix, 4) float32
-    (plus an optional (npix, 4) tangent tensor, needed by E2)."""
-    g = GBufferDesc(_dptr(planes[0]), _dptr(planes[1]), _dptr(planes[2]), _dptr(planes[3]), width, height,
-                    _dptr(tangent))
-    p = Params(seed & 0xFFFFFFFF, count_mode, evaluator, e2_samples)
+    (plus an optional (npix, 4) tangent tensor, needed by E2 and the MLP)."""
+    g = _gbuffer(planes, width, height, tangent)
+    p = _params(seed, count_mode, evaluator, e2_samples, mlp, p_scratch)
     dbg = None
     if debug is not None:
         dbg = Debug(*(_dptr(debug.get(k)) for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")))
     _check(lib.glint_shade(ctx.handle, env.handle, ctypes.byref(g), ctypes.byref(p), _dptr(out),
                            ctypes.byref(dbg) if dbg is not None else None, _stream_handle(stream)))
+
+
+def reflect_probs(ctx: Context, env: Env, planes, width: int, height: int, out, evaluator: int = EVAL_E1,
+                  e2_samples: int = 16, tangent=None, mlp=None, stream=None):
+    """glint_reflect_probs: p_k of every pixel into `out` (device, (npix, K) float32)."""
+    g = _gbuffer(planes, width, height, tangent)
+    p = _params(0, COUNT_INTEGER, evaluator, e2_samples, mlp, None)
+    _check(lib.glint_reflect_probs(ctx.handle, env.handle, ctypes.byref(g), ctypes.byref(p), _dptr(out),
+                                   _stream_handle(stream)))
+
+
+class Mlp:
+    """glint_mlp: the BF16 surrogate of p_k, its FP32 master weights and Adam state."""
+
+    def __init__(self, ctx: Context, K: int, max_batch: int, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib.glint_mlp_create(ctx.handle, K, max_batch, seed & 0xFFFFFFFF, ctypes.byref(h)))
+        self.handle = h
+        self.ctx = ctx
+        self.K = K
+        self.max_batch = max_batch
+        self.n_params = lib.glint_mlp_param_count()
+
+    def set_params(self, params: np.ndarray):
+        a = np.ascontiguousarray(params, np.float32)
+        _check(lib.glint_mlp_set_params(self.handle, a.ctypes.data, a.size))
+
+    def export(self, item: int = MLP_PARAMS) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        _check(lib.glint_mlp_export(self.handle, item, out.ctypes.data, out.size))
+        return out
+
+    def import_state(self, params, adam_m, adam_v, step: int):
+        arrs = [np.ascontiguousarray(a, np.float32) for a in (params, adam_m, adam_v)]
+        _check(lib.glint_mlp_import_state(self.handle, arrs[0].ctypes.data, arrs[1].ctypes.data,
+                                          arrs[2].ctypes.data, self.n_params, step))
+
+    @property
+    def step(self) -> int:
+        return lib.glint_mlp_step(self.handle)
+
+    def features(self, env: "Env", planes, width: int, height: int, tangent, x=None, lp=None, stream=None):
+        """glint_mlp_features: inputs (npix, 64) int16 BF16 patterns and
+        log-priors (npix, K) float32 of every pixel, on the device."""
+        return mlp_features(self.ctx, env, planes, width, height, tangent, x, lp, stream)
+
+    def forward(self, x, lp, out=None, stream=None):
+        """glint_mlp_forward on given inputs x ((n, 64) BF16 patterns) and lp ((n, K))."""
+        import torch
+        n = x.shape[0]
+        if out is None:
+            out = torch.empty(n, self.K, device=x.device)
+        _check(lib.glint_mlp_forward(self.handle, _dptr(x), _dptr(lp), n, _dptr(out), _stream_handle(stream)))
+        return out
+
+    def train_step(self, x, lp, targets, first: int, batch: int, lr: float, want_loss: bool = False, stream=None):
+        """glint_mlp_train_step on samples first .. first+batch-1 (wrapping) of x, lp, targets."""
+        loss = ctypes.c_float(0.0)
+        _check(lib.glint_mlp_train_step(self.handle, _dptr(x), _dptr(lp), _dptr(targets), x.shape[0], first, batch,
+                                        lr, ctypes.byref(loss) if want_loss else None, _stream_handle(stream)))
+        return float(loss.value) if want_loss else None
+
+    def infer(self, env: "Env", planes, width: int, height: int, tangent, out, stream=None):
+        """glint_mlp_infer: p_k of every pixel (inputs computed on the fly)."""
+        g = _gbuffer(planes, width, height, tangent)
+        _check(lib.glint_mlp_infer(self.handle, self.ctx.handle, env.handle, ctypes.byref(g), _dptr(out),
+                                   _stream_handle(stream)))
+        return out
+
+    def last_launches(self) -> int:
+        return lib.glint_mlp_last_launches(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib.glint_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mlp_features(ctx: Context, env: Env, planes, width: int, height: int, tangent, x=None, lp=None, stream=None):
+    """glint_mlp_features: the surrogate's inputs of every pixel under `env`:
+    x (npix, 64) int16 tensor of BF16 bit patterns, lp (npix, K) float32."""
+    import torch
+    n = width * height
+    dev = planes[0].device
+    if x is None:
+        x = torch.empty(n, 64, dtype=torch.int16, device=dev)
+    if lp is None:
+        lp = torch.empty(n, env.cfg.K, device=dev)
+    g = _gbuffer(planes, width, height, tangent)
+    _check(lib.glint_mlp_features(ctx.handle, env.handle, ctypes.byref(g), _dptr(x), _dptr(lp),
+                                  _stream_handle(stream)))
+    return x, lp
 
 
 def normal_quantile(p, out=None, stream=None):

@@ -352,3 +352,29 @@ def gbuffer_random(n: int, seed: int = 7, a_lo: float = 0.03, a_hi: float = 0.3,
     tan[:n, :3] = t
     tan[n:, 0] = 1.0
     return GBuffer(W, H, planes, f"random {n} px", tan.reshape(H, W, 4))
+
+
+def mlp_params(seed: int = 11, K: int = 8, bias: float = 0.1) -> np.ndarray:
+    """Float32 parameter vector of the p_k surrogate (layout W1 [64][64], b1,
+    W2 [64][64], b2, W3 [64][16], b3) with He-normal weights, small random
+    biases and zero unused output columns (>= K)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(size=(64, 64)) * np.sqrt(2.0 / 36.0)
+    W1[36:] = 0.0
+    W2 = rng.normal(size=(64, 64)) * np.sqrt(2.0 / 64.0)
+    W3 = rng.normal(size=(64, 16)) * np.sqrt(2.0 / 64.0)
+    W3[:, K:] = 0.0
+    b1, b2, b3 = (rng.uniform(-bias, bias, size=n) for n in (64, 64, 16))
+    b3[K:] = 0.0
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3]).astype(np.float32)
+
+
+def distributions(n: int, K: int, seed: int = 12, sharp: float = 2.0) -> np.ndarray:
+    """(n, K) float32 rows that are probability distributions (softmax of
+    Gaussian logits scaled by `sharp`), with about a tenth of the entries 0."""
+    rng = np.random.default_rng(seed)
+    z = rng.normal(size=(n, K)) * sharp
+    z[rng.uniform(size=(n, K)) < 0.1] = -np.inf
+    z[:, 0] = np.where(np.all(np.isinf(z), axis=1), 0.0, z[:, 0])
+    e = np.exp(z - z.max(axis=1, keepdims=True))
+    return (e / e.sum(axis=1, keepdims=True)).astype(np.float32)

@@ -40,11 +40,18 @@ def test_every_declared_symbol_is_exported(lib):
 def test_host_argument_checks_without_gpu(lib):
     lib.glint_last_error.restype = ctypes.c_char_p
     lib.glint_abi_version.restype = ctypes.c_int
-    assert lib.glint_abi_version() == 1
+    assert lib.glint_abi_version() == 2
     assert lib.glint_ctx_create(0, 0, 0, None) == 1
     assert b"NULL" in lib.glint_last_error()
     assert lib.glint_env_create(None, None, None) == 1
     assert lib.glint_shade(None, None, None, None, None, None, None) == 1
     assert lib.glint_env_update(None, None, None) == 1
+    assert lib.glint_reflect_probs(None, None, None, None, None, None) == 1
+    assert lib.glint_mlp_create(None, 8, ctypes.c_long(1024), 0, None) == 1
+    assert lib.glint_mlp_train_step(None, None, None, ctypes.c_long(0), ctypes.c_long(1), ctypes.c_float(0.0),
+                                    None, None) == 1
+    assert lib.glint_mlp_infer(None, None, None, None) == 1
+    assert lib.glint_mlp_param_count() == 64 * 64 + 64 + 64 * 64 + 64 + 64 * 16 + 16
     lib.glint_ctx_destroy(None)
     lib.glint_env_destroy(None)
+    lib.glint_mlp_destroy(None)

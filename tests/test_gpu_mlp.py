@@ -1,0 +1,325 @@
+"""The BF16 tensor-core surrogate of p_k against the FP64 reference network
+(oracle/mlp.py) and the oracle's inputs (or_mlp_features), through the C ABI:
+the inputs of every pixel, the network on given inputs, the loss gradient of
+a batch, the Adam step, determinism and checkpoint resume; the fused
+inference and the MLP shading path against their two-call forms; shading
+with given p_k against the oracle.
+
+Tolerances: the inputs must equal the oracle's after BF16 rounding unless a
+rounding boundary lies within the FP32 error of the filtered maps and
+directions; the network's outputs and gradients lie within the reference's
+error model of an FP32/BF16 evaluation (oracle.mlp.error_bounds), and their
+aggregate difference far below BF16 precision."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2507_02674_gb300 import synth
+from tests._pipeline import MethodParams, oracle_env, oracle_lut, oracle_shade
+from tests.test_gpu_parity import _cfg, _check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_02674_gb300 import build as B
+    B.build()
+    from paper_2507_02674_gb300 import glint, render
+    ctx = glint.Context(0, 64, 128)
+    return glint, render, ctx, torch
+
+
+def _bits(X) -> np.ndarray:
+    """Oracle inputs as BF16 bit patterns (the oracle's own rounding)."""
+    return (omlp.bf16(X).astype(np.float32).view(np.uint32) >> 16).astype(np.uint16).view(np.int16)
+
+
+def _setup(gl, orc, K, n, seed, Wo=128):
+    """An fp16 HDR map with suns, random pixels; the oracle's inputs."""
+    glint, render, ctx, torch = gl
+    mp = MethodParams(K=K, Wo=Wo, seed=seed)
+    env = synth.env_hdr(seed=seed, W=256, H=128)
+    gb = synth.gbuffer_random(n, seed=seed + 1, width=n)
+    gb.planes[0].reshape(-1, 4)[::17, 3] = 0.0  # some background pixels
+    e, pref = oracle_env(orc, env, mp)
+    X, lp = orc.mlp_features(gb.rows16(), gb.tangents(), pref, mp.s_min, mp.s_max, oracle_lut(orc, mp), K)
+    return mp, env, gb, X, lp
+
+
+def _dev_inputs(torch, X, lp):
+    return torch.from_numpy(_bits(X)).cuda(), torch.from_numpy(lp.astype(np.float32)).cuda()
+
+
+@pytest.mark.parametrize("K", [2, 4, 8])
+def test_mlp_inputs_match_oracle(gl, orc, K):
+    """glint_mlp_features against or_mlp_features, 1537 random pixels (ragged
+    tail, some background): E1's p_k within the shading parity tolerance
+    (2^-14 relative), tap weights within 2^-15 (filtered-map parity plus the
+    FP32 direction error), scalars within 2^-21; after BF16 rounding the
+    values must be equal unless a rounding boundary lies within that reach."""
+    glint, render, ctx, torch = gl
+    mp, env, gb, X, lp = _setup(gl, orc, K, 1537, 20 + K)
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    planes = render.gbuffer_tensors(gb)
+    x, l = glint.mlp_features(ctx, fr.env, planes, gb.width, gb.height, render.tangent_tensor(gb))
+    torch.cuda.synchronize()
+    xg = (x.cpu().numpy().view(np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    tol = np.zeros_like(X)
+    tol[:, :K] = 2.0 ** -14 * np.abs(X[:, :K]) + 2.0 ** -30
+    tol[:, K:6 * K] = 2.0 ** -15
+    tol[:, 6 * K:6 * K + 3] = 2.0 ** -21
+    fg = gb.rows16()[:, 3] > 0
+    assert (~fg).any()
+    allowed = omlp.rounding_delta(X, tol)
+    err = np.abs(xg - omlp.bf16(X))
+    bad = np.argwhere(err > allowed)
+    assert bad.size == 0, (bad[:5], xg[tuple(bad[0])], X[tuple(bad[0])])
+    exact = float(np.mean(err[fg] == 0))
+    print(f"K={K}: inputs equal after rounding {exact:.4%}")
+    lg = l.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(lg[fg], lp[fg], rtol=0, atol=2.0 ** -20 * np.abs(lp[fg]).max() + 1e-6)
+    assert np.all(xg[~fg] == 0) and np.all(lg[~fg] == 0)
+
+
+@pytest.mark.parametrize("K", [2, 4, 8])
+def test_mlp_forward_matches_oracle(gl, orc, K):
+    """The network on the oracle's inputs (1537 rows: 12 full tiles and a
+    ragged one), random weights, against the reference's error model."""
+    glint, render, ctx, torch = gl
+    mp, env, gb, X, lp = _setup(gl, orc, K, 1537, 30 + K)
+    prm = synth.mlp_params(seed=50 + K, K=K)
+    net = glint.Mlp(ctx, K, 4096)
+    net.set_params(prm)
+    x, l = _dev_inputs(torch, X, lp)
+    out = net.forward(x, l)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    lp32 = lp.astype(np.float32).astype(np.float64)
+    ref = omlp.forward(prm, omlp.bf16(X), K, lp32)["p"]
+    tol, _ = omlp.error_bounds(prm, omlp.bf16(X), None, K, lp32, feat_err=0.0)
+    err = np.abs(got - ref)
+    bad = np.argwhere(err > tol + 2.0 ** -24)
+    assert bad.size == 0, (bad[:5], err[tuple(bad[0])], tol[tuple(bad[0])])
+    rel = np.linalg.norm(err) / np.linalg.norm(ref)
+    print(f"K={K}: forward rel L2 {rel:.2e}, max abs {err.max():.2e}, rows within 1e-5: "
+          f"{np.mean(err.max(1) < 1e-5):.1%}")
+    assert rel < 2.0 ** -14
+    np.testing.assert_allclose(got.sum(1), 1.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("K,n,first,batch", [(4, 3000, 1700, 2500), (8, 3000, 0, 3000), (2, 1000, 900, 777),
+                                             (8, 70000, 5, 65613)])
+def test_mlp_gradient_matches_oracle(gl, K, n, first, batch):
+    """Gradient of the mean cross-entropy over `batch` samples starting at
+    `first` (wrapping around the data set), seeded inputs shaped like the
+    surrogate's; the largest case runs several 128-sample chunks per
+    resident block."""
+    glint, render, ctx, torch = gl
+    rng = np.random.default_rng(60 + K)
+    X = np.zeros((n, 64))
+    X[:, :6 * K] = rng.uniform(0, 1, size=(n, 6 * K))
+    X[:, 6 * K:6 * K + 3] = rng.uniform(0.1, 1, size=(n, 3))
+    X = omlp.bf16(X)
+    lp = np.log(np.maximum(synth.distributions(n, K, seed=61 + K), 1e-6)).astype(np.float32).astype(np.float64)
+    Y = synth.distributions(n, K, seed=70 + K)
+    prm = synth.mlp_params(seed=80 + K, K=K)
+    net = glint.Mlp(ctx, K, batch)
+    net.set_params(prm)
+    x, l = _dev_inputs(torch, X, lp)
+    loss = net.train_step(x, l, torch.from_numpy(Y).cuda(), first, batch, 0.0, want_loss=True)
+    got = net.export(glint.MLP_GRAD).astype(np.float64)
+    rows = (first + np.arange(batch)) % n
+    Yr = Y[rows].astype(np.float64)
+    g, mag, L = omlp.gradient(prm, X[rows], Yr, K, lp[rows])
+    _, tol = omlp.error_bounds(prm, X[rows], Yr, K, lp[rows], feat_err=0.0)
+    err = np.abs(got - g)
+    bad = np.nonzero(err > tol + 1e-12)[0]
+    assert bad.size == 0, (bad[:5], err[bad[:5]], tol[bad[:5]], g[bad[:5]])
+    rel = np.linalg.norm(got - g) / np.linalg.norm(g)
+    print(f"K={K} batch={batch}: gradient rel L2 {rel:.2e}, loss {loss:.6f} vs {L:.6f}")
+    assert rel < 2.0 ** -9
+    assert loss == pytest.approx(L, rel=1e-4)
+    assert np.all(got.reshape(-1)[omlp.N_PARAMS - 16 + K:] == 0.0)
+
+
+def test_mlp_adam_step_matches_oracle(gl):
+    """One Adam step (step 5 of a run) from given moments: every parameter lies
+    within the range of the oracle's updates over its gradient tolerance."""
+    glint, render, ctx, torch = gl
+    K, n = 8, 2000
+    rng = np.random.default_rng(90)
+    X = np.zeros((n, 64))
+    X[:, :51] = rng.uniform(0, 1, size=(n, 51))
+    X = omlp.bf16(X)
+    lp = np.zeros((n, K))
+    Y = synth.distributions(n, K, seed=91)
+    prm = synth.mlp_params(seed=92, K=K)
+    m0 = (rng.normal(size=omlp.N_PARAMS) * 1e-3).astype(np.float32)
+    v0 = rng.uniform(1e-7, 1e-5, size=omlp.N_PARAMS).astype(np.float32)
+    net = glint.Mlp(ctx, K, n)
+    net.import_state(prm, m0, v0, 4)
+    x, l = _dev_inputs(torch, X, lp)
+    lr = 1e-3
+    net.train_step(x, l, torch.from_numpy(Y).cuda(), 0, n, lr)
+    assert net.step == 5
+    w1 = net.export(glint.MLP_PARAMS).astype(np.float64)
+    g, _, _ = omlp.gradient(prm, X, Y.astype(np.float64), K, lp)
+    _, tol = omlp.error_bounds(prm, X, Y.astype(np.float64), K, lp, feat_err=0.0)
+    used = np.ones(omlp.N_PARAMS, bool)
+    W3 = np.arange(omlp.N_PARAMS - 16 - 64 * 16, omlp.N_PARAMS - 16).reshape(64, 16)
+    used[W3[:, K:].ravel()] = False
+    used[omlp.N_PARAMS - 16 + K:] = False
+    # the update is not monotone in g (m and sqrt(v) both move): scan the interval
+    ws = np.stack([omlp.adam(prm, g + s * tol, m0, v0, 5, lr)[0] for s in np.linspace(-1.0, 1.0, 65)])
+    lo, hi = ws.min(0), ws.max(0)
+    slack = 2.0 ** -22 * np.abs(prm) + 1e-3 * lr
+    assert np.all((w1 >= lo - slack) & (w1 <= hi + slack) | ~used)
+    assert np.all(w1[~used] == prm[~used])
+
+
+def test_mlp_training_is_deterministic_and_resumes(gl):
+    """Same inputs give bit-identical parameters; a run restored from a
+    checkpoint after 3 steps continues bit-identically."""
+    glint, render, ctx, torch = gl
+    K, n = 8, 20000
+    rng = np.random.default_rng(95)
+    X = np.zeros((n, 64))
+    X[:, :51] = rng.uniform(0, 1, size=(n, 51))
+    x = torch.from_numpy(_bits(X)).cuda()
+    l = torch.zeros(n, K, device="cuda")
+    Y = torch.from_numpy(synth.distributions(n, K, seed=96)).cuda()
+
+    def run(net, steps, start=0):
+        for s in range(start, steps):
+            net.train_step(x, l, Y, s * 4096, 4096, 2e-3)
+        torch.cuda.synchronize()
+
+    a = glint.Mlp(ctx, K, 4096, seed=7)
+    run(a, 3)
+    ck = [a.export(i) for i in (glint.MLP_PARAMS, glint.MLP_ADAM_M, glint.MLP_ADAM_V)]
+    run(a, 6, 3)
+    b = glint.Mlp(ctx, K, 4096, seed=7)
+    run(b, 6)
+    c = glint.Mlp(ctx, K, 4096, seed=123)
+    c.import_state(*ck, 3)
+    run(c, 6, 3)
+    pa, pb, pc = (v.export(glint.MLP_PARAMS) for v in (a, b, c))
+    assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+    assert np.array_equal(pa.view(np.uint32), pc.view(np.uint32))
+    assert a.step == b.step == c.step == 6
+    assert not np.array_equal(pa, ck[0])
+
+
+def test_shade_with_given_probabilities(gl, orc):
+    """GLINT_EVAL_GIVEN shades with caller-supplied p_k (seeded distributions);
+    counts, N_P, grid and radiance against the oracle given the same p_k."""
+    glint, render, ctx, torch = gl
+    K = 8
+    mp = MethodParams(K=K, Wo=128, seed=19)
+    env = synth.env_hdr(seed=6, W=256, H=128)
+    gb = synth.gbuffer_random(1537, seed=77, width=1537)
+    n = gb.width * gb.height
+    pk = synth.distributions(n, K, seed=78)
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    planes = render.gbuffer_tensors(gb)
+    dbg = glint.debug_buffers(n, K)
+    out = fr.shade(planes, gb.width, gb.height, seed=mp.seed, debug=dbg, evaluator=glint.EVAL_GIVEN,
+                   p_scratch=torch.from_numpy(pk).cuda())
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in dbg.items()}
+    res["rgb"] = out[:, :3].cpu().numpy().astype(np.float64)
+    fg = gb.rows16()[:, 3] > 0
+    assert np.array_equal(res["p"][fg], pk[fg])
+    o = oracle_shade(orc, gb.rows16(), env, mp, evaluator=2, pk_in=pk.astype(np.float64))
+    _check(orc, o, res)
+
+
+def test_mlp_paths_agree(gl):
+    """Fused inference = glint_mlp_features then glint_mlp_forward; the MLP
+    evaluator = fused inference into the scratch buffer then shading with those
+    p_k (both bit for bit); glint_reflect_probs agrees with the debug p_k of E1
+    and E2 shading to FP32 rounding."""
+    glint, render, ctx, torch = gl
+    K = 8
+    mp = MethodParams(K=K, Wo=128, seed=3)
+    env = synth.env_hdr(seed=6, W=256, H=128)
+    gb = synth.gbuffer_random(4000, seed=5, width=100)
+    n = gb.width * gb.height
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    planes = render.gbuffer_tensors(gb)
+    tan = render.tangent_tensor(gb)
+    net = glint.Mlp(ctx, K, 1024, seed=9)
+    net.set_params(synth.mlp_params(seed=10, K=K))
+    x, l = glint.mlp_features(ctx, fr.env, planes, gb.width, gb.height, tan)
+    p_two = net.forward(x, l)
+    p_inf = net.infer(fr.env, planes, gb.width, gb.height, tan, torch.empty(n, K, device="cuda"))
+    fg = torch.from_numpy(gb.rows16()[:, 3] > 0).cuda()
+    torch.cuda.synchronize()
+    assert torch.equal(p_inf[fg], p_two[fg]) and torch.all(p_inf[~fg] == 0)
+    scratch = torch.zeros(n, K, device="cuda")
+    dbg = glint.debug_buffers(n, K)
+    img = fr.shade(planes, gb.width, gb.height, seed=mp.seed, debug=dbg, tangent=tan, evaluator=glint.EVAL_MLP,
+                   mlp=net, p_scratch=scratch)
+    assert ctx.last_launches() == 2
+    img2 = fr.shade(planes, gb.width, gb.height, seed=mp.seed, evaluator=glint.EVAL_GIVEN, p_scratch=p_inf)
+    p_probs = fr.probs(planes, gb.width, gb.height, evaluator=glint.EVAL_MLP, tangent=tan, mlp=net)
+    torch.cuda.synchronize()
+    assert torch.equal(scratch, p_inf) and torch.equal(p_probs, p_inf)
+    assert torch.equal(img, img2)
+    assert torch.equal(dbg["p"][fg], p_inf[fg])
+    for ev in (glint.EVAL_E1, glint.EVAL_E2):
+        d = glint.debug_buffers(n, K)
+        fr.shade(planes, gb.width, gb.height, seed=mp.seed, debug=d, tangent=tan, evaluator=ev)
+        pr = fr.probs(planes, gb.width, gb.height, evaluator=ev, tangent=tan)
+        torch.cuda.synchronize()
+        # separately compiled kernels may contract multiply-adds differently
+        torch.testing.assert_close(pr[fg], d["p"][fg], rtol=2.0 ** -18, atol=2.0 ** -21)
+        assert torch.all(pr[~fg] == 0)
+
+
+def test_mlp_invalid_arguments(gl):
+    glint, render, ctx, torch = gl
+    with pytest.raises(glint.GlintError):
+        glint.Mlp(ctx, 3, 1024)
+    with pytest.raises(glint.GlintError) as e16:
+        glint.Mlp(ctx, 16, 1024)
+    assert e16.value.status == 6  # unsupported
+    with pytest.raises(glint.GlintError):
+        glint.Mlp(ctx, 8, 0)
+    net = glint.Mlp(ctx, 8, 256)
+    x = torch.zeros(300, 64, dtype=torch.int16, device="cuda")
+    l = torch.zeros(300, 8, device="cuda")
+    Y = torch.from_numpy(synth.distributions(300, 8)).cuda()
+    with pytest.raises(glint.GlintError):
+        net.train_step(x, l, Y, 0, 257, 1e-3)  # batch above max_batch
+    with pytest.raises(glint.GlintError):
+        net.train_step(x, l, Y, 0, 100, 1.5)  # lr outside [0, 1)
+    with pytest.raises(glint.GlintError):
+        net.train_step(x.view(-1)[1:1 + 299 * 64].view(299, 64), l, Y, 0, 100, 1e-3)  # 2-byte offset
+    with pytest.raises(glint.GlintError):
+        net.set_params(np.zeros(10, np.float32))
+    mp = MethodParams(K=4, Wo=64)
+    fr = render.Frame(ctx, synth.env_tiny(0), _cfg(glint, mp))
+    fr.update_env()
+    gb = synth.gbuffer_random(300, seed=1, width=300)
+    gpl = render.gbuffer_tensors(gb)
+    tan = render.tangent_tensor(gb)
+    out = torch.empty(300, 4, device="cuda")
+    with pytest.raises(glint.GlintError):  # network K 8, environment K 4
+        glint.shade(ctx, fr.env, gpl, 300, 1, out, tangent=tan, evaluator=glint.EVAL_MLP, mlp=net,
+                    p_scratch=torch.empty(300, 4, device="cuda"))
+    with pytest.raises(glint.GlintError):
+        net.infer(fr.env, gpl, 300, 1, tan, torch.empty(300, 8, device="cuda"))
+    with pytest.raises(glint.GlintError):  # no scratch buffer
+        glint.shade(ctx, fr.env, gpl, 300, 1, out, evaluator=glint.EVAL_GIVEN)
+    with pytest.raises(glint.GlintError):
+        glint.reflect_probs(ctx, fr.env, gpl, 300, 1, torch.empty(300, 4, device="cuda"), evaluator=glint.EVAL_GIVEN)
+    with pytest.raises(glint.GlintError):  # no tangent plane
+        glint.mlp_features(ctx, fr.env, gpl, 300, 1, None)

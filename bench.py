@@ -241,6 +241,108 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+SURROGATE_TRAIN_SCENES = (101, 102)   # scene seeds of the training pixels (the timed frame is seed 1)
+SURROGATE_STEPS, SURROGATE_BATCH, SURROGATE_LR = 6000, 8192, 2e-3
+SURROGATE_LABEL_S, E2_S = 32, 16
+
+
+def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed):
+    """Train the p_k surrogate for this environment on E2 labels of pixels of
+    other scenes, then time the surrogate path (env update + fused inference +
+    shading with the network's p_k) and the plain E2 path on the timed frame,
+    and measure the network's error against E2's p_k."""
+    import torch
+    from paper_2507_02674_gb300 import synth
+    dev = planes[0].device
+    t0 = time.time()
+    xs, ls, ys = [], [], []
+    for sd in SURROGATE_TRAIN_SCENES:
+        g = synth.gbuffer_scene(WIDTH, HEIGHT, seed=sd)
+        p = render.gbuffer_tensors(g, device=dev)
+        t = render.tangent_tensor(g, device=dev)
+        n = p[0].shape[0]
+        x, l = glint.mlp_features(ctx, fr.env, p, n, 1, t, stream=stream)
+        y = fr.probs(p, n, 1, evaluator=glint.EVAL_E2, e2_samples=SURROGATE_LABEL_S, tangent=t, stream=stream)
+        fg = p[0][:, 3] > 0
+        xs.append(x[fg]); ls.append(l[fg]); ys.append(y[fg])
+    gen = torch.Generator(device=dev).manual_seed(0)
+    X, L, Y = torch.cat(xs), torch.cat(ls), torch.cat(ys)
+    perm = torch.randperm(X.shape[0], device=dev, generator=gen)
+    X, L, Y = X[perm].contiguous(), L[perm].contiguous(), Y[perm].contiguous()
+    torch.cuda.synchronize(dev)
+    prep_s = time.time() - t0
+    net = glint.Mlp(ctx, K, SURROGATE_BATCH, seed=1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for i in range(SURROGATE_STEPS):
+        lr = max(SURROGATE_LR * 0.5 * (1 + math.cos(math.pi * i / SURROGATE_STEPS)), 1e-5)
+        net.train_step(X, L, Y, i * SURROGATE_BATCH, SURROGATE_BATCH, lr, stream=stream)
+    b.record(stream)
+    final_loss = net.train_step(X, L, Y, 0, SURROGATE_BATCH, 0.0, want_loss=True, stream=stream)
+    torch.cuda.synchronize(dev)
+    train_ms = a.elapsed_time(b)
+    n_train = X.shape[0]
+    del X, L, Y, xs, ls, ys
+
+    tan = render.tangent_tensor(gb, device=dev)
+    npix = WIDTH * HEIGHT
+    p_e2 = fr.probs(planes, WIDTH, HEIGHT, evaluator=glint.EVAL_E2, e2_samples=E2_S, tangent=tan, stream=stream)
+    p_e1 = fr.probs(planes, WIDTH, HEIGHT, evaluator=glint.EVAL_E1, tangent=tan, stream=stream)
+    p_nn = net.infer(fr.env, planes, WIDTH, HEIGHT, tan, torch.empty(npix, K, device=dev), stream=stream)
+    torch.cuda.synchronize(dev)
+    fgm = planes[0][:, 3] > 0
+
+    def err(p):
+        d = (p[fgm] - p_e2[fgm]).double()
+        per = torch.sqrt((d * d).mean(0)).cpu().numpy()
+        return {"rmse": round(float(torch.sqrt((d * d).mean())), 5), "max": round(float(d.abs().max()), 4),
+                "rmse_per_component": [round(float(v), 5) for v in per]}
+
+    scratch = torch.empty(npix, K, device=dev)
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for _ in range(3):
+            flush.zero_()
+            fn()
+        for e in evs:
+            flush.zero_()
+            e[0].record(stream)
+            fn()
+            e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        return np.array([e[0].elapsed_time(e[1]) for e in evs])
+
+    def mlp_step():
+        fr.update_env(stream)
+        fr.shade(planes, WIDTH, HEIGHT, out=out, seed=seed, stream=stream, tangent=tan, evaluator=glint.EVAL_MLP,
+                 mlp=net, p_scratch=scratch)
+
+    def e2_step():
+        fr.update_env(stream)
+        fr.shade(planes, WIDTH, HEIGHT, out=out, seed=seed, stream=stream, tangent=tan, evaluator=glint.EVAL_E2,
+                 e2_samples=E2_S)
+
+    ms_nn = timed(mlp_step, args.steps)
+    ms_e2 = timed(e2_step, max(3, min(args.steps, 10)))
+    return {
+        "path": "env update + glint_mlp_infer (fused inputs + BF16 mma.sync network) + shading with its p_k",
+        "value": round(npix / (float(ms_nn.mean()) / 1e3) / 1e6, 3), "unit": "Mpixel/s",
+        "ms_per_step": round(float(ms_nn.mean()), 4),
+        "p50_ms": round(float(np.percentile(ms_nn, 50)), 4), "p99_ms": round(float(np.percentile(ms_nn, 99)), 4),
+        "vs_e2": {"e2_samples": E2_S, "e2_value": round(npix / (float(ms_e2.mean()) / 1e3) / 1e6, 3),
+                  "e2_ms_per_step": round(float(ms_e2.mean()), 4),
+                  "speedup": round(float(ms_e2.mean() / ms_nn.mean()), 2)},
+        "error_vs_e2_p_k": err(p_nn), "e1_error_vs_e2_p_k": err(p_e1),
+        "train": {"samples": int(n_train), "label": f"E2 S={SURROGATE_LABEL_S}", "steps": SURROGATE_STEPS,
+                  "batch": SURROGATE_BATCH, "ms": round(train_ms, 1),
+                  "msamples_per_s": round(SURROGATE_STEPS * SURROGATE_BATCH / train_ms / 1e3, 2),
+                  "final_loss": round(final_loss, 5), "data_prep_s": round(prep_s, 2),
+                  "scenes": list(SURROGATE_TRAIN_SCENES)},
+        "gpu_launches_per_step": fr.env.last_launches() + ctx.last_launches(),
+    }
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -367,6 +469,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": launches_per_step * args.steps,
         }
+    if rank == 0 and not args.no_surrogate:
+        result["surrogate"] = surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed)
     if pg:
         pg.barrier()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -384,6 +488,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -323,3 +323,69 @@ def test_mlp_invalid_arguments(gl):
         glint.reflect_probs(ctx, fr.env, gpl, 300, 1, torch.empty(300, 4, device="cuda"), evaluator=glint.EVAL_GIVEN)
     with pytest.raises(glint.GlintError):  # no tangent plane
         glint.mlp_features(ctx, fr.env, gpl, 300, 1, None)
+
+
+def test_trained_network_gains_over_e1_and_e2(gl):
+    """What the learned part gains: trained on E2 labels of pixels of two
+    scenes under one map, the network's p_k on a third scene are much closer to
+    E2's than E1's are, at a fraction of E2's cost."""
+    glint, render, ctx, torch = gl
+    K = 8
+    cfg = glint.EnvConfig(K=K)
+    fr = render.Frame(ctx, synth.env_hdr(seed=2, W=512, H=256), cfg)
+    fr.update_env()
+    xs, ls, ys = [], [], []
+    for sd in (111, 112):
+        g = synth.gbuffer_scene(960, 540, seed=sd)
+        p, t = render.gbuffer_tensors(g), render.tangent_tensor(g)
+        n = p[0].shape[0]
+        x, l = glint.mlp_features(ctx, fr.env, p, n, 1, t)
+        y = fr.probs(p, n, 1, evaluator=glint.EVAL_E2, e2_samples=32, tangent=t)
+        fg = p[0][:, 3] > 0
+        xs.append(x[fg]); ls.append(l[fg]); ys.append(y[fg])
+    X, L, Y = torch.cat(xs), torch.cat(ls), torch.cat(ys)
+    perm = torch.randperm(X.shape[0], device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    X, L, Y = X[perm].contiguous(), L[perm].contiguous(), Y[perm].contiguous()
+    net = glint.Mlp(ctx, K, 8192, seed=1)
+    steps = 3000
+    first = net.train_step(X, L, Y, 0, 8192, 0.0, want_loss=True)
+    for i in range(steps):
+        net.train_step(X, L, Y, i * 8192, 8192, max(2e-3 * 0.5 * (1 + np.cos(np.pi * i / steps)), 1e-5))
+    last = net.train_step(X, L, Y, 0, 8192, 0.0, want_loss=True)
+    assert last < first
+
+    gb = synth.gbuffer_scene(960, 540, seed=3)
+    p, t = render.gbuffer_tensors(gb), render.tangent_tensor(gb)
+    n = gb.width * gb.height
+    pe2 = fr.probs(p, gb.width, gb.height, evaluator=glint.EVAL_E2, e2_samples=16, tangent=t)
+    pe1 = fr.probs(p, gb.width, gb.height, evaluator=glint.EVAL_E1, tangent=t)
+    pnn = net.infer(fr.env, p, gb.width, gb.height, t, torch.empty(n, K, device="cuda"))
+    fg = p[0][:, 3] > 0
+
+    def rmse(a):
+        d = (a[fg] - pe2[fg]).double()
+        return float(torch.sqrt((d * d).mean()))
+
+    r_nn, r_e1 = rmse(pnn), rmse(pe1)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = torch.empty(n, 4, device="cuda")
+    scratch = torch.empty(n, K, device="cuda")
+    t_nn = timed(lambda: fr.shade(p, gb.width, gb.height, out=out, tangent=t, evaluator=glint.EVAL_MLP, mlp=net,
+                                  p_scratch=scratch))
+    t_e2 = timed(lambda: fr.shade(p, gb.width, gb.height, out=out, tangent=t, evaluator=glint.EVAL_E2, e2_samples=16))
+    print(f"p_k RMSE vs E2: network {r_nn:.4f}, E1 {r_e1:.4f}; loss {first:.4f} -> {last:.4f}; "
+          f"shading {t_nn:.3f} ms (network) vs {t_e2:.3f} ms (E2)")
+    assert r_nn < 0.5 * r_e1
+    assert r_nn < 0.015
+    assert t_nn * 3 < t_e2

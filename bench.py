@@ -343,6 +343,121 @@ def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed
     }
 
 
+SERVE_REQUESTS, SERVE_RATE_HZ, SERVE_SEED = 256, 200.0, 3
+SERVE_RES = ((640, 360), (1280, 720), (1920, 1080), (3840, 2160))
+SERVE_ENVS = (1, 2, 3, 4)
+SERVE_BUDGET = 8 << 30
+
+
+def _train_net(glint, render, ctx, fr, scenes, steps, stream):
+    """A surrogate for environment `fr`, trained on E2 labels of `scenes`' pixels."""
+    import torch
+    xs, ls, ys = [], [], []
+    for g, p, t in scenes:
+        n = p[0].shape[0]
+        x, l = glint.mlp_features(ctx, fr.env, p, n, 1, t, stream=stream)
+        y = fr.probs(p, n, 1, evaluator=glint.EVAL_E2, e2_samples=SURROGATE_LABEL_S, tangent=t, stream=stream)
+        fg = p[0][:, 3] > 0
+        xs.append(x[fg]); ls.append(l[fg]); ys.append(y[fg])
+    X, L, Y = torch.cat(xs), torch.cat(ls), torch.cat(ys)
+    gen = torch.Generator(device=X.device).manual_seed(0)
+    perm = torch.randperm(X.shape[0], device=X.device, generator=gen)
+    X, L, Y = X[perm].contiguous(), L[perm].contiguous(), Y[perm].contiguous()
+    net = glint.Mlp(ctx, K, SURROGATE_BATCH, seed=1)
+    for i in range(steps):
+        lr = max(SURROGATE_LR * 0.5 * (1 + math.cos(math.pi * i / steps)), 1e-5)
+        net.train_step(X, L, Y, i * SURROGATE_BATCH, SURROGATE_BATCH, lr, stream=stream)
+    torch.cuda.synchronize(X.device)
+    return net
+
+
+def serving(args, glint, render, ctx, dev, stream):
+    """Continuous batching: SERVE_REQUESTS frames arrive as a Poisson process
+    (SERVE_RATE_HZ), resolution uniform over SERVE_RES, map uniform over the
+    resident maps; each is submitted from pinned host memory when it arrives,
+    and the server's ticks run until every frame has been copied back.  Frame
+    latency = copy-back completion - submission (host clock)."""
+    import torch
+    from paper_2507_02674_gb300 import synth
+    cfg = glint.EnvConfig(K=K, levels=R, samples=S, out_width=WO)
+    frs = []
+    for sd in SERVE_ENVS:
+        f = render.Frame(ctx, synth.env_hdr(seed=sd, W=ENV_W, H=ENV_H), cfg, device=dev)
+        f.update_env(stream)
+        frs.append(f)
+    train_scenes = []
+    for sd in SURROGATE_TRAIN_SCENES:
+        g = synth.gbuffer_scene(WIDTH, HEIGHT, seed=sd)
+        train_scenes.append((g, render.gbuffer_tensors(g, device=dev), render.tangent_tensor(g, device=dev)))
+    nets = [_train_net(glint, render, ctx, f, train_scenes, SURROGATE_STEPS // 2, stream) for f in frs]
+    del train_scenes
+    host = []
+    for i, (w, h) in enumerate(SERVE_RES):
+        g = synth.gbuffer_scene(w, h, seed=200 + i)
+        host.append((w, h, render.gbuffer_tensors(g, device="cpu", pinned=True),
+                     torch.from_numpy(g.tangents()).pin_memory()))
+    rng = np.random.default_rng(SERVE_SEED)
+    arrivals = np.cumsum(rng.exponential(1.0 / SERVE_RATE_HZ, SERVE_REQUESTS))
+    res_of = rng.integers(0, len(SERVE_RES), SERVE_REQUESTS)
+    env_of = rng.integers(0, len(SERVE_ENVS), SERVE_REQUESTS)
+    outs = {i: [] for i in range(len(SERVE_RES))}
+
+    def run(evaluator):
+        srv = glint.Server(ctx, K, SERVE_BUDGET, tick_pixels=1 << 22, tile_pixels=16384, max_frames=64)
+        eids = [srv.add_env(f.env, n) for f, n in zip(frs, nets)]
+        free = {i: list(outs[i]) for i in outs}
+        busy = {}
+        lat, npx = [], 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        k = 0
+        done_n = 0
+        while done_n < SERVE_REQUESTS:
+            now = time.perf_counter() - t0
+            if now > 120.0:
+                raise RuntimeError(f"serving: {SERVE_REQUESTS - done_n} frames unfinished after 120 s")
+            while k < SERVE_REQUESTS and arrivals[k] <= now:
+                r = int(res_of[k])
+                w, h, planes, tan = host[r]
+                if not free[r]:
+                    free[r].append(torch.empty(w * h, 4).pin_memory())
+                    outs[r].append(free[r][-1])
+                o = free[r].pop()
+                fid = srv.submit(eids[int(env_of[k])], planes, w, h, o, seed=k, evaluator=evaluator, tangent=tan)
+                busy[fid] = (r, o, w * h)
+                k += 1
+            srv.tick(stream)
+            for fid, sub_s, adm_s, done_s in srv.poll():
+                r, o, n = busy.pop(fid)
+                free[r].append(o)
+                lat.append((done_s - sub_s) * 1e3)
+                npx += n
+                done_n += 1
+            if k < SERVE_REQUESTS and not busy:
+                time.sleep(max(0.0, min(arrivals[k] - (time.perf_counter() - t0), 0.002)))
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat)
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "mean_ms": round(float(lat.mean()), 3), "max_ms": round(float(lat.max()), 3),
+                "mpix_s_offered": round(npx / wall / 1e6, 2), "wall_s": round(wall, 3),
+                "ticks": st["ticks"], "launches": st["launches"], "items": st["items"],
+                "peak_device_bytes": st["peak_bytes"]}
+
+    # outputs: two pinned buffers per resolution up front (more on demand)
+    for i, (w, h) in enumerate(SERVE_RES):
+        outs[i] = [torch.empty(w * h, 4).pin_memory() for _ in range(2)]
+    run(glint.EVAL_E1)  # warm-up pass (pinned pools, module loads)
+    plain = run(glint.EVAL_E1)
+    surrogate_ = run(glint.EVAL_MLP)
+    return {"requests": SERVE_REQUESTS, "arrivals": f"Poisson, mean {SERVE_RATE_HZ:.0f}/s, seed {SERVE_SEED}",
+            "resolutions": [f"{w}x{h}" for w, h in SERVE_RES], "envs": len(SERVE_ENVS),
+            "memory_budget_bytes": SERVE_BUDGET,
+            "latency": "host clock from submission to the completed copy back of the frame",
+            "plain": plain, "surrogate": surrogate_}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -471,6 +586,8 @@ def run_ours(args):
         }
     if rank == 0 and not args.no_surrogate:
         result["surrogate"] = surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed)
+    if rank == 0 and not args.no_serving:
+        result["serving"] = serving(args, glint, render, ctx, dev, stream)
     if pg:
         pg.barrier()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -489,6 +606,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -333,6 +333,109 @@ glint_status glint_mlp_infer(const glint_mlp *mlp, glint_ctx *ctx, const glint_e
 int glint_mlp_get_k(const glint_mlp *mlp);
 int glint_mlp_last_launches(const glint_mlp *mlp);
 
+/* ---------------------------------------------------------------------------
+ * Serving (no counterpart in the paper): a continuous-batching request loop.
+ * Frames of any resolution, each with one of the resident environments (and
+ * its surrogate), are submitted from host memory; a tick admits queued frames
+ * while their device buffers fit the memory budget (FIFO), copies their
+ * G-buffers to the device on a copy stream, and shades a tile of every
+ * admitted frame and then up to tick_pixels pixels in admission order, in one
+ * persistent launch over a work list of
+ * (frame, pixel range) items (plus, for frames on the surrogate path, one
+ * fused-inference launch per network first).  Finished frames are copied back
+ * on the copy stream and released; glint_server_poll reports them.  A frame's
+ * pixels are computed exactly as glint_shade's kernel computes them, whatever
+ * else shares its ticks.  One host thread drives a server.
+ * ------------------------------------------------------------------------- */
+typedef struct glint_server glint_server;
+
+typedef struct glint_server_desc {
+    size_t memory_budget;   /* device bytes for admitted frames' buffers (one allocation at creation) */
+    long tick_pixels;       /* pixels shaded per tick at most (0 = 4194304) */
+    int tile_pixels;        /* pixels per planned item, a multiple of 128 (0 = 16384); items are
+                               launched in pieces of 1024 pixels */
+    int max_frames;         /* admitted frames at most (0 = 64) */
+    int max_inflight_ticks; /* ticks enqueued on the GPU at most; a tick waits for older ones (0 = 2) */
+} glint_server_desc;
+
+/* A frame.  Planes are HOST memory in glint_gbuffer's layout (page-locked
+ * memory lets the copies overlap with shading); tangent is required on the
+ * surrogate path.  out_rgba: HOST, width*height float4.  The caller keeps all
+ * of them alive until glint_server_poll has reported the frame. */
+typedef struct glint_frame_request {
+    int env;          /* index from glint_server_add_env */
+    int width;
+    int height;
+    uint32_t seed;
+    int evaluator;    /* GLINT_EVAL_E1 or GLINT_EVAL_MLP */
+    const float *view_n0;
+    const float *normal_f0;
+    const float *uv_alpha;
+    const float *duv;
+    const float *tangent;
+    float *out_rgba;
+} glint_frame_request;
+
+/* A finished frame: its id and host-clock times (seconds since the server's
+ * creation) of submission, admission and the completed copy back. */
+typedef struct glint_frame_done {
+    long id;
+    double submit_s;
+    double admit_s;
+    double done_s;
+} glint_frame_done;
+
+typedef struct glint_server_stats {
+    long queued;          /* submitted, not admitted */
+    long active;          /* admitted, not reported */
+    long done;            /* reported by glint_server_poll */
+    size_t used_bytes;    /* device bytes held by admitted frames */
+    size_t peak_bytes;
+    long ticks;           /* ticks that launched work */
+    long launches;        /* kernel launches of those ticks */
+    long items;           /* work items of those ticks */
+} glint_server_stats;
+
+/* A server for environments with K components on ctx's device. */
+glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc *desc, glint_server **out);
+/* Waits for the server's work and frees it. */
+void glint_server_destroy(glint_server *server);
+/* Makes `env` (updated, same context and K) resident for requests; `mlp` (may
+ * be NULL) is its surrogate for GLINT_EVAL_MLP.  *env_id receives the index. */
+glint_status glint_server_add_env(glint_server *server, const glint_env *env, const glint_mlp *mlp, int *env_id);
+/* Queues a frame and returns its id; GLINT_ERR_INVALID_ARG if the request is
+ * malformed or its buffers could never fit the memory budget. */
+glint_status glint_server_submit(glint_server *server, const glint_frame_request *req, long *id);
+/* Admits, enqueues one tick of work on `stream` and the copies of finished
+ * frames; *launched (may be NULL) receives the kernel launches. */
+glint_status glint_server_tick(glint_server *server, void *stream, int *launched);
+/* Up to max_done finished frames (copied back), in completion order. */
+glint_status glint_server_poll(glint_server *server, glint_frame_done *done, int max_done, int *n_done);
+glint_status glint_server_stats_get(const glint_server *server, glint_server_stats *stats);
+
+/* Device-memory admission bookkeeping used by the server (host only, no
+ * device memory): first-fit over [0, bytes) with `align`-byte granularity and
+ * coalescing of freed neighbours. */
+typedef struct glint_arena glint_arena;
+glint_arena *glint_arena_create(size_t bytes, size_t align);
+void glint_arena_destroy(glint_arena *arena);
+/* Offset of a new block of `bytes`, or -1 if no free range holds it. */
+long long glint_arena_alloc(glint_arena *arena, size_t bytes);
+/* 0, or -1 if `offset` is not an allocated block. */
+int glint_arena_free(glint_arena *arena, long long offset);
+size_t glint_arena_used(const glint_arena *arena);
+size_t glint_arena_largest_free(const glint_arena *arena);
+
+/* The tick planner (host only): frames in admission order with next[f] of
+ * npix[f] pixels planned so far.  Items are ranges of at most tile_pixels
+ * pixels ending at multiples of tile_pixels (or the frame's end): first one
+ * item for every unfinished frame, so that every admitted frame progresses in
+ * every tick, then items in frame order until tick_pixels are planned; at most
+ * max_items in all.  Writes the items, advances next[] and returns the item
+ * count. */
+int glint_plan_tick(long *next, const long *npix, int nframes, long tick_pixels, int tile_pixels, int *item_frame,
+                    long *item_first, int *item_count, int max_items);
+
 /* Standard normal quantile z = Phi^-1(p) as the shading kernel evaluates it for
  * the Gaussian part of the dual-gated draw (Alg. 1): for n device floats p in
  * (0, 1), device output z.  Relative error below 2.3e-7 on the uniforms the

@@ -131,6 +131,14 @@ cudaError_t glint_launch_mlp_infer(const glint_ctx *ctx, const glint_env *env, c
                                    const glint_gbuffer *g, float *p, cudaStream_t s);
 int glint_mlp_k(const glint_mlp *m);
 int glint_mlp_device(const glint_mlp *m);
+// Serving launches (glint_serve.cu): the shading kernel and the surrogate's
+// fused inference over a work list; frames/items are device arrays.
+namespace glint { struct ShadeArgs; struct ServeItem; }
+cudaError_t glint_launch_serve(int K, bool given, const glint::ShadeArgs *frames, const glint::ServeItem *items,
+                               int nitems, int grid, cudaStream_t s);
+cudaError_t glint_launch_mlp_serve(int K, int num_sms, const glint::ShadeArgs *frames, const glint::ServeItem *items,
+                                   int nitems, cudaStream_t s);
+void glint_mlp_weights(const glint_mlp *m, const void **wt, const float **params);
 // p_k only (E1 or E2), background pixels 0.
 cudaError_t glint_launch_probs(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
                                const glint_params *p, float *p_out, cudaStream_t s);

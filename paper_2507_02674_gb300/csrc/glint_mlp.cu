@@ -322,6 +322,45 @@ __global__ void __launch_bounds__(kNT) k_mlp_infer(ShadeArgs a, const __nv_bfloa
     }
 }
 
+// Serving: fused inference over a work list of (frame, pixel range) items of
+// frames that may use different networks, writing each frame's p_k to its
+// p_out.  A block reloads the weights when an item's network differs from the
+// one it holds.  Items start at multiples of 128 pixels of their frame.
+template <int K>
+__global__ void __launch_bounds__(kNT) k_mlp_serve(const ShadeArgs *__restrict__ frames,
+                                                   const ServeItem *__restrict__ items, int nitems) {
+    __shared__ SmemInfer sm;
+    __shared__ ShadeArgs sa;
+    const void *held = nullptr;
+#pragma unroll 1
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const ServeItem item = items[it];
+        __syncthreads();
+        if (threadIdx.x == 0) sa = frames[item.frame];
+        __syncthreads();
+        if (sa.mlp_wt != held) {
+            held = sa.mlp_wt;
+            load_weights(sm.w, reinterpret_cast<const __nv_bfloat16 *>(sa.mlp_wt), sa.mlp_params);
+        }
+        const long end = item.first + item.count;
+#pragma unroll 1
+        for (long base = item.first; base < end; base += kNT) {
+            const long q = base + threadIdx.x;
+            float x[kMlpIn], lp[K];
+            bool fg = false;
+            if (q < end) {
+                const float4 g0 = ldg4(sa.view_n0 + q);
+                fg = g0.w > 0.f;
+                if (fg) mlp_features<K>(sa, q, g0, ldg4(sa.normal_f0 + q), ldg4(sa.uv_alpha + q), x, lp);
+            }
+            __syncthreads();
+            stage_row<K>(sm, threadIdx.x, x, lp, fg);
+            __syncthreads();
+            net_tile<1>(sm, base, end, K, sa.p_out);
+        }
+    }
+}
+
 // Inputs of every pixel: x (n x 64 BF16, background rows 0), lp (n x K).
 template <int K>
 __global__ void __launch_bounds__(kNT) k_mlp_features(ShadeArgs a, uint4 *__restrict__ x, float *__restrict__ lp) {
@@ -676,6 +715,33 @@ cudaError_t glint_launch_mlp_infer(const glint_ctx *ctx, const glint_env *env, c
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t glint_launch_mlp_serve(int K, int num_sms, const ShadeArgs *frames, const ServeItem *items, int nitems,
+                                   cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    static int per_sm[3] = {0, 0, 0};  // resident blocks per SM of k_mlp_serve<2, 4, 8>
+    const int ki = K == 2 ? 0 : K == 4 ? 1 : 2;
+    if (!per_sm[ki]) {
+        cudaError_t e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ki], k_mlp_serve<2>, kNT, 0)
+                      : K == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ki], k_mlp_serve<4>, kNT, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ki], k_mlp_serve<8>, kNT, 0);
+        if (e != cudaSuccess) return e;
+        per_sm[ki] = std::max(per_sm[ki], 1);
+    }
+    const int grid = std::min(nitems, per_sm[ki] * num_sms);
+    switch (K) {
+    case 2: k_mlp_serve<2><<<grid, kNT, 0, s>>>(frames, items, nitems); break;
+    case 4: k_mlp_serve<4><<<grid, kNT, 0, s>>>(frames, items, nitems); break;
+    case 8: k_mlp_serve<8><<<grid, kNT, 0, s>>>(frames, items, nitems); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+void glint_mlp_weights(const glint_mlp *g, const void **wt, const float **params) {
+    *wt = g->wt;
+    *params = g->params;
 }
 
 int glint_mlp_k(const glint_mlp *g) { return g ? g->K : 0; }

@@ -25,6 +25,16 @@ struct ShadeArgs {
     int envW, envH, envM, e2S;
     const float *pk_in;  // EV_GIVEN: p_k per pixel (npix x K)
     float *p_out;        // k_probs: p_k per pixel (npix x K)
+    const void *mlp_wt;       // serving: the frame's surrogate (BF16 weight copies)
+    const float *mlp_params;  //          and its FP32 parameters (biases)
+};
+
+// One work item of the serving kernels: pixels [first, first + count) of
+// frame `frame` (an index into the tick's frame table).
+struct ServeItem {
+    int frame;
+    int count;
+    long first;
 };
 
 // Source of the reflection probabilities p_k.

@@ -1,0 +1,535 @@
+// Serving: continuous batching of glint-shaded frames (no counterpart in the
+// paper).  Host runtime: FIFO admission by device memory (first-fit arena over
+// one allocation), G-buffer copies on an upload stream, per-tick work lists of
+// (frame, pixel range) items over all admitted frames, one persistent shading
+// launch per tick (plus the surrogate's fused inference first for frames on
+// that path), copies back of finished frames on a second copy stream (never
+// queued behind uploads) and their release.
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <iterator>
+#include <map>
+#include <vector>
+
+#include "glint_internal.cuh"
+#include "glint_probs.cuh"
+
+using namespace glint;
+
+// ------------------------------------------------------------------ arena
+struct glint_arena {
+    size_t bytes = 0, align = 256, used = 0;
+    std::map<size_t, size_t> free_;  // offset -> size, disjoint, coalesced
+    std::map<size_t, size_t> live;   // offset -> size
+};
+
+extern "C" {
+
+glint_arena *glint_arena_create(size_t bytes, size_t align) {
+    if (align == 0 || (align & (align - 1)) != 0) return nullptr;
+    glint_arena *a = new glint_arena();
+    a->align = align;
+    a->bytes = bytes / align * align;
+    if (a->bytes) a->free_[0] = a->bytes;
+    return a;
+}
+
+void glint_arena_destroy(glint_arena *a) { delete a; }
+
+long long glint_arena_alloc(glint_arena *a, size_t bytes) {
+    if (!a || bytes == 0) return -1;
+    const size_t need = (bytes + a->align - 1) / a->align * a->align;
+    for (auto it = a->free_.begin(); it != a->free_.end(); ++it) {
+        if (it->second < need) continue;
+        const size_t off = it->first, rest = it->second - need;
+        a->free_.erase(it);
+        if (rest) a->free_[off + need] = rest;
+        a->live[off] = need;
+        a->used += need;
+        return (long long)off;
+    }
+    return -1;
+}
+
+int glint_arena_free(glint_arena *a, long long offset) {
+    if (!a || offset < 0) return -1;
+    auto it = a->live.find((size_t)offset);
+    if (it == a->live.end()) return -1;
+    size_t off = it->first, size = it->second;
+    a->live.erase(it);
+    a->used -= size;
+    auto next = a->free_.lower_bound(off);
+    if (next != a->free_.end() && off + size == next->first) {  // merge with the following range
+        size += next->second;
+        next = a->free_.erase(next);
+    }
+    if (next != a->free_.begin()) {  // merge with the preceding range
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            prev->second += size;
+            return 0;
+        }
+    }
+    a->free_[off] = size;
+    return 0;
+}
+
+size_t glint_arena_used(const glint_arena *a) { return a ? a->used : 0; }
+
+size_t glint_arena_largest_free(const glint_arena *a) {
+    size_t m = 0;
+    if (a)
+        for (const auto &f : a->free_) m = std::max(m, f.second);
+    return m;
+}
+
+int glint_plan_tick(long *next, const long *npix, int nframes, long tick_pixels, int tile_pixels, int *item_frame,
+                    long *item_first, int *item_count, int max_items) {
+    if (!next || !npix || nframes <= 0 || tile_pixels <= 0 || max_items <= 0) return 0;
+    int n = 0;
+    long planned = 0;
+    auto take = [&](int f) {
+        const long c = std::min<long>(tile_pixels - next[f] % tile_pixels, npix[f] - next[f]);
+        item_frame[n] = f;
+        item_first[n] = next[f];
+        item_count[n] = (int)c;
+        ++n;
+        next[f] += c;
+        planned += c;
+    };
+    // every unfinished frame progresses by one tile, so frames admitted later
+    // are not starved by large ones ahead of them ...
+    for (int f = 0; f < nframes && n < max_items; ++f)
+        if (next[f] < npix[f]) take(f);
+    // ... then the rest of the budget goes to frames in admission order
+    for (int f = 0; f < nframes && n < max_items && planned < tick_pixels; ++f)
+        while (next[f] < npix[f] && n < max_items && planned < tick_pixels) take(f);
+    return n;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ server
+namespace {
+
+constexpr int kPiece = 1024;  // pixels per staged work item
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+struct Frame {
+    long id = 0;
+    glint_frame_request req{};
+    long npix = 0;
+    long next = 0;             // pixels enqueued for shading so far
+    long long arena_off = -1;
+    float *dev = nullptr;      // base of the frame's device block
+    glint_gbuffer gb{};        // device planes
+    float *out = nullptr;      // device output
+    float *p = nullptr;        // device p_k scratch (surrogate path)
+    cudaEvent_t uploaded = nullptr, downloaded = nullptr;
+    bool waited = false;       // the compute stream waits on `uploaded`
+    bool copying_back = false;
+    double submit_s = 0, admit_s = 0;
+};
+
+struct Slot {  // staging of one tick's frame table and work list
+    ShadeArgs *h_frames = nullptr, *d_frames = nullptr;
+    ServeItem *h_items = nullptr, *d_items = nullptr;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+
+}  // namespace
+
+struct glint_server {
+    glint_ctx *ctx = nullptr;
+    int K = 8;
+    glint_server_desc d{};
+    int max_items = 0;   // planned items per tick at most
+    int max_staged = 0;  // staged items per tick at most (planned items after cutting surrogate ones)
+    std::chrono::steady_clock::time_point t0;
+    char *pool = nullptr;
+    glint_arena *arena = nullptr;
+    cudaStream_t copy = nullptr;  // uploads
+    cudaStream_t back = nullptr;  // copies back (never queued behind uploads)
+    std::vector<std::pair<const glint_env *, const glint_mlp *>> envs;
+    std::deque<Frame> queue;
+    std::vector<Frame> active;  // admission order
+    std::vector<glint_frame_done> finished;
+    std::vector<Slot> slots;
+    long tick_no = 0;
+    long next_id = 1;
+    glint_server_stats st{};
+};
+
+namespace {
+
+size_t frame_bytes(const glint_frame_request &r, int K) {
+    const size_t n = (size_t)r.width * (size_t)r.height;
+    const size_t planes = (r.evaluator == GLINT_EVAL_MLP) ? 5 : 4;
+    const size_t pbytes = (r.evaluator == GLINT_EVAL_MLP) ? ((n * K * sizeof(float) + 255) / 256 * 256) : 0;
+    return (planes + 1) * ((n * 16 + 255) / 256 * 256) + pbytes;
+}
+
+void free_frame_events(Frame &f) {
+    if (f.uploaded) cudaEventDestroy(f.uploaded);
+    if (f.downloaded) cudaEventDestroy(f.downloaded);
+    f.uploaded = f.downloaded = nullptr;
+}
+
+// Moves frames whose copy back has completed to `finished` and frees them.
+void retire(glint_server *s) {
+    for (size_t i = 0; i < s->active.size();) {
+        Frame &f = s->active[i];
+        cudaError_t q = f.copying_back ? cudaEventQuery(f.downloaded) : cudaErrorNotReady;
+        // "not ready" is a state, not an error: drop it from the last-error slot only
+        if (q == cudaErrorNotReady && cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+        if (q == cudaSuccess) {
+            s->finished.push_back(glint_frame_done{f.id, f.submit_s, f.admit_s, now_s(s->t0)});
+            glint_arena_free(s->arena, f.arena_off);
+            free_frame_events(f);
+            s->active.erase(s->active.begin() + (long)i);
+            s->st.active -= 1;
+        } else {
+            ++i;
+        }
+    }
+}
+
+glint_status admit(glint_server *s) {
+    while (!s->queue.empty() && (int)s->active.size() < s->d.max_frames) {
+        Frame &q = s->queue.front();
+        const size_t bytes = frame_bytes(q.req, s->K);
+        const long long off = glint_arena_alloc(s->arena, bytes);
+        if (off < 0) break;  // FIFO: the head waits until memory frees up
+        Frame f = q;
+        s->queue.pop_front();
+        f.arena_off = off;
+        f.dev = reinterpret_cast<float *>(s->pool + off);
+        const size_t plane = ((size_t)f.npix * 16 + 255) / 256 * 256;
+        char *p = reinterpret_cast<char *>(f.dev);
+        const float *src[5] = {f.req.view_n0, f.req.normal_f0, f.req.uv_alpha, f.req.duv, f.req.tangent};
+        float *dst[5] = {};
+        const int nplanes = (f.req.evaluator == GLINT_EVAL_MLP) ? 5 : 4;
+        glint_status st = GLINT_OK;
+        for (int i = 0; i < nplanes; ++i) {
+            dst[i] = reinterpret_cast<float *>(p);
+            p += plane;
+            if (st == GLINT_OK)
+                st = cuda_status(cudaMemcpyAsync(dst[i], src[i], (size_t)f.npix * 16, cudaMemcpyHostToDevice, s->copy),
+                                 "glint_server_tick: upload");
+        }
+        f.out = reinterpret_cast<float *>(p);
+        p += plane;
+        f.p = (f.req.evaluator == GLINT_EVAL_MLP) ? reinterpret_cast<float *>(p) : nullptr;
+        f.gb = glint_gbuffer{dst[0], dst[1], dst[2], dst[3], f.req.width, f.req.height, dst[4]};
+        if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&f.uploaded, cudaEventDisableTiming), "glint_server_tick");
+        if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&f.downloaded, cudaEventDisableTiming), "glint_server_tick");
+        if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.uploaded, s->copy), "glint_server_tick");
+        if (st != GLINT_OK) {
+            glint_arena_free(s->arena, off);
+            free_frame_events(f);
+            return st;
+        }
+        f.admit_s = now_s(s->t0);
+        s->active.push_back(f);
+        s->st.queued -= 1;
+        s->st.active += 1;
+        s->st.used_bytes = glint_arena_used(s->arena);
+        s->st.peak_bytes = std::max(s->st.peak_bytes, s->st.used_bytes);
+    }
+    return GLINT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc *desc, glint_server **out) {
+    set_error("%s", "");
+    if (!ctx || !desc || !out) { set_error("glint_server_create: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (K != 2 && K != 4 && K != 8 && K != 16) { set_error("glint_server_create: K = %d", K); return GLINT_ERR_INVALID_ARG; }
+    glint_server_desc d = *desc;
+    if (d.tick_pixels == 0) d.tick_pixels = 4194304;
+    if (d.tile_pixels == 0) d.tile_pixels = 16384;
+    if (d.max_frames == 0) d.max_frames = 64;
+    if (d.max_inflight_ticks == 0) d.max_inflight_ticks = 2;
+    if (d.memory_budget < (1u << 20) || d.tick_pixels < 128 || d.tile_pixels < 128 || d.tile_pixels % 128 ||
+        d.max_frames < 1 || d.max_frames > 4096 || d.max_inflight_ticks < 1 || d.max_inflight_ticks > 16) {
+        set_error("glint_server_create: memory_budget >= 1 MiB, tick_pixels >= 128, tile_pixels a multiple of 128, "
+                  "max_frames in [1, 4096], max_inflight_ticks in [1, 16]");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) { set_error("glint_server_create: cannot select device"); return GLINT_ERR_CUDA; }
+    glint_server *s = new glint_server();
+    s->ctx = ctx;
+    s->K = K;
+    s->d = d;
+    s->t0 = std::chrono::steady_clock::now();
+    // a tick touches each admitted frame's ranges: at most tick_pixels / tile + one partial item per frame
+    s->max_items = (int)std::min<long>(d.tick_pixels / d.tile_pixels + 2L * d.max_frames, 1L << 20);
+    // a planned item spans at most tile_pixels pixels: cut into kPiece-pixel pieces it gives at most
+    // tile_pixels / kPiece + 1 of them
+    s->max_staged = s->max_items * (d.tile_pixels / kPiece + 2);
+    glint_status st = cuda_status(cudaMalloc(&s->pool, d.memory_budget), "glint_server_create: pool");
+    if (st == GLINT_OK) {
+        s->arena = glint_arena_create(d.memory_budget, 256);
+        if (!s->arena) st = GLINT_ERR_OOM;
+    }
+    if (st == GLINT_OK) st = cuda_status(cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking), "glint_server_create");
+    if (st == GLINT_OK) st = cuda_status(cudaStreamCreateWithFlags(&s->back, cudaStreamNonBlocking), "glint_server_create");
+    s->slots.resize(d.max_inflight_ticks + 1);
+    for (auto &sl : s->slots) {
+        if (st != GLINT_OK) break;
+        st = cuda_status(cudaMallocHost(&sl.h_frames, sizeof(ShadeArgs) * d.max_frames), "glint_server_create");
+        if (st == GLINT_OK) st = cuda_status(cudaMalloc(&sl.d_frames, sizeof(ShadeArgs) * d.max_frames), "glint_server_create");
+        if (st == GLINT_OK) st = cuda_status(cudaMallocHost(&sl.h_items, sizeof(ServeItem) * s->max_staged), "glint_server_create");
+        if (st == GLINT_OK) st = cuda_status(cudaMalloc(&sl.d_items, sizeof(ServeItem) * s->max_staged), "glint_server_create");
+        if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "glint_server_create");
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    if (st != GLINT_OK) {
+        glint_server_destroy(s);
+        return st;
+    }
+    *out = s;
+    return GLINT_OK;
+}
+
+void glint_server_destroy(glint_server *s) {
+    if (!s) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &f : s->active) free_frame_events(f);
+    for (auto &sl : s->slots) {
+        cudaFreeHost(sl.h_frames);
+        cudaFree(sl.d_frames);
+        cudaFreeHost(sl.h_items);
+        cudaFree(sl.d_items);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->back) cudaStreamDestroy(s->back);
+    cudaFree(s->pool);
+    glint_arena_destroy(s->arena);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete s;
+}
+
+glint_status glint_server_add_env(glint_server *s, const glint_env *env, const glint_mlp *mlp, int *env_id) {
+    set_error("%s", "");
+    if (!s || !env || !env_id) { set_error("glint_server_add_env: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (env->ctx != s->ctx || env->d.K != s->K) {
+        set_error("glint_server_add_env: environment of another context or K %d (server K %d)", env->d.K, s->K);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (mlp && (glint_mlp_k(mlp) != s->K || glint_mlp_device(mlp) != s->ctx->device)) {
+        set_error("glint_server_add_env: network K or device differs");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    s->envs.emplace_back(env, mlp);
+    *env_id = (int)s->envs.size() - 1;
+    return GLINT_OK;
+}
+
+glint_status glint_server_submit(glint_server *s, const glint_frame_request *r, long *id) {
+    set_error("%s", "");
+    if (!s || !r || !id) { set_error("glint_server_submit: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (r->env < 0 || r->env >= (int)s->envs.size()) { set_error("glint_server_submit: unknown env %d", r->env); return GLINT_ERR_INVALID_ARG; }
+    if (r->width < 1 || r->height < 1 || (long)r->width * r->height > (1L << 31)) {
+        set_error("glint_server_submit: width %d x height %d", r->width, r->height);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (r->evaluator != GLINT_EVAL_E1 && r->evaluator != GLINT_EVAL_MLP) {
+        set_error("glint_server_submit: evaluator %d (E1 or MLP)", r->evaluator);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (r->evaluator == GLINT_EVAL_MLP && (!s->envs[r->env].second || !r->tangent)) {
+        set_error("glint_server_submit: the surrogate path needs the environment's network and a tangent plane");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (!r->view_n0 || !r->normal_f0 || !r->uv_alpha || !r->duv || !r->out_rgba) {
+        set_error("glint_server_submit: NULL plane or output");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    const size_t bytes = frame_bytes(*r, s->K);
+    if (bytes > s->arena->bytes) {
+        set_error("glint_server_submit: the frame needs %zu bytes, more than the budget %zu", bytes, s->d.memory_budget);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    Frame f;
+    f.id = s->next_id++;
+    f.req = *r;
+    f.npix = (long)r->width * r->height;
+    f.submit_s = now_s(s->t0);
+    s->queue.push_back(f);
+    s->st.queued += 1;
+    *id = f.id;
+    return GLINT_OK;
+}
+
+glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
+    set_error("%s", "");
+    if (launched) *launched = 0;
+    if (!s) { set_error("glint_server_tick: NULL server"); return GLINT_ERR_INVALID_ARG; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != s->ctx->device) cudaSetDevice(s->ctx->device);
+    cudaStream_t cs = (cudaStream_t)stream;
+    retire(s);
+    glint_status st = admit(s);
+    // frames with pixels left, in admission order
+    std::vector<int> idx;
+    for (int i = 0; i < (int)s->active.size(); ++i)
+        if (s->active[i].next < s->active[i].npix) idx.push_back(i);
+    int nl = 0;
+    if (st == GLINT_OK && !idx.empty()) {
+        Slot &sl = s->slots[s->tick_no % s->slots.size()];
+        if (sl.used) st = cuda_status(cudaEventSynchronize(sl.done), "glint_server_tick: wait");
+        // plan: surrogate-path frames first (their items precede the plain ones)
+        std::vector<int> order;
+        for (int i : idx) if (s->active[i].req.evaluator == GLINT_EVAL_MLP) order.push_back(i);
+        const int n_mlp_frames = (int)order.size();
+        for (int i : idx) if (s->active[i].req.evaluator != GLINT_EVAL_MLP) order.push_back(i);
+        std::vector<long> next(order.size()), npix(order.size());
+        for (size_t j = 0; j < order.size(); ++j) {
+            next[j] = s->active[order[j]].next;
+            npix[j] = s->active[order[j]].npix;
+        }
+        std::vector<int> pf(s->max_items), pc(s->max_items);
+        std::vector<long> pfirst(s->max_items);
+        const int nit = glint_plan_tick(next.data(), npix.data(), (int)order.size(), s->d.tick_pixels,
+                                        s->d.tile_pixels, pf.data(), pfirst.data(), pc.data(), s->max_items);
+        // items of surrogate-path frames first (stable), grouped by network
+        std::vector<int> perm(nit);
+        for (int k = 0; k < nit; ++k) perm[k] = k;
+        std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) {
+            const bool mx = pf[x] < n_mlp_frames, my = pf[y] < n_mlp_frames;
+            if (mx != my) return mx;
+            if (!mx) return false;
+            return s->envs[s->active[order[pf[x]]].req.env].second < s->envs[s->active[order[pf[y]]].req.env].second;
+        });
+        // items are cut into pieces of kPiece pixels, so that a tick of a few
+        // frames still spreads over every SM
+        std::vector<int> it_f, it_c;
+        std::vector<long> it_first;
+        for (int k = 0; k < nit; ++k) {
+            const int j = pf[perm[k]];
+            long first = pfirst[perm[k]];
+            const long end = first + pc[perm[k]];
+            while (first < end) {
+                const long c = std::min<long>(kPiece - first % kPiece, end - first);
+                it_f.push_back(j);
+                it_first.push_back(first);
+                it_c.push_back((int)c);
+                first += c;
+            }
+        }
+        const int nit_all = (int)it_f.size();
+        if (nit_all > s->max_staged) {  // cannot happen with the bound above; refuse rather than overflow
+            set_error("glint_server_tick: %d staged items exceed the capacity %d", nit_all, s->max_staged);
+            st = GLINT_ERR_UNSUPPORTED;
+        }
+        // frame table of this tick (frames that received items) and the work list
+        std::vector<int> table_of(order.size(), -1);
+        int nframes = 0, n_mlp_items = 0;
+        for (int k = 0; k < nit_all && st == GLINT_OK; ++k) {
+            const int j = it_f[k];
+            if (table_of[j] < 0) {
+                Frame &f = s->active[order[j]];
+                glint_params prm{};
+                prm.seed = f.req.seed;
+                const glint_env *env = s->envs[f.req.env].first;
+                ShadeArgs a = make_args(s->ctx, env, &f.gb, &prm);
+                a.out = reinterpret_cast<float4 *>(f.out);
+                a.pk_in = f.p;
+                a.p_out = f.p;
+                if (f.req.evaluator == GLINT_EVAL_MLP)
+                    glint_mlp_weights(s->envs[f.req.env].second, &a.mlp_wt, &a.mlp_params);
+                table_of[j] = nframes;
+                sl.h_frames[nframes++] = a;
+                if (!f.waited) {
+                    st = cuda_status(cudaStreamWaitEvent(cs, f.uploaded, 0), "glint_server_tick");
+                    f.waited = true;
+                }
+            }
+            sl.h_items[k] = ServeItem{table_of[j], it_c[k], it_first[k]};
+            if (j < n_mlp_frames) ++n_mlp_items;
+        }
+        if (st == GLINT_OK)
+            st = cuda_status(cudaMemcpyAsync(sl.d_frames, sl.h_frames, sizeof(ShadeArgs) * nframes,
+                                             cudaMemcpyHostToDevice, cs), "glint_server_tick: table");
+        if (st == GLINT_OK)
+            st = cuda_status(cudaMemcpyAsync(sl.d_items, sl.h_items, sizeof(ServeItem) * nit_all,
+                                             cudaMemcpyHostToDevice, cs), "glint_server_tick: items");
+        // surrogate: one fused-inference launch over its frames' items (grouped by network)
+        if (st == GLINT_OK && n_mlp_items > 0) {
+            st = cuda_status(glint_launch_mlp_serve(s->K, s->ctx->num_sms, sl.d_frames, sl.d_items, n_mlp_items, cs),
+                             "glint_server_tick: inference");
+            ++nl;
+            if (st == GLINT_OK) {
+                const int grid = std::min(n_mlp_items, s->ctx->num_sms * 8);
+                st = cuda_status(glint_launch_serve(s->K, true, sl.d_frames, sl.d_items, n_mlp_items, grid, cs),
+                                 "glint_server_tick: shade");
+                ++nl;
+            }
+        }
+        if (st == GLINT_OK && nit_all > n_mlp_items) {
+            const int grid = std::min(nit_all - n_mlp_items, s->ctx->num_sms * 8);
+            st = cuda_status(glint_launch_serve(s->K, false, sl.d_frames, sl.d_items + n_mlp_items,
+                                                nit_all - n_mlp_items, grid, cs), "glint_server_tick: shade");
+            ++nl;
+        }
+        if (st == GLINT_OK) st = cuda_status(cudaEventRecord(sl.done, cs), "glint_server_tick");
+        sl.used = true;
+        // progress, and copies back of frames this tick completes
+        for (size_t j = 0; j < order.size() && st == GLINT_OK; ++j) {
+            Frame &f = s->active[order[j]];
+            f.next = next[j];
+            if (f.next == f.npix && !f.copying_back) {
+                st = cuda_status(cudaStreamWaitEvent(s->back, sl.done, 0), "glint_server_tick");
+                if (st == GLINT_OK)
+                    st = cuda_status(cudaMemcpyAsync(f.req.out_rgba, f.out, (size_t)f.npix * 16, cudaMemcpyDeviceToHost,
+                                                     s->back), "glint_server_tick: download");
+                if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.downloaded, s->back), "glint_server_tick");
+                f.copying_back = true;
+            }
+        }
+        s->tick_no += 1;
+        s->st.ticks += 1;
+        s->st.launches += nl;
+        s->st.items += nit_all;
+    }
+    if (launched) *launched = nl;
+    if (prev >= 0 && prev != s->ctx->device) cudaSetDevice(prev);
+    return st;
+}
+
+glint_status glint_server_poll(glint_server *s, glint_frame_done *done, int max_done, int *n_done) {
+    set_error("%s", "");
+    if (!s || !n_done || (max_done > 0 && !done)) { set_error("glint_server_poll: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    retire(s);
+    const int n = std::min<int>(max_done, (int)s->finished.size());
+    for (int i = 0; i < n; ++i) done[i] = s->finished[i];
+    s->finished.erase(s->finished.begin(), s->finished.begin() + n);
+    s->st.done += n;
+    *n_done = n;
+    s->st.used_bytes = glint_arena_used(s->arena);
+    return GLINT_OK;
+}
+
+glint_status glint_server_stats_get(const glint_server *s, glint_server_stats *out) {
+    if (!s || !out) return GLINT_ERR_INVALID_ARG;
+    *out = s->st;
+    return GLINT_OK;
+}
+
+}  // extern "C"

@@ -142,10 +142,9 @@ __global__ void __launch_bounds__(kShadeNT) k_probs(ShadeArgs a) {
     for (int k = 0; k < K; ++k) a.p_out[q * K + k] = p[k];
 }
 
+// Steps 1-5 for pixel q of the frame described by a.
 template <int K, bool INTEGER, bool DEBUG, int EV>
-__global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
-    const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
-    if (q >= a.npix) return;
+__device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
     const float4 g0 = ldg4(a.view_n0 + q);
     const float4 g1 = ldg4(a.normal_f0 + q);
     const float4 g2 = ldg4(a.uv_alpha + q);
@@ -331,6 +330,32 @@ __global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
     a.out[q] = o;
 }
 
+template <int K, bool INTEGER, bool DEBUG, int EV>
+__global__ void __launch_bounds__(kShadeNT, 8) k_shade(ShadeArgs a) {
+    const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
+    if (q >= a.npix) return;
+    shade_pixel<K, INTEGER, DEBUG, EV>(a, q);
+}
+
+// Serving: one launch over a work list of (frame, pixel range) items of many
+// frames (resolutions, maps and seeds may differ; K is shared).  Block b
+// takes items b, b + G, ...; the frame's arguments are staged in shared memory.
+template <int K, int EV>
+__global__ void __launch_bounds__(kShadeNT, 8) k_serve(const ShadeArgs *__restrict__ frames,
+                                                       const ServeItem *__restrict__ items, int nitems) {
+    __shared__ ShadeArgs sa;
+#pragma unroll 1
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const ServeItem item = items[it];
+        __syncthreads();  // the previous item's readers are done
+        if (threadIdx.x == 0) sa = frames[item.frame];
+        __syncthreads();
+#pragma unroll 1
+        for (int off = threadIdx.x; off < item.count; off += kShadeNT)
+            shade_pixel<K, true, false, EV>(sa, item.first + off);
+    }
+}
+
 __global__ void k_quantile(const float *__restrict__ p, float *__restrict__ z, long n) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) z[i] = normal_quantile(p[i]);
@@ -408,4 +433,21 @@ cudaError_t glint_launch_probs(const glint_ctx *ctx, const glint_env *env, const
     case 16: return launch_probs<16>(a, ev, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t glint_launch_serve(int K, bool given, const ShadeArgs *frames, const ServeItem *items, int nitems, int grid,
+                               cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    switch (K) {
+    case 2: given ? k_serve<2, EV_GIVEN><<<grid, kShadeNT, 0, s>>>(frames, items, nitems)
+                  : k_serve<2, EV_E1><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
+    case 4: given ? k_serve<4, EV_GIVEN><<<grid, kShadeNT, 0, s>>>(frames, items, nitems)
+                  : k_serve<4, EV_E1><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
+    case 8: given ? k_serve<8, EV_GIVEN><<<grid, kShadeNT, 0, s>>>(frames, items, nitems)
+                  : k_serve<8, EV_E1><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
+    case 16: given ? k_serve<16, EV_GIVEN><<<grid, kShadeNT, 0, s>>>(frames, items, nitems)
+                   : k_serve<16, EV_E1><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }

@@ -55,6 +55,29 @@ class Debug(ctypes.Structure):
                 ("nroot", ctypes.c_void_p), ("counts", ctypes.c_void_p), ("lo", ctypes.c_void_p)]
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_size_t), ("tick_pixels", ctypes.c_long), ("tile_pixels", ctypes.c_int),
+                ("max_frames", ctypes.c_int), ("max_inflight_ticks", ctypes.c_int)]
+
+
+class FrameRequest(ctypes.Structure):
+    _fields_ = [("env", ctypes.c_int), ("width", ctypes.c_int), ("height", ctypes.c_int), ("seed", ctypes.c_uint32),
+                ("evaluator", ctypes.c_int), ("view_n0", ctypes.c_void_p), ("normal_f0", ctypes.c_void_p),
+                ("uv_alpha", ctypes.c_void_p), ("duv", ctypes.c_void_p), ("tangent", ctypes.c_void_p),
+                ("out_rgba", ctypes.c_void_p)]
+
+
+class FrameDone(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_long), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_long), ("active", ctypes.c_long), ("done", ctypes.c_long),
+                ("used_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t), ("ticks", ctypes.c_long),
+                ("launches", ctypes.c_long), ("items", ctypes.c_long)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2507_02674_gb300.build.build() "
@@ -95,6 +118,27 @@ def _load():
     lib.glint_mlp_get_k.restype = I
     lib.glint_mlp_last_launches.argtypes = [P]
     lib.glint_mlp_last_launches.restype = I
+    Z, LL = ctypes.c_size_t, ctypes.c_longlong
+    lib.glint_arena_create.argtypes = [Z, Z]
+    lib.glint_arena_create.restype = P
+    lib.glint_arena_destroy.argtypes = [P]
+    lib.glint_arena_destroy.restype = None
+    lib.glint_arena_alloc.argtypes = [P, Z]
+    lib.glint_arena_alloc.restype = LL
+    lib.glint_arena_free.argtypes = [P, LL]
+    lib.glint_arena_used.argtypes = [P]
+    lib.glint_arena_used.restype = Z
+    lib.glint_arena_largest_free.argtypes = [P]
+    lib.glint_arena_largest_free.restype = Z
+    lib.glint_plan_tick.argtypes = [P, P, I, L, I, P, P, P, I]
+    lib.glint_server_create.argtypes = [P, I, ctypes.POINTER(ServerDesc), ctypes.POINTER(P)]
+    lib.glint_server_destroy.argtypes = [P]
+    lib.glint_server_destroy.restype = None
+    lib.glint_server_add_env.argtypes = [P, P, P, ctypes.POINTER(I)]
+    lib.glint_server_submit.argtypes = [P, ctypes.POINTER(FrameRequest), ctypes.POINTER(L)]
+    lib.glint_server_tick.argtypes = [P, P, ctypes.POINTER(I)]
+    lib.glint_server_poll.argtypes = [P, P, I, ctypes.POINTER(I)]
+    lib.glint_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
     lib.glint_env_last_launches.argtypes = [P]
     lib.glint_env_last_launches.restype = I
     lib.glint_ctx_last_launches.argtypes = [P]
@@ -354,6 +398,113 @@ def mlp_features(ctx: Context, env: Env, planes, width: int, height: int, tangen
     _check(lib.glint_mlp_features(ctx.handle, env.handle, ctypes.byref(g), _dptr(x), _dptr(lp),
                                   _stream_handle(stream)))
     return x, lp
+
+
+class Arena:
+    """glint_arena: host bookkeeping of device-memory admission (first fit, coalescing)."""
+
+    def __init__(self, nbytes: int, align: int = 256):
+        self.handle = lib.glint_arena_create(nbytes, align)
+        if not self.handle:
+            raise GlintError(1, "glint_arena_create: align must be a power of two")
+
+    def alloc(self, nbytes: int) -> int:
+        return lib.glint_arena_alloc(self.handle, nbytes)
+
+    def free(self, offset: int) -> int:
+        return lib.glint_arena_free(self.handle, offset)
+
+    @property
+    def used(self) -> int:
+        return lib.glint_arena_used(self.handle)
+
+    @property
+    def largest_free(self) -> int:
+        return lib.glint_arena_largest_free(self.handle)
+
+    def close(self):
+        if self.handle:
+            lib.glint_arena_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_tick(next_px, npix, tick_pixels: int, tile_pixels: int, max_items: int = 1 << 16):
+    """glint_plan_tick: (items as (frame, first, count) rows, advanced next)."""
+    nxt = np.ascontiguousarray(next_px, np.int64).copy()
+    npx = np.ascontiguousarray(npix, np.int64)
+    f = np.zeros(max_items, np.int32)
+    first = np.zeros(max_items, np.int64)
+    cnt = np.zeros(max_items, np.int32)
+    n = lib.glint_plan_tick(nxt.ctypes.data, npx.ctypes.data, len(npx), tick_pixels, tile_pixels, f.ctypes.data,
+                            first.ctypes.data, cnt.ctypes.data, max_items)
+    return np.stack([f[:n].astype(np.int64), first[:n], cnt[:n].astype(np.int64)], 1), nxt
+
+
+class Server:
+    """glint_server: continuous batching of frames submitted from host memory."""
+
+    def __init__(self, ctx: Context, K: int, memory_budget: int, tick_pixels: int = 0, tile_pixels: int = 0,
+                 max_frames: int = 0, max_inflight_ticks: int = 0):
+        self.ctx = ctx
+        self.desc = ServerDesc(memory_budget, tick_pixels, tile_pixels, max_frames, max_inflight_ticks)
+        h = ctypes.c_void_p()
+        _check(lib.glint_server_create(ctx.handle, K, ctypes.byref(self.desc), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def add_env(self, env: Env, mlp=None) -> int:
+        i = ctypes.c_int()
+        _check(lib.glint_server_add_env(self.handle, env.handle, mlp.handle if mlp is not None else None,
+                                        ctypes.byref(i)))
+        return i.value
+
+    def submit(self, env_id: int, planes, width: int, height: int, out, seed: int = 0,
+               evaluator: int = EVAL_E1, tangent=None) -> int:
+        """planes, tangent, out: host tensors (pinned for overlapped copies), kept alive until polled."""
+        r = FrameRequest(env_id, width, height, seed & 0xFFFFFFFF, evaluator, _dptr(planes[0]), _dptr(planes[1]),
+                         _dptr(planes[2]), _dptr(planes[3]), _dptr(tangent), _dptr(out))
+        fid = ctypes.c_long()
+        _check(lib.glint_server_submit(self.handle, ctypes.byref(r), ctypes.byref(fid)))
+        self._keep[fid.value] = (planes, tangent, out)
+        return fid.value
+
+    def tick(self, stream=None) -> int:
+        n = ctypes.c_int()
+        _check(lib.glint_server_tick(self.handle, _stream_handle(stream), ctypes.byref(n)))
+        return n.value
+
+    def poll(self, max_done: int = 256):
+        arr = (FrameDone * max_done)()
+        n = ctypes.c_int()
+        _check(lib.glint_server_poll(self.handle, arr, max_done, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            d = arr[i]
+            self._keep.pop(d.id, None)
+            out.append((d.id, d.submit_s, d.admit_s, d.done_s))
+        return out
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib.glint_server_stats_get(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib.glint_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def normal_quantile(p, out=None, stream=None):

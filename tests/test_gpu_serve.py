@@ -1,0 +1,125 @@
+"""The serving loop on the GPU: each frame's result is the same alone and in
+a mix of frames of other resolutions, maps, seeds and paths (bit for bit), and
+equals glint_shade's; admission by memory (frames wait for the budget, peak
+use stays within it); continuous batching (a small frame submitted after a
+large one finishes first)."""
+import numpy as np
+import pytest
+
+from paper_2507_02674_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_02674_gb300 import build as B
+    B.build()
+    from paper_2507_02674_gb300 import glint, render
+    ctx = glint.Context(0, 64, 128)
+    cfg = glint.EnvConfig(K=8, out_width=128)
+    frames = [render.Frame(ctx, synth.env_hdr(seed=s, W=256, H=128), cfg) for s in (6, 7)]
+    for f in frames:
+        f.update_env()
+    net = glint.Mlp(ctx, 8, 1024, seed=3)
+    net.set_params(synth.mlp_params(seed=4, K=8))
+    return glint, render, ctx, torch, frames, net
+
+
+class Req:
+    def __init__(self, torch, render, n, width, seed):
+        gb = synth.gbuffer_random(n, seed=seed, width=width)
+        self.gb = gb
+        self.w, self.h = gb.width, gb.height
+        self.planes = render.gbuffer_tensors(gb, device="cpu", pinned=True)
+        self.tan = torch.from_numpy(gb.tangents()).pin_memory()
+        self.out = torch.zeros(self.w * self.h, 4).pin_memory()
+
+
+def _drain(server, torch, limit=100000):
+    done = []
+    for _ in range(limit):
+        server.tick()
+        done += server.poll()
+        st = server.stats()
+        if st["queued"] == 0 and st["active"] == 0:
+            break
+    torch.cuda.synchronize()
+    return done
+
+
+def test_alone_equals_mix_equals_glint_shade(gl):
+    glint, render, ctx, torch, frames, net = gl
+    reqs = [Req(torch, render, 640 * 360, 640, 11), Req(torch, render, 300 * 200, 300, 12),
+            Req(torch, render, 1000 * 97 + 13, 1000, 13), Req(torch, render, 50000, 500, 14)]
+    plan = [(0, 5, glint.EVAL_E1), (1, 6, glint.EVAL_E1), (0, 7, glint.EVAL_MLP), (1, 8, glint.EVAL_MLP)]
+
+    def server():
+        s = glint.Server(ctx, 8, 1 << 30, tick_pixels=100000, tile_pixels=4096)
+        s.add_env(frames[0].env, net)
+        s.add_env(frames[1].env, net)
+        return s
+
+    alone = []
+    for r, (e, seed, ev) in zip(reqs, plan):
+        s = server()
+        s.submit(e, r.planes, r.w, r.h, r.out, seed, ev, r.tan)
+        _drain(s, torch)
+        alone.append(r.out.clone())
+        r.out.zero_()
+    s = server()
+    for r, (e, seed, ev) in zip(reqs, plan):
+        s.submit(e, r.planes, r.w, r.h, r.out, seed, ev, r.tan)
+    done = _drain(s, torch)
+    assert len(done) == len(reqs)
+    st = s.stats()
+    assert st["ticks"] > 1 and st["launches"] >= st["ticks"]
+    for r, a, (e, seed, ev) in zip(reqs, alone, plan):
+        assert torch.equal(r.out, a)  # bit for bit, alone and in the mix
+        # and as glint_shade computes the frame on its own
+        planes = [p.cuda() for p in r.planes]
+        ref = frames[e].shade(planes, r.w, r.h, seed=seed, evaluator=ev, tangent=r.tan.cuda(),
+                              mlp=net if ev == glint.EVAL_MLP else None).cpu()
+        same = float((ref == r.out).all(1).float().mean())
+        print(f"frame {r.w}x{r.h} env {e} path {ev}: equal to glint_shade at {same:.4%} of pixels")
+        torch.testing.assert_close(r.out, ref, rtol=1e-5, atol=1e-6 * float(ref.abs().max()))
+
+
+def test_admission_by_memory(gl):
+    glint, render, ctx, torch, frames, net = gl
+    r = [Req(torch, render, 640 * 360, 640, 20 + i) for i in range(5)]
+    per_frame = 5 * (640 * 360 * 16)  # 4 planes + output (each 256-byte aligned: exact here)
+    s = glint.Server(ctx, 8, 2 * per_frame + 4096, tick_pixels=1 << 22)
+    e = s.add_env(frames[0].env)
+    for i, q in enumerate(r):
+        s.submit(e, q.planes, q.w, q.h, q.out, i)
+    s.tick()
+    st = s.stats()
+    assert st["active"] == 2 and st["queued"] == 3
+    done = _drain(s, torch)
+    assert sorted(d[0] for d in done) == [1, 2, 3, 4, 5]
+    st = s.stats()
+    assert st["peak_bytes"] <= 2 * per_frame + 4096 and st["used_bytes"] == 0
+    big = Req(torch, render, 1200 * 600, 1200, 30)
+    with pytest.raises(glint.GlintError):  # can never fit
+        s.submit(e, big.planes, big.w, big.h, big.out, 0)
+
+
+def test_continuous_batching_small_frame_overtakes(gl):
+    glint, render, ctx, torch, frames, net = gl
+    big = Req(torch, render, 2000 * 1000, 2000, 40)
+    small = Req(torch, render, 200 * 100, 200, 41)
+    s = glint.Server(ctx, 8, 1 << 30, tick_pixels=200000, tile_pixels=16384)
+    e = s.add_env(frames[0].env)
+    i_big = s.submit(e, big.planes, big.w, big.h, big.out, 1)
+    s.tick()
+    s.tick()
+    i_small = s.submit(e, small.planes, small.w, small.h, small.out, 2)
+    done = _drain(s, torch)
+    order = [d[0] for d in done]
+    assert order.index(i_small) < order.index(i_big)
+    t = {d[0]: d for d in done}
+    assert t[i_small][2] < t[i_big][3]  # admitted while the big frame was in flight

@@ -109,7 +109,7 @@ class ClockSampler:
 
 def _source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("glint_shade.cu", "glint_internal.cuh"):
+    for f in ("glint_shade.cu", "glint_probs.cuh", "glint_quantile.cuh", "glint_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2507_02674_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -272,10 +272,11 @@ def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed
     torch.cuda.synchronize(dev)
     prep_s = time.time() - t0
     net = glint.Mlp(ctx, K, SURROGATE_BATCH, seed=1)
+    steps = args.surrogate_steps
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for i in range(SURROGATE_STEPS):
-        lr = max(SURROGATE_LR * 0.5 * (1 + math.cos(math.pi * i / SURROGATE_STEPS)), 1e-5)
+    for i in range(steps):
+        lr = max(SURROGATE_LR * 0.5 * (1 + math.cos(math.pi * i / steps)), 1e-5)
         net.train_step(X, L, Y, i * SURROGATE_BATCH, SURROGATE_BATCH, lr, stream=stream)
     b.record(stream)
     final_loss = net.train_step(X, L, Y, 0, SURROGATE_BATCH, 0.0, want_loss=True, stream=stream)
@@ -334,9 +335,9 @@ def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed
                   "e2_ms_per_step": round(float(ms_e2.mean()), 4),
                   "speedup": round(float(ms_e2.mean() / ms_nn.mean()), 2)},
         "error_vs_e2_p_k": err(p_nn), "e1_error_vs_e2_p_k": err(p_e1),
-        "train": {"samples": int(n_train), "label": f"E2 S={SURROGATE_LABEL_S}", "steps": SURROGATE_STEPS,
+        "train": {"samples": int(n_train), "label": f"E2 S={SURROGATE_LABEL_S}", "steps": steps,
                   "batch": SURROGATE_BATCH, "ms": round(train_ms, 1),
-                  "msamples_per_s": round(SURROGATE_STEPS * SURROGATE_BATCH / train_ms / 1e3, 2),
+                  "msamples_per_s": round(steps * SURROGATE_BATCH / train_ms / 1e3, 2),
                   "final_loss": round(final_loss, 5), "data_prep_s": round(prep_s, 2),
                   "scenes": list(SURROGATE_TRAIN_SCENES)},
         "gpu_launches_per_step": fr.env.last_launches() + ctx.last_launches(),
@@ -389,7 +390,7 @@ def serving(args, glint, render, ctx, dev, stream):
     for sd in SURROGATE_TRAIN_SCENES:
         g = synth.gbuffer_scene(WIDTH, HEIGHT, seed=sd)
         train_scenes.append((g, render.gbuffer_tensors(g, device=dev), render.tangent_tensor(g, device=dev)))
-    nets = [_train_net(glint, render, ctx, f, train_scenes, SURROGATE_STEPS // 2, stream) for f in frs]
+    nets = [_train_net(glint, render, ctx, f, train_scenes, max(1, args.surrogate_steps // 2), stream) for f in frs]
     del train_scenes
     host = []
     for i, (w, h) in enumerate(SERVE_RES):
@@ -607,6 +608,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--surrogate-steps", type=int, default=SURROGATE_STEPS,
+                    help="Adam steps of the surrogate's training (fewer only for profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GLINT_ABI_VERSION 2
+#define GLINT_ABI_VERSION 3
 #define GLINT_MAX_K 16
 
 typedef enum glint_status {
@@ -120,7 +120,15 @@ typedef struct glint_env_desc {
                          [min(8, out_width), out_width], height = width / 2 */
     float s_min;      /* sqrt(alpha) of filtered level 0, > 0 */
     float s_max;      /* sqrt(alpha) of filtered level R-1, >= s_min */
+    int weight_space; /* glint_weight_space: interpolation of the fuzzy weights between the two
+                         levels bracketing a texel's brightness (Sec. 7 "Linear vs Logarithmic
+                         Radiance"; the paper uses linear) */
 } glint_env_desc;
+
+typedef enum glint_weight_space {
+    GLINT_WEIGHTS_LINEAR = 0, /* w = (Y - L_j) / (L_{j+1} - L_j) (Eq. wkdefpractice) */
+    GLINT_WEIGHTS_LOG = 1     /* w = (ln Y - ln L_j) / (ln L_{j+1} - ln L_j); linear below L_2 (L_1 = 0) */
+} glint_weight_space;
 
 /* Allocates an environment's device buffers (levels, weights pyramid,
  * filtered maps, scratch) for the given description and builds the filter's
@@ -332,6 +340,23 @@ glint_status glint_mlp_infer(const glint_mlp *mlp, glint_ctx *ctx, const glint_e
 
 int glint_mlp_get_k(const glint_mlp *mlp);
 int glint_mlp_last_launches(const glint_mlp *mlp);
+
+/* Checkpoint: writes one line of JSON header ({"format": "glint_mlp",
+ * "version": 1, "K", "params", "step", "arrays": ["params", "adam_m",
+ * "adam_v"], "dtype": "float32-le"}) and then the three arrays as
+ * little-endian float32 to `path` (synchronous). */
+glint_status glint_mlp_save(const glint_mlp *mlp, const char *path);
+/* A network restored from a glint_mlp_save file (parameters, Adam moments and
+ * step: training continues bit-identically), trainable with batches of up to
+ * max_batch samples. */
+glint_status glint_mlp_load(glint_ctx *ctx, const char *path, long max_batch, glint_mlp **out);
+
+/* Training samples of every pixel of `gbuf` under `env`: the inputs and
+ * log-priors of glint_mlp_features and, as targets, E2's p_k with an
+ * e2_samples x e2_samples quadrature (glint_reflect_probs).  targets_out:
+ * device, width*height*K floats.  Enqueued on `stream`. */
+glint_status glint_mlp_generate(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf, int e2_samples,
+                                uint16_t *x_out, float *lp_out, float *targets_out, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Serving (no counterpart in the paper): a continuous-batching request loop.

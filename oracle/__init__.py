@@ -82,7 +82,7 @@ def _load():
         lib.or_dualgated_many.argtypes = [D, D, P, P, L, I, P, P]
         lib.or_total_area.argtypes = [D, I]
         lib.or_total_area.restype = D
-        lib.or_env_decompose.argtypes = [P, I, I, D, I, D, P, P, P]
+        lib.or_env_decompose.argtypes = [P, I, I, D, I, D, P, P, P, I]
         lib.or_mip_count.argtypes = [I]
         lib.or_mip_count.restype = I
         lib.or_env_mips.argtypes = [P, I, I, I, P]
@@ -201,14 +201,15 @@ class EnvOracle:
     mips_flat: np.ndarray
 
 
-def env_decompose(rgba: np.ndarray, scale: float, K: int, ell: float):
+def env_decompose(rgba: np.ndarray, scale: float, K: int, ell: float, log_space: bool = False):
     lib = _load()
     rgba = np.ascontiguousarray(rgba, dtype=np.float32)
     H, W = rgba.shape[:2]
     L = np.zeros(K)
     lohi = np.zeros(2)
     ch0 = np.zeros((H, W, 3 + K))
-    lib.or_env_decompose(_ptr(rgba), W, H, float(scale), K, float(ell), _ptr(L), _ptr(lohi), _ptr(ch0))
+    lib.or_env_decompose(_ptr(rgba), W, H, float(scale), K, float(ell), _ptr(L), _ptr(lohi), _ptr(ch0),
+                         int(log_space))
     return L, lohi, ch0
 
 
@@ -231,8 +232,8 @@ def env_mips(ch0: np.ndarray):
     return flat, levels
 
 
-def env_full(rgba: np.ndarray, scale: float, K: int, ell: float) -> EnvOracle:
-    L, lohi, ch0 = env_decompose(rgba, scale, K, ell)
+def env_full(rgba: np.ndarray, scale: float, K: int, ell: float, log_space: bool = False) -> EnvOracle:
+    L, lohi, ch0 = env_decompose(rgba, scale, K, ell, log_space)
     flat, levels = env_mips(ch0)
     return EnvOracle(L, lohi, ch0, levels, flat)
 

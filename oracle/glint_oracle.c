@@ -358,7 +358,7 @@ static void lut_fetch(const double *lut, int n, double mu, double s, double out[
  * rgba: H x W x 4 floats (stored radiance, multiplied by `scale`).
  * ch0: H x W x (3+K) output, channels (R, G, B, w_1 .. w_K). */
 void or_env_decompose(const float *rgba, int W, int H, double scale, int K, double ell,
-                      double *L, double *lohi, double *ch0)
+                      double *L, double *lohi, double *ch0, int log_space)
 {
     long n = (long)W * H;
     double ymin = INFINITY, ymax = -INFINITY;
@@ -390,7 +390,11 @@ void or_env_decompose(const float *rgba, int W, int H, double scale, int K, doub
             int j = 0; /* 0-based: L[j] <= Y < L[j+1] */
             for (int k = 1; k < K - 1; ++k)
                 if (L[k] <= Y) j = k;
-            double tt = (Y - L[j]) / (L[j + 1] - L[j]);
+            /* Sec. 7 "Linear vs Logarithmic Radiance": the paper assigns weights in
+             * linear space; log_space interpolates ln Y between ln L_j and
+             * ln L_{j+1} instead, except below L_2 where L_1 = 0 has no logarithm. */
+            double tt = (log_space && j > 0) ? (log(Y) - log(L[j])) / (log(L[j + 1]) - log(L[j]))
+                                             : (Y - L[j]) / (L[j + 1] - L[j]);
             o[3 + j] = 1.0 - tt;
             o[3 + j + 1] = tt;
         }

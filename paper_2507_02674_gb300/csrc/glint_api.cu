@@ -140,6 +140,10 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
         set_error("glint_env_create: ell must be > 0 and |scale_log2| <= 64");
         return GLINT_ERR_INVALID_ARG;
     }
+    if (d->weight_space != GLINT_WEIGHTS_LINEAR && d->weight_space != GLINT_WEIGHTS_LOG) {
+        set_error("glint_env_create: unknown weight space %d", d->weight_space);
+        return GLINT_ERR_INVALID_ARG;
+    }
     if (d->levels < 1 || d->levels > 32 || d->samples < 1 || d->samples > 2048 || !is_pow2(d->out_width) ||
         d->out_width < 4 || d->out_width > 4096) {
         set_error("glint_env_create: levels in [1,32], samples in [1,2048], out_width a power of two in [4,4096]");

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(kNT) k_levels(const float2 *__restrict__ parti
 
 // Channel vector (R, G, B, w_1 .. w_K, 0 padding) of one texel: the fuzzy
 // weights of the two levels bracketing its brightness (Eq. wkdefpractice).
-__device__ __forceinline__ void texel_channels(float4 t, float scale, int K, const float *L, int Cpad, float *v) {
+__device__ __forceinline__ void texel_channels(float4 t, float scale, int K, const float *L, int Cpad, bool log_w,
+                                               float *v) {
     const float R = t.x * scale, G = t.y * scale, B = t.z * scale;
     const float Y = fmaxf(0.2126f * R + 0.7152f * G + 0.0722f * B, 0.f);
     // bracket: largest j in [0, K-2] with L[j] <= Y; Y >= L[K-1] -> w_K = 1
@@ -106,7 +107,9 @@ __device__ __forceinline__ void texel_channels(float4 t, float scale, int K, con
     for (int k = 1; k < K - 1; ++k)
         if (L[k] <= Y) j = k;
     const bool top = Y >= L[K - 1];
-    const float tt = (Y - L[j]) / (L[j + 1] - L[j]);
+    // log space (optional, Sec. 7): between L_j > 0 and L_{j+1}; linear below L_2 (L_1 = 0)
+    const float tt = (log_w && j > 0) ? (logf(Y) - logf(L[j])) / (logf(L[j + 1]) - logf(L[j]))
+                                      : (Y - L[j]) / (L[j + 1] - L[j]);
     v[0] = R; v[1] = G; v[2] = B;
     for (int c = 3; c < Cpad; ++c) {
         const int k = c - 3;
@@ -131,7 +134,7 @@ template <bool FROM_TEXELS>
 __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels, int fmt, float scale, int K,
                                                    const float *__restrict__ levels, float *__restrict__ pyr,
                                                    const size_t *__restrict__ off, int m, int Ws, int Hs, int T,
-                                                   int nlev, int Cpad) {
+                                                   int nlev, int Cpad, int log_w) {
     extern __shared__ float smem[];
     float *bufA = smem;                       // T*T texels
     float *bufB = smem + (size_t)T * T * Cpad; // (T/2)^2 texels
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels
         float *v = bufA + (size_t)i * Cpad;
         if (FROM_TEXELS) {
             float tmp[3 + GLINT_MAX_K + 1];
-            texel_channels(load_texel(texels, fmt, (long)gi), scale, K, L, Cpad, tmp);
+            texel_channels(load_texel(texels, fmt, (long)gi), scale, K, L, Cpad, log_w != 0, tmp);
             float4 *dst = reinterpret_cast<float4 *>(pyr + off[0] + gi * Cpad);
             for (int c = 0; c < C4; ++c) {
                 const float4 q = make_float4(tmp[4 * c], tmp[4 * c + 1], tmp[4 * c + 2], tmp[4 * c + 3]);
@@ -370,11 +373,12 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
             if (first) {
                 cudaFuncSetAttribute(k_pyramid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 k_pyramid<true><<<blocks, kNT, smem, s>>>(texels, d.format, scale, d.K, env->levels, env->pyr,
-                                                           env->pyr_off_dev, 0, Ws, Hs, T, nlev, env->Cpad);
+                                                           env->pyr_off_dev, 0, Ws, Hs, T, nlev, env->Cpad,
+                                                           d.weight_space);
             } else {
                 cudaFuncSetAttribute(k_pyramid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 k_pyramid<false><<<blocks, kNT, smem, s>>>(nullptr, d.format, scale, d.K, env->levels, env->pyr,
-                                                            env->pyr_off_dev, m, Ws, Hs, T, nlev, env->Cpad);
+                                                            env->pyr_off_dev, m, Ws, Hs, T, nlev, env->Cpad, 0);
             }
             ++nl;
             first = false;

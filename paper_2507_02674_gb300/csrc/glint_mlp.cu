@@ -22,8 +22,12 @@
 // and loops over 128-row tiles.
 #include <cuda_bf16.h>
 
+#include <stdio.h>
+#include <string.h>
+
 #include <algorithm>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "glint_internal.cuh"
@@ -986,5 +990,78 @@ glint_status glint_mlp_infer(const glint_mlp *g, glint_ctx *ctx, const glint_env
 
 int glint_mlp_get_k(const glint_mlp *g) { return g ? g->K : 0; }
 int glint_mlp_last_launches(const glint_mlp *g) { return g ? g->last_launches : 0; }
+
+static bool little_endian() {
+    const uint32_t one = 1;
+    unsigned char b;
+    memcpy(&b, &one, 1);
+    return b == 1;
+}
+
+glint_status glint_mlp_save(const glint_mlp *g, const char *path) {
+    set_error("%s", "");
+    if (!g || !path) { set_error("glint_mlp_save: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (!little_endian()) { set_error("glint_mlp_save: big-endian host"); return GLINT_ERR_UNSUPPORTED; }
+    std::vector<float> buf(3 * (size_t)kP);
+    glint_status st = glint_mlp_export(g, GLINT_MLP_PARAMS, buf.data(), kP);
+    if (st == GLINT_OK) st = glint_mlp_export(g, GLINT_MLP_ADAM_M, buf.data() + kP, kP);
+    if (st == GLINT_OK) st = glint_mlp_export(g, GLINT_MLP_ADAM_V, buf.data() + 2 * kP, kP);
+    if (st != GLINT_OK) return st;
+    FILE *f = fopen(path, "wb");
+    if (!f) { set_error("glint_mlp_save: cannot open %s", path); return GLINT_ERR_INVALID_ARG; }
+    char head[256];
+    const int n = snprintf(head, sizeof(head),
+                           "{\"format\": \"glint_mlp\", \"version\": 1, \"K\": %d, \"params\": %d, \"step\": %ld, "
+                           "\"arrays\": [\"params\", \"adam_m\", \"adam_v\"], \"dtype\": \"float32-le\"}\n",
+                           g->K, kP, g->step);
+    const bool ok = fwrite(head, 1, (size_t)n, f) == (size_t)n && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    if (fclose(f) != 0 || !ok) { set_error("glint_mlp_save: write to %s failed", path); return GLINT_ERR_INVALID_ARG; }
+    return GLINT_OK;
+}
+
+glint_status glint_mlp_load(glint_ctx *ctx, const char *path, long max_batch, glint_mlp **out) {
+    set_error("%s", "");
+    if (!ctx || !path || !out) { set_error("glint_mlp_load: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!little_endian()) { set_error("glint_mlp_load: big-endian host"); return GLINT_ERR_UNSUPPORTED; }
+    FILE *f = fopen(path, "rb");
+    if (!f) { set_error("glint_mlp_load: cannot open %s", path); return GLINT_ERR_INVALID_ARG; }
+    char head[512] = {0};
+    if (!fgets(head, sizeof(head), f)) { fclose(f); set_error("glint_mlp_load: empty file"); return GLINT_ERR_INVALID_ARG; }
+    int K = 0, np = 0, ver = 0;
+    long step = -1;
+    const char *pk = strstr(head, "\"K\":"), *pp = strstr(head, "\"params\":"), *ps = strstr(head, "\"step\":"),
+               *pv = strstr(head, "\"version\":");
+    if (!strstr(head, "\"format\": \"glint_mlp\"") || !pk || !pp || !ps || !pv || sscanf(pk + 4, "%d", &K) != 1 ||
+        sscanf(pp + 9, "%d", &np) != 1 || sscanf(ps + 7, "%ld", &step) != 1 || sscanf(pv + 10, "%d", &ver) != 1 ||
+        ver != 1 || np != kP || step < 0) {
+        fclose(f);
+        set_error("glint_mlp_load: %s is not a version-1 glint_mlp file with %d parameters", path, kP);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    std::vector<float> buf(3 * (size_t)kP);
+    const bool ok = fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    fclose(f);
+    if (!ok) { set_error("glint_mlp_load: %s is truncated", path); return GLINT_ERR_INVALID_ARG; }
+    glint_mlp *g = nullptr;
+    glint_status st = glint_mlp_create(ctx, K, max_batch, 0u, &g);
+    if (st != GLINT_OK) return st;
+    st = glint_mlp_import_state(g, buf.data(), buf.data() + kP, buf.data() + 2 * kP, kP, step);
+    if (st != GLINT_OK) { glint_mlp_destroy(g); return st; }
+    *out = g;
+    return GLINT_OK;
+}
+
+glint_status glint_mlp_generate(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf, int e2_samples,
+                                uint16_t *x_out, float *lp_out, float *targets_out, void *stream) {
+    glint_status st = glint_mlp_features(ctx, env, gbuf, x_out, lp_out, stream);
+    if (st != GLINT_OK) return st;
+    glint_params p{};
+    p.evaluator = GLINT_EVAL_E2;
+    p.e2_samples = e2_samples;
+    st = glint_reflect_probs(ctx, env, gbuf, &p, targets_out, stream);
+    ctx->last_launches = 2;
+    return st;
+}
 
 }  // extern "C"

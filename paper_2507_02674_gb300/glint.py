@@ -21,7 +21,8 @@ FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
 EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN = 0, 1, 2, 3
 MLP_PARAMS, MLP_GRAD, MLP_ADAM_M, MLP_ADAM_V = 0, 1, 2, 3
-ABI_VERSION = 2
+ABI_VERSION = 3
+WEIGHTS_LINEAR, WEIGHTS_LOG = 0, 1
 ENV_LOHI, ENV_LEVELS, ENV_PYRAMID, ENV_FILTERED, ENV_TABLE, ENV_FILTERED_WIDTHS = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_READY", 5: "TIMEOUT", 6: "UNSUPPORTED"}
 
@@ -36,7 +37,7 @@ class EnvDesc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("format", ctypes.c_int),
                 ("scale_log2", ctypes.c_int), ("K", ctypes.c_int), ("ell", ctypes.c_float),
                 ("levels", ctypes.c_int), ("samples", ctypes.c_int), ("out_width", ctypes.c_int),
-                ("s_min", ctypes.c_float), ("s_max", ctypes.c_float)]
+                ("s_min", ctypes.c_float), ("s_max", ctypes.c_float), ("weight_space", ctypes.c_int)]
 
 
 class GBufferDesc(ctypes.Structure):
@@ -114,6 +115,9 @@ def _load():
     lib.glint_mlp_forward.argtypes = [P, P, P, L, P, P]
     lib.glint_mlp_train_step.argtypes = [P, P, P, P, L, L, L, F, ctypes.POINTER(F), P]
     lib.glint_mlp_infer.argtypes = [P, P, P, ctypes.POINTER(GBufferDesc), P, P]
+    lib.glint_mlp_save.argtypes = [P, ctypes.c_char_p]
+    lib.glint_mlp_load.argtypes = [P, ctypes.c_char_p, L, ctypes.POINTER(P)]
+    lib.glint_mlp_generate.argtypes = [P, P, ctypes.POINTER(GBufferDesc), I, P, P, P, P]
     lib.glint_mlp_get_k.argtypes = [P]
     lib.glint_mlp_get_k.restype = I
     lib.glint_mlp_last_launches.argtypes = [P]
@@ -208,6 +212,7 @@ class EnvConfig:
     out_width: int = 256
     s_min: float = 0.02 ** 0.5
     s_max: float = 0.5 ** 0.5
+    weight_space: int = 0  # WEIGHTS_LINEAR (the paper's) or WEIGHTS_LOG
 
 
 class Env:
@@ -217,7 +222,7 @@ class Env:
         self.ctx = ctx
         self.cfg = cfg
         self.desc = EnvDesc(width, height, fmt, scale_log2, cfg.K, cfg.ell, cfg.levels, cfg.samples, cfg.out_width,
-                            cfg.s_min, cfg.s_max)
+                            cfg.s_min, cfg.s_max, cfg.weight_space)
         h = ctypes.c_void_p()
         _check(lib.glint_env_create(ctx.handle, ctypes.byref(self.desc), ctypes.byref(h)))
         self.handle = h
@@ -369,6 +374,21 @@ class Mlp:
                                    _stream_handle(stream)))
         return out
 
+    def save(self, path: str):
+        """glint_mlp_save: parameters, Adam moments and step (JSON header + float32 LE)."""
+        _check(lib.glint_mlp_save(self.handle, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, ctx: Context, path: str, max_batch: int):
+        """glint_mlp_load: a network restored from a checkpoint file."""
+        h = ctypes.c_void_p()
+        _check(lib.glint_mlp_load(ctx.handle, os.fsencode(path), max_batch, ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.handle, self.ctx, self.max_batch = h, ctx, max_batch
+        self.K = lib.glint_mlp_get_k(h)
+        self.n_params = lib.glint_mlp_param_count()
+        return self
+
     def last_launches(self) -> int:
         return lib.glint_mlp_last_launches(self.handle)
 
@@ -505,6 +525,21 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def mlp_generate(ctx: Context, env: Env, planes, width: int, height: int, tangent, e2_samples: int = 32,
+                 stream=None):
+    """glint_mlp_generate: training inputs, log-priors and E2 targets of every pixel."""
+    import torch
+    n = width * height
+    dev = planes[0].device
+    x = torch.empty(n, 64, dtype=torch.int16, device=dev)
+    lp = torch.empty(n, env.cfg.K, device=dev)
+    y = torch.empty(n, env.cfg.K, device=dev)
+    g = _gbuffer(planes, width, height, tangent)
+    _check(lib.glint_mlp_generate(ctx.handle, env.handle, ctypes.byref(g), e2_samples, _dptr(x), _dptr(lp), _dptr(y),
+                                  _stream_handle(stream)))
+    return x, lp, y
 
 
 def normal_quantile(p, out=None, stream=None):

@@ -22,6 +22,7 @@ class MethodParams:
     Q: int = 128                   # table quadrature points per axis
     seed: int = 0
     integer_mode: bool = True
+    log_weights: bool = False      # fuzzy weights interpolated in log space (Sec. 7)
 
     def with_(self, **kw) -> "MethodParams":
         return replace(self, **kw)
@@ -38,7 +39,7 @@ def oracle_lut(orc, mp: MethodParams) -> np.ndarray:
 
 
 def oracle_env(orc, env, mp: MethodParams):
-    e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell)
+    e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell, mp.log_weights)
     pref = orc.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo)
     return e, pref
 

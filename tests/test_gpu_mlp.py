@@ -182,9 +182,9 @@ def test_mlp_adam_step_matches_oracle(gl):
     assert np.all(w1[~used] == prm[~used])
 
 
-def test_mlp_training_is_deterministic_and_resumes(gl):
-    """Same inputs give bit-identical parameters; a run restored from a
-    checkpoint after 3 steps continues bit-identically."""
+def test_mlp_training_is_deterministic_and_resumes(gl, tmp_path):
+    """Same inputs give bit-identical parameters; a run restored after 3 steps
+    (from exported state or from a checkpoint file) continues bit-identically."""
     glint, render, ctx, torch = gl
     K, n = 8, 20000
     rng = np.random.default_rng(95)
@@ -208,10 +208,21 @@ def test_mlp_training_is_deterministic_and_resumes(gl):
     c = glint.Mlp(ctx, K, 4096, seed=123)
     c.import_state(*ck, 3)
     run(c, 6, 3)
-    pa, pb, pc = (v.export(glint.MLP_PARAMS) for v in (a, b, c))
+    # and through a checkpoint file
+    path = str(tmp_path / "net.glint_mlp")
+    d0 = glint.Mlp(ctx, K, 4096, seed=7)
+    run(d0, 3)
+    d0.save(path)
+    head = open(path, "rb").readline()
+    assert b'"format": "glint_mlp"' in head and b'"step": 3' in head
+    d = glint.Mlp.load(ctx, path, 4096)
+    assert d.step == 3 and d.K == K
+    run(d, 6, 3)
+    pa, pb, pc, pd = (v.export(glint.MLP_PARAMS) for v in (a, b, c, d))
     assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
     assert np.array_equal(pa.view(np.uint32), pc.view(np.uint32))
-    assert a.step == b.step == c.step == 6
+    assert np.array_equal(pa.view(np.uint32), pd.view(np.uint32))
+    assert a.step == b.step == c.step == d.step == 6
     assert not np.array_equal(pa, ck[0])
 
 
@@ -258,6 +269,10 @@ def test_mlp_paths_agree(gl):
     net = glint.Mlp(ctx, K, 1024, seed=9)
     net.set_params(synth.mlp_params(seed=10, K=K))
     x, l = glint.mlp_features(ctx, fr.env, planes, gb.width, gb.height, tan)
+    x2, l2, y2 = glint.mlp_generate(ctx, fr.env, planes, gb.width, gb.height, tan, e2_samples=16)
+    pe2 = fr.probs(planes, gb.width, gb.height, evaluator=glint.EVAL_E2, e2_samples=16, tangent=tan)
+    torch.cuda.synchronize()
+    assert torch.equal(x2, x) and torch.equal(l2, l) and torch.equal(y2, pe2)
     p_two = net.forward(x, l)
     p_inf = net.infer(fr.env, planes, gb.width, gb.height, tan, torch.empty(n, K, device="cuda"))
     fg = torch.from_numpy(gb.rows16()[:, 3] > 0).cuda()

@@ -31,7 +31,7 @@ def gl():
 
 def _cfg(glint, mp: MethodParams):
     return glint.EnvConfig(K=mp.K, ell=mp.ell, levels=mp.R, samples=mp.S, out_width=mp.Wo, s_min=mp.s_min,
-                           s_max=mp.s_max)
+                           s_max=mp.s_max, weight_space=int(mp.log_weights))
 
 
 def _run(gl, env, gb, mp: MethodParams, debug=True, rows=None, evaluator=0, e2_S=16):
@@ -84,14 +84,17 @@ def test_tables(gl, orc):
 
 
 @pytest.mark.parametrize("which", ["tiny", "hdr"])
-def test_env_levels_weights_pyramid(gl, orc, which):
+@pytest.mark.parametrize("log_weights", [False, True])
+def test_env_levels_weights_pyramid(gl, orc, which, log_weights):
+    """Levels, fuzzy weights (linear, and log space as Sec. 7 compares) and the
+    pyramid; log-space weights carry FP32 logarithms (abs error ~1e-6)."""
     glint, render, ctx, torch = gl
     env = synth.env_tiny(0) if which == "tiny" else synth.env_hdr(seed=3, W=256, H=128)
-    mp = MethodParams(K=8, Wo=64)
+    mp = MethodParams(K=8, Wo=64, log_weights=log_weights)
     fr = render.Frame(ctx, env, _cfg(glint, mp))
     fr.update_env()
     torch.cuda.synchronize()
-    e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell)
+    e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell, log_weights)
     L = fr.env.levels().astype(np.float64)
     assert np.allclose(L, e.levels, rtol=3e-6, atol=0)
     lohi = fr.env.export(glint.ENV_LOHI).astype(np.float64)

@@ -176,3 +176,36 @@ def test_filter_close_to_exact_convolution(orc):
     rel = np.abs(lev[..., :3] - ex[..., :3]) / ex[..., :3]
     assert np.median(rel) < 0.03 and np.max(rel) < 0.12
     assert np.max(np.abs(lev[..., 3:] - ex[..., 3:])) < 0.05
+
+
+def test_log_space_weights(orc):
+    """Sec. 7 "Linear vs Logarithmic Radiance": weights interpolated in log
+    space reconstruct ln Y = sum_k w_k ln L_k exactly between L_2 and L_K, keep
+    the partition of unity, fall back to linear below L_2 (L_1 = 0) and give
+    w_K = 1 at the top; linear weights reconstruct Y instead."""
+    rng = np.random.default_rng(5)
+    H, W = 16, 32
+    rgba = np.zeros((H, W, 4), np.float32)
+    rgba[..., :3] = (10.0 ** rng.uniform(-3, 3, size=(H, W, 1))).astype(np.float32)
+    rgba[..., 3] = 1
+    K = 8
+    L, lohi, ch_lin = orc.env_decompose(rgba, 1.0, K, 1e-4)
+    L2, lohi2, ch_log = orc.env_decompose(rgba, 1.0, K, 1e-4, log_space=True)
+    assert np.array_equal(L, L2) and np.array_equal(lohi, lohi2)
+    Y = np.maximum(rgba[..., :3].astype(np.float64) @ [0.2126, 0.7152, 0.0722], 0)
+    w_lin, w_log = ch_lin[..., 3:], ch_log[..., 3:]
+    np.testing.assert_allclose(w_log.sum(-1), 1.0, atol=1e-12)
+    np.testing.assert_allclose((w_lin * L).sum(-1), Y, rtol=1e-12)
+    mid = (Y >= L[1]) & (Y < L[-1])
+    lnL = np.log(np.maximum(L, 1e-300))
+    recon = (w_log * np.where(L > 0, lnL, 0.0)).sum(-1)
+    np.testing.assert_allclose(recon[mid], np.log(Y[mid]), rtol=0, atol=1e-12)
+    low = Y < L[1]
+    assert low.any() and mid.any()
+    np.testing.assert_array_equal(w_log[low], w_lin[low])
+    top = Y >= L[-1]
+    assert np.all(w_log[top][:, -1] == 1.0)
+    # ln is concave, so the log-space factor (ln Y - ln L_j)/(ln L_{j+1} - ln L_j)
+    # is at least the linear one: log weights lean to the upper level
+    j = np.argmax(w_lin[mid] > 0, axis=-1)
+    assert np.all(w_log[mid][np.arange(j.size), j] <= w_lin[mid][np.arange(j.size), j] + 1e-12)

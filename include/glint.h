@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GLINT_ABI_VERSION 3
+#define GLINT_ABI_VERSION 4
 #define GLINT_MAX_K 16
 
 typedef enum glint_status {
@@ -200,7 +200,18 @@ typedef struct glint_params {
     float *p_scratch;     /* GLINT_EVAL_MLP: device, width*height*K floats (4-byte aligned) that
                              receive the network's p_k before shading; GLINT_EVAL_GIVEN: the
                              p_k to shade with (read only).  Caller-owned */
+    int draw;             /* glint_draw: binomial approximation at the tree nodes (0 = the paper's) */
+    float gamma;          /* GLINT_DRAW_WANG2020: reflection probability of a microfacet, (0, 1] */
 } glint_params;
+
+typedef enum glint_draw {
+    GLINT_DRAW_DUAL = 0,       /* dual-gated Gaussians (Alg. 1), the paper's method */
+    GLINT_DRAW_SINGLE = 1,     /* single-gated Gaussians generalised to real N (Eq. gated); comparison */
+    GLINT_DRAW_SINGLE_OLD = 2, /* the earlier single-gated form with a floor (Eq. oldgated); comparison */
+    GLINT_DRAW_WANG2020 = 3    /* Wang et al. 2020 on the same grid (Sec. 7): one single-gated count per
+                                  sample with probability gamma, independent of the map;
+                                  L^_o = L_o M / (N_P gamma); counts: bin 1 the glints, bin 2 the rest */
+} glint_draw;
 
 /* Optional per-pixel intermediate results (device; each pointer may be NULL).
  *   p:      npix x K   reflection probabilities p_k (Eq. probhk)

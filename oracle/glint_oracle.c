@@ -866,6 +866,7 @@ static void grid_vertices(float u, float v, int l, int64_t vx[3], int64_t vy[3],
  *                         single pyramid texels per quadrature point) */
 typedef struct {
     int K, integer_mode;
+    int draw; /* 0 dual-gated (Alg. 1), 1 single-gated (Eq. gated), 2 Eq. oldgated */
     uint32_t key0, key1, key2, seed;
     double P[2 * OR_MAXK];
     double tie[5];
@@ -873,6 +874,16 @@ typedef struct {
     double *out;     /* max_cand x K leaf counts */
     double *out_err; /* max_cand x K leaf count tolerance */
 } tree_ctx;
+
+/* Probability of no positive trial among N, in the small-p biased form of
+ * Sec. 5: (1 - c p)^(N/c), c = max(1, eps/p) (exactly (1-p)^N for p >= eps). */
+static double single_pnone(double N, double p)
+{
+    if (!(p > 0.0)) return 1.0;
+    if (p >= 1.0) return N > 0.0 ? 0.0 : 1.0;
+    double c = fmax(1.0, or_eps() / p);
+    return pow(1.0 - c * p, N / c);
+}
 
 static double thr_eval_err(double T, double a, double e_f)
 {
@@ -896,6 +907,96 @@ static int push_outcome(outcome *list, int cnt, double n, double nb, double en, 
 /* Evaluate node `node` of the multinomial tree (heap order) for the trials
  * N[node] (tolerance dN[node]) and recurse; every valid outcome is listed,
  * the nominal FP64 outcome first. */
+static void tree_rec(tree_ctx *t, int node, double *N, double *dN);
+
+/* One tree node with a single-gated Gaussian (Sec. 5: Eq. gated, or with
+ * draw 2 Eq. oldgated).  The gate opens when 1 - xi1 > (1 - c p)^(N/c) (at
+ * least one positive trial) and, for Eq. gated with real N, also xi1 < N p;
+ * an open gate gives the Gaussian N(1 + (N-1) p, (N-1) p (1-p)) clamped to
+ * [1, max(N, 1)] (rounded half up for integer counts; Eq. oldgated takes the
+ * floor), a closed one 0; the right child gets max(N - n, 0).  Decisions
+ * within the tie model's reach enumerate both outcomes, as for Alg. 1. */
+static void tree_single(tree_ctx *t, int node, double *N, double *dN, double Nn, double dNn, double PL, double PR,
+                        double p, double xi1, double xi2, int use_tie)
+{
+    int old = t->draw == 2;
+    double e_P = t->tie[0], e_z = t->tie[1], e_f = t->tie[2], d_a = t->tie[3], a_P = t->tie[4];
+    double xi1c = 1.0 - xi1;
+    double Pn = single_pnone(Nn, p);
+    double mu = 1.0 + (Nn - 1.0) * p, s2 = (Nn - 1.0) * p * (1.0 - p);
+    double sigma = s2 > 0.0 ? sqrt(s2) : 0.0;
+    double z = or_ndtri(xi2);
+    double G = mu + sigma * z;
+    double Np = Nn * p;
+    double tauP = 0.0, tauG = 0.0, tauN = 0.0;
+    if (use_tie) {
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            double pp = p;
+            if (PL + PR > 0.0) {
+                double pl = fmax(PL * (1.0 + sgn * e_P) + sgn * a_P, 0.0);
+                double pr = fmax(PR * (1.0 - sgn * e_P) - sgn * a_P, 0.0);
+                if (pl + pr > 0.0) pp = pl / (pl + pr);
+            }
+            for (int sn = -1; sn <= 1; sn += 2) {
+                double Nq = fmax(Nn + sn * dNn, 0.0);
+                tauP = fmax(tauP, fabs(single_pnone(Nq, pp) - Pn));
+                double s22 = (Nq - 1.0) * pp * (1.0 - pp);
+                double G2 = 1.0 + (Nq - 1.0) * pp + (s22 > 0.0 ? sqrt(s22) : 0.0) * z;
+                tauG = fmax(tauG, fabs(G2 - G));
+                tauN = fmax(tauN, fabs(Nq * pp - Np));
+            }
+        }
+        tauP += thr_eval_err(Pn, 1.0, e_f) + d_a;
+        tauG += sigma * (fabs(z) * e_z + 0x1p-22) + fabs(G) * 0x1p-22 + 0x1p-24;
+        tauN += Np * 0x1p-22 + d_a;
+    }
+    int real_gate = !t->integer_mode && !old;
+    int open_nom = (xi1c > Pn) && (!real_gate || xi1 < Np);
+    int can_open = (xi1c > Pn - tauP) && (!real_gate || xi1 < Np + tauN);
+    int can_close = (xi1c <= Pn + tauP) || (real_gate && xi1 >= Np - tauN);
+    double Nmax = fmax(Nn, 1.0);
+    outcome list[64];
+    int cnt = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int open = 1; open >= 0; --open) {
+            if (pass == 0 ? open != open_nom : !(open ? can_open : can_close)) continue;
+            if (!open) {
+                cnt = push_outcome(list, cnt, 0.0, Nn, 0.0, dNn);
+                continue;
+            }
+            if (t->integer_mode) {
+                if (Nn <= 1.0 && dNn <= 0.0) {  /* one trial: the gate decides */
+                    cnt = push_outcome(list, cnt, 1.0, Nn - 1.0, 0.0, 0.0);
+                    continue;
+                }
+                double r = old ? floor(G) : floor(G + 0.5);
+                double gn = fmin(fmax(r, 1.0), Nn);
+                double glo = fmin(fmax(old ? floor(G - tauG) : floor(G - tauG + 0.5), 1.0), Nn);
+                double ghi = fmin(fmax(old ? floor(G + tauG) : floor(G + tauG + 0.5), 1.0), Nn);
+                int interval = (dNn > 0.0) || (ghi - glo > 2.0);
+                double eG = interval ? tauG + 0.5 : 0.0;
+                cnt = push_outcome(list, cnt, gn, Nn - gn, eG, dNn + eG);
+                if (pass == 1 && !interval)
+                    for (double g = glo; g <= ghi; g += 1.0) cnt = push_outcome(list, cnt, g, Nn - g, 0.0, 0.0);
+            } else {
+                double g = fmin(fmax(G, 1.0), Nmax);
+                double n = old ? floor(g) : g;
+                double en = old ? 1.0 : tauG;
+                if (old && floor(g - tauG) == floor(g + tauG)) en = 0.0;
+                cnt = push_outcome(list, cnt, n, fmax(Nn - n, 0.0), en, en + dNn);
+            }
+        }
+    }
+    if (cnt > 1) t->flagged++;
+    for (int i = 0; i < cnt; ++i) {
+        N[2 * node] = list[i].n;
+        N[2 * node + 1] = list[i].nb;
+        dN[2 * node] = list[i].en;
+        dN[2 * node + 1] = list[i].eb;
+        tree_rec(t, node + 1, N, dN);
+    }
+}
+
 static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
 {
     int K = t->K;
@@ -923,6 +1024,10 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
     double e_P = t->tie[0], e_z = t->tie[1], e_f = t->tie[2], d_a = t->tie[3], a_P = t->tie[4];
     int use_tie = (e_P > 0.0 || e_z > 0.0 || e_f > 0.0 || d_a > 0.0 || a_P > 0.0);
 
+    if (t->draw == 1 || t->draw == 2) {
+        tree_single(t, node, N, dN, Nn, dNn, PL, PR, p, xi1, xi2, use_tie);
+        return;
+    }
     double T[4], mu, sigma;
     or_dualgated_thresholds(Nn, p, T, &mu, &sigma);
     double z = or_ndtri(xi2);
@@ -1063,6 +1168,11 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
  *    (0 when the denominator is 0).
  *
  * evaluator = 2 takes p_k from pk_in (npix x K) as given.
+ * draw selects the binomial approximation at the tree nodes: 0 dual-gated
+ * (Alg. 1), 1 single-gated (Eq. gated), 2 Eq. oldgated, 3 the Wang 2020
+ * comparison of Sec. 7 (one single-gated count per sample with probability
+ * gamma, independent of the map; counts (glints, rest) in bins 1 and 2;
+ * L^_o = L_o M_1 / (N_P gamma)).
  * evaluator = 1 replaces p_k by the E2 quadrature (or_e2_pk) of the
  * anisotropic footprint, with per-pixel tangents (npix x 4) and the pyramid
  * (mips, W x H level 0); e2_flags counts its near-boundary points.
@@ -1078,7 +1188,7 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
               const double *tie, int max_cand, double *rgb, double *lo, double *pk, float *np, int64_t *vert,
               double *wv, double *nroot, int32_t *ncand, double *cand, double *cand_err, int32_t *flags,
               int evaluator, const float *tangents, int e2_S, const double *mips, int W, int H, int32_t *e2_flags,
-              const double *pk_in)
+              const double *pk_in, int draw, double gamma)
 {
     long nbg = 0;
     for (long q = 0; q < npix; ++q) {
@@ -1154,8 +1264,19 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
         t.seed = seed;
         for (int i = 0; i < 5; ++i) t.tie[i] = tie[i];
         t.max_cand = max_cand;
+        t.draw = (draw == 3) ? 1 : draw;
         for (int k = 0; k < K; ++k) t.P[K + k] = p[k];
         for (int nd = K - 1; nd >= 1; --nd) t.P[nd] = t.P[2 * nd] + t.P[2 * nd + 1];
+        /* Wang 2020: a two-bin tree (glints gamma, rest 1 - gamma) at every sample */
+        double wang_buf[64 * 2], wang_err[64 * 2];
+        int K_tree = K;
+        if (draw == 3) {
+            K_tree = 2;
+            t.K = 2;
+            t.P[2] = gamma;
+            t.P[3] = 1.0 - gamma;
+            t.P[1] = 1.0;
+        }
 
         double Mk[OR_MAXK];
         for (int k = 0; k < K; ++k) Mk[k] = 0.0;
@@ -1188,13 +1309,22 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
                     N[1] = (double)NP;
                 }
                 nroot[q * OR_NV + v] = N[1];
-                t.out = cand + ((size_t)q * OR_NV + v) * max_cand * K;
-                t.out_err = cand_err + ((size_t)q * OR_NV + v) * max_cand * K;
+                double *co = cand + ((size_t)q * OR_NV + v) * max_cand * K;
+                double *ce = cand_err + ((size_t)q * OR_NV + v) * max_cand * K;
+                t.out = (K_tree == K) ? co : wang_buf;
+                t.out_err = (K_tree == K) ? ce : wang_err;
+                t.max_cand = (K_tree == K) ? max_cand : (max_cand < 64 ? max_cand : 64);
                 t.n_out = 0;
                 t.overflow = 0;
                 tree_rec(&t, 1, N, dN);
+                if (K_tree != K) /* two-bin outcomes into the first two of K bins */
+                    for (int i = 0; i < t.n_out; ++i)
+                        for (int k = 0; k < K; ++k) {
+                            co[i * K + k] = k < 2 ? wang_buf[i * 2 + k] : 0.0;
+                            ce[i * K + k] = k < 2 ? wang_err[i * 2 + k] : 0.0;
+                        }
                 ncand[q * OR_NV + v] = t.overflow ? -1 : t.n_out;
-                for (int k = 0; k < K; ++k) Mk[k] += w * t.out[k]; /* first = nominal outcome */
+                for (int k = 0; k < K; ++k) Mk[k] += w * co[k]; /* first = nominal outcome */
             }
         }
         flags[q] = t.flagged;
@@ -1204,6 +1334,10 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
             den += L[k] * p[k];
         }
         den *= (double)NP;
+        if (draw == 3) {
+            num = Mk[0];
+            den = (double)NP * gamma;
+        }
         if (den > 0.0)
             for (int c = 0; c < 3; ++c) rgb[3 * q + c] = Lo[c] * num / den;
     }
@@ -1214,7 +1348,7 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
  * (Eq. iblglints:fin): L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k),
  * M_k = sum_i w_i n_k(i). counts: 6 x K. */
 void or_radiance(const double *lo3, const double *pk, double np, const double *L, int K, const double *wv,
-                 const double *counts, double *rgb)
+                 const double *counts, double *rgb, int draw, double gamma)
 {
     double num = 0.0, den = 0.0;
     for (int k = 1; k < K; ++k) {
@@ -1224,17 +1358,24 @@ void or_radiance(const double *lo3, const double *pk, double np, const double *L
         den += L[k] * pk[k];
     }
     den *= np;
+    if (draw == 3) { /* Wang 2020: L_o M_1 / (N_P gamma) */
+        num = 0.0;
+        for (int v = 0; v < OR_NV; ++v) num += wv[v] * counts[v * K];
+        den = np * gamma;
+    }
     for (int c = 0; c < 3; ++c) rgb[c] = den > 0.0 ? lo3[c] * num / den : 0.0;
 }
 
 /* One hierarchical multinomial draw with explicit uniforms, for statistical
  * tests of the tree: K bins with probabilities p, N trials at the root, key
- * and seed as in or_shade; counts: K leaf counts (nominal outcome). */
+ * and seed as in or_shade, draw as in or_shade's tree (0 dual-gated, 1 Eq.
+ * gated, 2 Eq. oldgated); counts: K leaf counts (nominal outcome). */
 void or_multinomial(const double *p, int K, double N, uint32_t key0, uint32_t key1, uint32_t key2, uint32_t seed,
-                    int integer_mode, double *counts)
+                    int integer_mode, double *counts, int draw)
 {
     tree_ctx t;
     memset(&t, 0, sizeof(t));
+    t.draw = draw;
     double buf[OR_MAXK], ebuf[OR_MAXK];
     t.K = K;
     t.integer_mode = integer_mode;

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libglint.so")
-SOURCES = ["glint_api.cu", "glint_lut.cu", "glint_env.cu", "glint_shade.cu", "glint_noalloc.cu", "glint_mlp.cu", "glint_serve.cu"]
+SOURCES = ["glint_api.cu", "glint_lut.cu", "glint_env.cu", "glint_shade.cu", "glint_noalloc.cu", "glint_mlp.cu", "glint_serve.cu", "glint_variants.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

@@ -335,6 +335,18 @@ static glint_status check_shade_args(const char *who, glint_ctx *ctx, const glin
         set_error("%s: e2_samples %d outside [0, 256]", who, p->e2_samples);
         return GLINT_ERR_INVALID_ARG;
     }
+    if (p->draw < GLINT_DRAW_DUAL || p->draw > GLINT_DRAW_WANG2020) {
+        set_error("%s: unknown draw %d", who, p->draw);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (p->draw != GLINT_DRAW_DUAL && p->evaluator != GLINT_EVAL_E1) {
+        set_error("%s: the comparison draws run with the E1 evaluator", who);
+        return GLINT_ERR_UNSUPPORTED;
+    }
+    if (p->draw == GLINT_DRAW_WANG2020 && !(p->gamma > 0.f && p->gamma <= 1.f)) {
+        set_error("%s: gamma %g outside (0, 1]", who, (double)p->gamma);
+        return GLINT_ERR_INVALID_ARG;
+    }
     if (p->evaluator == GLINT_EVAL_MLP) {
         if (!p->mlp) { set_error("%s: the MLP evaluator needs params->mlp", who); return GLINT_ERR_INVALID_ARG; }
         if (glint_mlp_k(p->mlp) != env->d.K) {

@@ -25,6 +25,8 @@ struct ShadeArgs {
     int envW, envH, envM, e2S;
     const float *pk_in;  // EV_GIVEN: p_k per pixel (npix x K)
     float *p_out;        // k_probs: p_k per pixel (npix x K)
+    int draw;                 // kDraw*
+    float gamma;              // kDrawWang: the environment-independent reflection probability
     const void *mlp_wt;       // serving: the frame's surrogate (BF16 weight copies)
     const float *mlp_params;  //          and its FP32 parameters (biases)
 };
@@ -36,6 +38,9 @@ struct ServeItem {
     int count;
     long first;
 };
+
+// Binomial approximation at the tree nodes (glint_draw).
+constexpr int kDrawDual = 0, kDrawSingle = 1, kDrawSingleOld = 2, kDrawWang = 3;
 
 // Source of the reflection probabilities p_k.
 constexpr int EV_E1 = 0, EV_E2 = 1, EV_GIVEN = 2;
@@ -221,6 +226,8 @@ inline ShadeArgs make_args(const glint_ctx *ctx, const glint_env *env, const gli
     a.envH = env->d.height;
     a.envM = env->M;
     a.e2S = p->e2_samples > 0 ? p->e2_samples : 16;
+    a.draw = p->draw;
+    a.gamma = p->gamma;
     return a;
 }
 

@@ -21,7 +21,8 @@ FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
 EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN = 0, 1, 2, 3
 MLP_PARAMS, MLP_GRAD, MLP_ADAM_M, MLP_ADAM_V = 0, 1, 2, 3
-ABI_VERSION = 3
+ABI_VERSION = 4
+DRAW_DUAL, DRAW_SINGLE, DRAW_SINGLE_OLD, DRAW_WANG2020 = 0, 1, 2, 3
 WEIGHTS_LINEAR, WEIGHTS_LOG = 0, 1
 ENV_LOHI, ENV_LEVELS, ENV_PYRAMID, ENV_FILTERED, ENV_TABLE, ENV_FILTERED_WIDTHS = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_READY", 5: "TIMEOUT", 6: "UNSUPPORTED"}
@@ -48,7 +49,8 @@ class GBufferDesc(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint32), ("count_mode", ctypes.c_int), ("evaluator", ctypes.c_int),
-                ("e2_samples", ctypes.c_int), ("mlp", ctypes.c_void_p), ("p_scratch", ctypes.c_void_p)]
+                ("e2_samples", ctypes.c_int), ("mlp", ctypes.c_void_p), ("p_scratch", ctypes.c_void_p),
+                ("draw", ctypes.c_int), ("gamma", ctypes.c_float)]
 
 
 class Debug(ctypes.Structure):
@@ -288,18 +290,20 @@ def _gbuffer(planes, width: int, height: int, tangent=None) -> GBufferDesc:
                        _dptr(tangent))
 
 
-def _params(seed=0, count_mode=COUNT_INTEGER, evaluator=EVAL_E1, e2_samples=16, mlp=None, p_scratch=None):
+def _params(seed=0, count_mode=COUNT_INTEGER, evaluator=EVAL_E1, e2_samples=16, mlp=None, p_scratch=None,
+            draw=DRAW_DUAL, gamma=0.0):
     return Params(seed & 0xFFFFFFFF, count_mode, evaluator, e2_samples,
-                  mlp.handle.value if mlp is not None else None, _dptr(p_scratch))
+                  mlp.handle.value if mlp is not None else None, _dptr(p_scratch), draw, gamma)
 
 
 def shade(ctx: Context, env: Env, planes, width: int, height: int, out, seed: int = 0,
           count_mode: int = COUNT_INTEGER, debug: dict | None = None, stream=None, tangent=None,
-          evaluator: int = EVAL_E1, e2_samples: int = 16, mlp=None, p_scratch=None):
+          evaluator: int = EVAL_E1, e2_samples: int = 16, mlp=None, p_scratch=None, draw: int = DRAW_DUAL,
+          gamma: float = 0.0):
     """glint_shade over a G-buffer given as four device tensors of (npix, 4) float32
     (plus an optional (npix, 4) tangent tensor, needed by E2 and the MLP)."""
     g = _gbuffer(planes, width, height, tangent)
-    p = _params(seed, count_mode, evaluator, e2_samples, mlp, p_scratch)
+    p = _params(seed, count_mode, evaluator, e2_samples, mlp, p_scratch, draw, gamma)
     dbg = None
     if debug is not None:
         dbg = Debug(*(_dptr(debug.get(k)) for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")))

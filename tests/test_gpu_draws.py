@@ -1,0 +1,66 @@
+"""The comparison draws on the GPU against the oracle: single-gated Gaussians
+(Eq. gated), the older single-gated form (Eq. oldgated) and the Wang 2020
+glints (Sec. 7), integer and real counts: N_P, grid, root trials exact,
+counts in the oracle's valid set, radiance within 1e-4."""
+import numpy as np
+import pytest
+
+from paper_2507_02674_gb300 import synth
+from tests._pipeline import MethodParams, oracle_shade
+from tests.test_gpu_parity import _cfg, _check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_02674_gb300 import build as B
+    B.build()
+    from paper_2507_02674_gb300 import glint, render
+    ctx = glint.Context(0, 64, 128)
+    return glint, render, ctx, torch
+
+
+@pytest.mark.parametrize("draw", [1, 2, 3])
+@pytest.mark.parametrize("integer_mode", [True, False])
+def test_comparison_draws_match_oracle(gl, orc, draw, integer_mode):
+    glint, render, ctx, torch = gl
+    K = 8
+    mp = MethodParams(K=K, Wo=128, seed=29 + draw, integer_mode=integer_mode)
+    env = synth.env_hdr(seed=6, W=256, H=128)
+    gb = synth.gbuffer_random(2049, seed=40 + draw, width=2049, n_lo=0.1 if not integer_mode else 1e3)
+    n = gb.width * gb.height
+    gamma = 0.02 if draw == 3 else 0.0
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    planes = render.gbuffer_tensors(gb)
+    dbg = glint.debug_buffers(n, K)
+    mode = glint.COUNT_INTEGER if integer_mode else glint.COUNT_REAL
+    out = fr.shade(planes, gb.width, gb.height, seed=mp.seed, count_mode=mode, debug=dbg, draw=draw, gamma=gamma)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in dbg.items()}
+    res["rgb"] = out[:, :3].cpu().numpy().astype(np.float64)
+    o = oracle_shade(orc, gb.rows16(), env, mp, draw=draw, gamma=gamma)
+    rep = _check(orc, o, res, integer_mode=integer_mode)
+    if draw == 3:
+        c = res["counts"].reshape(n, 6, K)
+        assert np.all(c[:, :, 2:] == 0)
+
+
+def test_comparison_draw_arguments(gl):
+    glint, render, ctx, torch = gl
+    mp = MethodParams(K=4, Wo=64)
+    fr = render.Frame(ctx, synth.env_tiny(0), _cfg(glint, mp))
+    fr.update_env()
+    gb = synth.gbuffer_random(100, seed=1, width=100)
+    planes = render.gbuffer_tensors(gb)
+    with pytest.raises(glint.GlintError):
+        fr.shade(planes, 100, 1, draw=7)
+    with pytest.raises(glint.GlintError):
+        fr.shade(planes, 100, 1, draw=3, gamma=0.0)
+    with pytest.raises(glint.GlintError) as e:
+        fr.shade(planes, 100, 1, draw=1, evaluator=glint.EVAL_E2, tangent=render.tangent_tensor(gb))
+    assert e.value.status == 6

@@ -439,6 +439,15 @@ void glint_server_destroy(glint_server *server);
 /* Makes `env` (updated, same context and K) resident for requests; `mlp` (may
  * be NULL) is its surrogate for GLINT_EVAL_MLP.  *env_id receives the index. */
 glint_status glint_server_add_env(glint_server *server, const glint_env *env, const glint_mlp *mlp, int *env_id);
+/* Requests an update of resident map `env_id` from `texels` (device, the
+ * map's size and format; the caller keeps them unchanged until the update
+ * has run): frames submitted before the call are shaded with the map as it
+ * was, frames submitted after it with the updated map.  A tick runs the
+ * update (glint_env_update's launches, on the tick's stream) once no admitted
+ * or queued frame needs the previous version; until then the newer frames
+ * wait in the queue.  Several requests before it runs collapse into the
+ * latest. */
+glint_status glint_server_update_env(glint_server *server, int env_id, const void *texels);
 /* Queues a frame and returns its id; GLINT_ERR_INVALID_ARG if the request is
  * malformed or its buffers could never fit the memory budget. */
 glint_status glint_server_submit(glint_server *server, const glint_frame_request *req, long *id);

@@ -44,6 +44,7 @@ constexpr int kP = kIn * kHid + kHid + kHid * kHid + kHid + kHid * kOutPad + kOu
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kIn * kHid, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid,
               kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kOutPad;
 constexpr int kNT = 128;  // threads (samples) per block
+constexpr int kLpStride = 17;  // floats per log-prior row in shared memory (odd: no bank conflicts)
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -172,7 +173,7 @@ __device__ __forceinline__ void softmax_rows(float c[NT][4], int K, const float 
     const int t = threadIdx.x & 3, g = (threadIdx.x & 31) >> 2;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {  // rows g and g + 8
-        const float *lr = lp + (row0 + g + 8 * h) * kOutPad;
+        const float *lr = lp + (row0 + g + 8 * h) * kLpStride;
 #pragma unroll
         for (int j = 0; j < NT; ++j)
 #pragma unroll
@@ -213,7 +214,7 @@ __device__ __forceinline__ void softmax_rows(float c[NT][4], int K, const float 
 struct SmemInfer {
     SmemW w;
     __align__(16) __nv_bfloat16 xs[kNT * 64];
-    float lp[kNT * kOutPad];
+    float lp[kNT * kLpStride];
     int fg[kNT];
 };
 
@@ -265,7 +266,7 @@ __device__ __forceinline__ void stage_row(SmemInfer &sm, int r, const float *x, 
         x4[r * 8 + (q ^ (r & 7))] = v;
     }
 #pragma unroll
-    for (int k = 0; k < kOutPad; ++k) sm.lp[r * kOutPad + k] = (fg && k < K) ? lp[k] : 0.f;
+    for (int k = 0; k < kOutPad; ++k) sm.lp[r * kLpStride + k] = (fg && k < K) ? lp[k] : 0.f;
     sm.fg[r] = fg ? 1 : 0;
 }
 
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_forward(const uint4 *__restrict__ x
         }
         for (int idx = threadIdx.x; idx < kNT * kOutPad; idx += kNT) {
             const int r = idx / kOutPad, k = idx % kOutPad;
-            sm.lp[idx] = (base + r < n && k < K) ? __ldg(lp + (base + r) * K + k) : 0.f;
+            sm.lp[r * kLpStride + k] = (base + r < n && k < K) ? __ldg(lp + (base + r) * K + k) : 0.f;
         }
         sm.fg[threadIdx.x] = 1;
         __syncthreads();
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_forward(const uint4 *__restrict__ x
 
 // Features and network fused: p of every pixel of a G-buffer (background 0).
 template <int K>
-__global__ void __launch_bounds__(kNT) k_mlp_infer(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
+__global__ void __launch_bounds__(kNT, 4) k_mlp_infer(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
                                                    const float *__restrict__ params, float *__restrict__ p_out) {
     __shared__ SmemInfer sm;
     load_weights(sm.w, wt, params);
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_infer(ShadeArgs a, const __nv_bfloa
 // p_out.  A block reloads the weights when an item's network differs from the
 // one it holds.  Items start at multiples of 128 pixels of their frame.
 template <int K>
-__global__ void __launch_bounds__(kNT) k_mlp_serve(const ShadeArgs *__restrict__ frames,
+__global__ void __launch_bounds__(kNT, 4) k_mlp_serve(const ShadeArgs *__restrict__ frames,
                                                    const ServeItem *__restrict__ items, int nitems) {
     __shared__ SmemInfer sm;
     __shared__ ShadeArgs sa;
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
     __nv_bfloat16 *dz = h2 + kNT * 64;     // dZ2
     __nv_bfloat16 *dz3 = dz + kNT * 64;    // [kNT][16]
     float *red = reinterpret_cast<float *>(dz3 + kNT * 16);  // kNT floats
-    float *lps = red + kNT;                                   // [kNT][16] log-priors
+    float *lps = red + kNT;                                   // [kNT][kLpStride] log-priors
 
     load_weights(sw, wt, params);
     copy_swz(sb.w2, wb, kHid);
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
             for (int idx = threadIdx.x; idx < kNT * kOutPad; idx += kNT) {
                 const int r = idx / kOutPad, k = idx % kOutPad;
                 const long i = base + r;
-                lps[idx] = (i < nb && k < K) ? __ldg(lpg + (i % n_total) * K + k) : 0.f;
+                lps[r * kLpStride + k] = (i < nb && k < K) ? __ldg(lpg + (i % n_total) * K + k) : 0.f;
             }
         }
         __syncthreads();
@@ -688,7 +689,7 @@ constexpr int kNW = kIn * kHid + kHid * kHid + kHid * kOutPad;  // weights (no b
 
 size_t grad_smem() {
     return sizeof(SmemW) + sizeof(SmemWB) + sizeof(__nv_bfloat16) * (4 * kNT * 64 + kNT * 16) +
-           sizeof(float) * (kNT + kNT * kOutPad);
+           sizeof(float) * (kNT + kNT * kLpStride);
 }
 
 void mlp_free(glint_mlp *g) {

@@ -121,6 +121,7 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 
 struct Frame {
     long id = 0;
+    long env_version = 0;      // version of its map the frame is shaded with
     glint_frame_request req{};
     long npix = 0;
     long next = 0;             // pixels enqueued for shading so far
@@ -133,6 +134,14 @@ struct Frame {
     bool waited = false;       // the compute stream waits on `uploaded`
     bool copying_back = false;
     double submit_s = 0, admit_s = 0;
+};
+
+struct EnvEntry {  // a resident map
+    glint_env *env = nullptr;
+    const glint_mlp *mlp = nullptr;
+    long applied = 0;          // updates applied so far
+    long requested = 0;        // updates requested so far
+    const void *texels = nullptr;  // the latest requested update's texels (device)
 };
 
 struct Slot {  // staging of one tick's frame table and work list
@@ -155,7 +164,7 @@ struct glint_server {
     glint_arena *arena = nullptr;
     cudaStream_t copy = nullptr;  // uploads
     cudaStream_t back = nullptr;  // copies back (never queued behind uploads)
-    std::vector<std::pair<const glint_env *, const glint_mlp *>> envs;
+    std::vector<EnvEntry> envs;
     std::deque<Frame> queue;
     std::vector<Frame> active;  // admission order
     std::vector<glint_frame_done> finished;
@@ -202,6 +211,7 @@ void retire(glint_server *s) {
 glint_status admit(glint_server *s) {
     while (!s->queue.empty() && (int)s->active.size() < s->d.max_frames) {
         Frame &q = s->queue.front();
+        if (s->envs[q.req.env].applied < q.env_version) break;  // FIFO: waits for its map's update
         const size_t bytes = frame_bytes(q.req, s->K);
         const long long off = glint_arena_alloc(s->arena, bytes);
         if (off < 0) break;  // FIFO: the head waits until memory frees up
@@ -244,9 +254,46 @@ glint_status admit(glint_server *s) {
     return GLINT_OK;
 }
 
+// Applies each map's latest requested update once no admitted frame still
+// needs the previous version (queued frames of the previous version are
+// admitted and finished first, in FIFO order).  The update runs on the compute
+// stream, so later ticks see the new map.
+glint_status apply_updates(glint_server *s, cudaStream_t cs) {
+    for (size_t e = 0; e < s->envs.size(); ++e) {
+        EnvEntry &en = s->envs[e];
+        if (en.applied == en.requested) continue;
+        bool busy = false;
+        for (const Frame &f : s->active)
+            if (f.req.env == (int)e && f.env_version < en.requested) busy = true;
+        for (const Frame &f : s->queue)
+            if (f.req.env == (int)e && f.env_version < en.requested) busy = true;
+        if (busy) continue;
+        int nl = 0;
+        glint_status st = cuda_status(glint_launch_env(en.env, en.texels, cs, &nl), "glint_server_tick: map update");
+        if (st != GLINT_OK) return st;
+        en.env->last_launches = nl;
+        en.applied = en.requested;
+        s->st.launches += nl;
+    }
+    return GLINT_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+glint_status glint_server_update_env(glint_server *s, int env_id, const void *texels) {
+    set_error("%s", "");
+    if (!s || !texels) { set_error("glint_server_update_env: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (env_id < 0 || env_id >= (int)s->envs.size()) {
+        set_error("glint_server_update_env: unknown env %d", env_id);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    EnvEntry &en = s->envs[env_id];
+    en.texels = texels;
+    en.requested += 1;
+    return GLINT_OK;
+}
 
 glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc *desc, glint_server **out) {
     set_error("%s", "");
@@ -335,7 +382,10 @@ glint_status glint_server_add_env(glint_server *s, const glint_env *env, const g
         set_error("glint_server_add_env: network K or device differs");
         return GLINT_ERR_INVALID_ARG;
     }
-    s->envs.emplace_back(env, mlp);
+    EnvEntry e;
+    e.env = const_cast<glint_env *>(env);
+    e.mlp = mlp;
+    s->envs.push_back(e);
     *env_id = (int)s->envs.size() - 1;
     return GLINT_OK;
 }
@@ -352,7 +402,7 @@ glint_status glint_server_submit(glint_server *s, const glint_frame_request *r, 
         set_error("glint_server_submit: evaluator %d (E1 or MLP)", r->evaluator);
         return GLINT_ERR_INVALID_ARG;
     }
-    if (r->evaluator == GLINT_EVAL_MLP && (!s->envs[r->env].second || !r->tangent)) {
+    if (r->evaluator == GLINT_EVAL_MLP && (!s->envs[r->env].mlp || !r->tangent)) {
         set_error("glint_server_submit: the surrogate path needs the environment's network and a tangent plane");
         return GLINT_ERR_INVALID_ARG;
     }
@@ -367,6 +417,7 @@ glint_status glint_server_submit(glint_server *s, const glint_frame_request *r, 
     }
     Frame f;
     f.id = s->next_id++;
+    f.env_version = s->envs[r->env].requested;
     f.req = *r;
     f.npix = (long)r->width * r->height;
     f.submit_s = now_s(s->t0);
@@ -385,7 +436,8 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
     if (prev != s->ctx->device) cudaSetDevice(s->ctx->device);
     cudaStream_t cs = (cudaStream_t)stream;
     retire(s);
-    glint_status st = admit(s);
+    glint_status st = apply_updates(s, cs);
+    if (st == GLINT_OK) st = admit(s);
     // frames with pixels left, in admission order
     std::vector<int> idx;
     for (int i = 0; i < (int)s->active.size(); ++i)
@@ -415,7 +467,7 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
             const bool mx = pf[x] < n_mlp_frames, my = pf[y] < n_mlp_frames;
             if (mx != my) return mx;
             if (!mx) return false;
-            return s->envs[s->active[order[pf[x]]].req.env].second < s->envs[s->active[order[pf[y]]].req.env].second;
+            return s->envs[s->active[order[pf[x]]].req.env].mlp < s->envs[s->active[order[pf[y]]].req.env].mlp;
         });
         // items are cut into pieces of kPiece pixels, so that a tick of a few
         // frames still spreads over every SM
@@ -447,13 +499,13 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
                 Frame &f = s->active[order[j]];
                 glint_params prm{};
                 prm.seed = f.req.seed;
-                const glint_env *env = s->envs[f.req.env].first;
+                const glint_env *env = s->envs[f.req.env].env;
                 ShadeArgs a = make_args(s->ctx, env, &f.gb, &prm);
                 a.out = reinterpret_cast<float4 *>(f.out);
                 a.pk_in = f.p;
                 a.p_out = f.p;
                 if (f.req.evaluator == GLINT_EVAL_MLP)
-                    glint_mlp_weights(s->envs[f.req.env].second, &a.mlp_wt, &a.mlp_params);
+                    glint_mlp_weights(s->envs[f.req.env].mlp, &a.mlp_wt, &a.mlp_params);
                 table_of[j] = nframes;
                 sl.h_frames[nframes++] = a;
                 if (!f.waited) {

@@ -142,6 +142,7 @@ def _load():
     lib.glint_server_destroy.restype = None
     lib.glint_server_add_env.argtypes = [P, P, P, ctypes.POINTER(I)]
     lib.glint_server_submit.argtypes = [P, ctypes.POINTER(FrameRequest), ctypes.POINTER(L)]
+    lib.glint_server_update_env.argtypes = [P, I, P]
     lib.glint_server_tick.argtypes = [P, P, ctypes.POINTER(I)]
     lib.glint_server_poll.argtypes = [P, P, I, ctypes.POINTER(I)]
     lib.glint_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
@@ -487,6 +488,11 @@ class Server:
         _check(lib.glint_server_add_env(self.handle, env.handle, mlp.handle if mlp is not None else None,
                                         ctypes.byref(i)))
         return i.value
+
+    def update_env(self, env_id: int, texels):
+        """glint_server_update_env: later frames of this map use `texels` (device)."""
+        _check(lib.glint_server_update_env(self.handle, env_id, _dptr(texels)))
+        self._keep[("env", env_id, id(texels))] = texels
 
     def submit(self, env_id: int, planes, width: int, height: int, out, seed: int = 0,
                evaluator: int = EVAL_E1, tangent=None) -> int:

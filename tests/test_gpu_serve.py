@@ -123,3 +123,28 @@ def test_continuous_batching_small_frame_overtakes(gl):
     assert order.index(i_small) < order.index(i_big)
     t = {d[0]: d for d in done}
     assert t[i_small][2] < t[i_big][3]  # admitted while the big frame was in flight
+
+
+def test_map_update_between_frames(gl):
+    """A map updated while frames are queued: frames submitted before the
+    update are shaded with the old map, frames after it with the new one, each
+    as glint_shade computes it with that map."""
+    glint, render, ctx, torch, frames, net = gl
+    cfg = glint.EnvConfig(K=8, out_width=128)
+    env_a, env_b = synth.env_hdr(seed=21, W=256, H=128), synth.env_hdr(seed=22, W=256, H=128)
+    ref_a, ref_b, served = (render.Frame(ctx, e, cfg) for e in (env_a, env_b, env_a))
+    for f in (ref_a, ref_b, served):
+        f.update_env()
+    reqs = [Req(torch, render, 300 * 200, 300, 50 + i) for i in range(3)]
+    s = glint.Server(ctx, 8, 1 << 30, tick_pixels=20000, tile_pixels=4096)
+    e = s.add_env(served.env)
+    s.submit(e, reqs[0].planes, reqs[0].w, reqs[0].h, reqs[0].out, 1)
+    s.tick()
+    s.update_env(e, ref_b.texels)
+    s.submit(e, reqs[1].planes, reqs[1].w, reqs[1].h, reqs[1].out, 2)
+    s.submit(e, reqs[2].planes, reqs[2].w, reqs[2].h, reqs[2].out, 3)
+    done = _drain(s, torch)
+    assert len(done) == 3
+    for r, ref, seed in ((reqs[0], ref_a, 1), (reqs[1], ref_b, 2), (reqs[2], ref_b, 3)):
+        want = ref.shade([p.cuda() for p in r.planes], r.w, r.h, seed=seed).cpu()
+        assert torch.equal(r.out, want)

@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GLINT_ABI_VERSION 4
+#define GLINT_ABI_VERSION 5
 #define GLINT_MAX_K 16
 
 typedef enum glint_status {
@@ -123,7 +123,16 @@ typedef struct glint_env_desc {
     int weight_space; /* glint_weight_space: interpolation of the fuzzy weights between the two
                          levels bracketing a texel's brightness (Sec. 7 "Linear vs Logarithmic
                          Radiance"; the paper uses linear) */
+    int weight_format; /* glint_weight_format: storage of the filtered maps' weights W_k (Sec. 7
+                          "Texture Precision") */
 } glint_env_desc;
+
+typedef enum glint_weight_format {
+    GLINT_WFMT_F32 = 0,     /* float32 channels, (3+K) padded to a multiple of 4 per texel */
+    GLINT_WFMT_F16 = 1,     /* per texel: (R, G, B) float32 + K float16 weights (round to nearest even) */
+    GLINT_WFMT_UNORM16 = 2, /* ... + K 16-bit codes round(65535 W) */
+    GLINT_WFMT_UNORM8 = 3   /* ... + K 8-bit codes round(255 W): the precision the paper finds too low */
+} glint_weight_format;
 
 typedef enum glint_weight_space {
     GLINT_WEIGHTS_LINEAR = 0, /* w = (Y - L_j) / (L_{j+1} - L_j) (Eq. wkdefpractice) */

@@ -260,9 +260,30 @@ def filtered_widths(R: int, s_min: float, s_max: float, Wmax: int) -> np.ndarray
     return w
 
 
-def prefilter(env: EnvOracle, R: int, S: int, s_min: float, s_max: float, Wmax: int, idx=None):
+WFMT_F32, WFMT_F16, WFMT_UNORM16, WFMT_UNORM8 = 0, 1, 2, 3
+
+
+def quantize_weights(flat: np.ndarray, wfmt: int) -> np.ndarray:
+    """The filtered maps' weight channels (columns 3..) as the stored format
+    gives them back (Sec. 7 "Texture Precision"): float16 rounded to nearest
+    even, or unorm codes round(W (2^b - 1)) of the weight clamped to [0, 1]
+    (ties to even), divided back.  RGB is kept."""
+    out = np.array(flat, dtype=np.float64, copy=True)
+    w = out[:, 3:]
+    if wfmt == WFMT_F16:
+        out[:, 3:] = w.astype(np.float16).astype(np.float64)
+    elif wfmt in (WFMT_UNORM16, WFMT_UNORM8):
+        m = 65535.0 if wfmt == WFMT_UNORM16 else 255.0
+        out[:, 3:] = np.rint(np.clip(w, 0.0, 1.0) * m) / m
+    elif wfmt != WFMT_F32:
+        raise ValueError(wfmt)
+    return out
+
+
+def prefilter(env: EnvOracle, R: int, S: int, s_min: float, s_max: float, Wmax: int, idx=None, wfmt: int = 0):
     """Filtered environment as a Filtered (all levels), or only the listed flat
-    texel indices of the concatenation as an (n, C) array."""
+    texel indices of the concatenation as an (n, C) array; weights stored in
+    format wfmt (quantize_weights)."""
     lib = _load()
     H, W, C = env.ch0.shape
     table, nvalid = prefilter_table(R, S, s_min, s_max, W, H)
@@ -272,6 +293,7 @@ def prefilter(env: EnvOracle, R: int, S: int, s_min: float, s_max: float, Wmax: 
         flat = np.zeros((total, C))
         lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, _ptr(widths), None, 0,
                          _ptr(flat))
+        flat = quantize_weights(flat, wfmt)
         levels, off = [], 0
         for w in widths:
             n = int(w) * (int(w) // 2)
@@ -282,7 +304,7 @@ def prefilter(env: EnvOracle, R: int, S: int, s_min: float, s_max: float, Wmax: 
     out = np.zeros((len(idx), C))
     lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, _ptr(widths), _ptr(idx),
                      len(idx), _ptr(out))
-    return out
+    return quantize_weights(out, wfmt)
 
 
 def prefilter_exact(ch0: np.ndarray, alpha: float, dirs: np.ndarray) -> np.ndarray:

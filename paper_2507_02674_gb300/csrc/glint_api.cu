@@ -34,6 +34,7 @@ struct DeviceGuard {
     explicit DeviceGuard(int dev) {
         if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
         if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+        if (!ok) cudaGetLastError();  // a failed switch must not poison later calls' status
     }
     ~DeviceGuard() {
         int cur = -1;
@@ -42,6 +43,22 @@ struct DeviceGuard {
 };
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// IEEE 754 binary16 -> float (host).
+static float half_to_float(uint16_t h) {
+    const uint32_t sign = (uint32_t)(h >> 15) << 31;
+    const int e = (h >> 10) & 0x1f;
+    const uint32_t m = h & 0x3ffu;
+    float v;
+    if (e == 0) v = ldexpf((float)m, -24);                       // zero and subnormals
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = ldexpf((float)(m | 0x400u), e - 25);
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    b |= sign;
+    memcpy(&v, &b, 4);
+    return v;
+}
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace glint
@@ -140,6 +157,10 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
         set_error("glint_env_create: ell must be > 0 and |scale_log2| <= 64");
         return GLINT_ERR_INVALID_ARG;
     }
+    if (d->weight_format < GLINT_WFMT_F32 || d->weight_format > GLINT_WFMT_UNORM8) {
+        set_error("glint_env_create: unknown weight format %d", d->weight_format);
+        return GLINT_ERR_INVALID_ARG;
+    }
     if (d->weight_space != GLINT_WEIGHTS_LINEAR && d->weight_space != GLINT_WEIGHTS_LOG) {
         set_error("glint_env_create: unknown weight space %d", d->weight_space);
         return GLINT_ERR_INVALID_ARG;
@@ -156,6 +177,7 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
     DeviceGuard guard(ctx->device);
     glint_env *e = new glint_env();
     e->ctx = ctx;
+    e->device = ctx->device;
     e->d = *d;
     e->C = 3 + d->K;
     e->Cpad = (e->C + 3) / 4 * 4;
@@ -203,7 +225,12 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
     alloc((void **)&e->pyr_off_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
     alloc((void **)&e->table, sizeof(float4) * (size_t)d->levels * d->samples, "glint_env_create: filter table");
     alloc((void **)&e->nvalid, sizeof(int) * d->levels, "glint_env_create: filter table");
-    alloc((void **)&e->filt, sizeof(float) * (size_t)e->foff[d->levels] * e->Cpad, "glint_env_create: filtered maps");
+    if (d->weight_format != GLINT_WFMT_F32) {
+        const int bytes_w = d->K * (d->weight_format == GLINT_WFMT_UNORM8 ? 1 : 2);
+        e->frec4 = 1 + (bytes_w + 15) / 16;
+    }
+    const size_t frec_bytes = d->weight_format == GLINT_WFMT_F32 ? sizeof(float) * e->Cpad : 16u * (size_t)e->frec4;
+    alloc((void **)&e->filt, frec_bytes * (size_t)e->foff[d->levels], "glint_env_create: filtered maps");
     alloc((void **)&e->flev, sizeof(int2) * d->levels, "glint_env_create: filtered level table");
     if (st == GLINT_OK)
         st = cuda_status(cudaMemcpy(e->pyr_off4_dev, off4.data(), sizeof(size_t) * M, cudaMemcpyHostToDevice),
@@ -283,8 +310,35 @@ glint_status glint_env_export(const glint_env *env, int item, int index, void *h
     case GLINT_ENV_PYRAMID:
         if (index < 0 || index >= env->M) { set_error("glint_env_export: pyramid level %d out of range", index); return GLINT_ERR_INVALID_ARG; }
         return copy_unpadded(env->pyr + env->pyr_off[index], (size_t)(d.width >> index) * (d.height >> index));
-    case GLINT_ENV_FILTERED:
-        return copy_unpadded(env->filt, (size_t)env->foff[d.levels]);
+    case GLINT_ENV_FILTERED: {
+        const size_t texels = (size_t)env->foff[d.levels];
+        if (d.weight_format == GLINT_WFMT_F32) return copy_unpadded(env->filt, texels);
+        // compressed records: decode to the float layout (3 + K floats per texel)
+        const size_t n = texels * env->C * sizeof(float);
+        if (bytes < n) { set_error("glint_env_export: need %zu bytes, got %zu", n, bytes); return GLINT_ERR_INVALID_ARG; }
+        const size_t rb = 16u * (size_t)env->frec4;
+        std::vector<unsigned char> raw(texels * rb);
+        glint_status st = cuda_status(cudaMemcpy(raw.data(), env->filt, raw.size(), cudaMemcpyDeviceToHost),
+                                      "glint_env_export");
+        if (st != GLINT_OK) return st;
+        float *dst = (float *)host_dst;
+        for (size_t t = 0; t < texels; ++t) {
+            const unsigned char *r = raw.data() + t * rb;
+            memcpy(dst + t * env->C, r, 3 * sizeof(float));
+            for (int k = 0; k < d.K; ++k) {
+                float v;
+                if (d.weight_format == GLINT_WFMT_UNORM8) {
+                    v = (float)r[16 + k] * (1.f / 255.f);
+                } else {
+                    uint16_t c;
+                    memcpy(&c, r + 16 + 2 * k, 2);
+                    v = d.weight_format == GLINT_WFMT_F16 ? half_to_float(c) : (float)c * (1.f / 65535.f);
+                }
+                dst[t * env->C + 3 + k] = v;
+            }
+        }
+        return GLINT_OK;
+    }
     case GLINT_ENV_FILTERED_WIDTHS: {
         const size_t n = sizeof(int) * d.levels;
         if (bytes < n) { set_error("glint_env_export: need %zu bytes, got %zu", n, bytes); return GLINT_ERR_INVALID_ARG; }
@@ -308,7 +362,7 @@ glint_status glint_env_export(const glint_env *env, int item, int index, void *h
 
 void glint_env_destroy(glint_env *env) {
     if (!env) return;
-    DeviceGuard guard(env->ctx->device);
+    DeviceGuard guard(env->device);  // the context may already be gone
     env_free(env);
     delete env;
 }

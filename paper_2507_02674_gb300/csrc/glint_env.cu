@@ -270,7 +270,7 @@ template <int C4>
 __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, const size_t *__restrict__ off4,
                                                   int W, int H, int M, const float4 *__restrict__ table,
                                                   const int *__restrict__ nvalid, int S, const FilterLevels fl,
-                                                  float4 *__restrict__ out) {
+                                                  float4 *__restrict__ out, int wfmt, int rec4, int K) {
     extern __shared__ float4 tab[];
     int r = 0;
     while (r + 1 < fl.nlev && (int)blockIdx.x >= fl.blk[r + 1]) ++r;
@@ -339,10 +339,37 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
     }
     if (!active || g != 0) return;
     const float inv = nv > 0 ? 1.f / (float)nv : 0.f;
-    float4 *o = out + ((size_t)fl.off[r] + t) * C4;
+    if (wfmt == GLINT_WFMT_F32) {
+        float4 *o = out + ((size_t)fl.off[r] + t) * C4;
 #pragma unroll
-    for (int c = 0; c < C4; ++c)
-        o[c] = make_float4(acc[c].x * inv, acc[c].y * inv, acc[c].z * inv, acc[c].w * inv);
+        for (int c = 0; c < C4; ++c)
+            o[c] = make_float4(acc[c].x * inv, acc[c].y * inv, acc[c].z * inv, acc[c].w * inv);
+        return;
+    }
+    // compressed record: (R, G, B, 0) float32, then K weight codes
+    float ch[C4 * 4];
+#pragma unroll
+    for (int c = 0; c < C4; ++c) {
+        ch[4 * c] = acc[c].x * inv; ch[4 * c + 1] = acc[c].y * inv;
+        ch[4 * c + 2] = acc[c].z * inv; ch[4 * c + 3] = acc[c].w * inv;
+    }
+    float4 *o = out + ((size_t)fl.off[r] + t) * rec4;
+    o[0] = make_float4(ch[0], ch[1], ch[2], 0.f);
+    uint32_t words[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < C4 * 4 - 3; ++k) {
+        if (k >= K) break;
+        const float wv = fminf(fmaxf(ch[3 + k], 0.f), 1.f);
+        if (wfmt == GLINT_WFMT_UNORM8) {
+            words[k / 4] |= (__float2uint_rn(wv * 255.f) & 0xffu) << (8 * (k % 4));
+        } else {
+            const uint32_t c16 = (wfmt == GLINT_WFMT_F16) ? (uint32_t)__half_as_ushort(__float2half_rn(ch[3 + k]))
+                                                         : (__float2uint_rn(wv * 65535.f) & 0xffffu);
+            words[k / 2] |= c16 << (16 * (k % 2));
+        }
+    }
+    uint4 *q = reinterpret_cast<uint4 *>(o + 1);
+    for (int i = 0; i < rec4 - 1; ++i) q[i] = make_uint4(words[4 * i], words[4 * i + 1], words[4 * i + 2], words[4 * i + 3]);
 }
 
 }  // namespace
@@ -407,15 +434,15 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
         switch (C4) {
         case 2:
             k_filter<2><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                               d.samples, fl, out4);
+                                               d.samples, fl, out4, d.weight_format, env->frec4, d.K);
             break;
         case 3:
             k_filter<3><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                               d.samples, fl, out4);
+                                               d.samples, fl, out4, d.weight_format, env->frec4, d.K);
             break;
         case 5:
             k_filter<5><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                               d.samples, fl, out4);
+                                               d.samples, fl, out4, d.weight_format, env->frec4, d.K);
             break;
         default:
             return cudaErrorInvalidValue;

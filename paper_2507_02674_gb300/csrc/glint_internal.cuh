@@ -37,6 +37,7 @@ struct glint_ctx {
 
 struct glint_env {
     glint_ctx *ctx = nullptr;
+    int device = 0;            // ctx->device, kept for destruction after the context
     glint_env_desc d{};
     int C = 0;      // 3 + K channels
     int Cpad = 0;   // channels padded to a multiple of 4
@@ -50,7 +51,9 @@ struct glint_env {
     size_t *pyr_off_dev = nullptr;  // offsets in floats, on the device
     float4 *table = nullptr;   // R x S filter samples (built once at creation)
     int *nvalid = nullptr;     // R valid sample counts
-    float *filt = nullptr;     // filtered levels, concatenated, Cpad floats per texel
+    float *filt = nullptr;     // filtered levels, concatenated: Cpad floats per texel (F32 weights) or
+                               // records of frec4 x 16 bytes (compressed weights)
+    int frec4 = 0;             // 16-byte units per texel record of a compressed weight format
     int fw[33] = {};           // width of filtered level r (height fw/2)
     long long foff[33] = {};   // first texel of level r in filt; foff[R] = total
     int2 *flev = nullptr;      // device copy of (width, first texel) per level

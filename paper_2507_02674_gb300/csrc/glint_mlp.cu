@@ -673,6 +673,7 @@ __global__ void k_mlp_init(float *__restrict__ params, uint32_t seed, int K) {
 
 struct glint_mlp {
     glint_ctx *ctx = nullptr;
+    int device = 0;      // ctx->device
     int K = 8;
     long max_batch = 0;
     int max_grid = 0;    // resident training blocks (rows of `partial`)
@@ -750,7 +751,7 @@ void glint_mlp_weights(const glint_mlp *g, const void **wt, const float **params
 }
 
 int glint_mlp_k(const glint_mlp *g) { return g ? g->K : 0; }
-int glint_mlp_device(const glint_mlp *g) { return g ? g->ctx->device : -1; }
+int glint_mlp_device(const glint_mlp *g) { return g ? g->device : -1; }
 
 extern "C" {
 
@@ -773,6 +774,7 @@ glint_status glint_mlp_create(glint_ctx *ctx, int K, long max_batch, uint32_t se
     if (cudaSetDevice(ctx->device) != cudaSuccess) { set_error("glint_mlp_create: cannot select device"); return GLINT_ERR_CUDA; }
     glint_mlp *g = new glint_mlp();
     g->ctx = ctx;
+    g->device = ctx->device;
     g->K = K;
     g->max_batch = max_batch;
     glint_status st = GLINT_OK;
@@ -826,7 +828,11 @@ glint_status glint_mlp_create(glint_ctx *ctx, int K, long max_batch, uint32_t se
 
 void glint_mlp_destroy(glint_mlp *g) {
     if (!g) return;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != g->device && cudaSetDevice(g->device) != cudaSuccess) cudaGetLastError();
     mlp_free(g);
+    if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
     delete g;
 }
 

@@ -14,6 +14,8 @@ struct ShadeArgs {
     int lut_n;
     const float4 *filt;
     const int2 *flev;  // (width, first texel) of each filtered level
+    int wfmt;          // glint_weight_format of the filtered maps' weights
+    int frec4;         // 16-byte units per texel record of a compressed format
     int R;
     float s_min, s_max;
     const float *levels;
@@ -138,6 +140,87 @@ __device__ __forceinline__ float4 lut_fetch(const float4 *lut, int n, float mu, 
 }
 
 
+// Channels (R, G, B, W_1 .. W_K) of the filtered maps at direction (th, ph),
+// bilinear in the levels r0 and r1 blended by ft, into ch[0 .. 3+K) (RGB only
+// unless NEED_W).  FP32 maps hold C4 float4 per texel; compressed ones a
+// record of frec4 x 16 bytes: (R, G, B, -) as float4, then the K weights as
+// FP16, UNORM16 or UNORM8 codes.
+__device__ __forceinline__ float decode_w(uint32_t word, int j, int wfmt) {
+    if (wfmt == GLINT_WFMT_UNORM8) return (float)((word >> (8 * j)) & 0xffu) * (1.f / 255.f);
+    const uint32_t h = (word >> (16 * j)) & 0xffffu;
+    if (wfmt == GLINT_WFMT_F16) return __half2float(__ushort_as_half((unsigned short)h));
+    return (float)h * (1.f / 65535.f);
+}
+
+template <int K, int C4, bool NEED_W>
+__device__ __forceinline__ void filtered_channels(const ShadeArgs &a, float th, float ph, int r0, int r1, float ft,
+                                                  float *ch) {
+    if (a.wfmt == GLINT_WFMT_F32) {
+        float4 cc[C4];
+#pragma unroll
+        for (int c = 0; c < C4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int lv = 0; lv < 2; ++lv) {
+            const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
+            const int Wr = lev.x, Hr = lev.x / 2;
+            const Taps tp = equirect_taps(ph * (kInvTwoPi * (float)Wr) - 0.5f, th * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
+            const float4 *base = a.filt + (size_t)lev.y * C4;
+            const float wl = lv ? ft : 1.f - ft;
+            constexpr int CN = NEED_W ? C4 : 1;
+#pragma unroll
+            for (int c = 0; c < CN; ++c) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * C4 + c), v);
+                v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * C4 + c), v);
+                v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * C4 + c), v);
+                v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * C4 + c), v);
+                cc[c] = fma4(wl, v, cc[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C4; ++c) {
+            ch[4 * c] = cc[c].x; ch[4 * c + 1] = cc[c].y; ch[4 * c + 2] = cc[c].z; ch[4 * c + 3] = cc[c].w;
+        }
+        return;
+    }
+    // compressed weights
+    const int rec = a.frec4, wfmt = a.wfmt;
+    const int per_word = (wfmt == GLINT_WFMT_UNORM8) ? 4 : 2;
+    float4 rgb = make_float4(0.f, 0.f, 0.f, 0.f);
+    float w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = 0.f;
+#pragma unroll
+    for (int lv = 0; lv < 2; ++lv) {
+        const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
+        const int Wr = lev.x, Hr = lev.x / 2;
+        const Taps tp = equirect_taps(ph * (kInvTwoPi * (float)Wr) - 0.5f, th * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
+        const float4 *base = a.filt + (size_t)lev.y * rec;
+        const float wl = lv ? ft : 1.f - ft;
+        const int idx[4] = {tp.i00, tp.i01, tp.i10, tp.i11};
+        const float tw[4] = {tp.w00, tp.w01, tp.w10, tp.w11};
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v = fma4(tw[t], __ldg(base + (size_t)idx[t] * rec), v);
+        rgb = fma4(wl, v, rgb);
+        if (NEED_W) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t *codes = reinterpret_cast<const uint32_t *>(base + (size_t)idx[t] * rec + 1);
+                const float f = wl * tw[t];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const uint32_t word = __ldg(codes + k / per_word);  // same word: loaded once after CSE
+                    w[k] = fmaf(f, decode_w(word, k % per_word, wfmt), w[k]);
+                }
+            }
+        }
+    }
+    ch[0] = rgb.x; ch[1] = rgb.y; ch[2] = rgb.z;
+#pragma unroll
+    for (int k = 0; k < K; ++k) ch[3 + k] = w[k];
+}
+
 // Step 1: smooth radiance (L_o) and the reflection probabilities p_k.
 template <int K, int EV>
 __device__ __forceinline__ void smooth_and_probs(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
@@ -159,33 +242,9 @@ __device__ __forceinline__ void smooth_and_probs(const ShadeArgs &a, long q, flo
     const float th_r = acosf(fminf(fmaxf(ry, -1.f), 1.f));
     float ph_r = atan2f(rz, rx);
     if (ph_r < 0.f) ph_r += kTwoPi;
-    float4 cc[C4];
-#pragma unroll
-    for (int c = 0; c < C4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int lv = 0; lv < 2; ++lv) {
-        const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
-        const int Wr = lev.x, Hr = lev.x / 2;
-        const Taps tp = equirect_taps(ph_r * (kInvTwoPi * (float)Wr) - 0.5f, th_r * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
-        const float4 *base = a.filt + (size_t)lev.y * C4;
-        const float wl = lv ? ft : 1.f - ft;
-        // E2 and given p_k need the colour channels (first float4) only
-        constexpr int CN = (EV == EV_E1) ? C4 : 1;
-#pragma unroll
-        for (int c = 0; c < CN; ++c) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * C4 + c), v);
-            v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * C4 + c), v);
-            v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * C4 + c), v);
-            v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * C4 + c), v);
-            cc[c] = fma4(wl, v, cc[c]);
-        }
-    }
     float ch[C4 * 4];
-#pragma unroll
-    for (int c = 0; c < C4; ++c) {
-        ch[4 * c] = cc[c].x; ch[4 * c + 1] = cc[c].y; ch[4 * c + 2] = cc[c].z; ch[4 * c + 3] = cc[c].w;
-    }
+    // E2 and given p_k need the colour channels only
+    filtered_channels<K, C4, EV == EV_E1>(a, th_r, ph_r, r0, r1, ft, ch);
     const float Eb = g1.w * tab.z + tab.w;
     Lor = ch[0] * Eb;
     Log = ch[1] * Eb;
@@ -214,6 +273,8 @@ inline ShadeArgs make_args(const glint_ctx *ctx, const glint_env *env, const gli
     a.lut = ctx->lut;
     a.lut_n = ctx->lut_n;
     a.filt = reinterpret_cast<const float4 *>(env->filt);
+    a.wfmt = env->d.weight_format;
+    a.frec4 = env->frec4;
     a.R = env->d.levels;
     a.flev = env->flev;
     a.s_min = env->d.s_min;
@@ -262,31 +323,8 @@ __device__ __forceinline__ void filtered_weights(const ShadeArgs &a, float dx, f
     const float th = acosf(fminf(fmaxf(dy, -1.f), 1.f));
     float ph = atan2f(dz, dx);
     if (ph < 0.f) ph += kTwoPi;
-    float4 cc[C4];
-#pragma unroll
-    for (int c = 0; c < C4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int lv = 0; lv < 2; ++lv) {
-        const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
-        const int Wr = lev.x, Hr = lev.x / 2;
-        const Taps tp = equirect_taps(ph * (kInvTwoPi * (float)Wr) - 0.5f, th * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
-        const float4 *base = a.filt + (size_t)lev.y * C4;
-        const float wl = lv ? ft : 1.f - ft;
-#pragma unroll
-        for (int c = 0; c < C4; ++c) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * C4 + c), v);
-            v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * C4 + c), v);
-            v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * C4 + c), v);
-            v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * C4 + c), v);
-            cc[c] = fma4(wl, v, cc[c]);
-        }
-    }
     float ch[C4 * 4];
-#pragma unroll
-    for (int c = 0; c < C4; ++c) {
-        ch[4 * c] = cc[c].x; ch[4 * c + 1] = cc[c].y; ch[4 * c + 2] = cc[c].z; ch[4 * c + 3] = cc[c].w;
-    }
+    filtered_channels<K, C4, true>(a, th, ph, r0, r1, ft, ch);
 #pragma unroll
     for (int k = 0; k < K; ++k) W[k] = ch[3 + k];
 }

@@ -155,6 +155,7 @@ struct Slot {  // staging of one tick's frame table and work list
 
 struct glint_server {
     glint_ctx *ctx = nullptr;
+    int device = 0;  // ctx->device, kept for destruction after the context
     int K = 8;
     glint_server_desc d{};
     int max_items = 0;   // planned items per tick at most
@@ -316,6 +317,7 @@ glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc 
     if (cudaSetDevice(ctx->device) != cudaSuccess) { set_error("glint_server_create: cannot select device"); return GLINT_ERR_CUDA; }
     glint_server *s = new glint_server();
     s->ctx = ctx;
+    s->device = ctx->device;
     s->K = K;
     s->d = d;
     s->t0 = std::chrono::steady_clock::now();
@@ -352,8 +354,8 @@ glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc 
 void glint_server_destroy(glint_server *s) {
     if (!s) return;
     int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(s->ctx->device);
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != s->device && cudaSetDevice(s->device) != cudaSuccess) cudaGetLastError();
     cudaDeviceSynchronize();
     for (auto &f : s->active) free_frame_events(f);
     for (auto &sl : s->slots) {

@@ -21,7 +21,8 @@ FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
 EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN = 0, 1, 2, 3
 MLP_PARAMS, MLP_GRAD, MLP_ADAM_M, MLP_ADAM_V = 0, 1, 2, 3
-ABI_VERSION = 4
+ABI_VERSION = 5
+WFMT_F32, WFMT_F16, WFMT_UNORM16, WFMT_UNORM8 = 0, 1, 2, 3
 DRAW_DUAL, DRAW_SINGLE, DRAW_SINGLE_OLD, DRAW_WANG2020 = 0, 1, 2, 3
 WEIGHTS_LINEAR, WEIGHTS_LOG = 0, 1
 ENV_LOHI, ENV_LEVELS, ENV_PYRAMID, ENV_FILTERED, ENV_TABLE, ENV_FILTERED_WIDTHS = 0, 1, 2, 3, 4, 5
@@ -38,7 +39,8 @@ class EnvDesc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("format", ctypes.c_int),
                 ("scale_log2", ctypes.c_int), ("K", ctypes.c_int), ("ell", ctypes.c_float),
                 ("levels", ctypes.c_int), ("samples", ctypes.c_int), ("out_width", ctypes.c_int),
-                ("s_min", ctypes.c_float), ("s_max", ctypes.c_float), ("weight_space", ctypes.c_int)]
+                ("s_min", ctypes.c_float), ("s_max", ctypes.c_float), ("weight_space", ctypes.c_int),
+                ("weight_format", ctypes.c_int)]
 
 
 class GBufferDesc(ctypes.Structure):
@@ -216,6 +218,7 @@ class EnvConfig:
     s_min: float = 0.02 ** 0.5
     s_max: float = 0.5 ** 0.5
     weight_space: int = 0  # WEIGHTS_LINEAR (the paper's) or WEIGHTS_LOG
+    weight_format: int = 0  # WFMT_F32, WFMT_F16, WFMT_UNORM16 or WFMT_UNORM8 (filtered weights' storage)
 
 
 class Env:
@@ -225,7 +228,7 @@ class Env:
         self.ctx = ctx
         self.cfg = cfg
         self.desc = EnvDesc(width, height, fmt, scale_log2, cfg.K, cfg.ell, cfg.levels, cfg.samples, cfg.out_width,
-                            cfg.s_min, cfg.s_max, cfg.weight_space)
+                            cfg.s_min, cfg.s_max, cfg.weight_space, cfg.weight_format)
         h = ctypes.c_void_p()
         _check(lib.glint_env_create(ctx.handle, ctypes.byref(self.desc), ctypes.byref(h)))
         self.handle = h

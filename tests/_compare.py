@@ -50,14 +50,17 @@ def _rel(a, b, floor):
 
 
 def compare_shade(orc, o, gpu: dict, rgb_gpu: np.ndarray, integer_mode: bool = True, max_fail: int = 20,
-                  nonunique=None, p_atol: float = 0.0, p_rtol: float = P_RTOL) -> ShadeReport:
+                  nonunique=None, p_atol: float = 0.0, p_rtol: float = P_RTOL,
+                  rad_rtol: float = RAD_RTOL) -> ShadeReport:
     """o: oracle.ShadeOracle for n pixels; gpu: numpy copies of the debug outputs
     for the same pixels (keys p, np, vert, w, nroot, counts, lo); rgb_gpu (n, 3).
     nonunique: optional mask of pixels whose p_k an FP32 evaluation may not
     reproduce (e.g. an E2 quadrature point on the validity boundary); for those
     only the invariants (N_P, grid, root trials, count conservation) are
     checked.  p_atol: absolute error allowed on p_k on top of P_RTOL (the tie
-    model's absolute mass error)."""
+    model's absolute mass error).  rad_rtol: relative radiance tolerance (wider
+    when the two sides' p_k may legitimately differ, e.g. by one stored code of
+    a compressed weight)."""
     rep = ShadeReport(npix=len(o.np_))
     nu = np.zeros(len(o.np_), bool) if nonunique is None else np.asarray(nonunique, bool)
     rep.nonunique = int(nu.sum())
@@ -158,7 +161,7 @@ def compare_shade(orc, o, gpu: dict, rgb_gpu: np.ndarray, integer_mode: bool = T
             continue
         ref = orc.radiance(o, q, chosen) if nondefault else o.rgb[q]
         err = np.abs(rgb_gpu[q] - ref)
-        bound = RAD_RTOL * np.abs(ref) + RAD_ATOL_FRAC * scale_lo
+        bound = rad_rtol * np.abs(ref) + RAD_ATOL_FRAC * scale_lo
         rel = float(np.max(err / np.maximum(np.abs(ref), RAD_ATOL_FRAC * scale_lo)))
         rep.max_rad_rel = max(rep.max_rad_rel, rel)
         if np.any(err > bound):

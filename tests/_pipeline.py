@@ -23,6 +23,7 @@ class MethodParams:
     seed: int = 0
     integer_mode: bool = True
     log_weights: bool = False      # fuzzy weights interpolated in log space (Sec. 7)
+    wfmt: int = 0                  # storage of the filtered weights (0 float32, 1 float16, 2 unorm16, 3 unorm8)
 
     def with_(self, **kw) -> "MethodParams":
         return replace(self, **kw)
@@ -40,7 +41,7 @@ def oracle_lut(orc, mp: MethodParams) -> np.ndarray:
 
 def oracle_env(orc, env, mp: MethodParams):
     e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell, mp.log_weights)
-    pref = orc.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo)
+    pref = orc.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo, wfmt=mp.wfmt)
     return e, pref
 
 

@@ -31,7 +31,7 @@ def gl():
 
 def _cfg(glint, mp: MethodParams):
     return glint.EnvConfig(K=mp.K, ell=mp.ell, levels=mp.R, samples=mp.S, out_width=mp.Wo, s_min=mp.s_min,
-                           s_max=mp.s_max, weight_space=int(mp.log_weights))
+                           s_max=mp.s_max, weight_space=int(mp.log_weights), weight_format=mp.wfmt)
 
 
 def _run(gl, env, gb, mp: MethodParams, debug=True, rows=None, evaluator=0, e2_S=16):
@@ -153,9 +153,11 @@ def test_filtered_maps(gl, orc, K, which, Wo):
     assert np.percentile(w_rel, 99.9) < 5e-5
 
 
-def _check(orc, o, res, integer_mode=True, nonunique=None, tie=None):
+def _check(orc, o, res, integer_mode=True, nonunique=None, tie=None, rad_rtol=None):
     gpu = {k: res[k] for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")}
     kw = {} if tie is None else {"p_rtol": tie[0], "p_atol": tie[4]}
+    if rad_rtol is not None:
+        kw["rad_rtol"] = rad_rtol
     rep = compare_shade(orc, o, gpu, res["rgb"], integer_mode, nonunique=nonunique, **kw)
     print(rep.summary())
     assert rep.ok(), rep.failures
@@ -307,3 +309,58 @@ def test_invalid_arguments(gl):
     out = torch.zeros(9, 4, device="cuda")
     with pytest.raises(glint.GlintError):  # misaligned output
         glint.shade(ctx, env, planes, 8, 1, out.view(-1)[1:33].view(8, 4))
+
+
+@pytest.mark.parametrize("wfmt", [1, 2, 3])
+def test_filtered_maps_compressed_weights(gl, orc, wfmt):
+    """Filtered weights stored as float16 / unorm16 / unorm8 (Sec. 7 "Texture
+    Precision"): every stored weight equals the oracle's quantisation of its
+    own filtered weight, or its neighbour where the two filtered values
+    (within 5e-6 of each other) straddle a rounding boundary; RGB as for float32."""
+    glint, render, ctx, torch = gl
+    env = synth.env_hdr(seed=4, W=512, H=256)
+    mp = MethodParams(K=8, Wo=128, wfmt=wfmt)
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    torch.cuda.synchronize()
+    widths, g = fr.env.export(glint.ENV_FILTERED)
+    g = g.astype(np.float64)
+    e = orc.env_full(env.rgba32(), env.scale, mp.K, mp.ell)
+    raw = orc.prefilter(e, mp.R, mp.S, mp.s_min, mp.s_max, mp.Wo).flat  # unquantised weights
+    q = orc.quantize_weights(raw, wfmt)
+    assert g.shape == q.shape
+    rgb_rel = np.abs(g[:, :3] - q[:, :3]) / np.abs(q[:, :3])
+    assert rgb_rel.max() < 5e-5
+    w_or, w_gpu = raw[:, 3:], g[:, 3:]
+    if wfmt == 1:  # float16 values are exact in float32: compare values
+        code_gpu, code = w_gpu, q[:, 3:]
+        lo = orc.quantize_weights(np.c_[np.zeros((len(raw), 3)), w_or - 5e-6], 1)[:, 3:]
+        hi = orc.quantize_weights(np.c_[np.zeros((len(raw), 3)), w_or + 5e-6], 1)[:, 3:]
+    else:  # unorm: compare codes (the export divides in float32)
+        m = 65535.0 if wfmt == 2 else 255.0
+        code_gpu, code = np.rint(w_gpu * m), np.rint(q[:, 3:] * m)
+        lo = np.rint(np.clip(w_or - 5e-6, 0, 1) * m)
+        hi = np.rint(np.clip(w_or + 5e-6, 0, 1) * m)
+    ok = (code_gpu >= lo) & (code_gpu <= hi)
+    exact = float(np.mean(code_gpu == code))
+    print(f"format {wfmt}: stored weights equal to the oracle's quantisation at {exact:.5%}")
+    assert ok.all(), np.argwhere(~ok)[:5]
+    assert exact > 0.99
+
+
+@pytest.mark.parametrize("wfmt", [1, 2])
+def test_shade_compressed_weights(gl, orc, wfmt):
+    """Shading from 16-bit stored weights against the oracle shading from its
+    own quantised maps: p_k within one stored code (float16: 2^-10 relative;
+    unorm16: 2^-15 absolute), counts in the valid set, radiance within 1e-4."""
+    glint, render, ctx, torch = gl
+    mp = MethodParams(K=8, Wo=128, seed=13, wfmt=wfmt)
+    env = synth.env_hdr(seed=6, W=256, H=128)
+    gb = synth.gbuffer_random(2500, seed=15, width=2500)
+    res = _run(gl, env, gb, mp)
+    tie = (2.0 ** -10, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 0.0) if wfmt == 1 else \
+        (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -15)
+    o = oracle_shade(orc, gb.rows16(), env, mp, tie=tie)
+    # a stored code one step off (values straddling a rounding boundary) moves
+    # sum_k L_k p_k, and so the radiance, by up to the p_k tolerance
+    _check(orc, o, res, tie=tie, rad_rtol=tie[0] if wfmt == 1 else None)

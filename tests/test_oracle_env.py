@@ -209,3 +209,40 @@ def test_log_space_weights(orc):
     # is at least the linear one: log weights lean to the upper level
     j = np.argmax(w_lin[mid] > 0, axis=-1)
     assert np.all(w_log[mid][np.arange(j.size), j] <= w_lin[mid][np.arange(j.size), j] + 1e-12)
+
+
+def test_weight_storage_formats_and_precision_study(orc):
+    """Sec. 7 "Texture Precision": the filtered weights stored as float16,
+    unorm16 or unorm8.  The quantisers follow their definitions (hand values),
+    and the paper's finding holds: 16-bit storage changes p_k by ~1e-5 (RMSE)
+    while 8-bit loses small weights outright and changes the glint image far
+    more."""
+    from tests._pipeline import MethodParams, oracle_shade
+    flat = np.array([[1.0, 2.0, 3.0, 0.5, 1.0 / 3.0, 0.0, 1.0, 1e-3, -1e-9]])
+    u16 = orc.quantize_weights(flat, orc.WFMT_UNORM16)[0]
+    assert u16[3] == 32768 / 65535 and u16[4] == 21845 / 65535 and u16[5] == 0 and u16[6] == 1
+    assert u16[7] == 66 / 65535 and u16[8] == 0 and list(u16[:3]) == [1.0, 2.0, 3.0]
+    u8 = orc.quantize_weights(flat, orc.WFMT_UNORM8)[0]
+    assert u8[3] == 128 / 255 and u8[4] == 85 / 255 and u8[7] == 0.0
+    f16 = orc.quantize_weights(flat, orc.WFMT_F16)[0]
+    assert f16[4] == 0.333251953125 and f16[3] == 0.5 and f16[7] == 0.0010004043579101562
+
+    env = synth.env_hdr(seed=3, W=256, H=128)
+    rows = synth.gbuffer_random(1500, seed=5).rows16()
+    res = {}
+    for wf in (0, 1, 2, 3):
+        res[wf] = oracle_shade(orc, rows, env, MethodParams(K=8, Wo=128, wfmt=wf), tie=[0, 0, 0, 0, 0], max_cand=1)
+    fg = res[0].np_ > 0
+    p0 = res[0].pk[fg]
+
+    def p_rmse(wf):
+        return float(np.sqrt(np.mean((res[wf].pk[fg] - p0) ** 2)))
+
+    def img(wf):
+        d = np.abs(res[wf].rgb[fg] - res[0].rgb[fg]).sum(1) / np.maximum(res[0].rgb[fg].sum(1), 1e-12)
+        return float(np.median(d))
+
+    assert p_rmse(1) < 1e-4 and p_rmse(2) < 1e-4 and p_rmse(3) > 2e-4
+    assert img(3) > 10 * max(img(1), img(2))
+    small = (p0 > 1e-3) & (p0 < 1.5e-3)
+    assert small.any() and np.all(res[3].pk[fg][small] != p0[small])

@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GLINT_ABI_VERSION 5
+#define GLINT_ABI_VERSION 6
 #define GLINT_MAX_K 16
 
 typedef enum glint_status {
@@ -211,7 +211,15 @@ typedef struct glint_params {
                              p_k to shade with (read only).  Caller-owned */
     int draw;             /* glint_draw: binomial approximation at the tree nodes (0 = the paper's) */
     float gamma;          /* GLINT_DRAW_WANG2020: reflection probability of a microfacet, (0, 1] */
+    int grid;             /* glint_grid: the grid N_P is spread over (0 = two levels x uv triangle) */
 } glint_params;
+
+typedef enum glint_grid {
+    GLINT_GRID_ISOTROPIC = 0,  /* 2 footprint levels x 3 uv-triangle vertices = 6 samples (Sec. 3.3) */
+    GLINT_GRID_ANISOTROPIC = 1 /* the footprint's tetrahedral cell in (level, anisotropy, orientation)
+                                  x 3 vertices of a uv lattice stretched along the footprint:
+                                  12 samples; debug arrays hold 12 samples per pixel (E1, dual) */
+} glint_grid;
 
 typedef enum glint_draw {
     GLINT_DRAW_DUAL = 0,       /* dual-gated Gaussians (Alg. 1), the paper's method */
@@ -225,7 +233,9 @@ typedef enum glint_draw {
 /* Optional per-pixel intermediate results (device; each pointer may be NULL).
  *   p:      npix x K   reflection probabilities p_k (Eq. probhk)
  *   np:     npix       microfacet count N_P of the footprint
- *   vert:   npix x 6 x 3 int32: low 32 bits of grid vertex x, y, and level
+ *   vert:   npix x 6 x 3 int32: low 32 bits of grid vertex x, y, and level (anisotropic grid:
+ *           npix x 12 x 3, the third entry the packed (level, anisotropy, orientation) key;
+ *           w, nroot and counts likewise hold 12 samples per pixel)
  *   w:      npix x 6   grid sample weights w_i (Eq. anisogrid)
  *   nroot:  npix x 6   trials at each sample's tree root (float)
  *   counts: npix x 6 x K per-sample bin counts n_k(i) (float; integers in

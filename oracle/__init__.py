@@ -91,13 +91,13 @@ def _load():
         lib.or_prefilter.argtypes = [P, I, I, I, P, P, I, I, P, P, L, P]
         lib.or_prefilter_exact.argtypes = [P, I, I, I, D, P, L, P]
         lib.or_shade.argtypes = [P, L, P, I, P, I, D, D, P, I, P, I, U, I, P, I,
-                                 P, P, P, P, P, P, P, P, P, P, P, I, P, I, P, I, I, P, P, I, D]
+                                 P, P, P, P, P, P, P, P, P, P, P, I, P, I, P, I, I, P, P, I, D, I, P]
         lib.or_e2_pk.argtypes = [P, P, P, ctypes.c_float, ctypes.c_float, I, P, I, I, I, I, P]
         lib.or_e2_pk.restype = I
         lib.or_mlp_features.argtypes = [P, P, L, P, I, P, I, D, D, P, I, I, P, P, P]
         lib.or_mlp_features.restype = None
         lib.or_shade.restype = L
-        lib.or_radiance.argtypes = [P, P, D, P, I, P, P, P, I, D]
+        lib.or_radiance.argtypes = [P, P, D, P, I, P, P, P, I, D, I]
         lib.or_multinomial.argtypes = [P, I, D, U, U, U, U, I, P, I]
         _lib = lib
     return _lib
@@ -334,6 +334,8 @@ class ShadeOracle:
     e2_flags: np.ndarray  # (n,) E2 points on the validity boundary (0 for E1)
     draw: int = 0         # binomial approximation (0 dual-gated, 1 Eq. gated, 2 Eq. oldgated, 3 Wang 2020)
     gamma: float = 0.0    # Wang 2020 reflection probability
+    grid: int = 0         # 0 isotropic (6 samples per pixel), 1 anisotropic (12)
+    grid_flags: np.ndarray = None  # (n,) anisotropic cell decisions too close to call
 
 
 def gbuffer_rows(planes) -> np.ndarray:
@@ -344,7 +346,7 @@ def gbuffer_rows(planes) -> np.ndarray:
 def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab: np.ndarray, levels: np.ndarray,
           seed: int, integer_mode: bool = True, tie=TIE_DEFAULT, max_cand: int = 8, evaluator: int = 0,
           tangents=None, e2_S: int = 16, env: "EnvOracle | None" = None, pk_in=None, draw: int = 0,
-          gamma: float = 0.0) -> ShadeOracle:
+          gamma: float = 0.0, grid: int = 0) -> ShadeOracle:
     """Per-pixel shading (or_shade).  evaluator 0 = E1, 1 = E2 (needs tangents
     and env), 2 = the p_k given in pk_in (npix x K)."""
     lib = _load()
@@ -359,11 +361,13 @@ def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab:
     nlut = lut_tab.shape[0]
     levels = np.ascontiguousarray(levels, dtype=np.float64)
     tie_a = np.asarray(tie, dtype=np.float64)
+    nv = 12 if grid else NV
     o = ShadeOracle(rgb=np.zeros((n, 3)), lo=np.zeros((n, 3)), pk=np.zeros((n, K)), np_=np.zeros(n, np.float32),
-                    vert=np.zeros((n, NV, 3), np.int64), wv=np.zeros((n, NV)), nroot=np.zeros((n, NV)),
-                    ncand=np.zeros((n, NV), np.int32), cand=np.zeros((n, NV, max_cand, K)),
-                    cand_err=np.zeros((n, NV, max_cand, K)), flags=np.zeros(n, np.int32), levels=levels,
-                    e2_flags=np.zeros(n, np.int32), draw=int(draw), gamma=float(gamma))
+                    vert=np.zeros((n, nv, 3), np.int64), wv=np.zeros((n, nv)), nroot=np.zeros((n, nv)),
+                    ncand=np.zeros((n, nv), np.int32), cand=np.zeros((n, nv, max_cand, K)),
+                    cand_err=np.zeros((n, nv, max_cand, K)), flags=np.zeros(n, np.int32), levels=levels,
+                    e2_flags=np.zeros(n, np.int32), draw=int(draw), gamma=float(gamma), grid=int(grid),
+                    grid_flags=np.zeros(n, np.int32))
     if evaluator == 1:
         tangents = np.ascontiguousarray(tangents, dtype=np.float32).reshape(-1, 4)
         mips = env.mips_flat
@@ -379,7 +383,8 @@ def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab:
                  _ptr(o.rgb), _ptr(o.lo), _ptr(o.pk), _ptr(o.np_), _ptr(o.vert), _ptr(o.wv), _ptr(o.nroot),
                  _ptr(o.ncand), _ptr(o.cand), _ptr(o.cand_err), _ptr(o.flags), int(evaluator),
                  None if tangents is None else _ptr(tangents), int(e2_S), None if mips is None else _ptr(mips), W, H,
-                 _ptr(o.e2_flags), None if pk_in is None else _ptr(pk_in), int(draw), float(gamma))
+                 _ptr(o.e2_flags), None if pk_in is None else _ptr(pk_in), int(draw), float(gamma), int(grid),
+                 _ptr(o.grid_flags))
     return o
 
 
@@ -422,9 +427,10 @@ def radiance(o: ShadeOracle, q: int, counts: np.ndarray) -> np.ndarray:
     lo3 = np.ascontiguousarray(o.lo[q])
     pk = np.ascontiguousarray(o.pk[q])
     wv = np.ascontiguousarray(o.wv[q])
-    c = np.ascontiguousarray(counts, dtype=np.float64).reshape(NV, K)
+    nv = o.wv.shape[1]
+    c = np.ascontiguousarray(counts, dtype=np.float64).reshape(nv, K)
     lib.or_radiance(_ptr(lo3), _ptr(pk), float(o.np_[q]), _ptr(o.levels), K, _ptr(wv), _ptr(c), _ptr(out),
-                    int(o.draw), float(o.gamma))
+                    int(o.draw), float(o.gamma), nv)
     return out
 
 

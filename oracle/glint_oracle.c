@@ -835,10 +835,9 @@ static void grid_level(float area, int *l0, double *frac)
  * 0x3EBB67AF), the skewed cell (i, j) is split along its diagonal, and the
  * barycentric weights of the three corners are taken in skewed coordinates.
  * The skew and the vertex choice use FP32 operations in this order. */
-static void grid_vertices(float u, float v, int l, int64_t vx[3], int64_t vy[3], double b[3])
+static void lattice_vertices(float x, float y, int64_t vx[3], int64_t vy[3], double b[3])
 {
     const float F2 = 0x1.76cf5ep-2f; /* (sqrt(3)-1)/2 rounded to FP32 */
-    float x = ldexpf(u, -l), y = ldexpf(v, -l);
     float t = x + y;
     float s = t * F2;
     float xs = x + s, ys = y + s;
@@ -854,6 +853,85 @@ static void grid_vertices(float u, float v, int l, int64_t vx[3], int64_t vy[3],
         vx[1] = i; vy[1] = j + 1;
         b[0] = 1.0 - (double)fy; b[1] = (double)fy - (double)fx; b[2] = (double)fx;
     }
+}
+
+static void grid_vertices(float u, float v, int l, int64_t vx[3], int64_t vy[3], double b[3])
+{
+    lattice_vertices(ldexpf(u, -l), ldexpf(v, -l), vx, vy, b);
+}
+
+/* Anisotropic grid (SURVEY NEXT-1 reading of Sec. 3.3's "anisotropic grids":
+ * the footprint's length, anisotropy factor and orientation).  The footprint
+ * ellipse of the uv Jacobian J = [du/dx du/dy; dv/dx dv/dy] has eigenvalues
+ * lam1 >= lam2 of J J^T = [a b; b c].  Coordinates: the level L = l0 + fl
+ * (log2 sqrt|P|, as grid_level), the anisotropy A = (log2 lam1 - log2 |P|)/2
+ * = log2(sqrt(lam1/lam2))/2 clamped to [0, 2], and the orientation
+ * O = (4/pi) atan2(b, (a - c)/2) in [0, 8) (the major axis at O pi/8),
+ * periodic.  N_P is spread over the Freudenthal tetrahedron of the cell:
+ * fractions sorted in decreasing order (ties: L, A, O) give the unit steps
+ * and the weights 1 - f1, f1 - f2, f2 - f3, f3; vertices with a = 0 take
+ * o = 0.  Returns 1 when a decision (a floor or the order of two fractions)
+ * lies within reach of an FP32 evaluation of the same quantities. */
+static int footprint_cell(const float *g, float area, int l0, double fl, int tl[4], int ta[4], int to[4],
+                          double tw[4])
+{
+    double dudx = g[12], dvdx = g[13], dudy = g[14], dvdy = g[15];
+    double ea = dudx * dudx + dudy * dudy, ec = dvdx * dvdx + dvdy * dvdy, eb = dudx * dvdx + dudy * dvdy;
+    double hd = 0.5 * (ea - ec);
+    double rr = sqrt(hd * hd + eb * eb);
+    double lam1 = 0.5 * (ea + ec) + rr;
+    double Araw = 0.5 * (log2(lam1) - log2((double)area));
+    double A = fmin(fmax(Araw, 0.0), 2.0);
+    double O = atan2(eb, hd) * (4.0 / OR_PI);
+    if (O < 0.0) O += 8.0;
+    if (O >= 8.0) O -= 8.0;
+    int a0 = (A >= 2.0) ? 2 : (int)floor(A);
+    double fa = A - a0;
+    int o0 = (int)floor(O);
+    if (o0 > 7) o0 = 7;
+    double fo = O - o0;
+    double f[3] = {fl, fa, fo};
+    int ord[3] = {0, 1, 2};
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2 - i; ++j)
+            if (f[ord[j + 1]] > f[ord[j]]) { int t = ord[j]; ord[j] = ord[j + 1]; ord[j + 1] = t; }
+    int cl = l0, ca = a0, co = o0;
+    for (int v = 0; v < 4; ++v) {
+        if (v > 0) {
+            int ax = ord[v - 1];
+            if (ax == 0) ++cl; else if (ax == 1) ++ca; else co = (co + 1) & 7;
+        }
+        tl[v] = cl;
+        ta[v] = ca;
+        to[v] = (ca == 0) ? 0 : co;
+        double hi = (v == 0) ? 1.0 : f[ord[v - 1]];
+        double lo = (v == 3) ? 0.0 : f[ord[v]];
+        tw[v] = hi - lo;
+    }
+    /* reach of the FP32 evaluation: log2 and sqrt of values ~2^+-60 carry a
+     * few 1e-6 absolute; the orientation's angle is ill-conditioned when the
+     * footprint is nearly round (rr small against a + c) */
+    const double tau = 4e-5;
+    double tauO = tau + (4.0 / OR_PI) * 1e-6 * (ea + ec) / fmax(2.0 * rr, 1e-300);
+    int flag = 0;
+    if (Araw > tau && Araw < 2.0 - tau && fabs(A - floor(A + 0.5)) < tau) flag = 1;  /* floor of A */
+    double dO = fabs(O - floor(O + 0.5));
+    if (dO < tauO || 8.0 - O < tauO) flag = 1;                                          /* floor of O */
+    double tf[3] = {tau, tau, tauO};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (fabs(f[i] - f[j]) < tf[i] + tf[j]) flag = 1;                          /* step order */
+    return flag;
+}
+
+/* FP32 cos and sin of the orientations o pi / 8 of the anisotropic grid,
+ * built from cos(pi/8), sin(pi/8) and sqrt(2)/2 rounded to FP32. */
+static void orient_table(float cs[8], float sn[8])
+{
+    const float c1 = (float)cos(OR_PI / 8.0), s1 = (float)sin(OR_PI / 8.0), h = (float)(sqrt(2.0) / 2.0);
+    const float cc[8] = {1.0f, c1, h, s1, 0.0f, -s1, -h, -c1};
+    const float ss[8] = {0.0f, s1, h, c1, 1.0f, c1, h, s1};
+    for (int k = 0; k < 8; ++k) { cs[k] = cc[k]; sn[k] = ss[k]; }
 }
 
 /* Tie model of the FP32 kernel, used to decide when a decision is too close
@@ -1173,6 +1251,11 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
  * comparison of Sec. 7 (one single-gated count per sample with probability
  * gamma, independent of the map; counts (glints, rest) in bins 1 and 2;
  * L^_o = L_o M_1 / (N_P gamma)).
+ * grid = 1 spreads N_P over the anisotropic grid (footprint_cell: 4 cell
+ * vertices x 3 lattice vertices = 12 samples per pixel; the per-sample arrays
+ * then hold 12 entries per pixel and vert's third entry is the packed
+ * (level, anisotropy, orientation) key); grid_flags (optional) marks pixels
+ * whose cell decisions are too close to call.
  * evaluator = 1 replaces p_k by the E2 quadrature (or_e2_pk) of the
  * anisotropic footprint, with per-pixel tangents (npix x 4) and the pyramid
  * (mips, W x H level 0); e2_flags counts its near-boundary points.
@@ -1188,8 +1271,11 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
               const double *tie, int max_cand, double *rgb, double *lo, double *pk, float *np, int64_t *vert,
               double *wv, double *nroot, int32_t *ncand, double *cand, double *cand_err, int32_t *flags,
               int evaluator, const float *tangents, int e2_S, const double *mips, int W, int H, int32_t *e2_flags,
-              const double *pk_in, int draw, double gamma)
+              const double *pk_in, int draw, double gamma, int grid, int32_t *grid_flags)
 {
+    const int nv = grid ? 12 : OR_NV; /* grid samples per pixel */
+    float ocs[8], osn[8];
+    orient_table(ocs, osn);
     long nbg = 0;
     for (long q = 0; q < npix; ++q) {
         const float *g = gb + 16 * q;
@@ -1197,11 +1283,12 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
         for (int k = 0; k < K; ++k) pk[q * K + k] = 0.0;
         np[q] = 0.0f;
         flags[q] = 0;
-        for (int v = 0; v < OR_NV; ++v) {
-            wv[q * OR_NV + v] = 0.0;
-            nroot[q * OR_NV + v] = 0.0;
-            ncand[q * OR_NV + v] = 0;
-            for (int k = 0; k < 3; ++k) vert[(q * OR_NV + v) * 3 + k] = 0;
+        if (grid_flags) grid_flags[q] = 0;
+        for (int v = 0; v < nv; ++v) {
+            wv[q * nv + v] = 0.0;
+            nroot[q * nv + v] = 0.0;
+            ncand[q * nv + v] = 0;
+            for (int k = 0; k < 3; ++k) vert[(q * nv + v) * 3 + k] = 0;
         }
         if (!(g[3] > 0.0f)) { ++nbg; continue; }
 
@@ -1280,22 +1367,42 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
 
         double Mk[OR_MAXK];
         for (int k = 0; k < K; ++k) Mk[k] = 0.0;
-        for (int lv = 0; lv < 2; ++lv) {
-            int l = l0 + lv;
-            double lw = lv ? fl : 1.0 - fl;
+        int cl4[4], ta[4], to[4];
+        double tw[4];
+        if (grid) {
+            int fl_flag = footprint_cell(g, area, l0, fl, cl4, ta, to, tw);
+            if (grid_flags) grid_flags[q] = fl_flag;
+        }
+        for (int lv = 0; lv < (grid ? 4 : 2); ++lv) {
+            int l;
+            double lw;
             int64_t vx[3], vy[3];
             double b[3];
-            grid_vertices(g[8], g[9], l, vx, vy, b);
+            uint32_t key2;
+            if (grid) { /* the uv lattice stretched by 2^a along the orientation o pi/8 */
+                l = cl4[lv];
+                lw = tw[lv];
+                int an = ta[lv], o = to[lv];
+                float up = ocs[o] * g[8] + osn[o] * g[9];
+                float vp = ocs[o] * g[9] - osn[o] * g[8];
+                lattice_vertices(ldexpf(up, -(l + an)), ldexpf(vp, -(l - an)), vx, vy, b);
+                key2 = (((uint32_t)l) & 0x3FFu) | ((uint32_t)an << 10) | ((uint32_t)o << 12) | 0x8000u;
+            } else {
+                l = l0 + lv;
+                lw = lv ? fl : 1.0 - fl;
+                grid_vertices(g[8], g[9], l, vx, vy, b);
+                key2 = ((uint32_t)l) & 0xFFFFu;
+            }
             for (int c = 0; c < 3; ++c) {
                 int v = lv * 3 + c;
                 double w = lw * b[c];
-                wv[q * OR_NV + v] = w;
-                vert[(q * OR_NV + v) * 3 + 0] = vx[c];
-                vert[(q * OR_NV + v) * 3 + 1] = vy[c];
-                vert[(q * OR_NV + v) * 3 + 2] = l;
+                wv[q * nv + v] = w;
+                vert[(q * nv + v) * 3 + 0] = vx[c];
+                vert[(q * nv + v) * 3 + 1] = vy[c];
+                vert[(q * nv + v) * 3 + 2] = grid ? (int64_t)key2 : l;
                 t.key0 = (uint32_t)vx[c];
                 t.key1 = (uint32_t)vy[c];
-                t.key2 = ((uint32_t)l) & 0xFFFFu;
+                t.key2 = key2;
                 double N[2 * OR_MAXK], dN[2 * OR_MAXK];
                 for (int i = 0; i < 2 * OR_MAXK; ++i) N[i] = dN[i] = 0.0;
                 if (integer_mode) {
@@ -1308,9 +1415,9 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
                 } else {
                     N[1] = (double)NP;
                 }
-                nroot[q * OR_NV + v] = N[1];
-                double *co = cand + ((size_t)q * OR_NV + v) * max_cand * K;
-                double *ce = cand_err + ((size_t)q * OR_NV + v) * max_cand * K;
+                nroot[q * nv + v] = N[1];
+                double *co = cand + ((size_t)q * nv + v) * max_cand * K;
+                double *ce = cand_err + ((size_t)q * nv + v) * max_cand * K;
                 t.out = (K_tree == K) ? co : wang_buf;
                 t.out_err = (K_tree == K) ? ce : wang_err;
                 t.max_cand = (K_tree == K) ? max_cand : (max_cand < 64 ? max_cand : 64);
@@ -1323,7 +1430,7 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
                             co[i * K + k] = k < 2 ? wang_buf[i * 2 + k] : 0.0;
                             ce[i * K + k] = k < 2 ? wang_err[i * 2 + k] : 0.0;
                         }
-                ncand[q * OR_NV + v] = t.overflow ? -1 : t.n_out;
+                ncand[q * nv + v] = t.overflow ? -1 : t.n_out;
                 for (int k = 0; k < K; ++k) Mk[k] += w * co[k]; /* first = nominal outcome */
             }
         }
@@ -1348,19 +1455,19 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
  * (Eq. iblglints:fin): L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k),
  * M_k = sum_i w_i n_k(i). counts: 6 x K. */
 void or_radiance(const double *lo3, const double *pk, double np, const double *L, int K, const double *wv,
-                 const double *counts, double *rgb, int draw, double gamma)
+                 const double *counts, double *rgb, int draw, double gamma, int nv)
 {
     double num = 0.0, den = 0.0;
     for (int k = 1; k < K; ++k) {
         double M = 0.0;
-        for (int v = 0; v < OR_NV; ++v) M += wv[v] * counts[v * K + k];
+        for (int v = 0; v < nv; ++v) M += wv[v] * counts[v * K + k];
         num += L[k] * M;
         den += L[k] * pk[k];
     }
     den *= np;
     if (draw == 3) { /* Wang 2020: L_o M_1 / (N_P gamma) */
         num = 0.0;
-        for (int v = 0; v < OR_NV; ++v) num += wv[v] * counts[v * K];
+        for (int v = 0; v < nv; ++v) num += wv[v] * counts[v * K];
         den = np * gamma;
     }
     for (int c = 0; c < 3; ++c) rgb[c] = den > 0.0 ? lo3[c] * num / den : 0.0;

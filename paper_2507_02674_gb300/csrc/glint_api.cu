@@ -397,6 +397,14 @@ static glint_status check_shade_args(const char *who, glint_ctx *ctx, const glin
         set_error("%s: the comparison draws run with the E1 evaluator", who);
         return GLINT_ERR_UNSUPPORTED;
     }
+    if (p->grid != GLINT_GRID_ISOTROPIC && p->grid != GLINT_GRID_ANISOTROPIC) {
+        set_error("%s: unknown grid %d", who, p->grid);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (p->grid == GLINT_GRID_ANISOTROPIC && (p->draw != GLINT_DRAW_DUAL || p->evaluator != GLINT_EVAL_E1)) {
+        set_error("%s: the anisotropic grid runs with the E1 evaluator and dual-gated draws", who);
+        return GLINT_ERR_UNSUPPORTED;
+    }
     if (p->draw == GLINT_DRAW_WANG2020 && !(p->gamma > 0.f && p->gamma <= 1.f)) {
         set_error("%s: gamma %g outside (0, 1]", who, (double)p->gamma);
         return GLINT_ERR_INVALID_ARG;

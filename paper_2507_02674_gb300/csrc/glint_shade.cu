@@ -116,9 +116,9 @@ cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const
     a.out = reinterpret_cast<float4 *>(out);
     a.dbg = dbg ? *dbg : glint_debug{};
     a.pk_in = pk_in;
-    if (p->draw != GLINT_DRAW_DUAL) {  // comparison draws (E1 only)
+    if (p->draw != GLINT_DRAW_DUAL || p->grid != GLINT_GRID_ISOTROPIC) {  // comparison draws, anisotropic grid
         if (launches) *launches = a.npix ? 1 : 0;
-        return glint_launch_shade_variant(a, env->d.K, p->count_mode == GLINT_COUNT_INTEGER, p->draw, s);
+        return glint_launch_shade_variant(a, env->d.K, p->count_mode == GLINT_COUNT_INTEGER, p->draw, p->grid, s);
     }
     const int ev = pk_in ? EV_GIVEN : (p->evaluator == GLINT_EVAL_E2 ? EV_E2 : EV_E1);
     const bool debug = dbg != nullptr;

@@ -171,13 +171,72 @@ __device__ __forceinline__ void draw_single_real(float N, const NodeParams &np, 
     nbar = fmaxf(N - n, 0.f);
 }
 
+// Orientations of the anisotropic grid: phi_o = o pi / 8, o = 0 .. 7, as FP32
+// values of cos and sin (cos(pi/8), sin(pi/8), sqrt(2)/2 rounded to nearest).
+__device__ __constant__ float kOrientCos[8] = {1.f, 0x1.d906bcp-1f, 0x1.6a09e6p-1f, 0x1.87de2ap-2f,
+                                               0.f, -0x1.87de2ap-2f, -0x1.6a09e6p-1f, -0x1.d906bcp-1f};
+__device__ __constant__ float kOrientSin[8] = {0.f, 0x1.87de2ap-2f, 0x1.6a09e6p-1f, 0x1.d906bcp-1f,
+                                               1.f, 0x1.d906bcp-1f, 0x1.6a09e6p-1f, 0x1.87de2ap-2f};
+
+// The anisotropic grid's footprint cell (Sec. 3.3, after the anisotropic
+// grids the paper builds on): the footprint ellipse of the uv Jacobian has
+// eigenvalues lam1 >= lam2 of J J^T; its coordinates are the level
+// L = l0 + fl = log2 sqrt|P| (as the isotropic grid), the anisotropy
+// A = log2(sqrt(lam1/lam2)) / 2 = (log2 lam1 - log2 |P|) / 2 clamped to [0, 2]
+// (a lattice stretched by 2^a along the major axis and shrunk by 2^a across
+// it), and the orientation O = theta / (pi/8) in [0, 8), theta = atan2(2b,
+// a - c) / 2 the major axis' angle, periodic.  N_P is spread over the four
+// vertices of the cell's Freudenthal tetrahedron: fractions sorted in
+// decreasing order (ties: L, then A, then O) give the path of unit steps and
+// the weights 1 - f1, f1 - f2, f2 - f3, f3.  Vertices with a = 0 use o = 0
+// (an unstretched lattice has no orientation).
+__device__ __forceinline__ void footprint_cell(float4 g3, float area, int l0, float fl, int *tl, int *ta, int *to,
+                                               float *tw) {
+    const float ea = g3.x * g3.x + g3.z * g3.z, ec = g3.y * g3.y + g3.w * g3.w;
+    const float eb = g3.x * g3.y + g3.z * g3.w;
+    const float hd = 0.5f * (ea - ec);
+    const float lam1 = 0.5f * (ea + ec) + sqrtf(hd * hd + eb * eb);
+    float A = 0.5f * (log2f(lam1) - log2f(area));
+    A = fminf(fmaxf(A, 0.f), 2.f);
+    float O = atan2f(eb, hd) * 1.27323954473516268615f;  // 4 / pi
+    if (O < 0.f) O += 8.f;
+    if (O >= 8.f) O -= 8.f;
+    const int a0 = (A >= 2.f) ? 2 : (int)floorf(A);
+    const float fa = A - (float)a0;
+    const int o0 = min((int)floorf(O), 7);
+    const float fo = O - (float)o0;
+    // order of the unit steps: by decreasing fraction, ties in the order L, A, O
+    const float f[3] = {fl, fa, fo};
+    int ord[3] = {0, 1, 2};
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2 - i; ++j)
+            if (f[ord[j + 1]] > f[ord[j]]) { const int t = ord[j]; ord[j] = ord[j + 1]; ord[j + 1] = t; }
+    int cl = l0, ca = a0, co = o0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        if (v > 0) {
+            const int ax = ord[v - 1];
+            if (ax == 0) ++cl; else if (ax == 1) ++ca; else co = (co + 1) & 7;
+        }
+        tl[v] = cl;
+        ta[v] = ca;
+        to[v] = (ca == 0) ? 0 : co;
+        const float hi = (v == 0) ? 1.f : f[ord[v - 1]];
+        const float lo = (v == 3) ? 0.f : f[ord[v]];
+        tw[v] = hi - lo;
+    }
+}
+
 // Steps 1-5 for pixel q of the frame described by a.  DRAW selects the binomial
 // approximation at the tree nodes: dual-gated (the paper's), single-gated
 // (Eq. gated), the older single-gated form (Eq. oldgated), or the Wang 2020
 // comparison (a single-gated glint count with the environment-independent
 // probability gamma, radiance L_o M / (N_P gamma); Sec. 7).
-template <int K, bool INTEGER, bool DEBUG, int EV, int DRAW = kDrawDual>
+template <int K, bool INTEGER, bool DEBUG, int EV, int DRAW = kDrawDual, int GRID = 0>
 __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
+    constexpr int NS = GRID ? 12 : 6;  // grid samples per pixel
     const float4 g0 = ldg4(a.view_n0 + q);
     const float4 g1 = ldg4(a.normal_f0 + q);
     const float4 g2 = ldg4(a.uv_alpha + q);
@@ -189,11 +248,11 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
             if (a.dbg.np) a.dbg.np[q] = 0.f;
             if (a.dbg.p) for (int k = 0; k < K; ++k) a.dbg.p[q * K + k] = 0.f;
             if (a.dbg.lo) for (int c = 0; c < 3; ++c) a.dbg.lo[q * 3 + c] = 0.f;
-            for (int v = 0; v < 6; ++v) {
-                if (a.dbg.w) a.dbg.w[q * 6 + v] = 0.f;
-                if (a.dbg.nroot) a.dbg.nroot[q * 6 + v] = 0.f;
-                if (a.dbg.vert) for (int c = 0; c < 3; ++c) a.dbg.vert[(q * 6 + v) * 3 + c] = 0;
-                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * 6 + v) * K + k] = 0.f;
+            for (int v = 0; v < NS; ++v) {
+                if (a.dbg.w) a.dbg.w[q * NS + v] = 0.f;
+                if (a.dbg.nroot) a.dbg.nroot[q * NS + v] = 0.f;
+                if (a.dbg.vert) for (int c = 0; c < 3; ++c) a.dbg.vert[(q * NS + v) * 3 + c] = 0;
+                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * NS + v) * K + k] = 0.f;
             }
         }
         return;
@@ -220,11 +279,11 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
     if (!(area > 0.f) || !(NP > 0.f)) {
         a.out[q] = make_float4(0.f, 0.f, 0.f, 1.f);
         if (DEBUG) {
-            for (int v = 0; v < 6; ++v) {
-                if (a.dbg.w) a.dbg.w[q * 6 + v] = 0.f;
-                if (a.dbg.nroot) a.dbg.nroot[q * 6 + v] = 0.f;
-                if (a.dbg.vert) for (int c = 0; c < 3; ++c) a.dbg.vert[(q * 6 + v) * 3 + c] = 0;
-                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * 6 + v) * K + k] = 0.f;
+            for (int v = 0; v < NS; ++v) {
+                if (a.dbg.w) a.dbg.w[q * NS + v] = 0.f;
+                if (a.dbg.nroot) a.dbg.nroot[q * NS + v] = 0.f;
+                if (a.dbg.vert) for (int c = 0; c < 3; ++c) a.dbg.vert[(q * NS + v) * 3 + c] = 0;
+                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * NS + v) * K + k] = 0.f;
             }
         }
         return;
@@ -267,11 +326,32 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
     const float F2 = 0x1.76cf5ep-2f;  // (sqrt(3) - 1) / 2
     const float fN = floorf(NP);
     const float fracN = NP - fN;
+    // anisotropic grid: the footprint's cell in (level, anisotropy, orientation)
+    int tv_l[4], tv_a[4], tv_o[4];
+    float tv_w[4];
+    if (GRID) footprint_cell(g3, area, l0, fl, tv_l, tv_a, tv_o, tv_w);
 #pragma unroll 1
-    for (int lv = 0; lv < 2; ++lv) {
-        const int l = l0 + lv;
-        const float lw = lv ? fl : 1.f - fl;
-        const float x = ldexpf(g2.x, -l), y = ldexpf(g2.y, -l);
+    for (int lv = 0; lv < (GRID ? 4 : 2); ++lv) {
+        int l;
+        float lw, x, y;
+        uint32_t key2;
+        if (GRID) {  // the uv lattice stretched along the vertex's orientation
+            l = tv_l[lv];
+            lw = tv_w[lv];
+            const int an = tv_a[lv], o = tv_o[lv];
+            const float cs = kOrientCos[o], sn = kOrientSin[o];
+            const float up = __fadd_rn(__fmul_rn(cs, g2.x), __fmul_rn(sn, g2.y));
+            const float vp = __fsub_rn(__fmul_rn(cs, g2.y), __fmul_rn(sn, g2.x));
+            x = ldexpf(up, -(l + an));
+            y = ldexpf(vp, -(l - an));
+            key2 = (((uint32_t)l) & 0x3FFu) | ((uint32_t)an << 10) | ((uint32_t)o << 12) | 0x8000u;
+        } else {
+            l = l0 + lv;
+            lw = lv ? fl : 1.f - fl;
+            x = ldexpf(g2.x, -l);
+            y = ldexpf(g2.y, -l);
+            key2 = ((uint32_t)l) & 0xFFFFu;
+        }
         const float sk = __fmul_rn(__fadd_rn(x, y), F2);
         const float xs = __fadd_rn(x, sk), ys = __fadd_rn(y, sk);
         const float fi = floorf(xs), fj = floorf(ys);
@@ -279,7 +359,6 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
         const uint32_t ii = low32_of_integral(fi), jj = low32_of_integral(fj);
         const bool tri = fx > fy;
         const float bmax = tri ? fx : fy, bmin = tri ? fy : fx;
-        const uint32_t key2 = ((uint32_t)l) & 0xFFFFu;
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {
             const uint32_t vx = ii + ((c == 2 || (c == 1 && tri)) ? 1u : 0u);
@@ -344,14 +423,14 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
             for (int k = 0; k < K; ++k) M[k] = fmaf(w, cnt[k], M[k]);
             if (DEBUG) {
                 const int v = lv * 3 + c;
-                if (a.dbg.w) a.dbg.w[q * 6 + v] = w;
-                if (a.dbg.nroot) a.dbg.nroot[q * 6 + v] = nroot;
+                if (a.dbg.w) a.dbg.w[q * NS + v] = w;
+                if (a.dbg.nroot) a.dbg.nroot[q * NS + v] = nroot;
                 if (a.dbg.vert) {
-                    a.dbg.vert[(q * 6 + v) * 3 + 0] = (int32_t)vx;
-                    a.dbg.vert[(q * 6 + v) * 3 + 1] = (int32_t)vy;
-                    a.dbg.vert[(q * 6 + v) * 3 + 2] = l;
+                    a.dbg.vert[(q * NS + v) * 3 + 0] = (int32_t)vx;
+                    a.dbg.vert[(q * NS + v) * 3 + 1] = (int32_t)vy;
+                    a.dbg.vert[(q * NS + v) * 3 + 2] = GRID ? (int32_t)key2 : l;
                 }
-                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * 6 + v) * K + k] = cnt[k];
+                if (a.dbg.counts) for (int k = 0; k < K; ++k) a.dbg.counts[(q * NS + v) * K + k] = cnt[k];
             }
         }
     }

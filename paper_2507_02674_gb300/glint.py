@@ -21,7 +21,8 @@ FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
 EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN = 0, 1, 2, 3
 MLP_PARAMS, MLP_GRAD, MLP_ADAM_M, MLP_ADAM_V = 0, 1, 2, 3
-ABI_VERSION = 5
+ABI_VERSION = 6
+GRID_ISOTROPIC, GRID_ANISOTROPIC = 0, 1
 WFMT_F32, WFMT_F16, WFMT_UNORM16, WFMT_UNORM8 = 0, 1, 2, 3
 DRAW_DUAL, DRAW_SINGLE, DRAW_SINGLE_OLD, DRAW_WANG2020 = 0, 1, 2, 3
 WEIGHTS_LINEAR, WEIGHTS_LOG = 0, 1
@@ -52,7 +53,7 @@ class GBufferDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint32), ("count_mode", ctypes.c_int), ("evaluator", ctypes.c_int),
                 ("e2_samples", ctypes.c_int), ("mlp", ctypes.c_void_p), ("p_scratch", ctypes.c_void_p),
-                ("draw", ctypes.c_int), ("gamma", ctypes.c_float)]
+                ("draw", ctypes.c_int), ("gamma", ctypes.c_float), ("grid", ctypes.c_int)]
 
 
 class Debug(ctypes.Structure):
@@ -295,19 +296,19 @@ def _gbuffer(planes, width: int, height: int, tangent=None) -> GBufferDesc:
 
 
 def _params(seed=0, count_mode=COUNT_INTEGER, evaluator=EVAL_E1, e2_samples=16, mlp=None, p_scratch=None,
-            draw=DRAW_DUAL, gamma=0.0):
+            draw=DRAW_DUAL, gamma=0.0, grid=GRID_ISOTROPIC):
     return Params(seed & 0xFFFFFFFF, count_mode, evaluator, e2_samples,
-                  mlp.handle.value if mlp is not None else None, _dptr(p_scratch), draw, gamma)
+                  mlp.handle.value if mlp is not None else None, _dptr(p_scratch), draw, gamma, grid)
 
 
 def shade(ctx: Context, env: Env, planes, width: int, height: int, out, seed: int = 0,
           count_mode: int = COUNT_INTEGER, debug: dict | None = None, stream=None, tangent=None,
           evaluator: int = EVAL_E1, e2_samples: int = 16, mlp=None, p_scratch=None, draw: int = DRAW_DUAL,
-          gamma: float = 0.0):
+          gamma: float = 0.0, grid: int = GRID_ISOTROPIC):
     """glint_shade over a G-buffer given as four device tensors of (npix, 4) float32
     (plus an optional (npix, 4) tangent tensor, needed by E2 and the MLP)."""
     g = _gbuffer(planes, width, height, tangent)
-    p = _params(seed, count_mode, evaluator, e2_samples, mlp, p_scratch, draw, gamma)
+    p = _params(seed, count_mode, evaluator, e2_samples, mlp, p_scratch, draw, gamma, grid)
     dbg = None
     if debug is not None:
         dbg = Debug(*(_dptr(debug.get(k)) for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")))
@@ -564,10 +565,11 @@ def normal_quantile(p, out=None, stream=None):
     return out
 
 
-def debug_buffers(npix: int, K: int, device="cuda"):
-    """Device tensors for every optional intermediate output of glint_shade."""
+def debug_buffers(npix: int, K: int, device="cuda", samples: int = 6):
+    """Device tensors for every optional intermediate output of glint_shade
+    (samples: 6 for the isotropic grid, 12 for the anisotropic one)."""
     import torch
     return {"p": torch.zeros(npix, K, device=device), "np": torch.zeros(npix, device=device),
-            "vert": torch.zeros(npix, 6, 3, dtype=torch.int32, device=device),
-            "w": torch.zeros(npix, 6, device=device), "nroot": torch.zeros(npix, 6, device=device),
-            "counts": torch.zeros(npix, 6, K, device=device), "lo": torch.zeros(npix, 3, device=device)}
+            "vert": torch.zeros(npix, samples, 3, dtype=torch.int32, device=device),
+            "w": torch.zeros(npix, samples, device=device), "nroot": torch.zeros(npix, samples, device=device),
+            "counts": torch.zeros(npix, samples, K, device=device), "lo": torch.zeros(npix, 3, device=device)}

@@ -44,13 +44,14 @@ class Frame:
 
     def shade(self, planes, width: int, height: int, out=None, seed: int = 0, count_mode: int = glint.COUNT_INTEGER,
               debug=None, stream=None, tangent=None, evaluator: int = glint.EVAL_E1, e2_samples: int = 16,
-              mlp=None, p_scratch=None, draw: int = glint.DRAW_DUAL, gamma: float = 0.0):
+              mlp=None, p_scratch=None, draw: int = glint.DRAW_DUAL, gamma: float = 0.0,
+              grid: int = glint.GRID_ISOTROPIC):
         if out is None:
             out = torch.empty(width * height, 4, device=planes[0].device)
         if evaluator == glint.EVAL_MLP and p_scratch is None:
             p_scratch = torch.empty(width * height, self.cfg.K, device=planes[0].device)
         glint.shade(self.ctx, self.env, planes, width, height, out, seed, count_mode, debug, stream, tangent,
-                    evaluator, e2_samples, mlp, p_scratch, draw, gamma)
+                    evaluator, e2_samples, mlp, p_scratch, draw, gamma, grid)
         return out
 
     def probs(self, planes, width: int, height: int, evaluator: int = glint.EVAL_E1, e2_samples: int = 16,

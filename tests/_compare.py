@@ -96,23 +96,24 @@ def compare_shade(orc, o, gpu: dict, rgb_gpu: np.ndarray, integer_mode: bool = T
     if rep.max_lo_rel > LO_RTOL:
         fail(f"L_o rel error {rep.max_lo_rel:.3e}")
 
-    # grid samples
+    # grid samples (on the anisotropic grid a nonunique pixel's cell itself may differ)
+    vchk = fg_all & ~nu if getattr(o, "grid", 0) else fg_all
     vo = o.vert.copy()
     vo[..., :2] = vo[..., :2] & 0xFFFFFFFF
     vg = gpu["vert"].astype(np.int64)
     vg[..., :2] = vg[..., :2] & 0xFFFFFFFF
-    badv = np.nonzero(np.any(vo[fg_all] != vg[fg_all], axis=(1, 2)))[0]
+    badv = np.nonzero(np.any(vo[vchk] != vg[vchk], axis=(1, 2)))[0]
     for q in badv[:5]:
-        fail(f"grid vertices pixel {np.nonzero(fg_all)[0][q]}: oracle {vo[fg_all][q].tolist()} "
-             f"gpu {vg[fg_all][q].tolist()}")
-    wd = np.abs(gpu["w"][fg_all] - o.wv[fg_all])
+        fail(f"grid vertices pixel {np.nonzero(vchk)[0][q]}: oracle {vo[vchk][q].tolist()} "
+             f"gpu {vg[vchk][q].tolist()}")
+    wd = np.abs(gpu["w"][vchk] - o.wv[vchk])
     if wd.size and wd.max() > W_ATOL:
         fail(f"grid weights differ by {wd.max():.3e}")
     if integer_mode:
-        badn = np.nonzero(np.any(gpu["nroot"][fg_all] != o.nroot[fg_all], axis=1))[0]
+        badn = np.nonzero(np.any(gpu["nroot"][vchk] != o.nroot[vchk], axis=1))[0]
         for q in badn[:5]:
-            fail(f"root trials pixel {np.nonzero(fg_all)[0][q]}: oracle {o.nroot[fg_all][q]} "
-                 f"gpu {gpu['nroot'][fg_all][q]}")
+            fail(f"root trials pixel {np.nonzero(vchk)[0][q]}: oracle {o.nroot[vchk][q]} "
+                 f"gpu {gpu['nroot'][vchk][q]}")
         # debug counts are float32: above 2^24 each carries a rounding of N 2^-24
         cs = gpu["counts"].astype(np.float64).sum(-1)
         nr = gpu["nroot"].astype(np.float64)
@@ -124,10 +125,11 @@ def compare_shade(orc, o, gpu: dict, rgb_gpu: np.ndarray, integer_mode: bool = T
     # counts: membership in the oracle's valid set; radiance for the chosen vectors
     cg = gpu["counts"].astype(np.float64)
     for q in np.nonzero(fg)[0]:
-        chosen = np.zeros((6, K))
+        nv = o.wv.shape[1]
+        chosen = np.zeros((nv, K))
         nondefault = False
         unresolved = False
-        for v in range(6):
+        for v in range(nv):
             rep.trees += 1
             nc = o.ncand[q, v]
             cvec = cg[q, v]

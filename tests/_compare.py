@@ -154,7 +154,14 @@ def compare_shade(orc, o, gpu: dict, rgb_gpu: np.ndarray, integer_mode: bool = T
                      f"tol={tol[0].tolist()} ncand={nc}")
                 chosen[v] = cands[0]
                 continue
-            chosen[v] = cands[hit[0]]
+            if np.any(tol[hit[0]] > 0):
+                # an interval candidate (counts known to the oracle only within
+                # its tie-model tolerance): the radiance is evaluated at the
+                # counts the kernel produced, which were just checked against it
+                chosen[v] = cvec
+                nondefault = True
+            else:
+                chosen[v] = cands[hit[0]]
             if hit[0] != 0:
                 rep.nondefault += 1
                 nondefault = True

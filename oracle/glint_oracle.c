@@ -42,8 +42,10 @@
  * The paper stores random seeds theta_i at the grid vertices (Sec. 3.3,
  * Eq. anisogrid) but does not name a generator.  Reading: pcg4d of
  * Jarzynski & Olano, "Hash Functions for GPU Rendering", JCGT 9(3), 2020,
- * applied to (vertex x, vertex y, level | node << 16, user seed); its four
- * output words give xi0 (dither), xi1 (gating) and xi2 (Gaussian).
+ * applied to (vertex x, vertex y, level | call << 16, user seed).  Call 1
+ * gives xi0 (the root's dither, word 0) and node 1's xi1 (gating) and xi2
+ * (Gaussian) in words 1 and 2; the sibling nodes 2m and 2m+1 of the balanced
+ * tree share call m + 1, node 2m taking words 0, 1 and node 2m+1 words 2, 3.
  * ------------------------------------------------------------------------ */
 void or_pcg4d(const uint32_t in[4], uint32_t out[4])
 {
@@ -1094,9 +1096,14 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
         tree_rec(t, node + 1, N, dN);
         return;
     }
-    uint32_t in[4] = {t->key0, t->key1, t->key2 | ((uint32_t)node << 16), t->seed}, h[4];
+    /* the node's two uniforms: node 1 takes words 1 and 2 of hash call 1
+     * (word 0 is the dither); siblings 2m and 2m+1 share hash call m + 1,
+     * words 0, 1 and 2, 3 respectively */
+    uint32_t call = (node == 1) ? 1u : 1u + (uint32_t)node / 2u;
+    uint32_t in[4] = {t->key0, t->key1, t->key2 | (call << 16), t->seed}, h[4];
     or_pcg4d(in, h);
-    double xi1 = or_xi(h[1]), xi2 = or_xi(h[2]);
+    int w0 = (node == 1) ? 1 : (node & 1) ? 2 : 0;
+    double xi1 = or_xi(h[w0]), xi2 = or_xi(h[w0 + 1]);
     double PL = t->P[2 * node], PR = t->P[2 * node + 1];
     double p = (PL + PR > 0.0) ? PL / (PL + PR) : 0.0;
     double e_P = t->tie[0], e_z = t->tie[1], e_f = t->tie[2], d_a = t->tie[3], a_P = t->tie[4];

@@ -76,13 +76,16 @@ __device__ __forceinline__ uint4 pcg4d(uint4 v) {
     return v;
 }
 
-// Uniform in (0,1) from the top 23 bits of a hash word, (2m+1) 2^-24: exact in
-// FP32, never 0 or 1, and 1 - xi is exact.
+// Uniform in (0,1) from the top 23 bits m of a hash word, (2m+1) 2^-24: exact
+// in FP32, never 0 or 1, and 1 - xi is exact.  Built without an integer
+// conversion: the float with exponent 0 and mantissa m is 1 + m 2^-23, and
+// subtracting 1 - 2^-24 leaves (2m+1) 2^-24, which has at most 24 significant
+// bits and so is the exact difference (checked for every m).
 __device__ __forceinline__ float hash_uniform(uint32_t h) {
-    return __uint2float_rn(((h >> 9) << 1) | 1u) * 0x1p-24f;
+    return __fsub_rn(__uint_as_float((h >> 9) | 0x3F800000u), 0x1.fffffep-1f);
 }
 __device__ __forceinline__ float hash_uniform_complement(uint32_t h) {
-    return __uint2float_rn((0x1000000u - (((h >> 9) << 1) | 1u))) * 0x1p-24f;
+    return __fsub_rn(1.f, hash_uniform(h));
 }
 
 // Equirect texel coordinates of a direction (texel centres at integers).

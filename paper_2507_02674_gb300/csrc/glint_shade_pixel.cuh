@@ -59,7 +59,9 @@ struct NodeParams {
 // returns n (nbar = N - n).  Regions of xi1 (same as the printed masks):
 // [0, P_{n=N}) -> N;  [P_{n=N}, P_{n=N} + P_{n=1}) -> 1;
 // 1 - xi1 <= P_{nbar=N} + P_{nbar=1} -> 0;  otherwise the clamped, rounded
-// Gaussian when N > 1, else 0.
+// Gaussian when N > 1, else 0.  Evaluated without branches (the Gaussian is
+// computed for every lane and the gates select), so that a warp whose lanes
+// take different regions does not run the paths one after another.
 __device__ __forceinline__ uint32_t draw_integer(uint32_t N, const NodeParams &np, uint32_t h1, uint32_t h2) {
     const float xi1 = hash_uniform(h1);
     const float xi1c = hash_uniform_complement(h1);
@@ -70,15 +72,15 @@ __device__ __forceinline__ uint32_t draw_integer(uint32_t N, const NodeParams &n
     const float Pall = a * fast_exp2(N2 * np.lp);
     const float T1 = Pall + b * np.p;
     const float Sneg = a * fast_exp2(N2 * np.lq) + b * np.q;
-    if (xi1 < Pall) return N;
-    if (xi1 < T1) return 1u;
-    if (xi1c <= Sneg || N < 2u) return 0u;
     const float mu = 1.f + (N2 - 2.f) * np.p;
     const float sigma = fast_sqrt((N2 - 2.f) * np.p * np.q);
     const float z = normal_quantile(hash_uniform(h2));
     float G = floorf(fmaf(sigma, z, mu) + 0.5f);
     G = fminf(fmaxf(G, 1.f), kMaxCount);
-    return min((uint32_t)G, N - 1u);
+    uint32_t r = min((uint32_t)G, N - 1u);
+    r = (xi1c <= Sneg || N < 2u) ? 0u : r;
+    r = (xi1 < T1) ? 1u : r;
+    return (xi1 < Pall) ? N : r;
 }
 
 // Dual-gated Gaussian (Alg. 1) with real-valued N and counts.
@@ -365,6 +367,9 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
             const uint32_t vy = jj + ((c == 2 || (c == 1 && !tri)) ? 1u : 0u);
             const float bc = (c == 0) ? 1.f - bmax : (c == 1) ? bmax - bmin : bmin;
             const float w = lw * bc;
+            // the vertex's uniforms: hash call 1 gives the root's dither (word 0)
+            // and node 1's pair (words 1, 2); siblings 2m, 2m+1 share call m + 1
+            // (words 0, 1 and 2, 3), made once either of them has trials
             uint4 h = pcg4d(make_uint4(vx, vy, key2 | (1u << 16), a.seed));
             float cnt[K];
             float nroot;
@@ -382,10 +387,13 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
 #pragma unroll
                     for (int n = 1; n < K; ++n) {
                         uint32_t nl = 0u, nr = 0u;
+                        if (n >= 2 && !(n & 1) && (N[n] | N[n + 1]))
+                            h = pcg4d(make_uint4(vx, vy, key2 | ((uint32_t)(1 + n / 2) << 16), a.seed));
+                        const uint32_t u1 = (n == 1) ? h.y : (n & 1) ? h.z : h.x;
+                        const uint32_t u2 = (n == 1) ? h.z : (n & 1) ? h.w : h.y;
                         if (N[n] > 0u) {
-                            if (n > 1) h = pcg4d(make_uint4(vx, vy, key2 | ((uint32_t)n << 16), a.seed));
-                            nl = (DRAW == kDrawDual) ? draw_integer(N[n], nd[n], h.y, h.z)
-                                                     : draw_single_integer(N[n], nd[n], h.y, h.z, DRAW == kDrawSingleOld);
+                            nl = (DRAW == kDrawDual) ? draw_integer(N[n], nd[n], u1, u2)
+                                                     : draw_single_integer(N[n], nd[n], u1, u2, DRAW == kDrawSingleOld);
                             nr = N[n] - nl;
                         }
                         N[2 * n] = nl;
@@ -406,10 +414,13 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
 #pragma unroll
                     for (int n = 1; n < K; ++n) {
                         float nl = 0.f, nr = 0.f;
+                        if (n >= 2 && !(n & 1) && (N[n] > 0.f || N[n + 1] > 0.f))
+                            h = pcg4d(make_uint4(vx, vy, key2 | ((uint32_t)(1 + n / 2) << 16), a.seed));
+                        const uint32_t u1 = (n == 1) ? h.y : (n & 1) ? h.z : h.x;
+                        const uint32_t u2 = (n == 1) ? h.z : (n & 1) ? h.w : h.y;
                         if (N[n] > 0.f) {
-                            if (n > 1) h = pcg4d(make_uint4(vx, vy, key2 | ((uint32_t)n << 16), a.seed));
-                            if (DRAW == kDrawDual) draw_real(N[n], nd[n], h.y, h.z, nl, nr);
-                            else draw_single_real(N[n], nd[n], h.y, h.z, DRAW == kDrawSingleOld, nl, nr);
+                            if (DRAW == kDrawDual) draw_real(N[n], nd[n], u1, u2, nl, nr);
+                            else draw_single_real(N[n], nd[n], u1, u2, DRAW == kDrawSingleOld, nl, nr);
                         }
                         N[2 * n] = nl;
                         N[2 * n + 1] = nr;

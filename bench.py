@@ -109,7 +109,7 @@ class ClockSampler:
 
 def _source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("glint_shade.cu", "glint_probs.cuh", "glint_quantile.cuh", "glint_internal.cuh"):
+    for f in ("glint_shade.cu", "glint_shade_pixel.cuh", "glint_probs.cuh", "glint_quantile.cuh", "glint_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2507_02674_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

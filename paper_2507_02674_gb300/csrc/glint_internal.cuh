@@ -11,6 +11,14 @@
 
 namespace glint {
 
+// Resident blocks per SM of the shading kernels (k_shade, k_serve,
+// k_shade_var; 128 threads each), their launch bound and the serving grid's
+// unit.  Six blocks give 80 registers a thread: the per-node draw code
+// spills at 64 registers (eight blocks), and a wider budget leaves too few
+// warps to fill the issue slots (1080p frame, K = 8: 0.378 ms at 8 blocks,
+// 0.342 ms at 6, 0.354 ms at 5, 0.403 ms at 4).
+constexpr int kShadeMinBlocks = 6;
+
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kInvTwoPi = 0.159154943091895335769f;

@@ -530,14 +530,14 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
                              "glint_server_tick: inference");
             ++nl;
             if (st == GLINT_OK) {
-                const int grid = std::min(n_mlp_items, s->ctx->num_sms * 8);
+                const int grid = std::min(n_mlp_items, s->ctx->num_sms * glint::kShadeMinBlocks);
                 st = cuda_status(glint_launch_serve(s->K, true, sl.d_frames, sl.d_items, n_mlp_items, grid, cs),
                                  "glint_server_tick: shade");
                 ++nl;
             }
         }
         if (st == GLINT_OK && nit_all > n_mlp_items) {
-            const int grid = std::min(nit_all - n_mlp_items, s->ctx->num_sms * 8);
+            const int grid = std::min(nit_all - n_mlp_items, s->ctx->num_sms * glint::kShadeMinBlocks);
             st = cuda_status(glint_launch_serve(s->K, false, sl.d_frames, sl.d_items + n_mlp_items,
                                                 nit_all - n_mlp_items, grid, cs), "glint_server_tick: shade");
             ++nl;

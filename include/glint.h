@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GLINT_ABI_VERSION 6
+#define GLINT_ABI_VERSION 7
 #define GLINT_MAX_K 16
 
 typedef enum glint_status {
@@ -268,6 +268,63 @@ typedef struct glint_debug {
  * `stream`; env must have been updated on the same stream (or synchronised). */
 glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuffer *gbuf,
                          const glint_params *params, float *out_rgba, const glint_debug *dbg, void *stream);
+
+/* ---- shading a frame held in host memory ----
+ * The same per-pixel shading as glint_shade (Sec. 4 Eq. iblglints:fin; each
+ * pixel depends only on its own G-buffer texel, the environment and the seed,
+ * so results equal glint_shade's bit for bit), for a caller whose G-buffer
+ * and output live in host memory.  Two ways, chosen per call:
+ *  - in place: when every buffer lies in page-locked host memory the device
+ *    can address (cudaHostAlloc / cudaMallocHost, or cudaHostRegister), the
+ *    shading kernels read the planes and write the output there directly
+ *    over the host link, in one pass: the transfer overlaps the arithmetic
+ *    inside the kernel, with no staging and no copies;
+ *  - staged (pageable buffers, or GLINT_HOST_STAGED): the frame is cut into
+ *    bands of whole rows, and band b's planes are copied host -> device on
+ *    the pipe's upload stream, shaded on `stream`, and its output copied
+ *    device -> host on the pipe's download stream, so that the copies of one
+ *    band overlap the shading of the others.  A glint_hostpipe owns the device staging for `slots` bands (2 to 16)
+ * of up to band_pixels pixels each (five 16-byte input planes and one 16-byte
+ * output plane per pixel, allocated once at creation on ctx's device), the two
+ * copy streams and the events that order them.  Uploads run at most `slots`
+ * bands ahead of the shading: as many slots as a frame has bands let the
+ * upload link run without waiting for the shading. */
+typedef struct glint_hostpipe glint_hostpipe;
+
+glint_status glint_hostpipe_create(glint_ctx *ctx, long band_pixels, int slots, glint_hostpipe **out);
+/* Waits for the pipe's copies, then frees it.  NULL is ignored. */
+void glint_hostpipe_destroy(glint_hostpipe *pipe);
+
+/* host_gbuf: HOST pointers to the width*height float4 planes (tangent only for
+ * E2 and the MLP evaluator; it is uploaded whenever non-NULL); out_rgba_host:
+ * HOST, width*height float4.  Pinned host memory (cudaHostAlloc or
+ * cudaHostRegister) lets the copies overlap; pageable memory gives the same
+ * results with copies that block the calling thread.  params as glint_shade
+ * (params->p_scratch stays a DEVICE buffer of width*height*K floats for the
+ * MLP and GIVEN evaluators; band b uses its rows of it).  rows_per_band: 0
+ * picks about an eighth of the frame, capped by the pipe's band_pixels; a
+ * band of more pixels than band_pixels, or a row wider than it, is
+ * GLINT_ERR_INVALID_ARG.  The uploads start after the work enqueued on
+ * `stream` before the call, unless flags holds GLINT_HOST_INPUTS_READY: the
+ * host planes are final when the call is made, and the uploads start at once,
+ * alongside that work (an environment update enqueued just before, say); the
+ * shading of each band still follows it on `stream` (in place, the kernels
+ * read the planes in stream order and the flag changes nothing).  The call
+ * returns once
+ * everything is enqueued and `stream` then waits for the last download, so
+ * out_rgba_host is complete when `stream` is.  The host buffers must stay
+ * valid and unchanged until then.  Calls on one pipe are ordered through its
+ * staging: a call's uploads wait until the previous call's shading has read
+ * the slots they overwrite.  Unknown flag bits are GLINT_ERR_INVALID_ARG. */
+#define GLINT_HOST_INPUTS_READY 1u
+#define GLINT_HOST_STAGED 2u /* stage through the pipe even when the buffers could be used in place */
+glint_status glint_shade_host(glint_hostpipe *pipe, const glint_env *env, const glint_gbuffer *host_gbuf,
+                              const glint_params *params, float *out_rgba_host, int rows_per_band,
+                              unsigned flags, void *stream);
+/* Kernel launches of the last glint_shade_host call on `pipe` (every band). */
+int glint_hostpipe_last_launches(const glint_hostpipe *pipe);
+/* 1 if the last glint_shade_host call on `pipe` shaded in place, 0 if staged. */
+int glint_hostpipe_last_in_place(const glint_hostpipe *pipe);
 
 /* Reflection probabilities p_k (Eq. probhk) of every pixel of `gbuf` under
  * params->evaluator (E1, E2 or MLP; GIVEN is rejected; seed and count mode

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "glint_internal.cuh"
@@ -467,6 +468,216 @@ glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuff
     st = cuda_status(glint_launch_shade(ctx, env, g, p, pk_in, out_rgba, dbg, (cudaStream_t)stream, &nl),
                      "glint_shade");
     ctx->last_launches = nl + (p->evaluator == GLINT_EVAL_MLP && npix > 0 ? 1 : 0);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// Shading a frame held in host memory: bands of whole rows, uploaded on the
+// pipe's upload stream, shaded on the caller's stream, downloaded on the
+// pipe's download stream.  Slot s of the staging is reused by every band
+// b = s (mod slots); four events per slot order the reuse:
+//   uploaded[s]   the band's planes are on the device      (upload -> shade)
+//   shaded[s]     the shading has read the planes           (shade -> next upload)
+//   downloaded[s] the output has left the slot              (download -> next shade)
+// ---------------------------------------------------------------------------
+struct glint_hostpipe {
+    static constexpr int kMaxSlots = 16;
+    glint_ctx *ctx = nullptr;
+    int device = 0;
+    long band = 0;                 // pixels per slot
+    int slots = 0;
+    char *mem = nullptr;           // slots x 6 planes x band float4
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t entry = nullptr;
+    cudaEvent_t uploaded[kMaxSlots] = {}, shaded[kMaxSlots] = {}, downloaded[kMaxSlots] = {};
+    int last_launches = 0;
+    int last_in_place = 0;
+    float4 *plane(int slot, int i) const {  // i = 0..4 inputs, 5 output
+        return reinterpret_cast<float4 *>(mem) + ((size_t)slot * 6 + i) * (size_t)band;
+    }
+};
+
+static void hostpipe_free(glint_hostpipe *hp) {
+    if (hp->up) cudaStreamSynchronize(hp->up);
+    if (hp->down) cudaStreamSynchronize(hp->down);
+    for (int s = 0; s < glint_hostpipe::kMaxSlots; ++s) {
+        if (hp->uploaded[s]) cudaEventDestroy(hp->uploaded[s]);
+        if (hp->shaded[s]) cudaEventDestroy(hp->shaded[s]);
+        if (hp->downloaded[s]) cudaEventDestroy(hp->downloaded[s]);
+    }
+    if (hp->entry) cudaEventDestroy(hp->entry);
+    if (hp->up) cudaStreamDestroy(hp->up);
+    if (hp->down) cudaStreamDestroy(hp->down);
+    cudaFree(hp->mem);
+    delete hp;
+}
+
+glint_status glint_hostpipe_create(glint_ctx *ctx, long band_pixels, int slots, glint_hostpipe **out) {
+    g_err[0] = 0;
+    if (!ctx || !out) { set_error("glint_hostpipe_create: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (band_pixels < 1 || band_pixels > (1L << 28) || slots < 2 || slots > glint_hostpipe::kMaxSlots) {
+        set_error("glint_hostpipe_create: band_pixels %ld must be in [1, 2^28], slots %d in [2, %d]", band_pixels, slots,
+                  glint_hostpipe::kMaxSlots);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) { set_error("glint_hostpipe_create: cannot select device %d", ctx->device); return GLINT_ERR_CUDA; }
+    glint_hostpipe *hp = new glint_hostpipe();
+    hp->ctx = ctx;
+    hp->device = ctx->device;
+    hp->band = band_pixels;
+    hp->slots = slots;
+    glint_status st = cuda_status(cudaMalloc(&hp->mem, sizeof(float4) * 6 * (size_t)slots * (size_t)band_pixels),
+                                  "glint_hostpipe_create: staging");
+    if (st == GLINT_OK) st = cuda_status(cudaStreamCreateWithFlags(&hp->up, cudaStreamNonBlocking), "glint_hostpipe_create");
+    if (st == GLINT_OK) st = cuda_status(cudaStreamCreateWithFlags(&hp->down, cudaStreamNonBlocking), "glint_hostpipe_create");
+    if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&hp->entry, cudaEventDisableTiming), "glint_hostpipe_create");
+    for (int s = 0; s < slots && st == GLINT_OK; ++s) {
+        st = cuda_status(cudaEventCreateWithFlags(&hp->uploaded[s], cudaEventDisableTiming), "glint_hostpipe_create");
+        if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&hp->shaded[s], cudaEventDisableTiming), "glint_hostpipe_create");
+        if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&hp->downloaded[s], cudaEventDisableTiming), "glint_hostpipe_create");
+    }
+    if (st != GLINT_OK) {
+        hostpipe_free(hp);
+        return st;
+    }
+    *out = hp;
+    return GLINT_OK;
+}
+
+void glint_hostpipe_destroy(glint_hostpipe *pipe) {
+    if (!pipe) return;
+    DeviceGuard guard(pipe->device);
+    hostpipe_free(pipe);
+}
+
+int glint_hostpipe_last_launches(const glint_hostpipe *pipe) { return pipe ? pipe->last_launches : 0; }
+int glint_hostpipe_last_in_place(const glint_hostpipe *pipe) { return pipe ? pipe->last_in_place : 0; }
+
+// Device address of `bytes` bytes of host memory at `p` when all of them lie
+// in one page-locked allocation the current device can address, else NULL.
+static const void *device_view_of_host(const void *p, size_t bytes) {
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const char *last = static_cast<const char *>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    if (b.type != cudaMemoryTypeHost ||
+        static_cast<const char *>(b.devicePointer) != static_cast<const char *>(a.devicePointer) + (bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
+glint_status glint_shade_host(glint_hostpipe *pipe, const glint_env *env, const glint_gbuffer *hg,
+                              const glint_params *p, float *out_host, int rows_per_band, unsigned flags,
+                              void *stream) {
+    g_err[0] = 0;
+    if (!pipe) { set_error("glint_shade_host: NULL pipe"); return GLINT_ERR_INVALID_ARG; }
+    if (flags & ~(GLINT_HOST_INPUTS_READY | GLINT_HOST_STAGED)) {
+        set_error("glint_shade_host: unknown flags 0x%x", flags);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    glint_status st = check_shade_args("glint_shade_host", pipe->ctx, env, hg, p, out_host);
+    if (st != GLINT_OK) return st;
+    pipe->last_launches = 0;
+    pipe->last_in_place = 0;
+    const int W = hg->width, H = hg->height;
+    if ((long)W * H == 0) return GLINT_OK;
+    if (!hg->view_n0 || !hg->normal_f0 || !hg->uv_alpha || !hg->duv) {
+        set_error("glint_shade_host: NULL G-buffer plane");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    const bool with_tangent = hg->tangent != nullptr;
+    DeviceGuard guard(pipe->device);
+    if (!guard.ok) { set_error("glint_shade_host: cannot select device %d", pipe->device); return GLINT_ERR_CUDA; }
+    if (!(flags & GLINT_HOST_STAGED)) {
+        // in place: every buffer in page-locked memory this device addresses
+        const size_t plane_bytes = sizeof(float4) * (size_t)W * H;
+        const float *src[5] = {hg->view_n0, hg->normal_f0, hg->uv_alpha, hg->duv, hg->tangent};
+        const void *dv[6] = {};
+        bool in_place = true;
+        for (int i = 0; i < 5 && in_place; ++i) {
+            if (i == 4 && !with_tangent) break;
+            dv[i] = device_view_of_host(src[i], plane_bytes);
+            in_place = dv[i] != nullptr;
+        }
+        if (in_place) {
+            dv[5] = device_view_of_host(out_host, plane_bytes);
+            in_place = dv[5] != nullptr;
+        }
+        if (in_place) {
+            glint_gbuffer g = {static_cast<const float *>(dv[0]), static_cast<const float *>(dv[1]),
+                               static_cast<const float *>(dv[2]), static_cast<const float *>(dv[3]), W, H,
+                               with_tangent ? static_cast<const float *>(dv[4]) : nullptr};
+            st = glint_shade(pipe->ctx, env, &g, p, static_cast<float *>(const_cast<void *>(dv[5])), nullptr, stream);
+            pipe->last_launches = pipe->ctx->last_launches;
+            pipe->last_in_place = 1;
+            return st;
+        }
+    }
+    if ((long)W > pipe->band) {
+        set_error("glint_shade_host: a row of %d pixels does not fit a band of %ld", W, pipe->band);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    const long cap_rows = pipe->band / W;
+    long rpb = rows_per_band;
+    if (rpb < 0 || rpb > cap_rows) {
+        set_error("glint_shade_host: rows_per_band %d outside [0, %ld] for width %d and bands of %ld pixels",
+                  rows_per_band, cap_rows, W, pipe->band);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (rpb == 0) rpb = std::min(cap_rows, std::max(1L, ((long)H + 7) / 8));
+    const int K = env->d.K;
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (!(flags & GLINT_HOST_INPUTS_READY)) {  // uploads after the stream's earlier work
+        st = cuda_status(cudaEventRecord(pipe->entry, cs), "glint_shade_host: entry");
+        if (st == GLINT_OK) st = cuda_status(cudaStreamWaitEvent(pipe->up, pipe->entry, 0), "glint_shade_host: entry");
+    }
+    const long nb = ((long)H + rpb - 1) / rpb;
+    const float *src[5] = {hg->view_n0, hg->normal_f0, hg->uv_alpha, hg->duv, hg->tangent};
+    int launches = 0;
+    for (long b = 0; b < nb && st == GLINT_OK; ++b) {
+        const int s = (int)(b % pipe->slots);
+        const long r0 = b * rpb;
+        const int rows = (int)std::min(rpb, (long)H - r0);
+        const size_t off = (size_t)r0 * W, n = (size_t)rows * W;
+        // upload once the shading of the slot's previous band has read it
+        st = cuda_status(cudaStreamWaitEvent(pipe->up, pipe->shaded[s], 0), "glint_shade_host: upload");
+        for (int i = 0; i < 5 && st == GLINT_OK; ++i) {
+            if (i == 4 && !with_tangent) break;
+            st = cuda_status(cudaMemcpyAsync(pipe->plane(s, i), src[i] + 4 * off, sizeof(float4) * n,
+                                             cudaMemcpyHostToDevice, pipe->up), "glint_shade_host: upload");
+        }
+        if (st == GLINT_OK) st = cuda_status(cudaEventRecord(pipe->uploaded[s], pipe->up), "glint_shade_host: upload");
+        // shade once the planes are there and the slot's previous output has left
+        if (st == GLINT_OK) st = cuda_status(cudaStreamWaitEvent(cs, pipe->uploaded[s], 0), "glint_shade_host: shade");
+        if (st == GLINT_OK) st = cuda_status(cudaStreamWaitEvent(cs, pipe->downloaded[s], 0), "glint_shade_host: shade");
+        if (st != GLINT_OK) break;
+        glint_gbuffer g = {reinterpret_cast<const float *>(pipe->plane(s, 0)),
+                           reinterpret_cast<const float *>(pipe->plane(s, 1)),
+                           reinterpret_cast<const float *>(pipe->plane(s, 2)),
+                           reinterpret_cast<const float *>(pipe->plane(s, 3)), W, rows,
+                           with_tangent ? reinterpret_cast<const float *>(pipe->plane(s, 4)) : nullptr};
+        glint_params pb = *p;
+        if (pb.p_scratch) pb.p_scratch = p->p_scratch + off * (size_t)K;
+        float *outb = reinterpret_cast<float *>(pipe->plane(s, 5));
+        st = glint_shade(pipe->ctx, env, &g, &pb, outb, nullptr, stream);
+        if (st != GLINT_OK) break;
+        launches += pipe->ctx->last_launches;
+        st = cuda_status(cudaEventRecord(pipe->shaded[s], cs), "glint_shade_host: shade");
+        // download once shaded
+        if (st == GLINT_OK) st = cuda_status(cudaStreamWaitEvent(pipe->down, pipe->shaded[s], 0), "glint_shade_host: download");
+        if (st == GLINT_OK)
+            st = cuda_status(cudaMemcpyAsync(out_host + 4 * off, outb, sizeof(float4) * n, cudaMemcpyDeviceToHost,
+                                             pipe->down), "glint_shade_host: download");
+        if (st == GLINT_OK) st = cuda_status(cudaEventRecord(pipe->downloaded[s], pipe->down), "glint_shade_host: download");
+    }
+    // the caller's stream completes after the last download (the download stream is in order)
+    if (st == GLINT_OK)
+        st = cuda_status(cudaStreamWaitEvent(cs, pipe->downloaded[(int)((nb - 1) % pipe->slots)], 0),
+                         "glint_shade_host: completion");
+    pipe->last_launches = launches;
     return st;
 }
 

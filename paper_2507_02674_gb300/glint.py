@@ -21,7 +21,9 @@ FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
 EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN = 0, 1, 2, 3
 MLP_PARAMS, MLP_GRAD, MLP_ADAM_M, MLP_ADAM_V = 0, 1, 2, 3
-ABI_VERSION = 6
+ABI_VERSION = 7
+HOST_INPUTS_READY = 1
+HOST_STAGED = 2
 GRID_ISOTROPIC, GRID_ANISOTROPIC = 0, 1
 WFMT_F32, WFMT_F16, WFMT_UNORM16, WFMT_UNORM8 = 0, 1, 2, 3
 DRAW_DUAL, DRAW_SINGLE, DRAW_SINGLE_OLD, DRAW_WANG2020 = 0, 1, 2, 3
@@ -106,6 +108,15 @@ def _load():
                                 ctypes.POINTER(Debug), P]
     lib.glint_normal_quantile.argtypes = [P, P, ctypes.c_long, P]
     lib.glint_reflect_probs.argtypes = [P, P, ctypes.POINTER(GBufferDesc), ctypes.POINTER(Params), P, P]
+    lib.glint_hostpipe_create.argtypes = [P, ctypes.c_long, I, ctypes.POINTER(P)]
+    lib.glint_hostpipe_destroy.argtypes = [P]
+    lib.glint_hostpipe_destroy.restype = None
+    lib.glint_hostpipe_last_launches.argtypes = [P]
+    lib.glint_hostpipe_last_launches.restype = I
+    lib.glint_hostpipe_last_in_place.argtypes = [P]
+    lib.glint_hostpipe_last_in_place.restype = I
+    lib.glint_shade_host.argtypes = [P, P, ctypes.POINTER(GBufferDesc), ctypes.POINTER(Params), P, I,
+                                     ctypes.c_uint, P]
     L, F = ctypes.c_long, ctypes.c_float
     lib.glint_mlp_param_count.restype = I
     lib.glint_mlp_create.argtypes = [P, I, L, ctypes.c_uint32, ctypes.POINTER(P)]
@@ -314,6 +325,53 @@ def shade(ctx: Context, env: Env, planes, width: int, height: int, out, seed: in
         dbg = Debug(*(_dptr(debug.get(k)) for k in ("p", "np", "vert", "w", "nroot", "counts", "lo")))
     _check(lib.glint_shade(ctx.handle, env.handle, ctypes.byref(g), ctypes.byref(p), _dptr(out),
                            ctypes.byref(dbg) if dbg is not None else None, _stream_handle(stream)))
+
+
+class HostPipe:
+    """glint_hostpipe: device staging, copy streams and events for shading
+    frames held in host memory (glint_shade_host), in bands of whole rows."""
+
+    def __init__(self, ctx: Context, band_pixels: int, slots: int = 2):
+        h = ctypes.c_void_p()
+        _check(lib.glint_hostpipe_create(ctx.handle, band_pixels, slots, ctypes.byref(h)))
+        self.handle = h
+        self.ctx = ctx
+
+    def shade(self, env: "Env", planes, width: int, height: int, out, seed: int = 0,
+              count_mode: int = COUNT_INTEGER, stream=None, tangent=None, evaluator: int = EVAL_E1,
+              e2_samples: int = 16, mlp=None, p_scratch=None, draw: int = DRAW_DUAL, gamma: float = 0.0,
+              grid: int = GRID_ISOTROPIC, rows_per_band: int = 0, inputs_ready: bool = False,
+              staged: bool = False):
+        """glint_shade_host: planes (and tangent) are HOST tensors of (npix, 4)
+        float32, pinned for overlapped copies; out a HOST (npix, 4) float32
+        tensor, complete once `stream` is; p_scratch stays on the device.
+        Pinned buffers are shaded in place (the kernels read and write host
+        memory directly) unless staged; others go through the pipe's bands.
+        inputs_ready: the host planes are final now, so staged uploads need
+        not wait for the work already enqueued on `stream`."""
+        g = _gbuffer(planes, width, height, tangent)
+        p = _params(seed, count_mode, evaluator, e2_samples, mlp, p_scratch, draw, gamma, grid)
+        _check(lib.glint_shade_host(self.handle, env.handle, ctypes.byref(g), ctypes.byref(p), _dptr(out),
+                                    rows_per_band,
+                                    (HOST_INPUTS_READY if inputs_ready else 0) | (HOST_STAGED if staged else 0),
+                                    _stream_handle(stream)))
+
+    def last_launches(self) -> int:
+        return lib.glint_hostpipe_last_launches(self.handle)
+
+    def last_in_place(self) -> bool:
+        return bool(lib.glint_hostpipe_last_in_place(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib.glint_hostpipe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def reflect_probs(ctx: Context, env: Env, planes, width: int, height: int, out, evaluator: int = EVAL_E1,

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_host_argument_checks_without_gpu(lib):
     lib.glint_last_error.restype = ctypes.c_char_p
     lib.glint_abi_version.restype = ctypes.c_int
-    assert lib.glint_abi_version() == 6
+    assert lib.glint_abi_version() == 7
     assert lib.glint_ctx_create(0, 0, 0, None) == 1
     assert b"NULL" in lib.glint_last_error()
     assert lib.glint_env_create(None, None, None) == 1
@@ -52,6 +52,12 @@ def test_host_argument_checks_without_gpu(lib):
                                     None, None) == 1
     assert lib.glint_mlp_infer(None, None, None, None) == 1
     assert lib.glint_mlp_param_count() == 64 * 64 + 64 + 64 * 64 + 64 + 64 * 16 + 16
+    lib.glint_hostpipe_create.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]
+    assert lib.glint_hostpipe_create(None, ctypes.c_long(1024), 2, None) == 1
+    lib.glint_shade_host.argtypes = [ctypes.c_void_p] * 5 + [ctypes.c_int, ctypes.c_uint, ctypes.c_void_p]
+    assert lib.glint_shade_host(None, None, None, None, None, 0, 0, None) == 1
+    assert b"NULL" in lib.glint_last_error()
     lib.glint_ctx_destroy(None)
     lib.glint_env_destroy(None)
     lib.glint_mlp_destroy(None)
+    lib.glint_hostpipe_destroy(None)

@@ -129,6 +129,7 @@ static void env_free(glint_env *e) {
     cudaFree(e->flev);
     cudaFree(e->levels);
     cudaFree(e->partial);
+    cudaFree(e->done);
     cudaFree(e->pyr);
     cudaFree(e->pyr_off4_dev);
     cudaFree(e->pyr_off_dev);
@@ -221,6 +222,8 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
     };
     alloc((void **)&e->levels, sizeof(float) * (d->K + 2), "glint_env_create: levels");
     alloc((void **)&e->partial, sizeof(float2) * e->nblk_minmax, "glint_env_create: scratch");
+    alloc((void **)&e->done, sizeof(unsigned) * 2, "glint_env_create: scratch");
+    if (st == GLINT_OK) st = cuda_status(cudaMemset(e->done, 0, sizeof(unsigned) * 2), "glint_env_create: scratch");
     alloc((void **)&e->pyr, sizeof(float) * off, "glint_env_create: pyramid");
     alloc((void **)&e->pyr_off4_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
     alloc((void **)&e->pyr_off_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");

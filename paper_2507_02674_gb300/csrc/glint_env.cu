@@ -35,40 +35,15 @@ __device__ __forceinline__ float brightness(float4 t, float scale) {
     return fmaxf(y, 0.f);
 }
 
-// Step 1: per-block min / max of the brightness into the scratch array.
-__global__ void __launch_bounds__(kNT) k_minmax(const void *__restrict__ texels, int fmt, long n, float scale,
-                                                  float2 *__restrict__ partial) {
-    float lo = INFINITY, hi = -INFINITY;
-    for (long i = (long)blockIdx.x * kNT + threadIdx.x; i < n; i += (long)gridDim.x * kNT) {
-        const float y = brightness(load_texel(texels, fmt, i), scale);
-        lo = fminf(lo, y);
-        hi = fmaxf(hi, y);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    __shared__ float2 red[kNT / 32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(lo, hi);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        float2 v = threadIdx.x < kNT / 32 ? red[threadIdx.x] : make_float2(INFINITY, -INFINITY);
-        for (int o = 16; o > 0; o >>= 1) {
-            v.x = fminf(v.x, __shfl_xor_sync(0xffffffffu, v.x, o));
-            v.y = fmaxf(v.y, __shfl_xor_sync(0xffffffffu, v.y, o));
-        }
-        if (threadIdx.x == 0) partial[blockIdx.x] = v;
-    }
-}
-
-// Step 2: lo = max(min Y, ell), hi = max(max Y, lo);
-// L_1 = 0, L_k = lo (hi/lo)^((k-1)/(K-1)) = exp(lerp(ln lo, ln hi, (k-1)/(K-1))).
-__global__ void __launch_bounds__(kNT) k_levels(const float2 *__restrict__ partial, int nblk, int K, float ell,
-                                                  float *__restrict__ levels) {
+// Step 2 from the per-block (min, max) pairs: lo = max(min Y, ell),
+// hi = max(max Y, lo); L_1 = 0, L_k = lo (hi/lo)^((k-1)/(K-1)) =
+// exp(lerp(ln lo, ln hi, (k-1)/(K-1))).  Run by one block.
+__device__ void levels_from_partials(const float2 *partial, int nblk, int K, float ell, float *levels) {
     float lo = INFINITY, hi = -INFINITY;
     for (int i = threadIdx.x; i < nblk; i += kNT) {
-        lo = fminf(lo, partial[i].x);
-        hi = fmaxf(hi, partial[i].y);
+        const float2 v = __ldcg(partial + i);  // written by other blocks: read from L2
+        lo = fminf(lo, v.x);
+        hi = fmaxf(hi, v.y);
     }
     for (int o = 16; o > 0; o >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
@@ -94,6 +69,45 @@ __global__ void __launch_bounds__(kNT) k_levels(const float2 *__restrict__ parti
         levels[K] = lo;
         levels[K + 1] = hi;
     }
+}
+
+// Steps 1 and 2: per-block min / max of the brightness into the scratch
+// array; the last block to finish (counted in *done, which it resets) turns
+// the pairs into the levels.
+__global__ void __launch_bounds__(kNT) k_minmax(const void *__restrict__ texels, int fmt, long n, float scale,
+                                                  float2 *__restrict__ partial, unsigned *__restrict__ done, int K,
+                                                  float ell, float *__restrict__ levels) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (long i = (long)blockIdx.x * kNT + threadIdx.x; i < n; i += (long)gridDim.x * kNT) {
+        const float y = brightness(load_texel(texels, fmt, i), scale);
+        lo = fminf(lo, y);
+        hi = fmaxf(hi, y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    __shared__ float2 red[kNT / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(lo, hi);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float2 v = threadIdx.x < kNT / 32 ? red[threadIdx.x] : make_float2(INFINITY, -INFINITY);
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x = fminf(v.x, __shfl_xor_sync(0xffffffffu, v.x, o));
+            v.y = fmaxf(v.y, __shfl_xor_sync(0xffffffffu, v.y, o));
+        }
+        if (threadIdx.x == 0) partial[blockIdx.x] = v;
+    }
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's pair is visible before it is counted
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    levels_from_partials(partial, gridDim.x, K, ell, levels);
+    if (threadIdx.x == 0) *done = 0u;
 }
 
 // Channel vector (R, G, B, w_1 .. w_K, 0 padding) of one texel: the fuzzy
@@ -129,81 +143,127 @@ __device__ __forceinline__ void texel_channels(float4 t, float scale, int K, con
 // writing each.  A texel of level l+1 is the solid-angle weighted mean of its
 // 2 x 2 children; the weight of a row spanning [theta0, theta1] is
 // cos theta0 - cos theta1 = 2 sin(mid) sin(half), written as a product to stay
-// accurate near the poles.
-template <bool FROM_TEXELS>
+// accurate near the poles.  With tail_to > m + nlev the last block to finish
+// (counted in *done, which it resets) builds levels m + nlev + 1 .. tail_to
+// from level m + nlev, which every block has written by then.
+template <bool FROM_TEXELS, int C4>
 __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels, int fmt, float scale, int K,
                                                    const float *__restrict__ levels, float *__restrict__ pyr,
                                                    const size_t *__restrict__ off, int m, int Ws, int Hs, int T,
-                                                   int nlev, int Cpad, int log_w) {
-    extern __shared__ float smem[];
-    float *bufA = smem;                       // T*T texels
-    float *bufB = smem + (size_t)T * T * Cpad; // (T/2)^2 texels
+                                                   int nlev, int log_w, int tail_to, unsigned *__restrict__ done) {
+    constexpr int Cpad = 4 * C4;
+    extern __shared__ float4 smem4[];
+    float4 *bufA = smem4;                        // T*T texels of C4 float4
+    float4 *bufB = smem4 + (size_t)T * T * C4;   // (T/2)^2 texels
     __shared__ float L[GLINT_MAX_K];
-    __shared__ float2 rw[16];  // row weights of the level being built
+    __shared__ float4 rw[16];  // per row of the level being built: w0, w1, 1 / (2 (w0 + w1))
     if (FROM_TEXELS) {
         if (threadIdx.x < K) L[threadIdx.x] = levels[threadIdx.x];
         __syncthreads();
     }
-    const int tiles_x = Ws / T;
-    const int tx0 = (blockIdx.x % tiles_x) * T, ty0 = (blockIdx.x / tiles_x) * T;
-    const int C4 = Cpad / 4;
+    // T is a power of two (2^nlev): tile coordinates by shifts and masks
+    const int tiles_x = Ws >> nlev;
+    const int tx0 = ((int)blockIdx.x & (tiles_x - 1)) << nlev, ty0 = ((int)blockIdx.x / tiles_x) << nlev;
     for (int i = threadIdx.x; i < T * T; i += kNT) {
-        const int lx = i % T, ly = i / T;
+        const int lx = i & (T - 1), ly = i >> nlev;
         const size_t gi = (size_t)(ty0 + ly) * Ws + (tx0 + lx);
-        float *v = bufA + (size_t)i * Cpad;
+        float4 *v = bufA + (size_t)i * C4;
         if (FROM_TEXELS) {
             float tmp[3 + GLINT_MAX_K + 1];
             texel_channels(load_texel(texels, fmt, (long)gi), scale, K, L, Cpad, log_w != 0, tmp);
-            float4 *dst = reinterpret_cast<float4 *>(pyr + off[0] + gi * Cpad);
+            float4 *dst = reinterpret_cast<float4 *>(pyr + off[0]) + gi * C4;
+#pragma unroll
             for (int c = 0; c < C4; ++c) {
                 const float4 q = make_float4(tmp[4 * c], tmp[4 * c + 1], tmp[4 * c + 2], tmp[4 * c + 3]);
                 dst[c] = q;
-                reinterpret_cast<float4 *>(v)[c] = q;
+                v[c] = q;
             }
         } else {
-            const float4 *src = reinterpret_cast<const float4 *>(pyr + off[m] + gi * Cpad);
-            for (int c = 0; c < C4; ++c) reinterpret_cast<float4 *>(v)[c] = src[c];
+            const float4 *src = reinterpret_cast<const float4 *>(pyr + off[m]) + gi * C4;
+#pragma unroll
+            for (int c = 0; c < C4; ++c) v[c] = src[c];
         }
     }
     __syncthreads();
     int cur = T;
     for (int l = 1; l <= nlev; ++l) {
-        const int nxt = cur / 2;
+        const int nxt = cur / 2, lg = nlev - l;  // nxt = 2^lg
         const int Hp = Hs >> (l - 1), Wd = Ws >> l;  // parent height, level width
         const float half = 0.5f * kPi / (float)Hp;
         const int X0 = tx0 >> l, Y0 = ty0 >> l;
         if (threadIdx.x < nxt) {
             const int Y = Y0 + threadIdx.x;
-            rw[threadIdx.x] = make_float2(sinf((2.f * Y + 0.5f) * (kPi / (float)Hp)) * sinf(half),
-                                          sinf((2.f * Y + 1.5f) * (kPi / (float)Hp)) * sinf(half));
+            const float w0 = sinf((2.f * Y + 0.5f) * (kPi / (float)Hp)) * sinf(half);
+            const float w1 = sinf((2.f * Y + 1.5f) * (kPi / (float)Hp)) * sinf(half);
+            rw[threadIdx.x] = make_float4(w0, w1, 1.f / (2.f * (w0 + w1)), 0.f);
         }
         __syncthreads();
+        float4 *lev = reinterpret_cast<float4 *>(pyr + off[m + l]);
         for (int i = threadIdx.x; i < nxt * nxt * C4; i += kNT) {
+            const int c = i % C4, t = i / C4;  // C4 is a constant: no division
+            const int x = t & (nxt - 1), y = t >> lg;
+            const float4 wr = rw[y];
+            const float w0 = wr.x, w1 = wr.y, inv = wr.z;
+            const float4 a0 = bufA[((2 * y) * cur + 2 * x) * C4 + c];
+            const float4 a1 = bufA[((2 * y) * cur + 2 * x + 1) * C4 + c];
+            const float4 b0 = bufA[((2 * y + 1) * cur + 2 * x) * C4 + c];
+            const float4 b1 = bufA[((2 * y + 1) * cur + 2 * x + 1) * C4 + c];
+            float4 r;
+            r.x = (w0 * (a0.x + a1.x) + w1 * (b0.x + b1.x)) * inv;
+            r.y = (w0 * (a0.y + a1.y) + w1 * (b0.y + b1.y)) * inv;
+            r.z = (w0 * (a0.z + a1.z) + w1 * (b0.z + b1.z)) * inv;
+            r.w = (w0 * (a0.w + a1.w) + w1 * (b0.w + b1.w)) * inv;
+            bufB[t * C4 + c] = r;
+            lev[((size_t)(Y0 + y) * Wd + X0 + x) * C4 + c] = r;
+        }
+        __syncthreads();
+        float4 *tmp = bufA;
+        bufA = bufB;
+        bufB = tmp;
+        cur = nxt;
+    }
+    if (tail_to <= m + nlev) return;
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's levels are visible before it is counted
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int Wc = Ws >> nlev, Hc = Hs >> nlev;  // level m + nlev, the parent of the first tail level
+    for (int l = m + nlev + 1; l <= tail_to; ++l) {
+        const int Wd = Wc / 2, Hd = Hc / 2;
+        const float half = 0.5f * kPi / (float)Hc;
+        const float4 *src = reinterpret_cast<const float4 *>(pyr + off[l - 1]);
+        float4 *dst = reinterpret_cast<float4 *>(pyr + off[l]);
+        for (int i = threadIdx.x; i < Wd * Hd * C4; i += kNT) {
             const int c = i % C4, t = i / C4;
-            const int x = t % nxt, y = t / nxt;
-            const int Y = Y0 + y;
-            const float w0 = rw[y].x, w1 = rw[y].y;
-            const float4 *src = reinterpret_cast<const float4 *>(bufA);
-            const float4 a0 = src[((2 * y) * cur + 2 * x) * C4 + c];
-            const float4 a1 = src[((2 * y) * cur + 2 * x + 1) * C4 + c];
-            const float4 b0 = src[((2 * y + 1) * cur + 2 * x) * C4 + c];
-            const float4 b1 = src[((2 * y + 1) * cur + 2 * x + 1) * C4 + c];
+            const int x = t % Wd, Y = t / Wd;
+            const float w0 = sinf((2.f * Y + 0.5f) * (kPi / (float)Hc)) * sinf(half);
+            const float w1 = sinf((2.f * Y + 1.5f) * (kPi / (float)Hc)) * sinf(half);
+            const float4 a0 = __ldcg(src + ((size_t)(2 * Y) * Wc + 2 * x) * C4 + c);
+            const float4 a1 = __ldcg(src + ((size_t)(2 * Y) * Wc + 2 * x + 1) * C4 + c);
+            const float4 b0 = __ldcg(src + ((size_t)(2 * Y + 1) * Wc + 2 * x) * C4 + c);
+            const float4 b1 = __ldcg(src + ((size_t)(2 * Y + 1) * Wc + 2 * x + 1) * C4 + c);
             const float inv = 1.f / (2.f * (w0 + w1));
             float4 r;
             r.x = (w0 * (a0.x + a1.x) + w1 * (b0.x + b1.x)) * inv;
             r.y = (w0 * (a0.y + a1.y) + w1 * (b0.y + b1.y)) * inv;
             r.z = (w0 * (a0.z + a1.z) + w1 * (b0.z + b1.z)) * inv;
             r.w = (w0 * (a0.w + a1.w) + w1 * (b0.w + b1.w)) * inv;
-            reinterpret_cast<float4 *>(bufB)[t * C4 + c] = r;
-            reinterpret_cast<float4 *>(pyr + off[m + l])[((size_t)Y * Wd + X0 + x) * C4 + c] = r;
+            dst[(size_t)Y * Wd * C4 + (size_t)x * C4 + c] = r;
         }
-        __syncthreads();
-        float *tmp = bufA;
-        bufA = bufB;
-        bufB = tmp;
-        cur = nxt;
+        __syncthreads();  // level l complete before it is read
+        Wc = Wd;
+        Hc = Hd;
     }
+    if (threadIdx.x == 0) *done = 0u;
 }
+
+// Upper pyramid levels whose base holds at most this many texels are built
+// by the last block of the launch that writes the base.
+constexpr long kPyrTailTexels = 2048;
 
 // Step 5a: filter sample table (Hammersley points mapped through the GGX
 // distribution of microfacet normals weighted by cos theta_h):
@@ -374,6 +434,24 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
 
 }  // namespace
 
+template <int C4>
+cudaError_t launch_pyramid(bool first, unsigned blocks, size_t smem, cudaStream_t s, const void *texels,
+                           const glint_env_desc &d, float scale, glint_env *env, int m, int Ws, int Hs, int T, int nlev,
+                           int tail_to) {
+    if (first) {
+        cudaFuncSetAttribute(k_pyramid<true, C4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_pyramid<true, C4><<<blocks, kNT, smem, s>>>(texels, d.format, scale, d.K, env->levels, env->pyr,
+                                                       env->pyr_off_dev, 0, Ws, Hs, T, nlev, d.weight_space, tail_to,
+                                                       env->done + 1);
+    } else {
+        cudaFuncSetAttribute(k_pyramid<false, C4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_pyramid<false, C4><<<blocks, kNT, smem, s>>>(nullptr, d.format, scale, d.K, env->levels, env->pyr,
+                                                        env->pyr_off_dev, m, Ws, Hs, T, nlev, 0, tail_to,
+                                                        env->done + 1);
+    }
+    return cudaGetLastError();
+}
+
 // Pyramid level offsets (float4 units) are in a small device array that
 // glint_env_create fills.
 cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s, int *launches) {
@@ -383,36 +461,37 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
     const int C4 = env->Cpad / 4;
     (void)n;
     int nl = 0;
-    k_minmax<<<env->nblk_minmax, kNT, 0, s>>>(texels, d.format, n, scale, env->partial);
-    ++nl;
-    k_levels<<<1, kNT, 0, s>>>(env->partial, env->nblk_minmax, d.K, d.ell, env->levels);
+    k_minmax<<<env->nblk_minmax, kNT, 0, s>>>(texels, d.format, n, scale, env->partial, env->done, d.K, d.ell,
+                                                env->levels);
     ++nl;
     {
-        // level 0 and the next log2 T levels from the texels, then the rest
+        // level 0 and the next log2 T levels from the texels (T = 16: many
+        // small blocks), then tiles of 32 while the base is large, and the
+        // last levels by the last block of the launch that writes their base
         int m = 0, Ws = d.width, Hs = d.height;
         bool first = true;
         while (first || m < env->M - 1) {
-            const int T = Hs < 32 ? Hs : 32;
+            const int T = first ? (Hs < 16 ? Hs : 16) : (Hs < 32 ? Hs : 32);
             int nlev = 0;
             while ((1 << nlev) < T) ++nlev;
+            const bool tail = m + nlev < env->M - 1 && (long)(Ws >> nlev) * (Hs >> nlev) <= kPyrTailTexels;
+            const int tail_to = tail ? env->M - 1 : -1;
             const size_t smem = sizeof(float) * env->Cpad * ((size_t)T * T + (size_t)(T / 2) * (T / 2));
             const unsigned blocks = (unsigned)((Ws / T) * (Hs / T));
-            if (first) {
-                cudaFuncSetAttribute(k_pyramid<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                k_pyramid<true><<<blocks, kNT, smem, s>>>(texels, d.format, scale, d.K, env->levels, env->pyr,
-                                                           env->pyr_off_dev, 0, Ws, Hs, T, nlev, env->Cpad,
-                                                           d.weight_space);
-            } else {
-                cudaFuncSetAttribute(k_pyramid<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                k_pyramid<false><<<blocks, kNT, smem, s>>>(nullptr, d.format, scale, d.K, env->levels, env->pyr,
-                                                            env->pyr_off_dev, m, Ws, Hs, T, nlev, env->Cpad, 0);
+            cudaError_t e = cudaSuccess;
+            switch (C4) {
+            case 2: e = launch_pyramid<2>(first, blocks, smem, s, texels, d, scale, env, m, Ws, Hs, T, nlev, tail_to); break;
+            case 3: e = launch_pyramid<3>(first, blocks, smem, s, texels, d, scale, env, m, Ws, Hs, T, nlev, tail_to); break;
+            case 5: e = launch_pyramid<5>(first, blocks, smem, s, texels, d, scale, env, m, Ws, Hs, T, nlev, tail_to); break;
+            default: return cudaErrorInvalidValue;
             }
+            if (e != cudaSuccess) return e;
             ++nl;
             first = false;
             m += nlev;
             Ws >>= nlev;
             Hs >>= nlev;
-            if (nlev == 0) break;
+            if (tail || nlev == 0) break;
         }
     }
     {

@@ -53,6 +53,7 @@ struct glint_env {
     int nblk_minmax = 0;
     float *levels = nullptr;   // K levels, then lo, hi
     float2 *partial = nullptr; // scratch: per-block (min, max) of the brightness
+    unsigned *done = nullptr;  // scratch: two counters of finished blocks (min/max, pyramid), 0 between updates
     float *pyr = nullptr;      // pyramid, all levels, Cpad floats per texel
     size_t pyr_off[24] = {};   // float offset of each level
     size_t *pyr_off4_dev = nullptr; // same offsets in float4 units, on the device

@@ -218,6 +218,38 @@ struct SmemInfer {
     int fg[kNT];
 };
 
+// Sink of mlp_features into row r of the staged tile: each pair of inputs is
+// rounded to BF16 and stored at its swizzled word as soon as it is computed.
+template <int K>
+struct SmemRowSink {
+    SmemInfer &sm;
+    int r;
+    __device__ __forceinline__ void group(int i, const float *v) {
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(sm.xs);
+#pragma unroll
+        for (int j = 0; j < K / 2; ++j) w32[word_at(r, i / 2 + j)] = pack_bf16(v[2 * j], v[2 * j + 1]);
+    }
+    __device__ __forceinline__ void log_prior(const float *l) {
+#pragma unroll
+        for (int k = 0; k < kOutPad; ++k) sm.lp[r * kLpStride + k] = k < K ? l[k] : 0.f;
+    }
+    __device__ __forceinline__ void tail(int i, const float *v) {
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(sm.xs);
+        w32[word_at(r, i / 2)] = pack_bf16(v[0], v[1]);
+        w32[word_at(r, i / 2 + 1)] = pack_bf16(v[2], 0.f);
+#pragma unroll
+        for (int w = 3 * K + 2; w < 32; ++w) w32[word_at(r, w)] = 0u;
+    }
+    // a background row or one past the end: zero inputs and log-priors
+    __device__ __forceinline__ void zero() {
+        uint4 *x4 = reinterpret_cast<uint4 *>(sm.xs);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x4[r * 8 + q] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int k = 0; k < kOutPad; ++k) sm.lp[r * kLpStride + k] = 0.f;
+    }
+};
+
 // Network on the staged tile: rows [0, 128) of xs/lp; p of live rows to
 // p_out[(base + r) K + k] (0 where fg[r] == 0).
 template <int NT>
@@ -313,15 +345,16 @@ __global__ void __launch_bounds__(kNT, 4) k_mlp_infer(ShadeArgs a, const __nv_bf
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long base = tile * kNT;
         const long q = base + threadIdx.x;
-        float x[kMlpIn], lp[K];
+        __syncthreads();  // the previous tile's readers are done
+        SmemRowSink<K> sink{sm, (int)threadIdx.x};
         bool fg = false;
         if (q < a.npix) {
             const float4 g0 = ldg4(a.view_n0 + q);
             fg = g0.w > 0.f;
-            if (fg) mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), x, lp);
+            if (fg) mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), sink);
         }
-        __syncthreads();  // the previous tile's readers are done
-        stage_row<K>(sm, threadIdx.x, x, lp, fg);
+        if (!fg) sink.zero();
+        sm.fg[threadIdx.x] = fg ? 1 : 0;
         __syncthreads();
         net_tile<(K > 8 ? 2 : 1)>(sm, base, a.npix, K, p_out);
     }
@@ -351,15 +384,16 @@ __global__ void __launch_bounds__(kNT, 4) k_mlp_serve(const ShadeArgs *__restric
 #pragma unroll 1
         for (long base = item.first; base < end; base += kNT) {
             const long q = base + threadIdx.x;
-            float x[kMlpIn], lp[K];
+            __syncthreads();  // the previous tile's readers are done
+            SmemRowSink<K> sink{sm, (int)threadIdx.x};
             bool fg = false;
             if (q < end) {
                 const float4 g0 = ldg4(sa.view_n0 + q);
                 fg = g0.w > 0.f;
-                if (fg) mlp_features<K>(sa, q, g0, ldg4(sa.normal_f0 + q), ldg4(sa.uv_alpha + q), x, lp);
+                if (fg) mlp_features<K>(sa, q, g0, ldg4(sa.normal_f0 + q), ldg4(sa.uv_alpha + q), sink);
             }
-            __syncthreads();
-            stage_row<K>(sm, threadIdx.x, x, lp, fg);
+            if (!fg) sink.zero();
+            sm.fg[threadIdx.x] = fg ? 1 : 0;
             __syncthreads();
             net_tile<1>(sm, base, end, K, sa.p_out);
         }
@@ -375,7 +409,8 @@ __global__ void __launch_bounds__(kNT) k_mlp_features(ShadeArgs a, uint4 *__rest
     const float4 g0 = ldg4(a.view_n0 + q);
     const bool fg = g0.w > 0.f;
     if (fg) {
-        mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), f, l);
+        ArraySink<K> sink{f, l};
+        mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), sink);
     } else {
 #pragma unroll
         for (int i = 0; i < kMlpIn; ++i) f[i] = 0.f;

@@ -329,16 +329,23 @@ __device__ __forceinline__ void filtered_weights(const ShadeArgs &a, float dx, f
     for (int k = 0; k < K; ++k) W[k] = ch[3 + k];
 }
 
-// The surrogate's inputs x[0 .. 6K+3) (the rest of the 64 are zero) and
-// log-prior lp[K] of foreground pixel q.
-template <int K>
-__device__ __forceinline__ void mlp_features(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2, float *x,
-                                             float *lp) {
+// The surrogate's inputs of foreground pixel q, handed to `sink` as they are
+// computed (so that no caller has to hold all 64 at once): sink.group(i, v)
+// receives inputs i .. i+K (E1's p_k at 0, tap t's weights at K + t K),
+// sink.log_prior(lp) the K log-priors, and sink.tail(i, s) the scalars
+// mu, sqrt a_x, sqrt a_y at 6K .. 6K+3, after which the inputs up to 64 are 0.
+template <int K, class Sink>
+__device__ __forceinline__ void mlp_features(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
+                                             Sink &sink) {
     constexpr int C4 = (3 + K + 3) / 4;
     float lr, lg, lb;
-    smooth_and_probs<K, EV_E1>(a, q, g0, g1, g2, lr, lg, lb, x);
+    float pe[K];
+    smooth_and_probs<K, EV_E1>(a, q, g0, g1, g2, lr, lg, lb, pe);
+    sink.group(0, pe);
+    float lp[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) lp[k] = logf(fmaxf(x[k], kPriorFloor));
+    for (int k = 0; k < K; ++k) lp[k] = logf(fmaxf(pe[k], kPriorFloor));
+    sink.log_prior(lp);
     const float4 tg = ldg4(a.tangent + q);
     const float tn = tg.x * g1.x + tg.y * g1.y + tg.z * g1.z;
     float tx = tg.x - tn * g1.x, ty = tg.y - tn * g1.y, tz = tg.z - tn * g1.z;
@@ -363,13 +370,33 @@ __device__ __forceinline__ void mlp_features(const ShadeArgs &a, long q, float4 
             dz += e * ((tap <= 2) ? jtz : jbz);
         }
         const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-        filtered_weights<K, C4>(a, dx * il, dy * il, dz * il, s, x + K + tap * K);
+        float w[K];
+        filtered_weights<K, C4>(a, dx * il, dy * il, dz * il, s, w);
+        sink.group(K + tap * K, w);
     }
-    x[6 * K] = mu;
-    x[6 * K + 1] = sqrtf(g2.z);
-    x[6 * K + 2] = sqrtf(g2.w);
-#pragma unroll
-    for (int i = 6 * K + 3; i < kMlpIn; ++i) x[i] = 0.f;
+    const float sc[3] = {mu, sqrtf(g2.z), sqrtf(g2.w)};
+    sink.tail(6 * K, sc);
 }
+
+// Sink into plain arrays: x[0 .. 64) and lp[0 .. K).
+template <int K>
+struct ArraySink {
+    float *x, *lp;
+    __device__ __forceinline__ void group(int i, const float *v) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) x[i + k] = v[k];
+    }
+    __device__ __forceinline__ void log_prior(const float *l) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) lp[k] = l[k];
+    }
+    __device__ __forceinline__ void tail(int i, const float *v) {
+        x[i] = v[0];
+        x[i + 1] = v[1];
+        x[i + 2] = v[2];
+#pragma unroll
+        for (int j = 6 * K + 3; j < kMlpIn; ++j) x[j] = 0.f;
+    }
+};
 
 }  // namespace glint

@@ -136,6 +136,7 @@ static void env_free(glint_env *e) {
     cudaFree(e->table);
     cudaFree(e->nvalid);
     cudaFree(e->filt);
+    cudaFree(e->filtw);
 }
 
 glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env **out) {
@@ -235,6 +236,8 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
     }
     const size_t frec_bytes = d->weight_format == GLINT_WFMT_F32 ? sizeof(float) * e->Cpad : 16u * (size_t)e->frec4;
     alloc((void **)&e->filt, frec_bytes * (size_t)e->foff[d->levels], "glint_env_create: filtered maps");
+    alloc((void **)&e->filtw, sizeof(float4) * ((d->K + 3) / 4) * (size_t)e->foff[d->levels],
+          "glint_env_create: filtered weights");
     alloc((void **)&e->flev, sizeof(int2) * d->levels, "glint_env_create: filtered level table");
     if (st == GLINT_OK)
         st = cuda_status(cudaMemcpy(e->pyr_off4_dev, off4.data(), sizeof(size_t) * M, cudaMemcpyHostToDevice),

@@ -330,7 +330,8 @@ template <int C4>
 __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, const size_t *__restrict__ off4,
                                                   int W, int H, int M, const float4 *__restrict__ table,
                                                   const int *__restrict__ nvalid, int S, const FilterLevels fl,
-                                                  float4 *__restrict__ out, int wfmt, int rec4, int K) {
+                                                  float4 *__restrict__ out, float4 *__restrict__ outw, int wfmt,
+                                                  int rec4, int K) {
     extern __shared__ float4 tab[];
     int r = 0;
     while (r + 1 < fl.nlev && (int)blockIdx.x >= fl.blk[r + 1]) ++r;
@@ -399,11 +400,24 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
     }
     if (!active || g != 0) return;
     const float inv = nv > 0 ? 1.f / (float)nv : 0.f;
+    const int kw4 = (K + 3) / 4;
+    float4 *ow = outw + ((size_t)fl.off[r] + t) * kw4;
     if (wfmt == GLINT_WFMT_F32) {
         float4 *o = out + ((size_t)fl.off[r] + t) * C4;
+        float ch[C4 * 4 + 4];
 #pragma unroll
-        for (int c = 0; c < C4; ++c)
+        for (int c = 0; c < C4; ++c) {
             o[c] = make_float4(acc[c].x * inv, acc[c].y * inv, acc[c].z * inv, acc[c].w * inv);
+            ch[4 * c] = acc[c].x * inv; ch[4 * c + 1] = acc[c].y * inv;
+            ch[4 * c + 2] = acc[c].z * inv; ch[4 * c + 3] = acc[c].w * inv;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ch[C4 * 4 + i] = 0.f;
+#pragma unroll
+        for (int c = 0; c < C4; ++c)  // weights w_k are channels 3 + k; zero past K
+            if (c < kw4)
+                ow[c] = make_float4(4 * c < K ? ch[3 + 4 * c] : 0.f, 4 * c + 1 < K ? ch[4 + 4 * c] : 0.f,
+                                    4 * c + 2 < K ? ch[5 + 4 * c] : 0.f, 4 * c + 3 < K ? ch[6 + 4 * c] : 0.f);
         return;
     }
     // compressed record: (R, G, B, 0) float32, then K weight codes
@@ -416,18 +430,28 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
     float4 *o = out + ((size_t)fl.off[r] + t) * rec4;
     o[0] = make_float4(ch[0], ch[1], ch[2], 0.f);
     uint32_t words[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    float dec[C4 * 4];  // the weights as the stored codes decode
+#pragma unroll
+    for (int k = 0; k < C4 * 4; ++k) dec[k] = 0.f;
 #pragma unroll
     for (int k = 0; k < C4 * 4 - 3; ++k) {
         if (k >= K) break;
         const float wv = fminf(fmaxf(ch[3 + k], 0.f), 1.f);
         if (wfmt == GLINT_WFMT_UNORM8) {
-            words[k / 4] |= (__float2uint_rn(wv * 255.f) & 0xffu) << (8 * (k % 4));
+            const uint32_t c8 = __float2uint_rn(wv * 255.f) & 0xffu;
+            words[k / 4] |= c8 << (8 * (k % 4));
+            dec[k] = (float)c8 * (1.f / 255.f);
         } else {
             const uint32_t c16 = (wfmt == GLINT_WFMT_F16) ? (uint32_t)__half_as_ushort(__float2half_rn(ch[3 + k]))
                                                          : (__float2uint_rn(wv * 65535.f) & 0xffffu);
             words[k / 2] |= c16 << (16 * (k % 2));
+            dec[k] = (wfmt == GLINT_WFMT_F16) ? __half2float(__ushort_as_half((unsigned short)c16))
+                                              : (float)c16 * (1.f / 65535.f);
         }
     }
+#pragma unroll
+    for (int c = 0; c < C4; ++c)
+        if (c < kw4) ow[c] = make_float4(dec[4 * c], dec[4 * c + 1], dec[4 * c + 2], dec[4 * c + 3]);
     uint4 *q = reinterpret_cast<uint4 *>(o + 1);
     for (int i = 0; i < rec4 - 1; ++i) q[i] = make_uint4(words[4 * i], words[4 * i + 1], words[4 * i + 2], words[4 * i + 3]);
 }
@@ -513,15 +537,15 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
         switch (C4) {
         case 2:
             k_filter<2><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                               d.samples, fl, out4, d.weight_format, env->frec4, d.K);
+                                               d.samples, fl, out4, env->filtw, d.weight_format, env->frec4, d.K);
             break;
         case 3:
             k_filter<3><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                               d.samples, fl, out4, d.weight_format, env->frec4, d.K);
+                                               d.samples, fl, out4, env->filtw, d.weight_format, env->frec4, d.K);
             break;
         case 5:
             k_filter<5><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
-                                               d.samples, fl, out4, d.weight_format, env->frec4, d.K);
+                                               d.samples, fl, out4, env->filtw, d.weight_format, env->frec4, d.K);
             break;
         default:
             return cudaErrorInvalidValue;

@@ -63,6 +63,8 @@ struct glint_env {
     float *filt = nullptr;     // filtered levels, concatenated: Cpad floats per texel (F32 weights) or
                                // records of frec4 x 16 bytes (compressed weights)
     int frec4 = 0;             // 16-byte units per texel record of a compressed weight format
+    float4 *filtw = nullptr;   // the filtered weights alone, ceil(K/4) float4 per filtered texel (as decoded
+                               // from the stored format): the surrogate's input look-ups read only these
     int fw[33] = {};           // width of filtered level r (height fw/2)
     long long foff[33] = {};   // first texel of level r in filt; foff[R] = total
     int2 *flev = nullptr;      // device copy of (width, first texel) per level

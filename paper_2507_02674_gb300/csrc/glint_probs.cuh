@@ -13,6 +13,7 @@ struct ShadeArgs {
     const float4 *lut;
     int lut_n;
     const float4 *filt;
+    const float4 *filtw;  // the filtered weights alone: ceil(K/4) float4 per texel
     const int2 *flev;  // (width, first texel) of each filtered level
     int wfmt;          // glint_weight_format of the filtered maps' weights
     int frec4;         // 16-byte units per texel record of a compressed format
@@ -273,6 +274,7 @@ inline ShadeArgs make_args(const glint_ctx *ctx, const glint_env *env, const gli
     a.lut = ctx->lut;
     a.lut_n = ctx->lut_n;
     a.filt = reinterpret_cast<const float4 *>(env->filt);
+    a.filtw = env->filtw;
     a.wfmt = env->d.weight_format;
     a.frec4 = env->frec4;
     a.R = env->d.levels;
@@ -311,10 +313,47 @@ constexpr int kMlpIn = 64;
 constexpr int kMlpTaps = 5;
 constexpr float kPriorFloor = 1e-6f;
 
+// The filtered weights W_1 .. W_K alone at direction (th, ph), bilinear in
+// the levels r0 and r1 blended by ft, from the weights-only copy of the
+// filtered maps (ceil(K/4) float4 per texel instead of the full record).
+// Each weight goes through the same multiply-adds, in the same order, as in
+// filtered_channels with FP32 weights, so the values are the same.
+template <int K>
+__device__ __forceinline__ void filtered_w(const ShadeArgs &a, float th, float ph, int r0, int r1, float ft,
+                                           float *W) {
+    constexpr int KW4 = (K + 3) / 4;
+    float4 cc[KW4];
+#pragma unroll
+    for (int c = 0; c < KW4; ++c) cc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int lv = 0; lv < 2; ++lv) {
+        const int2 lev = __ldg(a.flev + (lv ? r1 : r0));
+        const int Wr = lev.x, Hr = lev.x / 2;
+        const Taps tp = equirect_taps(ph * (kInvTwoPi * (float)Wr) - 0.5f, th * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
+        const float4 *base = a.filtw + (size_t)lev.y * KW4;
+        const float wl = lv ? ft : 1.f - ft;
+#pragma unroll
+        for (int c = 0; c < KW4; ++c) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * KW4 + c), v);
+            v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * KW4 + c), v);
+            v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * KW4 + c), v);
+            v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * KW4 + c), v);
+            cc[c] = fma4(wl, v, cc[c]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float4 v = cc[k / 4];
+        W[k] = (k % 4 == 0) ? v.x : (k % 4 == 1) ? v.y : (k % 4 == 2) ? v.z : v.w;
+    }
+}
+
 // W_1 .. W_K of the filtered maps at unit direction d and roughness parameter
 // s (the two levels bracketing s, bilinear in each, as E1 does for w_r).
-template <int K, int C4>
-__device__ __forceinline__ void filtered_weights(const ShadeArgs &a, float dx, float dy, float dz, float s, float *W) {
+template <int K>
+__device__ __forceinline__ void filtered_weights_only(const ShadeArgs &a, float dx, float dy, float dz, float s,
+                                                      float *W) {
     float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
     tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
     const int r0 = (int)floorf(tl);
@@ -323,10 +362,33 @@ __device__ __forceinline__ void filtered_weights(const ShadeArgs &a, float dx, f
     const float th = acosf(fminf(fmaxf(dy, -1.f), 1.f));
     float ph = atan2f(dz, dx);
     if (ph < 0.f) ph += kTwoPi;
-    float ch[C4 * 4];
-    filtered_channels<K, C4, true>(a, th, ph, r0, r1, ft, ch);
+    filtered_w<K>(a, th, ph, r0, r1, ft, W);
+}
+
+// E1's p_k (step 1 of smooth_and_probs without the colour channels), from
+// the weights-only copy: p_1 = U + V W_1, p_k = V W_k.
+template <int K>
+__device__ __forceinline__ void e1_probs(const ShadeArgs &a, float4 g0, float4 g1, float4 g2, float *p) {
+    const float mu_o = g1.x * g0.x + g1.y * g0.y + g1.z * g0.z;
+    const float rx = 2.f * mu_o * g1.x - g0.x;
+    const float ry = 2.f * mu_o * g1.y - g0.y;
+    const float rz = 2.f * mu_o * g1.z - g0.z;
+    const float mu_c = fminf(fmaxf(mu_o, 1e-4f), 1.f);
+    const float s = sqrtf(sqrtf(g2.z * g2.w));
+    const float4 tab = lut_fetch(a.lut, a.lut_n, mu_c, s);  // V, U, A, B
+    float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
+    tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
+    const int r0 = (int)floorf(tl);
+    const int r1 = min(r0 + 1, a.R - 1);
+    const float ft = tl - (float)r0;
+    const float th_r = acosf(fminf(fmaxf(ry, -1.f), 1.f));
+    float ph_r = atan2f(rz, rx);
+    if (ph_r < 0.f) ph_r += kTwoPi;
+    float W[K];
+    filtered_w<K>(a, th_r, ph_r, r0, r1, ft, W);
+    p[0] = tab.y + tab.x * W[0];
 #pragma unroll
-    for (int k = 0; k < K; ++k) W[k] = ch[3 + k];
+    for (int k = 1; k < K; ++k) p[k] = tab.x * W[k];
 }
 
 // The surrogate's inputs of foreground pixel q, handed to `sink` as they are
@@ -337,10 +399,8 @@ __device__ __forceinline__ void filtered_weights(const ShadeArgs &a, float dx, f
 template <int K, class Sink>
 __device__ __forceinline__ void mlp_features(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
                                              Sink &sink) {
-    constexpr int C4 = (3 + K + 3) / 4;
-    float lr, lg, lb;
     float pe[K];
-    smooth_and_probs<K, EV_E1>(a, q, g0, g1, g2, lr, lg, lb, pe);
+    e1_probs<K>(a, g0, g1, g2, pe);
     sink.group(0, pe);
     float lp[K];
 #pragma unroll
@@ -371,7 +431,7 @@ __device__ __forceinline__ void mlp_features(const ShadeArgs &a, long q, float4 
         }
         const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
         float w[K];
-        filtered_weights<K, C4>(a, dx * il, dy * il, dz * il, s, w);
+        filtered_weights_only<K>(a, dx * il, dy * il, dz * il, s, w);
         sink.group(K + tap * K, w);
     }
     const float sc[3] = {mu, sqrtf(g2.z), sqrtf(g2.w)};

@@ -313,6 +313,14 @@ constexpr int kMlpIn = 64;
 constexpr int kMlpTaps = 5;
 constexpr float kPriorFloor = 1e-6f;
 
+// Two float4 at a 32-byte aligned address in one 256-bit read-only load
+// (ld.global.nc.v8, sm_100 and later).
+__device__ __forceinline__ void ldg8(const float4 *p, float4 &lo, float4 &hi) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+        : "l"(p));
+}
+
 // The filtered weights W_1 .. W_K alone at direction (th, ph), bilinear in
 // the levels r0 and r1 blended by ft, from the weights-only copy of the
 // filtered maps (ceil(K/4) float4 per texel instead of the full record).
@@ -332,14 +340,32 @@ __device__ __forceinline__ void filtered_w(const ShadeArgs &a, float th, float p
         const Taps tp = equirect_taps(ph * (kInvTwoPi * (float)Wr) - 0.5f, th * (kInvPi * (float)Hr) - 0.5f, Wr, Hr);
         const float4 *base = a.filtw + (size_t)lev.y * KW4;
         const float wl = lv ? ft : 1.f - ft;
+        if constexpr (KW4 == 2) {
+            // 32-byte texels in a cudaMalloc'd buffer: every texel is 32-byte aligned
+            float4 t[4][2];
+            ldg8(base + (size_t)tp.i00 * 2, t[0][0], t[0][1]);
+            ldg8(base + (size_t)tp.i01 * 2, t[1][0], t[1][1]);
+            ldg8(base + (size_t)tp.i10 * 2, t[2][0], t[2][1]);
+            ldg8(base + (size_t)tp.i11 * 2, t[3][0], t[3][1]);
 #pragma unroll
-        for (int c = 0; c < KW4; ++c) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * KW4 + c), v);
-            v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * KW4 + c), v);
-            v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * KW4 + c), v);
-            v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * KW4 + c), v);
-            cc[c] = fma4(wl, v, cc[c]);
+            for (int c = 0; c < 2; ++c) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                v = fma4(tp.w00, t[0][c], v);
+                v = fma4(tp.w01, t[1][c], v);
+                v = fma4(tp.w10, t[2][c], v);
+                v = fma4(tp.w11, t[3][c], v);
+                cc[c] = fma4(wl, v, cc[c]);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < KW4; ++c) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * KW4 + c), v);
+                v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * KW4 + c), v);
+                v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * KW4 + c), v);
+                v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * KW4 + c), v);
+                cc[c] = fma4(wl, v, cc[c]);
+            }
         }
     }
 #pragma unroll

@@ -131,8 +131,8 @@ static void env_free(glint_env *e) {
     cudaFree(e->partial);
     cudaFree(e->done);
     cudaFree(e->pyr);
-    cudaFree(e->pyr_off4_dev);
-    cudaFree(e->pyr_off_dev);
+    cudaFree(e->pyr_rgb4_dev);
+    cudaFree(e->pyr_w4_dev);
     cudaFree(e->table);
     cudaFree(e->nvalid);
     cudaFree(e->filt);
@@ -208,12 +208,12 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
     int M = 1;
     while ((d->height >> (M - 1)) > 1) ++M;
     e->M = M;
-    size_t off = 0;
-    std::vector<size_t> off4(M);
+    size_t off4 = 0;  // float4 units
     for (int m = 0; m < M; ++m) {
-        e->pyr_off[m] = off;
-        off4[m] = off / 4;
-        off += (size_t)(d->width >> m) * (d->height >> m) * e->Cpad;
+        const size_t nm = (size_t)(d->width >> m) * (d->height >> m);
+        e->pyr_rgb4[m] = off4;
+        e->pyr_w4[m] = off4 + nm;
+        off4 += nm * (size_t)(e->Cpad / 4);
     }
     const long n = (long)d->width * d->height;
     e->nblk_minmax = (int)std::min<long>((n + 255) / 256, (long)std::max(ctx->num_sms, 1) * 8);
@@ -225,9 +225,9 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
     alloc((void **)&e->partial, sizeof(float2) * e->nblk_minmax, "glint_env_create: scratch");
     alloc((void **)&e->done, sizeof(unsigned) * 2, "glint_env_create: scratch");
     if (st == GLINT_OK) st = cuda_status(cudaMemset(e->done, 0, sizeof(unsigned) * 2), "glint_env_create: scratch");
-    alloc((void **)&e->pyr, sizeof(float) * off, "glint_env_create: pyramid");
-    alloc((void **)&e->pyr_off4_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
-    alloc((void **)&e->pyr_off_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
+    alloc((void **)&e->pyr, sizeof(float4) * off4, "glint_env_create: pyramid");
+    alloc((void **)&e->pyr_rgb4_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
+    alloc((void **)&e->pyr_w4_dev, sizeof(size_t) * M, "glint_env_create: pyramid offsets");
     alloc((void **)&e->table, sizeof(float4) * (size_t)d->levels * d->samples, "glint_env_create: filter table");
     alloc((void **)&e->nvalid, sizeof(int) * d->levels, "glint_env_create: filter table");
     if (d->weight_format != GLINT_WFMT_F32) {
@@ -240,10 +240,10 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *d, glint_env
           "glint_env_create: filtered weights");
     alloc((void **)&e->flev, sizeof(int2) * d->levels, "glint_env_create: filtered level table");
     if (st == GLINT_OK)
-        st = cuda_status(cudaMemcpy(e->pyr_off4_dev, off4.data(), sizeof(size_t) * M, cudaMemcpyHostToDevice),
+        st = cuda_status(cudaMemcpy(e->pyr_rgb4_dev, e->pyr_rgb4, sizeof(size_t) * M, cudaMemcpyHostToDevice),
                          "glint_env_create: pyramid offsets");
     if (st == GLINT_OK)
-        st = cuda_status(cudaMemcpy(e->pyr_off_dev, e->pyr_off, sizeof(size_t) * M, cudaMemcpyHostToDevice),
+        st = cuda_status(cudaMemcpy(e->pyr_w4_dev, e->pyr_w4, sizeof(size_t) * M, cudaMemcpyHostToDevice),
                          "glint_env_create: pyramid offsets");
     if (st == GLINT_OK) {
         std::vector<int2> lev(d->levels);
@@ -316,7 +316,25 @@ glint_status glint_env_export(const glint_env *env, int item, int index, void *h
     case GLINT_ENV_LEVELS: return copy(env->levels, d.K * sizeof(float));
     case GLINT_ENV_PYRAMID:
         if (index < 0 || index >= env->M) { set_error("glint_env_export: pyramid level %d out of range", index); return GLINT_ERR_INVALID_ARG; }
-        return copy_unpadded(env->pyr + env->pyr_off[index], (size_t)(d.width >> index) * (d.height >> index));
+    {
+        // colour and weights of the level, interleaved into 3 + K floats per texel
+        const size_t texels = (size_t)(d.width >> index) * (d.height >> index);
+        const size_t n = texels * env->C * sizeof(float);
+        if (bytes < n) { set_error("glint_env_export: need %zu bytes, got %zu", n, bytes); return GLINT_ERR_INVALID_ARG; }
+        const int kw4 = env->Cpad / 4 - 1;
+        std::vector<float> tmp(texels * env->Cpad);
+        const float4 *p4 = reinterpret_cast<const float4 *>(env->pyr);
+        glint_status st = cuda_status(cudaMemcpy(tmp.data(), p4 + env->pyr_rgb4[index], tmp.size() * sizeof(float),
+                                                 cudaMemcpyDeviceToHost), "glint_env_export");
+        if (st != GLINT_OK) return st;
+        const float *rgb = tmp.data(), *w = tmp.data() + 4 * texels;
+        float *dst = (float *)host_dst;
+        for (size_t t = 0; t < texels; ++t) {
+            memcpy(dst + t * env->C, rgb + 4 * t, sizeof(float) * 3);
+            memcpy(dst + t * env->C + 3, w + (size_t)4 * kw4 * t, sizeof(float) * d.K);
+        }
+        return GLINT_OK;
+    }
     case GLINT_ENV_FILTERED: {
         const size_t texels = (size_t)env->foff[d.levels];
         if (d.weight_format == GLINT_WFMT_F32) return copy_unpadded(env->filt, texels);

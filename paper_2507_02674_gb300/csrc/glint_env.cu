@@ -110,8 +110,9 @@ __global__ void __launch_bounds__(kNT) k_minmax(const void *__restrict__ texels,
     if (threadIdx.x == 0) *done = 0u;
 }
 
-// Channel vector (R, G, B, w_1 .. w_K, 0 padding) of one texel: the fuzzy
-// weights of the two levels bracketing its brightness (Eq. wkdefpractice).
+// Channel vector of one texel in the pyramid's slot order (R, G, B, 0,
+// w_1 .. w_K, 0 padding; Cpad floats): the fuzzy weights of the two levels
+// bracketing its brightness (Eq. wkdefpractice).
 __device__ __forceinline__ void texel_channels(float4 t, float scale, int K, const float *L, int Cpad, bool log_w,
                                                float *v) {
     const float R = t.x * scale, G = t.y * scale, B = t.z * scale;
@@ -124,9 +125,9 @@ __device__ __forceinline__ void texel_channels(float4 t, float scale, int K, con
     // log space (optional, Sec. 7): between L_j > 0 and L_{j+1}; linear below L_2 (L_1 = 0)
     const float tt = (log_w && j > 0) ? (logf(Y) - logf(L[j])) / (logf(L[j + 1]) - logf(L[j]))
                                       : (Y - L[j]) / (L[j + 1] - L[j]);
-    v[0] = R; v[1] = G; v[2] = B;
-    for (int c = 3; c < Cpad; ++c) {
-        const int k = c - 3;
+    v[0] = R; v[1] = G; v[2] = B; v[3] = 0.f;
+    for (int c = 4; c < Cpad; ++c) {
+        const int k = c - 4;
         float val = 0.f;
         if (k < K) {
             if (top) val = (k == K - 1) ? 1.f : 0.f;
@@ -135,6 +136,14 @@ __device__ __forceinline__ void texel_channels(float4 t, float scale, int K, con
         }
         v[c] = val;
     }
+}
+
+// Slot c of texel i of a pyramid level (float4 units of the split storage):
+// slot 0 is the colour (R, G, B, 0) at rgb4 + i, slots 1 .. C4-1 the weights
+// at w4 + i (C4 - 1) + c - 1.
+template <int C4>
+__device__ __forceinline__ size_t pyr_slot(size_t rgb4, size_t w4, size_t i, int c) {
+    return c == 0 ? rgb4 + i : w4 + i * (C4 - 1) + (c - 1);
 }
 
 // Steps 3 and 4: pyramid.  Each block takes a T x T tile of pyramid level m
@@ -148,9 +157,10 @@ __device__ __forceinline__ void texel_channels(float4 t, float scale, int K, con
 // from level m + nlev, which every block has written by then.
 template <bool FROM_TEXELS, int C4>
 __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels, int fmt, float scale, int K,
-                                                   const float *__restrict__ levels, float *__restrict__ pyr,
-                                                   const size_t *__restrict__ off, int m, int Ws, int Hs, int T,
-                                                   int nlev, int log_w, int tail_to, unsigned *__restrict__ done) {
+                                                   const float *__restrict__ levels, float4 *__restrict__ pyr,
+                                                   const size_t *__restrict__ rgb4, const size_t *__restrict__ w4,
+                                                   int m, int Ws, int Hs, int T, int nlev, int log_w, int tail_to,
+                                                   unsigned *__restrict__ done) {
     constexpr int Cpad = 4 * C4;
     extern __shared__ float4 smem4[];
     float4 *bufA = smem4;                        // T*T texels of C4 float4
@@ -171,17 +181,14 @@ __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels
         if (FROM_TEXELS) {
             float tmp[3 + GLINT_MAX_K + 1];
             texel_channels(load_texel(texels, fmt, (long)gi), scale, K, L, Cpad, log_w != 0, tmp);
-            float4 *dst = reinterpret_cast<float4 *>(pyr + off[0]) + gi * C4;
 #pragma unroll
             for (int c = 0; c < C4; ++c) {
-                const float4 q = make_float4(tmp[4 * c], tmp[4 * c + 1], tmp[4 * c + 2], tmp[4 * c + 3]);
-                dst[c] = q;
-                v[c] = q;
+                v[c] = make_float4(tmp[4 * c], tmp[4 * c + 1], tmp[4 * c + 2], tmp[4 * c + 3]);
+                pyr[pyr_slot<C4>(rgb4[0], w4[0], gi, c)] = v[c];
             }
         } else {
-            const float4 *src = reinterpret_cast<const float4 *>(pyr + off[m]) + gi * C4;
 #pragma unroll
-            for (int c = 0; c < C4; ++c) v[c] = src[c];
+            for (int c = 0; c < C4; ++c) v[c] = __ldcg(pyr + pyr_slot<C4>(rgb4[m], w4[m], gi, c));
         }
     }
     __syncthreads();
@@ -198,7 +205,6 @@ __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels
             rw[threadIdx.x] = make_float4(w0, w1, 1.f / (2.f * (w0 + w1)), 0.f);
         }
         __syncthreads();
-        float4 *lev = reinterpret_cast<float4 *>(pyr + off[m + l]);
         for (int i = threadIdx.x; i < nxt * nxt * C4; i += kNT) {
             const int c = i % C4, t = i / C4;  // C4 is a constant: no division
             const int x = t & (nxt - 1), y = t >> lg;
@@ -214,9 +220,9 @@ __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels
             r.z = (w0 * (a0.z + a1.z) + w1 * (b0.z + b1.z)) * inv;
             r.w = (w0 * (a0.w + a1.w) + w1 * (b0.w + b1.w)) * inv;
             bufB[t * C4 + c] = r;
-            lev[((size_t)(Y0 + y) * Wd + X0 + x) * C4 + c] = r;
+            pyr[pyr_slot<C4>(rgb4[m + l], w4[m + l], (size_t)(Y0 + y) * Wd + X0 + x, c)] = r;
         }
-        __syncthreads();
+        __syncthreads();  // (also: every store of the level issued before the block is counted as done)
         float4 *tmp = bufA;
         bufA = bufB;
         bufB = tmp;
@@ -235,24 +241,23 @@ __global__ void __launch_bounds__(kNT) k_pyramid(const void *__restrict__ texels
     for (int l = m + nlev + 1; l <= tail_to; ++l) {
         const int Wd = Wc / 2, Hd = Hc / 2;
         const float half = 0.5f * kPi / (float)Hc;
-        const float4 *src = reinterpret_cast<const float4 *>(pyr + off[l - 1]);
-        float4 *dst = reinterpret_cast<float4 *>(pyr + off[l]);
         for (int i = threadIdx.x; i < Wd * Hd * C4; i += kNT) {
             const int c = i % C4, t = i / C4;
             const int x = t % Wd, Y = t / Wd;
             const float w0 = sinf((2.f * Y + 0.5f) * (kPi / (float)Hc)) * sinf(half);
             const float w1 = sinf((2.f * Y + 1.5f) * (kPi / (float)Hc)) * sinf(half);
-            const float4 a0 = __ldcg(src + ((size_t)(2 * Y) * Wc + 2 * x) * C4 + c);
-            const float4 a1 = __ldcg(src + ((size_t)(2 * Y) * Wc + 2 * x + 1) * C4 + c);
-            const float4 b0 = __ldcg(src + ((size_t)(2 * Y + 1) * Wc + 2 * x) * C4 + c);
-            const float4 b1 = __ldcg(src + ((size_t)(2 * Y + 1) * Wc + 2 * x + 1) * C4 + c);
+            const size_t r4 = rgb4[l - 1], ww4 = w4[l - 1];
+            const float4 a0 = __ldcg(pyr + pyr_slot<C4>(r4, ww4, (size_t)(2 * Y) * Wc + 2 * x, c));
+            const float4 a1 = __ldcg(pyr + pyr_slot<C4>(r4, ww4, (size_t)(2 * Y) * Wc + 2 * x + 1, c));
+            const float4 b0 = __ldcg(pyr + pyr_slot<C4>(r4, ww4, (size_t)(2 * Y + 1) * Wc + 2 * x, c));
+            const float4 b1 = __ldcg(pyr + pyr_slot<C4>(r4, ww4, (size_t)(2 * Y + 1) * Wc + 2 * x + 1, c));
             const float inv = 1.f / (2.f * (w0 + w1));
             float4 r;
             r.x = (w0 * (a0.x + a1.x) + w1 * (b0.x + b1.x)) * inv;
             r.y = (w0 * (a0.y + a1.y) + w1 * (b0.y + b1.y)) * inv;
             r.z = (w0 * (a0.z + a1.z) + w1 * (b0.z + b1.z)) * inv;
             r.w = (w0 * (a0.w + a1.w) + w1 * (b0.w + b1.w)) * inv;
-            dst[(size_t)Y * Wd * C4 + (size_t)x * C4 + c] = r;
+            pyr[pyr_slot<C4>(rgb4[l], w4[l], (size_t)Y * Wd + x, c)] = r;
         }
         __syncthreads();  // level l complete before it is read
         Wc = Wd;
@@ -327,7 +332,8 @@ struct FilterLevels {
 constexpr int kFilterSplit = 2;  // threads per output texel (samples strided over them)
 
 template <int C4>
-__global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, const size_t *__restrict__ off4,
+__global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, const size_t *__restrict__ rgb4,
+                                                  const size_t *__restrict__ w4,
                                                   int W, int H, int M, const float4 *__restrict__ table,
                                                   const int *__restrict__ nvalid, int S, const FilterLevels fl,
                                                   float4 *__restrict__ out, float4 *__restrict__ outw, int wfmt,
@@ -352,9 +358,13 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
     const float rx = st * cp, ry = ct, rz = st * sp;
     const float e1x = ct * cp, e1y = -st, e1z = ct * sp;
     const float e2x = -sp, e2z = cp;
-    float4 acc[C4];
+    // colour and weights accumulated apart (the pyramid's split storage);
+    // every channel goes through the same multiply-adds as in the record layout
+    constexpr int KW4 = C4 - 1;
+    float4 accr = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 accw[KW4];
 #pragma unroll
-    for (int c = 0; c < C4; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < KW4; ++c) accw[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int k = g; k < nv; k += kFilterSplit) {
         const float4 smp = tab[k];
         const float dx = smp.x * e1x + smp.y * e2x + smp.z * rx;
@@ -375,28 +385,62 @@ __global__ void __launch_bounds__(128) k_filter(const float4 *__restrict__ pyr, 
             const float xx = ph_i * (kInvTwoPi * (float)Wm) - 0.5f;
             const float yy = th_i * (kInvPi * (float)Hm) - 0.5f;
             const Taps tp = equirect_taps(xx, yy, Wm, Hm);
-            const float4 *base = pyr + off4[m];
+            const float4 *prgb = pyr + rgb4[m], *pw = pyr + w4[m];
+            const int idx[4] = {tp.i00, tp.i01, tp.i10, tp.i11};
+            float4 tr[4], tw[4][KW4];
 #pragma unroll
-            for (int c = 0; c < C4; ++c) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                v = fma4(tp.w00, __ldg(base + (size_t)tp.i00 * C4 + c), v);
-                v = fma4(tp.w01, __ldg(base + (size_t)tp.i01 * C4 + c), v);
-                v = fma4(tp.w10, __ldg(base + (size_t)tp.i10 * C4 + c), v);
-                v = fma4(tp.w11, __ldg(base + (size_t)tp.i11 * C4 + c), v);
-                acc[c] = fma4(wl, v, acc[c]);
+            for (int j = 0; j < 4; ++j) {
+                tr[j] = __ldg(prgb + idx[j]);
+                if constexpr (KW4 == 2) {
+                    ldg8(pw + (size_t)idx[j] * 2, tw[j][0], tw[j][1]);  // 32-byte aligned (even level offsets)
+                } else {
+#pragma unroll
+                    for (int c = 0; c < KW4; ++c) tw[j][c] = __ldg(pw + (size_t)idx[j] * KW4 + c);
+                }
+            }
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            v = fma4(tp.w00, tr[0], v);
+            v = fma4(tp.w01, tr[1], v);
+            v = fma4(tp.w10, tr[2], v);
+            v = fma4(tp.w11, tr[3], v);
+            accr = fma4(wl, v, accr);
+#pragma unroll
+            for (int c = 0; c < KW4; ++c) {
+                float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+                u = fma4(tp.w00, tw[0][c], u);
+                u = fma4(tp.w01, tw[1][c], u);
+                u = fma4(tp.w10, tw[2][c], u);
+                u = fma4(tp.w11, tw[3][c], u);
+                accw[c] = fma4(wl, u, accw[c]);
             }
         }
     }
     // sum the partial means of the kFilterSplit adjacent lanes of a texel
 #pragma unroll
-    for (int c = 0; c < C4; ++c) {
+    for (int o = 1; o < kFilterSplit; o <<= 1) {
+        accr.x += __shfl_xor_sync(0xffffffffu, accr.x, o);
+        accr.y += __shfl_xor_sync(0xffffffffu, accr.y, o);
+        accr.z += __shfl_xor_sync(0xffffffffu, accr.z, o);
 #pragma unroll
-        for (int o = 1; o < kFilterSplit; o <<= 1) {
-            acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
-            acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
-            acc[c].z += __shfl_xor_sync(0xffffffffu, acc[c].z, o);
-            acc[c].w += __shfl_xor_sync(0xffffffffu, acc[c].w, o);
+        for (int c = 0; c < KW4; ++c) {
+            accw[c].x += __shfl_xor_sync(0xffffffffu, accw[c].x, o);
+            accw[c].y += __shfl_xor_sync(0xffffffffu, accw[c].y, o);
+            accw[c].z += __shfl_xor_sync(0xffffffffu, accw[c].z, o);
+            accw[c].w += __shfl_xor_sync(0xffffffffu, accw[c].w, o);
         }
+    }
+    // back to the record layout (R, G, B, W_1 .. W_K, zero padding)
+    float4 acc[C4];
+    {
+        float ch[4 * C4];
+        ch[0] = accr.x; ch[1] = accr.y; ch[2] = accr.z;
+#pragma unroll
+        for (int c = 0; c < KW4; ++c) {
+            ch[3 + 4 * c] = accw[c].x; ch[4 + 4 * c] = accw[c].y; ch[5 + 4 * c] = accw[c].z; ch[6 + 4 * c] = accw[c].w;
+        }
+        ch[4 * C4 - 1] = 0.f;
+#pragma unroll
+        for (int c = 0; c < C4; ++c) acc[c] = make_float4(ch[4 * c], ch[4 * c + 1], ch[4 * c + 2], ch[4 * c + 3]);
     }
     if (!active || g != 0) return;
     const float inv = nv > 0 ? 1.f / (float)nv : 0.f;
@@ -464,13 +508,15 @@ cudaError_t launch_pyramid(bool first, unsigned blocks, size_t smem, cudaStream_
                            int tail_to) {
     if (first) {
         cudaFuncSetAttribute(k_pyramid<true, C4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_pyramid<true, C4><<<blocks, kNT, smem, s>>>(texels, d.format, scale, d.K, env->levels, env->pyr,
-                                                       env->pyr_off_dev, 0, Ws, Hs, T, nlev, d.weight_space, tail_to,
+        k_pyramid<true, C4><<<blocks, kNT, smem, s>>>(texels, d.format, scale, d.K, env->levels,
+                                                       reinterpret_cast<float4 *>(env->pyr), env->pyr_rgb4_dev,
+                                                       env->pyr_w4_dev, 0, Ws, Hs, T, nlev, d.weight_space, tail_to,
                                                        env->done + 1);
     } else {
         cudaFuncSetAttribute(k_pyramid<false, C4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_pyramid<false, C4><<<blocks, kNT, smem, s>>>(nullptr, d.format, scale, d.K, env->levels, env->pyr,
-                                                        env->pyr_off_dev, m, Ws, Hs, T, nlev, 0, tail_to,
+        k_pyramid<false, C4><<<blocks, kNT, smem, s>>>(nullptr, d.format, scale, d.K, env->levels,
+                                                        reinterpret_cast<float4 *>(env->pyr), env->pyr_rgb4_dev,
+                                                        env->pyr_w4_dev, m, Ws, Hs, T, nlev, 0, tail_to,
                                                         env->done + 1);
     }
     return cudaGetLastError();
@@ -532,19 +578,18 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
         fl.blk[d.levels] = blk;
         const size_t smem = sizeof(float4) * (size_t)d.samples;
         const float4 *pyr4 = reinterpret_cast<const float4 *>(env->pyr);
-        const size_t *off4 = env->pyr_off4_dev;
         float4 *out4 = reinterpret_cast<float4 *>(env->filt);
         switch (C4) {
         case 2:
-            k_filter<2><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
+            k_filter<2><<<blk, 128, smem, s>>>(pyr4, env->pyr_rgb4_dev, env->pyr_w4_dev, d.width, d.height, env->M, env->table, env->nvalid,
                                                d.samples, fl, out4, env->filtw, d.weight_format, env->frec4, d.K);
             break;
         case 3:
-            k_filter<3><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
+            k_filter<3><<<blk, 128, smem, s>>>(pyr4, env->pyr_rgb4_dev, env->pyr_w4_dev, d.width, d.height, env->M, env->table, env->nvalid,
                                                d.samples, fl, out4, env->filtw, d.weight_format, env->frec4, d.K);
             break;
         case 5:
-            k_filter<5><<<blk, 128, smem, s>>>(pyr4, off4, d.width, d.height, env->M, env->table, env->nvalid,
+            k_filter<5><<<blk, 128, smem, s>>>(pyr4, env->pyr_rgb4_dev, env->pyr_w4_dev, d.width, d.height, env->M, env->table, env->nvalid,
                                                d.samples, fl, out4, env->filtw, d.weight_format, env->frec4, d.K);
             break;
         default:

@@ -55,9 +55,14 @@ struct glint_env {
     float2 *partial = nullptr; // scratch: per-block (min, max) of the brightness
     unsigned *done = nullptr;  // scratch: two counters of finished blocks (min/max, pyramid), 0 between updates
     float *pyr = nullptr;      // pyramid, all levels, Cpad floats per texel
-    size_t pyr_off[24] = {};   // float offset of each level
-    size_t *pyr_off4_dev = nullptr; // same offsets in float4 units, on the device
-    size_t *pyr_off_dev = nullptr;  // offsets in floats, on the device
+    // Pyramid level m, in float4 units of `pyr`: its n_m texels' colour (R, G, B, 0)
+    // at pyr_rgb4[m], then their weights W_1 .. W_K (Cpad/4 - 1 float4 per texel,
+    // zero past K) at pyr_w4[m] = pyr_rgb4[m] + n_m.  n_m is even, so at K = 8
+    // every texel's 32 bytes of weights are 32-byte aligned.
+    size_t pyr_rgb4[24] = {};
+    size_t pyr_w4[24] = {};
+    size_t *pyr_rgb4_dev = nullptr;  // the same offsets on the device
+    size_t *pyr_w4_dev = nullptr;
     float4 *table = nullptr;   // R x S filter samples (built once at creation)
     int *nvalid = nullptr;     // R valid sample counts
     float *filt = nullptr;     // filtered levels, concatenated: Cpad floats per texel (F32 weights) or
@@ -129,6 +134,13 @@ __device__ __forceinline__ Taps equirect_taps(float x, float y, int W, int H) {
 }
 
 __device__ __forceinline__ float4 ldg4(const float4 *p) { return __ldg(p); }
+// Two float4 at a 32-byte aligned address in one 256-bit read-only load
+// (ld.global.nc.v8, sm_100 and later).
+__device__ __forceinline__ void ldg8(const float4 *p, float4 &lo, float4 &hi) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+        : "l"(p));
+}
 
 __device__ __forceinline__ float4 fma4(float w, float4 a, float4 acc) {
     acc.x = fmaf(w, a.x, acc.x); acc.y = fmaf(w, a.y, acc.y);

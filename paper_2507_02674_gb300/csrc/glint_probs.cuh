@@ -24,7 +24,7 @@ struct ShadeArgs {
     glint_debug dbg;
     // E2: weights pyramid
     const float4 *pyr;
-    const size_t *pyr_off4;
+    const size_t *pyr_w4;  // float4 offset of each pyramid level's weights (C4 - 1 float4 per texel)
     int envW, envH, envM, e2S;
     const float *pk_in;  // EV_GIVEN: p_k per pixel (npix x K)
     float *p_out;        // k_probs: p_k per pixel (npix x K)
@@ -72,7 +72,8 @@ __device__ __forceinline__ void e2_probabilities(const ShadeArgs &a, long q, flo
     for (int k = 0; k < a.envM; ++k)
         if ((float)(a.envH >> k) * lx >= kPi) m = k;
     const int Wm = a.envW >> m, Hm = a.envH >> m;
-    const float4 *lev = a.pyr + a.pyr_off4[m];
+    constexpr int KW4 = C4 - 1;
+    const float4 *levw = a.pyr + a.pyr_w4[m];  // the level's weights W_1 .. W_K
     const float ax2 = g2.z * g2.z, ay2 = g2.w * g2.w;
     float sum_all = 0.f, sum_inv = 0.f;
     float acc[K];
@@ -105,18 +106,29 @@ __device__ __forceinline__ void e2_probabilities(const ShadeArgs &a, long q, flo
             float ex, ey;
             dir_to_texel(dx, dy, dz, Wm, Hm, ex, ey);
             const Taps tp = equirect_taps(ex, ey, Wm, Hm);
-            float w[C4 * 4];
+            float w[KW4 * 4];
+            const int idx[4] = {tp.i00, tp.i01, tp.i10, tp.i11};
+            float4 tw[4][KW4];
 #pragma unroll
-            for (int c = 0; c < C4; ++c) {
+            for (int j = 0; j < 4; ++j) {
+                if constexpr (KW4 == 2) {
+                    ldg8(levw + (size_t)idx[j] * 2, tw[j][0], tw[j][1]);  // 32-byte aligned (even level offsets)
+                } else {
+#pragma unroll
+                    for (int c = 0; c < KW4; ++c) tw[j][c] = __ldg(levw + (size_t)idx[j] * KW4 + c);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < KW4; ++c) {
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                v = fma4(tp.w00, __ldg(lev + (size_t)tp.i00 * C4 + c), v);
-                v = fma4(tp.w01, __ldg(lev + (size_t)tp.i01 * C4 + c), v);
-                v = fma4(tp.w10, __ldg(lev + (size_t)tp.i10 * C4 + c), v);
-                v = fma4(tp.w11, __ldg(lev + (size_t)tp.i11 * C4 + c), v);
+                v = fma4(tp.w00, tw[0][c], v);
+                v = fma4(tp.w01, tw[1][c], v);
+                v = fma4(tp.w10, tw[2][c], v);
+                v = fma4(tp.w11, tw[3][c], v);
                 w[4 * c] = v.x; w[4 * c + 1] = v.y; w[4 * c + 2] = v.z; w[4 * c + 3] = v.w;
             }
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc[k] = fmaf(wgt, w[3 + k], acc[k]);
+            for (int k = 0; k < K; ++k) acc[k] = fmaf(wgt, w[k], acc[k]);
         }
     }
     const float inv = 1.f / sum_all;
@@ -284,7 +296,7 @@ inline ShadeArgs make_args(const glint_ctx *ctx, const glint_env *env, const gli
     a.levels = env->levels;
     a.seed = p->seed;
     a.pyr = reinterpret_cast<const float4 *>(env->pyr);
-    a.pyr_off4 = env->pyr_off4_dev;
+    a.pyr_w4 = env->pyr_w4_dev;
     a.envW = env->d.width;
     a.envH = env->d.height;
     a.envM = env->M;
@@ -312,14 +324,6 @@ namespace glint {
 constexpr int kMlpIn = 64;
 constexpr int kMlpTaps = 5;
 constexpr float kPriorFloor = 1e-6f;
-
-// Two float4 at a 32-byte aligned address in one 256-bit read-only load
-// (ld.global.nc.v8, sm_100 and later).
-__device__ __forceinline__ void ldg8(const float4 *p, float4 &lo, float4 &hi) {
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
-        : "l"(p));
-}
 
 // The filtered weights W_1 .. W_K alone at direction (th, ph), bilinear in
 // the levels r0 and r1 blended by ft, from the weights-only copy of the

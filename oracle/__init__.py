@@ -64,6 +64,10 @@ def _load():
         lib.or_pcg4d.argtypes = [P, P]
         lib.or_xi.argtypes = [U]
         lib.or_xi.restype = D
+        lib.or_node_stream.argtypes = [ctypes.c_int, P, P]
+        lib.or_node_stream.restype = None
+        lib.or_node_uniforms.argtypes = [U, U, U, U, ctypes.c_int, P]
+        lib.or_node_uniforms.restype = None
         lib.or_ndtri.argtypes = [D]
         lib.or_ndtri.restype = D
         lib.or_eps.restype = D
@@ -119,6 +123,21 @@ def pcg4d(v) -> np.ndarray:
 
 def xi(h: int) -> float:
     return _load().or_xi(int(h) & 0xFFFFFFFF)
+
+
+def node_stream(node: int) -> tuple:
+    """(hash call index, first output word) of tree node `node`'s two uniforms."""
+    c, w = ctypes.c_int(), ctypes.c_int()
+    _load().or_node_stream(int(node), ctypes.byref(c), ctypes.byref(w))
+    return c.value, w.value
+
+
+def node_uniforms(key, seed: int, node: int) -> np.ndarray:
+    """xi1, xi2 of tree node `node` at the grid vertex keyed (x, y, level key)."""
+    out = np.zeros(2)
+    _load().or_node_uniforms(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF, int(key[2]) & 0xFFFFFFFF,
+                             int(seed) & 0xFFFFFFFF, int(node), _ptr(out))
+    return out
 
 
 def ndtri(p: float) -> float:

@@ -67,6 +67,28 @@ double or_xi(uint32_t h)
     return (2.0 * (double)(h >> 9) + 1.0) * 0x1p-24;
 }
 
+/* Where tree node `node` (heap order, 1 .. K-1) of the vertex keyed
+ * (key0, key1, key2) takes its two uniforms xi1, xi2: the hash call index
+ * (`call`, put in bits 16+ of the third key word) and the first of the two
+ * consecutive output words (`word`).  Node 1: call 1, words 1 and 2 (word 0
+ * is the root's dither); siblings 2m and 2m+1 share call m + 1, words 0, 1
+ * and 2, 3. */
+void or_node_stream(int node, int *call, int *word)
+{
+    *call = (node == 1) ? 1 : 1 + node / 2;
+    *word = (node == 1) ? 1 : (node & 1) ? 2 : 0;
+}
+
+void or_node_uniforms(uint32_t key0, uint32_t key1, uint32_t key2, uint32_t seed, int node, double xi[2])
+{
+    int call, word;
+    or_node_stream(node, &call, &word);
+    uint32_t in[4] = {key0, key1, key2 | ((uint32_t)call << 16), seed}, h[4];
+    or_pcg4d(in, h);
+    xi[0] = or_xi(h[word]);
+    xi[1] = or_xi(h[word + 1]);
+}
+
 /* Standard normal quantile Phi^-1(p) in FP64.  Starting value from
  * Abramowitz & Stegun 26.2.23 (absolute error < 4.5e-4), refined by Newton
  * steps on Phi(x) = erfc(-x/sqrt 2)/2 from the C library. */
@@ -1096,14 +1118,9 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
         tree_rec(t, node + 1, N, dN);
         return;
     }
-    /* the node's two uniforms: node 1 takes words 1 and 2 of hash call 1
-     * (word 0 is the dither); siblings 2m and 2m+1 share hash call m + 1,
-     * words 0, 1 and 2, 3 respectively */
-    uint32_t call = (node == 1) ? 1u : 1u + (uint32_t)node / 2u;
-    uint32_t in[4] = {t->key0, t->key1, t->key2 | (call << 16), t->seed}, h[4];
-    or_pcg4d(in, h);
-    int w0 = (node == 1) ? 1 : (node & 1) ? 2 : 0;
-    double xi1 = or_xi(h[w0]), xi2 = or_xi(h[w0 + 1]);
+    double xi[2];
+    or_node_uniforms(t->key0, t->key1, t->key2, t->seed, node, xi);
+    double xi1 = xi[0], xi2 = xi[1];
     double PL = t->P[2 * node], PR = t->P[2 * node + 1];
     double p = (PL + PR > 0.0) ? PL / (PL + PR) : 0.0;
     double e_P = t->tie[0], e_z = t->tie[1], e_f = t->tie[2], d_a = t->tie[3], a_P = t->tie[4];

@@ -187,3 +187,49 @@ def test_pcg4d_statistics(orc):
         b = orc.pcg4d([i ^ 1, 7, 9, 11])
         flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b)))
     assert 48 <= np.mean(flips) <= 80
+
+
+@pytest.mark.parametrize("K", [2, 4, 8, 16])
+def test_node_uniforms_use_each_hash_word_once(orc, K):
+    """Reading of the per-vertex seed (the paper stores one random seed per grid
+    vertex and names no per-node stream): node 1 takes words 1, 2 of hash call 1
+    beside the root's dither (word 0), siblings 2m and 2m+1 share call m + 1
+    (words 0, 1 and 2, 3).  Within one tree no (call, word) serves two uniforms,
+    so every draw's xi1 and xi2 are distinct, independent hash words; a K = 8
+    tree needs 4 calls."""
+    used = {(1, 0)}  # the root's dither
+    calls = set()
+    for n in range(1, K):
+        call, word = orc.node_stream(n)
+        assert word in (0, 1, 2) and word + 1 <= 3
+        for w in (word, word + 1):
+            assert (call, w) not in used, (n, call, w)
+            used.add((call, w))
+        calls.add(call)
+        if n >= 2:
+            assert call == 1 + n // 2 and word == (2 if n & 1 else 0)
+    assert len(used) == 2 * (K - 1) + 1
+    assert sorted(calls) == list(range(1, K // 2 + 1))  # K/2 calls per tree (4 at K = 8)
+    # the helper reads those words of that call
+    key, seed = (12, -7, 5 | 0x8000), 99
+    for n in range(1, K):
+        call, word = orc.node_stream(n)
+        h = orc.pcg4d([key[0] & 0xFFFFFFFF, key[1] & 0xFFFFFFFF, key[2] | (call << 16), seed])
+        xi = orc.node_uniforms(key, seed, n)
+        assert xi[0] == orc.xi(int(h[word])) and xi[1] == orc.xi(int(h[word + 1]))
+
+
+def test_sibling_uniforms_are_uncorrelated(orc):
+    """The two siblings that share a hash call draw from disjoint words: over
+    many vertices their xi1 are uniform and uncorrelated, as are each node's xi1
+    and xi2."""
+    n = 4096
+    rng = np.random.default_rng(5)
+    keys = rng.integers(-5000, 5000, size=(n, 2))
+    u = np.array([[*orc.node_uniforms((int(a), int(b), 7), 3, 2), *orc.node_uniforms((int(a), int(b), 7), 3, 3)]
+                  for a, b in keys])
+    c = np.corrcoef(u.T)
+    assert np.max(np.abs(c - np.eye(4))) < 0.06
+    for j in range(4):
+        hist, _ = np.histogram(u[:, j], bins=16, range=(0, 1))
+        assert np.sum((hist - n / 16) ** 2 / (n / 16)) < stats.chi2.ppf(0.9999, 15)

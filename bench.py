@@ -548,7 +548,7 @@ def run_ours(args):
     d2h = host_out.numel() * 4
     pipe = glint.HostPipe(ctx, band_pixels=WIDTH * E2E_BAND_ROWS, slots=-(-HEIGHT // E2E_BAND_ROWS))
     frs = [fr, render.Frame(ctx, env, cfg, device=dev)]
-    side = torch.cuda.Stream(dev)
+    side = torch.cuda.Stream(dev, priority=-1)  # the next map update runs ahead of queued shading blocks
     env_ready = [torch.cuda.Event() for _ in range(2)]
     env_free = [torch.cuda.Event() for _ in range(2)]
 

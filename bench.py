@@ -116,21 +116,23 @@ def _source_sha() -> str:
 
 
 def _profile_traffic():
-    """DRAM bytes per shade launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+    """DRAM bytes per shade launch and the fraction of issue slots used, from
+    the committed ncu summary, if it was taken on the current kernel source."""
     try:
         txt = open(PROFILE_SUMMARY).read()
     except OSError:
-        return None, None
-    sha = traffic = None
+        return None, None, None
+    sha = traffic = issue = None
     for line in txt.splitlines():
         if line.startswith("kernel_source_sha:"):
             sha = line.split(":", 1)[1].strip()
         if line.startswith("dram_bytes_per_launch:"):
             traffic = float(line.split(":", 1)[1].strip())
+        if line.startswith("issue_active_frac:"):
+            issue = float(line.split(":", 1)[1].strip())
     if sha != _source_sha():
-        return None, sha
-    return traffic, sha
+        return None, None, sha
+    return traffic, issue, sha
 
 
 def max_over_ranks(x: float, dist=None, device=None) -> float:
@@ -603,7 +605,7 @@ def run_ours(args):
         algo = MUFU_PER_DRAW * 6 * (K - 1) * npix
         achieved = algo / shade_avg_s / 1e12
         peak = n_sm * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e12
-        traffic, _ = _profile_traffic()
+        traffic, issue_frac, _ = _profile_traffic()
         result = {
             "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -620,6 +622,9 @@ def run_ours(args):
             "roofline": {"kernel": "k_shade<8,integer>", "bound": "alu", "achieved": round(achieved, 4),
                          "peak": round(peak, 4), "unit": "TMUFU/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic,
+                         "issue_active_frac": issue_frac,
+                         "bound_note": ("instruction issue bounds the kernel: issue_active_frac is the share of "
+                                        "issue slots used (ncu, same kernel source); the MUFU fraction is lower"),
                          "basis": (f"{MUFU_PER_DRAW} transcendentals x 6 samples x {K - 1} draws = "
                                    f"{MUFU_PER_DRAW * 6 * (K - 1)} per pixel; peak = {n_sm} SMs x "
                                    f"{MUFU_PER_SM_CLK} MUFU/clk x {sm_mhz:.0f} MHz (median SM clock sampled "

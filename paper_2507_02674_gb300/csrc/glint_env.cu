@@ -3,11 +3,15 @@
 // Functions", Eq. wkdefpractice, "Integrated NDF" Eq. rtiblndf; Sec. 3.4
 // Eq. rtibl).
 //
-// Data layout in HBM: every per-texel channel vector (R, G, B, w_1..w_K) is
-// stored contiguously and padded to Cpad = 4 ceil((3+K)/4) floats, so one texel
-// is Cpad/4 aligned float4 loads (3 for K = 8).  The pyramid levels are
-// concatenated; the filtered maps are R levels of W_r/2 x W_r texels of the
-// same layout, also concatenated.  Brightness min/max go through a small per-block scratch array.
+// Data layout in HBM.  Pyramid: per level, the texels' colour (R, G, B, 0),
+// one float4 each, then their weights w_1..w_K, Cpad/4 - 1 float4 each
+// (Cpad = 4 ceil((3+K)/4); 32 bytes at K = 8, read with one 256-bit load);
+// levels concatenated.  Filtered maps: R levels of W_r/2 x W_r texels, each
+// texel the record (R, G, B, w_1..w_K, 0 padding) of Cpad floats (or an fp32
+// colour and K codes for a compressed format), levels concatenated; beside
+// them a weights-only copy (Cpad/4 - 1 float4 a texel, the weights as stored).
+// Brightness min/max go through a small per-block scratch array and a
+// finished-block counter.
 #include <stdio.h>
 
 #include "glint_internal.cuh"

@@ -285,23 +285,6 @@ __device__ __forceinline__ void net_tile(const SmemInfer &sm, long base, long n,
     }
 }
 
-// Write one row of inputs (64 floats, rounded to BF16) and its log-prior.
-template <int K>
-__device__ __forceinline__ void stage_row(SmemInfer &sm, int r, const float *x, const float *lp, bool fg) {
-    uint4 *x4 = reinterpret_cast<uint4 *>(sm.xs);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (fg)
-            v = make_uint4(pack_bf16(x[8 * q], x[8 * q + 1]), pack_bf16(x[8 * q + 2], x[8 * q + 3]),
-                           pack_bf16(x[8 * q + 4], x[8 * q + 5]), pack_bf16(x[8 * q + 6], x[8 * q + 7]));
-        x4[r * 8 + (q ^ (r & 7))] = v;
-    }
-#pragma unroll
-    for (int k = 0; k < kOutPad; ++k) sm.lp[r * kLpStride + k] = (fg && k < K) ? lp[k] : 0.f;
-    sm.fg[r] = fg ? 1 : 0;
-}
-
 // p of given inputs: x (n x 64 BF16, row-major), lp (n x K).  Persistent.
 template <int NT>
 __global__ void __launch_bounds__(kNT) k_mlp_forward(const uint4 *__restrict__ x, const float *__restrict__ lp, long n,

@@ -299,7 +299,8 @@ void glint_hostpipe_destroy(glint_hostpipe *pipe);
  * E2 and the MLP evaluator; it is uploaded whenever non-NULL); out_rgba_host:
  * HOST, width*height float4.  Pinned host memory (cudaHostAlloc or
  * cudaHostRegister) lets the copies overlap; pageable memory gives the same
- * results with copies that block the calling thread.  params as glint_shade
+ * results with copies that block the calling thread (device buffers work too:
+ * the staged copies take their direction from the addresses).  params as glint_shade
  * (params->p_scratch stays a DEVICE buffer of width*height*K floats for the
  * MLP and GIVEN evaluators; band b uses its rows of it).  rows_per_band: 0
  * picks about an eighth of the frame, capped by the pipe's band_pixels; a

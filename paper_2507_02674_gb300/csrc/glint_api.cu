@@ -671,7 +671,7 @@ glint_status glint_shade_host(glint_hostpipe *pipe, const glint_env *env, const 
         for (int i = 0; i < 5 && st == GLINT_OK; ++i) {
             if (i == 4 && !with_tangent) break;
             st = cuda_status(cudaMemcpyAsync(pipe->plane(s, i), src[i] + 4 * off, sizeof(float4) * n,
-                                             cudaMemcpyHostToDevice, pipe->up), "glint_shade_host: upload");
+                                             cudaMemcpyDefault, pipe->up), "glint_shade_host: upload");
         }
         if (st == GLINT_OK) st = cuda_status(cudaEventRecord(pipe->uploaded[s], pipe->up), "glint_shade_host: upload");
         // shade once the planes are there and the slot's previous output has left
@@ -693,7 +693,7 @@ glint_status glint_shade_host(glint_hostpipe *pipe, const glint_env *env, const 
         // download once shaded
         if (st == GLINT_OK) st = cuda_status(cudaStreamWaitEvent(pipe->down, pipe->shaded[s], 0), "glint_shade_host: download");
         if (st == GLINT_OK)
-            st = cuda_status(cudaMemcpyAsync(out_host + 4 * off, outb, sizeof(float4) * n, cudaMemcpyDeviceToHost,
+            st = cuda_status(cudaMemcpyAsync(out_host + 4 * off, outb, sizeof(float4) * n, cudaMemcpyDefault,
                                              pipe->down), "glint_shade_host: download");
         if (st == GLINT_OK) st = cuda_status(cudaEventRecord(pipe->downloaded[s], pipe->down), "glint_shade_host: download");
     }

@@ -117,3 +117,16 @@ def test_sizes_the_pipe_cannot_hold_are_rejected(gl):
         glint.HostPipe(ctx, band_pixels=1024, slots=17)
     pipe.shade(fr.env, host, W, 0, out)  # an empty frame is a no-op
     assert pipe.last_launches() == 0
+
+
+def test_device_buffers_are_staged_and_equal(gl):
+    """Buffers that are not host memory at all (device tensors) go through the
+    staged path, whose copies take their direction from the addresses."""
+    glint, render, torch, ctx, fr, gb, net, host, tan = gl
+    planes = [p.cuda() for p in host]
+    out = torch.zeros(W * H, 4, device="cuda")
+    pipe = glint.HostPipe(ctx, band_pixels=W * 64, slots=2)
+    pipe.shade(fr.env, planes, W, H, out, seed=33)
+    torch.cuda.synchronize()
+    assert not pipe.last_in_place()
+    assert torch.equal(out.cpu(), _direct(torch, fr, host, tan, 33, glint.EVAL_E1, None))

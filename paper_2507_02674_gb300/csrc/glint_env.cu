@@ -539,13 +539,15 @@ cudaError_t glint_launch_env(glint_env *env, const void *texels, cudaStream_t s,
                                                 env->levels);
     ++nl;
     {
-        // level 0 and the next log2 T levels from the texels (T = 16: many
-        // small blocks), then tiles of 32 while the base is large, and the
-        // last levels by the last block of the launch that writes their base
+        // level 0 and the next log2 T levels from the texels (T = 32), then
+        // tiles of 32 while the base is large, and the last levels by the last
+        // block of the launch that writes their base (1024 x 512 map: one
+        // launch, levels 0-5 by tiles and 6-9 by the last block; 16 x 16
+        // tiles left a 64 x 32 base whose five serial levels cost more)
         int m = 0, Ws = d.width, Hs = d.height;
         bool first = true;
         while (first || m < env->M - 1) {
-            const int T = first ? (Hs < 16 ? Hs : 16) : (Hs < 32 ? Hs : 32);
+            const int T = Hs < 32 ? Hs : 32;
             int nlev = 0;
             while ((1 << nlev) < T) ++nlev;
             const bool tail = m + nlev < env->M - 1 && (long)(Ws >> nlev) * (Hs >> nlev) <= kPyrTailTexels;

@@ -302,10 +302,10 @@ void glint_hostpipe_destroy(glint_hostpipe *pipe);
  * results with copies that block the calling thread (device buffers work too:
  * the staged copies take their direction from the addresses).  params as glint_shade
  * (params->p_scratch stays a DEVICE buffer of width*height*K floats for the
- * MLP and GIVEN evaluators; band b uses its rows of it).  rows_per_band: 0
- * picks about an eighth of the frame, capped by the pipe's band_pixels; a
- * band of more pixels than band_pixels, or a row wider than it, is
- * GLINT_ERR_INVALID_ARG.  The uploads start after the work enqueued on
+ * MLP and GIVEN evaluators; band b uses its rows of it).  rows_per_band (staged
+ * frames only; a frame shaded in place ignores it): 0 picks about an eighth of
+ * the frame, capped by the pipe's band_pixels; a band of more pixels than
+ * band_pixels, or a row wider than it, is GLINT_ERR_INVALID_ARG.  The uploads start after the work enqueued on
  * `stream` before the call, unless flags holds GLINT_HOST_INPUTS_READY: the
  * host planes are final when the call is made, and the uploads start at once,
  * alongside that work (an environment update enqueued just before, say); the

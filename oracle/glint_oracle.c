@@ -884,8 +884,8 @@ static void grid_vertices(float u, float v, int l, int64_t vx[3], int64_t vy[3],
     lattice_vertices(ldexpf(u, -l), ldexpf(v, -l), vx, vy, b);
 }
 
-/* Anisotropic grid (SURVEY NEXT-1 reading of Sec. 3.3's "anisotropic grids":
- * the footprint's length, anisotropy factor and orientation).  The footprint
+/* Anisotropic grid (our reading of the anisotropic grids Sec. 3.3 builds on:
+ * cells over the footprint's length, anisotropy factor and orientation).  The footprint
  * ellipse of the uv Jacobian J = [du/dx du/dy; dv/dx dv/dy] has eigenvalues
  * lam1 >= lam2 of J J^T = [a b; b c].  Coordinates: the level L = l0 + fl
  * (log2 sqrt|P|, as grid_level), the anisotropy A = (log2 lam1 - log2 |P|)/2

@@ -1,5 +1,5 @@
 """Pins of the oracle's anisotropic grid (the footprint's level, anisotropy and
-orientation cell of Sec. 3.3): weights form a partition of
+orientation cell, our reading of the anisotropic grids of Sec. 3.3): weights form a partition of
 unity; a round footprint reduces to the isotropic grid's two levels and
 lattices; an elongated, rotated footprint lands in the cell its axes and angle
 predict; counts conserve N; the estimator averages to the smooth radiance.

@@ -83,14 +83,16 @@ def test_tables(gl, orc):
     assert np.max(np.abs(g - o) / np.maximum(np.abs(o), 1e-3)) < 2e-5
 
 
-@pytest.mark.parametrize("which", ["tiny", "hdr"])
-@pytest.mark.parametrize("log_weights", [False, True])
-def test_env_levels_weights_pyramid(gl, orc, which, log_weights):
+@pytest.mark.parametrize("which,log_weights,K", [("tiny", False, 8), ("tiny", True, 8), ("hdr", False, 8),
+                                                 ("hdr", True, 8), ("hdr", False, 4), ("hdr", False, 16)])
+def test_env_levels_weights_pyramid(gl, orc, which, log_weights, K):
     """Levels, fuzzy weights (linear, and log space as Sec. 7 compares) and the
-    pyramid; log-space weights carry FP32 logarithms (abs error ~1e-6)."""
+    pyramid; log-space weights carry FP32 logarithms (abs error ~1e-6).  K = 4,
+    8 and 16 cover the pyramid's three storage widths (colour, then 1, 2 or 4
+    float4 of weights per texel)."""
     glint, render, ctx, torch = gl
     env = synth.env_tiny(0) if which == "tiny" else synth.env_hdr(seed=3, W=256, H=128)
-    mp = MethodParams(K=8, Wo=64, log_weights=log_weights)
+    mp = MethodParams(K=K, Wo=64, log_weights=log_weights)
     fr = render.Frame(ctx, env, _cfg(glint, mp))
     fr.update_env()
     torch.cuda.synchronize()

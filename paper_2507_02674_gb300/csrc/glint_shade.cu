@@ -13,12 +13,13 @@
 //      p, its complement q (both from the subtree masses), log2 p and the log2
 //      of the small-p biased complement, each logarithm taken of whichever of
 //      p, q is below 1/2 -- computed once per pixel, reused by all six samples;
-//   4. six samples x (K-1) dual-gated draws: a pcg4d hash of (vertex, level,
-//      node, seed) gives the uniforms, two hardware exp2 give the gate
-//      probabilities, and the normal quantile is evaluated only when the
-//      Gaussian branch is taken;
-// 64 registers per thread (8 blocks of 128 threads per SM) measured fastest.
+//   4. six samples x (K-1) dual-gated draws: pcg4d hashes of (vertex, level,
+//      call, seed) give the uniforms (one call for the root's dither and node
+//      1, one per pair of sibling nodes), two hardware exp2 give the gate
+//      probabilities, and the Gaussian (normal quantile) is computed for every
+//      node, the gates selecting among the outcomes without branches;
 //   5. L^_o = L_o sum_k L_k M_k / (N_P sum_k L_k p_k).
+// 80 registers per thread (6 blocks of 128 threads per SM) measured fastest.
 #include "glint_shade_pixel.cuh"
 
 using namespace glint;

@@ -157,7 +157,10 @@ glint_status glint_env_create(glint_ctx *ctx, const glint_env_desc *desc, glint_
  *   5. for each of R roughness levels the map filtered with the kernel
  *      p_{L_i} ~ D(h) under n = v = r (Sec. 3.4 Eq. rtibl, Sec. 4
  *      Eq. rtiblndf) by filtered importance sampling with S Hammersley samples.
- * The texels must not change until the stream has passed this work. */
+ * The texels must not change until the stream has passed this work.  Two
+ * updates of one environment must not overlap on the GPU (they share its
+ * buffers and its finished-block counters); order them on one stream, or
+ * give each frame in flight its own environment. */
 glint_status glint_env_update(glint_env *env, const void *texels, void *stream);
 
 /* Copies the K radiance levels to host memory (K floats).  Synchronous. */
@@ -316,7 +319,8 @@ void glint_hostpipe_destroy(glint_hostpipe *pipe);
  * out_rgba_host is complete when `stream` is.  The host buffers must stay
  * valid and unchanged until then.  Calls on one pipe are ordered through its
  * staging: a call's uploads wait until the previous call's shading has read
- * the slots they overwrite.  Unknown flag bits are GLINT_ERR_INVALID_ARG. */
+ * the slots they overwrite; one host thread at a time may call with a given
+ * pipe.  Unknown flag bits are GLINT_ERR_INVALID_ARG. */
 #define GLINT_HOST_INPUTS_READY 1u
 #define GLINT_HOST_STAGED 2u /* stage through the pipe even when the buffers could be used in place */
 glint_status glint_shade_host(glint_hostpipe *pipe, const glint_env *env, const glint_gbuffer *host_gbuf,

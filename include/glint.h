@@ -587,11 +587,14 @@ glint_status glint_normal_quantile(const float *p, float *z, long n, void *strea
  * written as L_1 .. L_K, lo, hi (the layout glint_env_levels and
  * GLINT_ENV_LOHI report).  Work is enqueued on `stream` of device `device`.
  * The block partials of the reduction go to a fixed array inside the library
- * that every GPU loading it holds until the process exits.  The first call on a
- * device looks up that array's device address; make the first call before any
- * stream capture.  All calls on a device share the array and it keeps the last
- * call's contents; calls whose work overlaps on the GPU race on it, so issue
- * them on one stream or order them. */
+ * that every GPU loading it holds until the process exits.  Every call looks
+ * up that array's address in the calling thread's current context for
+ * `device` (a host query that allocates nothing), so the call stays correct
+ * after cudaDeviceReset or when a host makes its own context current; the
+ * first call on a device may load the library's module there, so make it
+ * before any stream capture.  All calls in a context share the array and it
+ * keeps the last call's contents; calls whose work overlaps on the GPU race on
+ * it, so issue them on one stream or order them. */
 glint_status glint_env_levels_noalloc(int device, const void *texels, int width, int height, int format,
                                       int scale_log2, int K, float ell, float *levels_out, void *stream);
 

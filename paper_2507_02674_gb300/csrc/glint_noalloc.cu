@@ -12,8 +12,6 @@
 // contents.  Nothing in it needs to start at zero: each block overwrites its
 // own slot before the levels kernel of the same call reads it.  Calls whose
 // work overlaps on the GPU (e.g. on two streams at once) race on the array.
-#include <mutex>
-
 #include "glint_internal.cuh"
 
 using namespace glint;
@@ -22,15 +20,9 @@ namespace {
 
 constexpr int kNT = 256;
 constexpr int kMaxBlocks = GLINT_NOALLOC_MAX_BLOCKS;
-constexpr int kMaxDevices = 64;
 
 // Scratch: one (min, max) pair per reduction block, kMaxBlocks * 8 bytes.
 static __device__ __align__(256) float2 g_noalloc_partial[kMaxBlocks];
-
-// Device address of g_noalloc_partial on each device, looked up once per
-// device (with that device current) by the first call on it.
-float2 *g_partial_addr[kMaxDevices] = {};
-std::mutex g_partial_mutex;
 
 __device__ __forceinline__ float4 load_texel_na(const void *texels, int fmt, long i) {
     if (fmt == GLINT_FMT_RGBA16F) {
@@ -98,20 +90,16 @@ __global__ void __launch_bounds__(kNT) k_levels_na(const float2 *__restrict__ pa
     }
 }
 
-// Device address of the scratch array on the current device `dev`.
-glint_status scratch_address(int dev, float2 **out) {
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("glint_env_levels_noalloc: device %d beyond the %d supported", dev, kMaxDevices);
-        return GLINT_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_partial_mutex);
-    if (!g_partial_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
-        if (e != cudaSuccess) return cuda_status(e, "glint_env_levels_noalloc: cudaGetSymbolAddress");
-        g_partial_addr[dev] = reinterpret_cast<float2 *>(p);
-    }
-    *out = g_partial_addr[dev];
+// Device address of the scratch array in the current context.  In host code
+// g_noalloc_partial names a host-side stand-in, not device memory, so the
+// address is asked of the runtime on every call: a cached address would go
+// stale when the module is loaded again (after cudaDeviceReset, or in another
+// context that a plug-in host makes current), and the query allocates nothing.
+glint_status scratch_address(float2 **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+    if (e != cudaSuccess) return cuda_status(e, "glint_env_levels_noalloc: cudaGetSymbolAddress");
+    *out = reinterpret_cast<float2 *>(p);
     return GLINT_OK;
 }
 
@@ -159,7 +147,7 @@ extern "C" glint_status glint_env_levels_noalloc(int device, const void *texels,
         if (st != GLINT_OK) return st;
     }
     float2 *partial = nullptr;
-    glint_status st = scratch_address(device, &partial);
+    glint_status st = scratch_address(&partial);
     if (st == GLINT_OK) {
         const long n = (long)width * height;
         const int nblk = (int)((n + kNT - 1) / kNT < kMaxBlocks ? (n + kNT - 1) / kNT : kMaxBlocks);

@@ -59,26 +59,29 @@ struct NodeParams {
 // returns n (nbar = N - n).  Regions of xi1 (same as the printed masks):
 // [0, P_{n=N}) -> N;  [P_{n=N}, P_{n=N} + P_{n=1}) -> 1;
 // 1 - xi1 <= P_{nbar=N} + P_{nbar=1} -> 0;  otherwise the clamped, rounded
-// Gaussian when N > 1, else 0.  Evaluated without branches (the Gaussian is
-// computed for every lane and the gates select), so that a warp whose lanes
-// take different regions does not run the paths one after another.
+// Gaussian when N > 1, else 0.  For N >= 2 the single-trial terms vanish, so
+// P_{n=N} = p^N and P_{nbar=N} = (1 - c p)^(N/c); for N = 1 the draw is one
+// Bernoulli trial with probability p.  Evaluated without branches (the
+// Gaussian is computed for every lane and the gates select), so that a warp
+// whose lanes take different regions does not run the paths one after
+// another.  The Gaussian N(mu, sigma^2), mu = 1 + (N - 2) p, is rounded half
+// up as floor(sigma z + (mu + 1/2)).
 __device__ __forceinline__ uint32_t draw_integer(uint32_t N, const NodeParams &np, uint32_t h1, uint32_t h2) {
     const float xi1 = hash_uniform(h1);
     const float xi1c = hash_uniform_complement(h1);
     const float Nf = __uint2float_rn(N);
-    const float N2 = fmaxf(2.f, Nf);
-    const float a = (N >= 2u) ? 1.f : 0.f;
-    const float b = (N == 1u) ? 1.f : 0.f;
-    const float Pall = a * fast_exp2(N2 * np.lp);
-    const float T1 = Pall + b * np.p;
-    const float Sneg = a * fast_exp2(N2 * np.lq) + b * np.q;
-    const float mu = 1.f + (N2 - 2.f) * np.p;
-    const float sigma = fast_sqrt((N2 - 2.f) * np.p * np.q);
+    const float m = fmaxf(Nf - 2.f, 0.f);  // N - 2 trials left to the Gaussian (0 below N = 2)
+    const float N2 = m + 2.f;
+    const bool many = N >= 2u;
+    const float Pall = many ? fast_exp2(N2 * np.lp) : 0.f;
+    const float T1 = many ? Pall : np.p;
+    const float Sneg = fast_exp2(N2 * np.lq);  // decides only for N >= 2
+    const float muh = fmaf(m, np.p, 1.5f);
+    const float sigma = fast_sqrt(m * np.p * np.q);
     const float z = normal_quantile(hash_uniform(h2));
-    float G = floorf(fmaf(sigma, z, mu) + 0.5f);
-    G = fminf(fmaxf(G, 1.f), kMaxCount);
+    const float G = fminf(fmaxf(floorf(fmaf(sigma, z, muh)), 1.f), kMaxCount);
     uint32_t r = min((uint32_t)G, N - 1u);
-    r = (xi1c <= Sneg || N < 2u) ? 0u : r;
+    r = (xi1c <= Sneg || !many) ? 0u : r;
     r = (xi1 < T1) ? 1u : r;
     return (xi1 < Pall) ? N : r;
 }
@@ -113,7 +116,10 @@ __device__ __forceinline__ void draw_real(float N, const NodeParams &np, uint32_
 
 // Node parameters of a binary split with probabilities p (left) and q = 1 - p
 // (right): log2 p and log2 of the small-p biased complement, each logarithm
-// taken of whichever of p, q is the smaller (1 - x near 1 is not accurate).
+// taken of whichever of p, q is the smaller (1 - x near 1 is not accurate):
+// log2 of the smaller one by the hardware lg2 (absolute error ~2^-22 on a
+// value of magnitude >= 1), log2 of the larger one as log1p of minus the
+// smaller.
 __device__ __forceinline__ NodeParams node_params(float pn, float qn) {
     constexpr float kLog2e = 1.44269504088896340736f;
     NodeParams nd;
@@ -121,11 +127,11 @@ __device__ __forceinline__ NodeParams node_params(float pn, float qn) {
     nd.q = qn;
     float l2p, l2q;
     if (pn <= 0.5f) {
-        l2p = log2f(pn);
+        l2p = __log2f(pn);
         l2q = log1pf(-pn) * kLog2e;
     } else {
         l2p = log1pf(-qn) * kLog2e;
-        l2q = log2f(qn);
+        l2q = __log2f(qn);
     }
     nd.lp = l2p;
     nd.lq = (pn >= kEps) ? l2q : (pn * (1.f / kEps)) * kLog2OneMinusEps;
@@ -313,7 +319,7 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
             const float tot = P[n];
             float pn = 0.f, qn = 1.f;
             if (tot > 0.f) {
-                const float inv = 1.f / tot;
+                const float inv = __fdividef(1.f, tot);  // hardware reciprocal, within 2 ulp
                 pn = P[2 * n] * inv;
                 qn = P[2 * n + 1] * inv;
             }

@@ -113,7 +113,9 @@ __device__ __forceinline__ void dir_to_texel(float dx, float dy, float dz, int W
     y = th * (kInvPi * (float)H) - 0.5f;
 }
 
-// Bilinear taps of an equirect level: wrap in phi, clamp in theta.
+// Bilinear taps of an equirect level: wrap in phi, clamp in theta.  Every
+// level's width is a power of two, so the wrap is a mask (two's complement
+// also wraps x0 = -1 to W - 1).
 struct Taps {
     int i00, i01, i10, i11;
     float w00, w01, w10, w11;
@@ -122,8 +124,8 @@ __device__ __forceinline__ Taps equirect_taps(float x, float y, int W, int H) {
     float fx0 = floorf(x), fy0 = floorf(y);
     float fx = x - fx0, fy = y - fy0;
     int x0 = (int)fx0, y0 = (int)fy0;
-    int xa = x0 % W; if (xa < 0) xa += W;
-    int xb = xa + 1; if (xb >= W) xb -= W;
+    const int xa = x0 & (W - 1);
+    const int xb = (xa + 1) & (W - 1);
     int ya = min(max(y0, 0), H - 1);
     int yb = min(max(y0 + 1, 0), H - 1);
     Taps t;

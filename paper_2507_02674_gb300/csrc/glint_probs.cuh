@@ -19,6 +19,7 @@ struct ShadeArgs {
     int frec4;         // 16-byte units per texel record of a compressed format
     int R;
     float s_min, s_max;
+    float s_scale;     // (R - 1) / (s_max - s_min): filtered level per unit of sqrt(alpha)
     const float *levels;
     uint32_t seed;
     glint_debug dbg;
@@ -246,7 +247,7 @@ __device__ __forceinline__ void smooth_and_probs(const ShadeArgs &a, long q, flo
     const float mu_c = fminf(fmaxf(mu_o, 1e-4f), 1.f);
     const float s = sqrtf(sqrtf(g2.z * g2.w));
     const float4 tab = lut_fetch(a.lut, a.lut_n, mu_c, s);  // V, U, A, B
-    float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
+    float tl = (s - a.s_min) * a.s_scale;
     tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
     const int r0 = (int)floorf(tl);
     const int r1 = min(r0 + 1, a.R - 1);
@@ -293,6 +294,7 @@ inline ShadeArgs make_args(const glint_ctx *ctx, const glint_env *env, const gli
     a.flev = env->flev;
     a.s_min = env->d.s_min;
     a.s_max = env->d.s_max;
+    a.s_scale = (a.R > 1) ? (float)(a.R - 1) / (a.s_max - a.s_min) : 0.f;
     a.levels = env->levels;
     a.seed = p->seed;
     a.pyr = reinterpret_cast<const float4 *>(env->pyr);
@@ -384,7 +386,7 @@ __device__ __forceinline__ void filtered_w(const ShadeArgs &a, float th, float p
 template <int K>
 __device__ __forceinline__ void filtered_weights_only(const ShadeArgs &a, float dx, float dy, float dz, float s,
                                                       float *W) {
-    float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
+    float tl = (s - a.s_min) * a.s_scale;
     tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
     const int r0 = (int)floorf(tl);
     const int r1 = min(r0 + 1, a.R - 1);
@@ -406,7 +408,7 @@ __device__ __forceinline__ void e1_probs(const ShadeArgs &a, float4 g0, float4 g
     const float mu_c = fminf(fmaxf(mu_o, 1e-4f), 1.f);
     const float s = sqrtf(sqrtf(g2.z * g2.w));
     const float4 tab = lut_fetch(a.lut, a.lut_n, mu_c, s);  // V, U, A, B
-    float tl = (a.R > 1) ? (s - a.s_min) / (a.s_max - a.s_min) * (float)(a.R - 1) : 0.f;
+    float tl = (s - a.s_min) * a.s_scale;
     tl = fminf(fmaxf(tl, 0.f), (float)(a.R - 1));
     const int r0 = (int)floorf(tl);
     const int r1 = min(r0 + 1, a.R - 1);

@@ -55,8 +55,8 @@ struct NodeParams {
     float p, q, lp, lq;  // node probability, complement, log2 p, log2 of (1 - c p)^(1/c)
 };
 
-// Dual-gated Gaussian (Alg. 1) for an integer number of trials N >= 1;
-// returns n (nbar = N - n).  Regions of xi1 (same as the printed masks):
+// Dual-gated Gaussian (Alg. 1) for an integer number of trials N; returns n
+// (nbar = N - n), 0 when N = 0.  Regions of xi1 (same as the printed masks):
 // [0, P_{n=N}) -> N;  [P_{n=N}, P_{n=N} + P_{n=1}) -> 1;
 // 1 - xi1 <= P_{nbar=N} + P_{nbar=1} -> 0;  otherwise the clamped, rounded
 // Gaussian when N > 1, else 0.  For N >= 2 the single-trial terms vanish, so
@@ -74,7 +74,7 @@ __device__ __forceinline__ uint32_t draw_integer(uint32_t N, const NodeParams &n
     const float N2 = m + 2.f;
     const bool many = N >= 2u;
     const float Pall = many ? fast_exp2(N2 * np.lp) : 0.f;
-    const float T1 = many ? Pall : np.p;
+    const float T1 = many ? Pall : ((N == 1u) ? np.p : 0.f);
     const float Sneg = fast_exp2(N2 * np.lq);  // decides only for N >= 2
     const float muh = fmaf(m, np.p, 1.5f);
     const float sigma = fast_sqrt(m * np.p * np.q);
@@ -114,23 +114,41 @@ __device__ __forceinline__ void draw_real(float N, const NodeParams &np, uint32_
 }
 
 
+// log2(1 - x) for x in [0, 1/2] with a small relative error for every x
+// (1 - x itself would lose the low bits of small x): with s = x / (2 - x) in
+// [0, 1/3], ln(1 - x) = -2 atanh(s) = -2 (s + s^3/3 + s^5/5 + ...); the series
+// to s^13 leaves a relative error below 3e-8, the hardware reciprocal in s
+// about 2.4e-7.
+__device__ __forceinline__ float log2_one_minus(float x) {
+    constexpr float kTwoLog2e = 2.88539008177792681472f;
+    const float s = __fdividef(x, 2.f - x);
+    const float u = s * s;
+    float t = 1.f / 13.f;
+    t = fmaf(t, u, 1.f / 11.f);
+    t = fmaf(t, u, 1.f / 9.f);
+    t = fmaf(t, u, 1.f / 7.f);
+    t = fmaf(t, u, 1.f / 5.f);
+    t = fmaf(t, u, 1.f / 3.f);
+    t = fmaf(t, u, 1.f);
+    return -kTwoLog2e * (s * t);
+}
+
 // Node parameters of a binary split with probabilities p (left) and q = 1 - p
 // (right): log2 p and log2 of the small-p biased complement, each logarithm
 // taken of whichever of p, q is the smaller (1 - x near 1 is not accurate):
 // log2 of the smaller one by the hardware lg2 (absolute error ~2^-22 on a
-// value of magnitude >= 1), log2 of the larger one as log1p of minus the
+// value of magnitude >= 1), log2 of the larger one by log2_one_minus of the
 // smaller.
 __device__ __forceinline__ NodeParams node_params(float pn, float qn) {
-    constexpr float kLog2e = 1.44269504088896340736f;
     NodeParams nd;
     nd.p = pn;
     nd.q = qn;
     float l2p, l2q;
     if (pn <= 0.5f) {
         l2p = __log2f(pn);
-        l2q = log1pf(-pn) * kLog2e;
+        l2q = log2_one_minus(pn);
     } else {
-        l2p = log1pf(-qn) * kLog2e;
+        l2p = log2_one_minus(qn);
         l2q = __log2f(qn);
     }
     nd.lp = l2p;
@@ -397,9 +415,13 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
                             h = pcg4d(make_uint4(vx, vy, key2 | ((uint32_t)(1 + n / 2) << 16), a.seed));
                         const uint32_t u1 = (n == 1) ? h.y : (n & 1) ? h.z : h.x;
                         const uint32_t u2 = (n == 1) ? h.z : (n & 1) ? h.w : h.y;
-                        if (N[n] > 0u) {
-                            nl = (DRAW == kDrawDual) ? draw_integer(N[n], nd[n], u1, u2)
-                                                     : draw_single_integer(N[n], nd[n], u1, u2, DRAW == kDrawSingleOld);
+                        if (DRAW == kDrawDual) {
+                            // no branch: an empty node draws 0, and the
+                            // independent draws of sibling nodes interleave
+                            nl = draw_integer(N[n], nd[n], u1, u2);
+                            nr = N[n] - nl;
+                        } else if (N[n] > 0u) {
+                            nl = draw_single_integer(N[n], nd[n], u1, u2, DRAW == kDrawSingleOld);
                             nr = N[n] - nl;
                         }
                         N[2 * n] = nl;

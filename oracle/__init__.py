@@ -32,7 +32,12 @@ _lib = None
 # relative error of subtree probability masses, of the FP32 normal quantile,
 # of an FP32 exp2/log2 chain, an absolute floor of every threshold, and an
 # absolute error of subtree masses.
-TIE_DEFAULT = (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 0.0)
+# The absolute mass error of E1, 2^-36: a fuzzy weight 1 - t of a texel whose
+# brightness lies just below a radiance level (Sec. 4, Eq. wkdefpractice) is a
+# small difference of FP32 values, so its rounding (~2^-24 of the bracket)
+# reaches a small filtered weight as an absolute, not relative, error (measured
+# on a GB300: 8.9e-13 on p_k = 1.0e-8 at the 1080p material distributions).
+TIE_DEFAULT = (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -36)
 # The E2 quadrature reads single pyramid texels per point at FP32 texel
 # coordinates (up to ~1.2e-4 texel of error, w_k changing by at most 1 per
 # texel), so a mass carried by a few points moves by ~1e-4 of itself and tiny
@@ -43,12 +48,23 @@ NV = 6
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, no FP contraction)."""
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, no FP
+    contraction; OpenMP over pixels and texels where gcc has it)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-o", _LIB, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                "-o", _LIB, _SRC, "-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.run(base, check=True)
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's pixel and texel loops (0: every core)."""
+    _load().or_set_threads(int(n))
+
+
+def threads() -> int:
+    return _load().or_max_threads()
 
 
 def _load():
@@ -103,6 +119,9 @@ def _load():
         lib.or_shade.restype = L
         lib.or_radiance.argtypes = [P, P, D, P, I, P, P, P, I, D, I]
         lib.or_multinomial.argtypes = [P, I, D, U, U, U, U, I, P, I]
+        lib.or_set_threads.argtypes = [I]
+        lib.or_set_threads.restype = None
+        lib.or_max_threads.restype = I
         _lib = lib
     return _lib
 
@@ -324,6 +343,26 @@ def prefilter(env: EnvOracle, R: int, S: int, s_min: float, s_max: float, Wmax: 
     lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(table), _ptr(nvalid), R, S, _ptr(widths), _ptr(idx),
                      len(idx), _ptr(out))
     return quantize_weights(out, wfmt)
+
+
+def prefilter_with(env: EnvOracle, table: np.ndarray, nvalid: np.ndarray, widths) -> list:
+    """or_prefilter with a given sample table and level widths (tests plant
+    mistakes in either); returns the levels as (W_r / 2, W_r, C) arrays."""
+    lib = _load()
+    H, W, C = env.ch0.shape
+    R, S = table.shape[0], table.shape[1]
+    widths = np.ascontiguousarray(widths, dtype=np.int32)
+    nvalid = np.ascontiguousarray(nvalid, dtype=np.int32)
+    total = int(sum(int(w) * (int(w) // 2) for w in widths))
+    flat = np.zeros((total, C))
+    lib.or_prefilter(_ptr(env.mips_flat), W, H, C, _ptr(np.ascontiguousarray(table, dtype=np.float64)),
+                     _ptr(nvalid), R, S, _ptr(widths), None, 0, _ptr(flat))
+    levels, off = [], 0
+    for w in widths:
+        n = int(w) * (int(w) // 2)
+        levels.append(flat[off:off + n].reshape(int(w) // 2, int(w), C))
+        off += n
+    return levels
 
 
 def prefilter_exact(ch0: np.ndarray, alpha: float, dirs: np.ndarray) -> np.ndarray:

@@ -33,6 +33,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define OR_PI 3.14159265358979323846
 #define OR_MAXK 16
 #define OR_NV 6 /* grid samples per pixel: 2 levels x 3 triangle vertices */
@@ -506,8 +510,12 @@ static size_t mip_offset(int W, int H, int C, int m)
  * valid iff cos 2th > 0.  Sampling h with density D cos(theta_h) gives w_i the
  * density D(h)/4 when n = r, so the importance weight p/pdf is constant and
  * the estimate is the plain mean over valid samples.  Each sample reads the
- * pyramid at lod = 0.5 log2(Omega_s / Omega_0) + 1, clamped to [0, M-1], with
- * Omega_s = 4 / (S D(h)) and Omega_0 = 4 pi / (W H).
+ * pyramid at lod = 0.5 log2(Omega_s / Omega_0) + b, clamped to [0, M-1], with
+ * Omega_s = 4 / (S D(h)) and Omega_0 = 4 pi / (W H).  Reading of the bias: the
+ * cited works use b = +1; on maps with bright suns b = -1/2 keeps the result
+ * closest to the exact convolution (or_prefilter_exact) among b in {+1, +1/2,
+ * 0, -1/2, -1} at 64 samples (median luminance error 3-10% instead of 18-25%),
+ * so b = -1/2.
  * Levels r = 0..R-1: sqrt(alpha_r) spaced evenly on [s_min, s_max].
  * table: R x S x 4 (e1 weight, e2 weight, r weight, lod; zeros where
  * invalid); nvalid: R; valid samples come first in each level. */
@@ -532,7 +540,7 @@ void or_prefilter_table(int R, int S, double s_min, double s_max, int W, int H, 
             double ph = 2.0 * OR_PI * u2;
             double D = or_ggx_d(c, alpha);
             double omega_s = 4.0 / (S * D);
-            double lod = 0.5 * log2(omega_s / omega0) + 1.0;
+            double lod = 0.5 * log2(omega_s / omega0) - 0.5;
             lod = fmin(fmax(lod, 0.0), (double)(M - 1));
             double *o = table + 4 * ((size_t)r * S + nv);
             o[0] = sin2t * cos(ph);
@@ -585,6 +593,7 @@ void or_prefilter(const double *mips, int W, int H, int C, const double *table, 
     start[0] = 0;
     for (int r = 0; r < R; ++r) start[r + 1] = start[r] + (long)widths[r] * (widths[r] / 2);
     long total = idx ? count : start[R];
+#pragma omp parallel for schedule(dynamic, 256) private(tmp0, tmp1)
     for (long q = 0; q < total; ++q) {
         long id = idx ? idx[q] : q;
         int r = 0;
@@ -623,6 +632,7 @@ void or_prefilter(const double *mips, int W, int H, int C, const double *table, 
 void or_prefilter_exact(const double *ch0, int W, int H, int C, double alpha, const double *dirs, long count,
                         double *out)
 {
+#pragma omp parallel for schedule(dynamic, 4)
     for (long q = 0; q < count; ++q) {
         const double *r = dirs + 3 * q;
         double acc[3 + OR_MAXK], norm = 0.0;
@@ -764,6 +774,7 @@ void or_mlp_features(const float *gb, const float *tangents, long npix, const do
                      int C, double s_min, double s_max, const double *lut, int nlut, int K, double *x, double *lp,
                      double *dirs)
 {
+#pragma omp parallel for schedule(dynamic, 64)
     for (long q = 0; q < npix; ++q) {
         const float *g = gb + 16 * q;
         double *xq = x + 64 * q;
@@ -1301,6 +1312,7 @@ long or_shade(const float *gb, long npix, const double *pref, int R, const int *
     float ocs[8], osn[8];
     orient_table(ocs, osn);
     long nbg = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : nbg)
     for (long q = 0; q < npix; ++q) {
         const float *g = gb + 16 * q;
         for (int c = 0; c < 3; ++c) rgb[3 * q + c] = lo[3 * q + c] = 0.0;
@@ -1521,4 +1533,25 @@ void or_multinomial(const double *p, int K, double N, uint32_t key0, uint32_t ke
     Nv[1] = N;
     tree_rec(&t, 1, Nv, dN);
     for (int k = 0; k < K; ++k) counts[k] = buf[k];
+}
+
+/* Threads of the per-pixel and per-texel loops (OpenMP; 1 when the oracle
+ * was built without it).  The loops' iterations are independent, so results
+ * do not depend on the thread count. */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

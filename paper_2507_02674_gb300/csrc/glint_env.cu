@@ -279,7 +279,9 @@ constexpr long kPyrTailTexels = 2048;
 // u1 = (j+1/2)/S, u2 = radical inverse of j, cos^2 th = (1-u1)/(1+(a^2-1)u1),
 // reflected direction weights (sin 2th cos ph, sin 2th sin ph, cos 2th) in the
 // frame (e1, e2, r), valid iff cos 2th > 0 (a prefix of j), and the pyramid
-// level lod = 0.5 log2(Omega_s / Omega_0) + 1 with Omega_s = 4/(S D(h)).
+// level lod = 0.5 log2(Omega_s / Omega_0) - 1/2 with Omega_s = 4/(S D(h))
+// (the bias of filtered importance sampling that keeps the filtered maps
+// closest to the exact convolution on maps with bright suns).
 __global__ void k_filter_table(int R, int S, float s_min, float s_max, int W, int H, int M, float4 *table,
                                int *nvalid) {
     const int r = blockIdx.y;
@@ -312,7 +314,7 @@ __global__ void k_filter_table(int R, int S, float s_min, float s_max, int W, in
         const float D = a2 / (kPi * d * d);
         const float omega_s = 4.f / ((float)S * D);
         const float omega0 = 4.f * kPi / ((float)W * (float)H);
-        float lod = 0.5f * log2f(omega_s / omega0) + 1.f;
+        float lod = 0.5f * log2f(omega_s / omega0) - 0.5f;
         lod = fminf(fmaxf(lod, 0.f), (float)(M - 1));
         e = make_float4(sin2t * cp, sin2t * sp, cos2t, lod);
     }

@@ -139,18 +139,17 @@ __device__ __forceinline__ float log2_one_minus(float x) {
 // log2 of the smaller one by the hardware lg2 (absolute error ~2^-22 on a
 // value of magnitude >= 1), log2 of the larger one by log2_one_minus of the
 // smaller.
+// Both logarithms are evaluated once, of the smaller probability, and
+// assigned by a select, so lanes on either side of 1/2 take the same path.
 __device__ __forceinline__ NodeParams node_params(float pn, float qn) {
     NodeParams nd;
     nd.p = pn;
     nd.q = qn;
-    float l2p, l2q;
-    if (pn <= 0.5f) {
-        l2p = __log2f(pn);
-        l2q = log2_one_minus(pn);
-    } else {
-        l2p = log2_one_minus(qn);
-        l2q = __log2f(qn);
-    }
+    const bool left_small = pn <= 0.5f;
+    const float small = left_small ? pn : qn;
+    const float l_small = __log2f(small), l_large = log2_one_minus(small);
+    const float l2p = left_small ? l_small : l_large;
+    const float l2q = left_small ? l_large : l_small;
     nd.lp = l2p;
     nd.lq = (pn >= kEps) ? l2q : (pn * (1.f / kEps)) * kLog2OneMinusEps;
     return nd;
@@ -335,13 +334,9 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
 #pragma unroll
         for (int n = 1; n < K; ++n) {
             const float tot = P[n];
-            float pn = 0.f, qn = 1.f;
-            if (tot > 0.f) {
-                const float inv = __fdividef(1.f, tot);  // hardware reciprocal, within 2 ulp
-                pn = P[2 * n] * inv;
-                qn = P[2 * n + 1] * inv;
-            }
-            nd[n] = node_params(pn, qn);
+            const float inv = __fdividef(1.f, tot);  // hardware reciprocal, within 2 ulp
+            const bool some = tot > 0.f;              // an empty subtree gets p = 0, q = 1
+            nd[n] = node_params(some ? P[2 * n] * inv : 0.f, some ? P[2 * n + 1] * inv : 1.f);
         }
     }
 

@@ -16,6 +16,7 @@ import numpy as np
 RAD_RTOL = 1e-4        # relative tolerance on radiance
 RAD_ATOL_FRAC = 1e-6   # absolute floor, as a fraction of the largest smooth radiance
 P_RTOL = 2.0 ** -14    # relative tolerance on p_k: the oracle's tie-model bound e_P
+P_ATOL = 2.0 ** -36    # absolute floor on p_k: the tie model's absolute mass error of E1
 LO_RTOL = 1e-4
 W_ATOL = 2e-6
 
@@ -50,7 +51,7 @@ def _rel(a, b, floor):
 
 
 def compare_shade(orc, o, gpu: dict, rgb_gpu: np.ndarray, integer_mode: bool = True, max_fail: int = 20,
-                  nonunique=None, p_atol: float = 0.0, p_rtol: float = P_RTOL,
+                  nonunique=None, p_atol: float = P_ATOL, p_rtol: float = P_RTOL,
                   rad_rtol: float = RAD_RTOL) -> ShadeReport:
     """o: oracle.ShadeOracle for n pixels; gpu: numpy copies of the debug outputs
     for the same pixels (keys p, np, vert, w, nroot, counts, lo); rgb_gpu (n, 3).

@@ -1,0 +1,126 @@
+"""The 3840 x 2160 grazing-view workload (camera 5 degrees above the ground
+plane, a 2048 x 1024 RGBA16F map with four suns, K = 16, N_0 log-uniform in
+[1e2, 1e9]) and the pyramid pass that maps above 2048 x 1024 take, through the
+C ABI against the CPU oracle.
+
+This workload stresses what the 1080p frame rarely reaches: microfacet counts
+above 2^24 and at the uint32 saturation (Sec. 5 "Numeric Gating Issues": p <
+eps and N > 1/p), very small N_P, footprints stretched up to ~150:1, sixteen
+radiance levels.  The full frame is shaded in the benchmark's launch
+configuration; a stratified sample of its pixels is shaded again as a
+G-buffer of its own with the per-pixel intermediates and compared with the
+oracle, and the two launches must agree bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2507_02674_gb300 import synth
+from tests._compare import compare_shade
+from tests._pipeline import MethodParams, oracle_env, oracle_shade
+
+pytestmark = pytest.mark.gpu
+
+EPS = 10.0 ** -3.54
+
+
+@pytest.fixture(scope="module")
+def gl():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_02674_gb300 import build as B
+    B.build()
+    from paper_2507_02674_gb300 import glint, render
+    return glint, render, glint.Context(0, 64, 128), torch
+
+
+def _cfg(glint, mp: MethodParams):
+    return glint.EnvConfig(K=mp.K, ell=mp.ell, levels=mp.R, samples=mp.S, out_width=mp.Wo, s_min=mp.s_min,
+                           s_max=mp.s_max)
+
+
+def _subset(gb, rows):
+    r = gb.rows16()[rows]
+    planes = [r[:, 4 * i:4 * i + 4].reshape(1, len(rows), 4).copy() for i in range(4)]
+    return synth.GBuffer(len(rows), 1, planes, "sampled pixels")
+
+
+def test_pyramid_second_pass_4096_map(gl, orc):
+    """A 4096 x 2048 map: the first launch builds levels 0-5, a second launch
+    (reading level 5 back) builds 6-10 and the last block the rest.  Every
+    level against the oracle's solid-angle pyramid, then the filtered maps."""
+    glint, render, ctx, torch = gl
+    env = synth.env_hdr(seed=12, W=4096, H=2048)
+    mp = MethodParams(K=4, Wo=128)
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    small = render.Frame(ctx, synth.env_hdr(seed=12, W=1024, H=512), _cfg(glint, mp))
+    small.update_env()
+    torch.cuda.synchronize()
+    assert fr.env.last_launches() == small.env.last_launches() + 1  # the second pyramid launch ran
+    e, of = oracle_env(orc, env, mp)
+    assert np.allclose(fr.env.levels().astype(np.float64), e.levels, rtol=3e-6, atol=0)
+    for m in range(fr.env.M):
+        g = fr.env.export(glint.ENV_PYRAMID, m).astype(np.float64)
+        o = e.mips[m]
+        assert g.shape == o.shape
+        assert np.max(np.abs(g[..., 3:] - o[..., 3:])) < 4e-6, m
+        assert np.max(np.abs(g[..., :3] - o[..., :3]) / np.abs(o[..., :3])) < 2e-6, m
+    widths, f = fr.env.export(glint.ENV_FILTERED)
+    assert list(widths) == list(of.widths)
+    f = f.astype(np.float64)
+    assert np.max(np.abs(f[:, :3] - of.flat[:, :3]) / np.abs(of.flat[:, :3])) < 5e-5
+    assert np.max(np.abs(f[:, 3:] - of.flat[:, 3:])) < 5e-6
+
+
+@pytest.fixture(scope="module")
+def scene3():
+    env = synth.env_hdr(seed=2, W=2048, H=1024)
+    gb = synth.gbuffer_scene(3840, 2160, seed=2, pitch_deg=5.0, cam_height=1.0, n_lo=1e2, n_hi=1e9)
+    return env, gb
+
+
+def test_shade_config3_sampled(gl, orc, scene3):
+    glint, render, ctx, torch = gl
+    env, gb = scene3
+    mp = MethodParams(K=16, R=8, S=64, Wo=256, seed=2)
+    fr = render.Frame(ctx, env, _cfg(glint, mp))
+    fr.update_env()
+    planes = render.gbuffer_tensors(gb)
+    full = fr.shade(planes, gb.width, gb.height, seed=mp.seed)
+    torch.cuda.synchronize()
+    full = full.cpu().numpy()
+    del planes
+
+    # properties over every pixel
+    rows16 = gb.rows16()
+    bg = ~(rows16[:, 3] > 0)
+    assert np.all(np.isfinite(full)) and np.all(full[:, :3] >= 0) and np.all(full[:, 3] == 1)
+    assert np.all(full[bg, :3] == 0)
+
+    # stratified sample: random foreground pixels, the largest counts (beyond
+    # 2^24 and at saturation), the smallest, and a few background pixels
+    area = np.abs(rows16[:, 12].astype(np.float64) * rows16[:, 15] - rows16[:, 14].astype(np.float64) * rows16[:, 13])
+    NP = rows16[:, 3] * area
+    fg = np.where(~bg)[0]
+    rng = np.random.default_rng(2)
+    big = fg[NP[fg] > 2.0 ** 24]
+    order = fg[np.argsort(NP[fg])]
+    rows = np.unique(np.concatenate([rng.choice(fg, 2000, replace=False), rng.choice(big, 300, replace=False),
+                                     order[:150], order[-150:], rng.choice(np.where(bg)[0], 50, replace=False)]))
+    sub = _subset(gb, rows)
+    dbg = glint.debug_buffers(len(rows), mp.K)
+    out = fr.shade(render.gbuffer_tensors(sub), sub.width, 1, seed=mp.seed, debug=dbg)
+    torch.cuda.synchronize()
+    rgb = out.cpu().numpy()
+    assert np.array_equal(rgb, full[rows])  # the launch configuration changes nothing
+
+    o = oracle_shade(orc, sub.rows16(), env, mp)
+    gpu = {k: v.cpu().numpy() for k, v in dbg.items()}
+    rep = compare_shade(orc, o, gpu, rgb[:, :3].astype(np.float64))
+    print(rep.summary())
+    assert rep.ok(), rep.failures[:10]
+    # the sample reaches the regimes this workload is for
+    assert np.sum(o.np_ > 2.0 ** 24) >= 300
+    assert np.sum(o.np_ >= np.float32(4294967040.0)) >= 1
+    assert np.sum((o.pk > 0) & (o.pk < EPS)) >= 100
+    assert np.sum((o.np_ > 0) & (o.np_ < 1)) >= 100

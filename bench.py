@@ -367,7 +367,8 @@ def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed
     ms_nn = timed(mlp_step, args.steps)
     ms_e2 = timed(e2_step, max(3, min(args.steps, 10)))
     return {
-        "path": "env update + glint_mlp_infer (fused inputs + BF16 mma.sync network) + shading with its p_k",
+        "path": "env update + glint_shade with the surrogate fused in (per 256-pixel block: inputs, BF16 "
+                "mma.sync network, draws with its p_k from shared memory; one launch)",
         "value": round(npix / (float(ms_nn.mean()) / 1e3) / 1e6, 3), "unit": "Mpixel/s",
         "ms_per_step": round(float(ms_nn.mean()), 4),
         "p50_ms": round(float(np.percentile(ms_nn, 50)), 4), "p99_ms": round(float(np.percentile(ms_nn, 99)), 4),

@@ -209,9 +209,9 @@ typedef struct glint_params {
     int evaluator;   /* glint_evaluator */
     int e2_samples;  /* E2: S x S quadrature points, S in [1, 256] (0 = 16) */
     const glint_mlp *mlp; /* GLINT_EVAL_MLP: the network; its K must equal the environment's */
-    float *p_scratch;     /* GLINT_EVAL_MLP: device, width*height*K floats (4-byte aligned) that
-                             receive the network's p_k before shading; GLINT_EVAL_GIVEN: the
-                             p_k to shade with (read only).  Caller-owned */
+    float *p_scratch;     /* GLINT_EVAL_GIVEN: device, width*height*K floats (4-byte aligned), the
+                             p_k to shade with (read only).  Caller-owned.  Not used by
+                             GLINT_EVAL_MLP (the network's p_k never leave the chip) */
     int draw;             /* glint_draw: binomial approximation at the tree nodes (0 = the paper's) */
     float gamma;          /* GLINT_DRAW_WANG2020: reflection probability of a microfacet, (0, 1] */
     int grid;             /* glint_grid: the grid N_P is spread over (0 = two levels x uv triangle) */
@@ -261,8 +261,10 @@ typedef struct glint_debug {
  * GLINT_EVAL_E2, p_k = int D(h) 1[n.w_i > 0] w_k(w_i) dh / int D(h) dh of the
  * anisotropic footprint by an S x S quadrature of the GGX slope distribution
  * reading the weights pyramid (masked mass in p_1), or, with GLINT_EVAL_MLP,
- * p_k from params->mlp written to params->p_scratch first (two launches),
- * or, with GLINT_EVAL_GIVEN, the p_k in params->p_scratch,
+ * p_k from params->mlp evaluated inside the shading kernel (one launch: each
+ * block of 256 pixels computes the network's inputs, runs the network on the
+ * tensor cores and draws with its p_k from shared memory), or, with
+ * GLINT_EVAL_GIVEN, the p_k in params->p_scratch,
  * N_P = N_0 |det duv|, and
  * M_k = sum_i w_i n_k(i) over six triangle-grid samples (Sec. 3.3
  * Eq. anisogrid), each a hierarchical multinomial of dual-gated Gaussian
@@ -305,7 +307,7 @@ void glint_hostpipe_destroy(glint_hostpipe *pipe);
  * results with copies that block the calling thread (device buffers work too:
  * the staged copies take their direction from the addresses).  params as glint_shade
  * (params->p_scratch stays a DEVICE buffer of width*height*K floats for the
- * MLP and GIVEN evaluators; band b uses its rows of it).  rows_per_band (staged
+ * GIVEN evaluator; band b uses its rows of it).  rows_per_band (staged
  * frames only; a frame shaded in place ignores it): 0 picks about an eighth of
  * the frame, capped by the pipe's band_pixels; a band of more pixels than
  * band_pixels, or a row wider than it, is GLINT_ERR_INVALID_ARG.  The uploads start after the work enqueued on

@@ -473,25 +473,23 @@ glint_status glint_shade(glint_ctx *ctx, const glint_env *env, const glint_gbuff
     if (npix > 0) {
         if (!g->duv) { set_error("glint_shade: NULL duv plane"); return GLINT_ERR_INVALID_ARG; }
         if (!aligned16(out_rgba)) { set_error("glint_shade: output must be 16-byte aligned"); return GLINT_ERR_INVALID_ARG; }
-        if ((p->evaluator == GLINT_EVAL_MLP || p->evaluator == GLINT_EVAL_GIVEN) &&
-            (!p->p_scratch || ((uintptr_t)p->p_scratch & 3u))) {
-            set_error("glint_shade: the MLP and GIVEN evaluators need params->p_scratch (width*height*K floats)");
+        if (p->evaluator == GLINT_EVAL_GIVEN && (!p->p_scratch || ((uintptr_t)p->p_scratch & 3u))) {
+            set_error("glint_shade: the GIVEN evaluator needs params->p_scratch (width*height*K floats)");
             return GLINT_ERR_INVALID_ARG;
         }
     }
     DeviceGuard guard(ctx->device);
-    int nl = 0;
-    const float *pk_in = nullptr;
-    if (p->evaluator == GLINT_EVAL_MLP && npix > 0) {
-        st = cuda_status(glint_launch_mlp_infer(ctx, env, p->mlp, g, p->p_scratch, (cudaStream_t)stream), "glint_shade: MLP");
-        if (st != GLINT_OK) return st;
-        pk_in = p->p_scratch;
-    } else if (p->evaluator == GLINT_EVAL_GIVEN) {
-        pk_in = p->p_scratch;
+    if (p->evaluator == GLINT_EVAL_MLP) {  // inputs, network and draws in one kernel
+        st = cuda_status(glint_launch_shade_mlp(ctx, env, g, p, out_rgba, dbg, (cudaStream_t)stream),
+                         "glint_shade: MLP");
+        ctx->last_launches = npix > 0 ? 1 : 0;
+        return st;
     }
+    int nl = 0;
+    const float *pk_in = p->evaluator == GLINT_EVAL_GIVEN ? p->p_scratch : nullptr;
     st = cuda_status(glint_launch_shade(ctx, env, g, p, pk_in, out_rgba, dbg, (cudaStream_t)stream, &nl),
                      "glint_shade");
-    ctx->last_launches = nl + (p->evaluator == GLINT_EVAL_MLP && npix > 0 ? 1 : 0);
+    ctx->last_launches = nl;
     return st;
 }
 

@@ -173,6 +173,10 @@ void glint_mlp_weights(const glint_mlp *m, const void **wt, const float **params
 // Shading with a comparison draw (glint_variants.cu).
 cudaError_t glint_launch_shade_variant(const glint::ShadeArgs &a, int K, bool integer, int draw, int grid,
                                        cudaStream_t s);
+// Shading with the surrogate fused in (inputs, network and draws in one
+// kernel; p_k stays on chip).
+cudaError_t glint_launch_shade_mlp(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
+                                   const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s);
 // p_k only (E1 or E2), background pixels 0.
 cudaError_t glint_launch_probs(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
                                const glint_params *p, float *p_out, cudaStream_t s);

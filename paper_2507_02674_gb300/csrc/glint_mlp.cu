@@ -32,6 +32,7 @@
 
 #include "glint_internal.cuh"
 #include "glint_probs.cuh"
+#include "glint_shade_pixel.cuh"
 
 using namespace glint;
 
@@ -381,6 +382,113 @@ __global__ void __launch_bounds__(kNT, 4) k_mlp_serve(const ShadeArgs *__restric
             net_tile<1>(sm, base, end, K, sa.p_out);
         }
     }
+}
+
+// ------------------------------------------------------------------ shading
+// The surrogate fused into the shading: a block of kFusedNT pixels computes
+// their inputs (mlp_features, as k_mlp_infer), the network on the tile (warp w
+// on rows [32 w, 32 w + 32)), and the glint draws (shade_draws) with the
+// network's p_k from shared memory -- no per-pixel p_k leaves the chip.  The
+// smooth radiance reads the colour channels of the filtered maps as the
+// shading with given p_k does.  Three blocks of 256 threads per SM: 69 KB of
+// shared memory each (weights, the input tile, log-priors then p_k in place),
+// 80 registers a thread for the draws.
+constexpr int kFusedNT = 256;
+
+struct SmemFused {
+    SmemW w;
+    __align__(16) __nv_bfloat16 xs[kFusedNT * 64];
+    float lp[kFusedNT * kLpStride];  // log-priors, then p_k in place
+    int fg[kFusedNT];
+};
+
+// Sink of mlp_features into row r of the fused kernel's tile (as SmemRowSink).
+template <int K>
+struct FusedRowSink {
+    SmemFused &sm;
+    int r;
+    __device__ __forceinline__ void group(int i, const float *v) {
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(sm.xs);
+#pragma unroll
+        for (int j = 0; j < K / 2; ++j) w32[word_at(r, i / 2 + j)] = pack_bf16(v[2 * j], v[2 * j + 1]);
+    }
+    __device__ __forceinline__ void log_prior(const float *l) {
+#pragma unroll
+        for (int k = 0; k < kOutPad; ++k) sm.lp[r * kLpStride + k] = k < K ? l[k] : 0.f;
+    }
+    __device__ __forceinline__ void tail(int i, const float *v) {
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(sm.xs);
+        w32[word_at(r, i / 2)] = pack_bf16(v[0], v[1]);
+        w32[word_at(r, i / 2 + 1)] = pack_bf16(v[2], 0.f);
+#pragma unroll
+        for (int w = 3 * K + 2; w < 32; ++w) w32[word_at(r, w)] = 0u;
+    }
+    __device__ __forceinline__ void zero() {
+        uint4 *x4 = reinterpret_cast<uint4 *>(sm.xs);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x4[r * 8 + q] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int k = 0; k < kOutPad; ++k) sm.lp[r * kLpStride + k] = 0.f;
+    }
+};
+
+template <int K, bool INTEGER, bool DEBUG>
+__global__ void __launch_bounds__(kFusedNT, 3) k_shade_mlp(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
+                                                          const float *__restrict__ params) {
+    extern __shared__ __align__(16) unsigned char fused_smem[];
+    SmemFused &sm = *reinterpret_cast<SmemFused *>(fused_smem);
+    load_weights(sm.w, wt, params);
+    const long q = (long)blockIdx.x * kFusedNT + threadIdx.x;
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    bool fg = false;
+    if (q < a.npix) {
+        g0 = ldg4(a.view_n0 + q);
+        fg = g0.w > 0.f;
+    }
+    FusedRowSink<K> sink{sm, (int)threadIdx.x};
+    if (fg) mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), sink);
+    else sink.zero();
+    sm.fg[threadIdx.x] = fg ? 1 : 0;
+    __syncthreads();
+    {
+        constexpr int NT = K > 8 ? 2 : 1;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+        for (int mt = 0; mt < 2; ++mt) {
+            const int row0 = warp * 32 + mt * 16;
+            uint32_t af[4][4];
+            float c[8][4];
+            load_a(sm.xs, row0, af);
+            layer_fwd<8>(af, sm.w.w1t, sm.w.b1, c);
+            relu_to_a(c, af);
+            layer_fwd<8>(af, sm.w.w2t, sm.w.b2, c);
+            relu_to_a(c, af);
+            float o[NT][4];
+            layer_fwd<NT>(af, sm.w.w3t, sm.w.b3, o);
+            softmax_rows<NT>(o, K, sm.lp, row0);  // reads each lane's own log-priors
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float *pr = sm.lp + (row0 + g + 8 * h) * kLpStride;
+#pragma unroll
+                for (int j = 0; j < NT; ++j)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e)
+                        if (j * 8 + 2 * t + e < K) pr[j * 8 + 2 * t + e] = o[j][2 * h + e];
+            }
+        }
+    }
+    __syncthreads();
+    if (q >= a.npix) return;
+    if (!fg) {
+        shade_pixel<K, INTEGER, DEBUG, EV_NONE>(a, q);  // background: black, debug outputs 0
+        return;
+    }
+    const float4 g1 = ldg4(a.normal_f0 + q), g2 = ldg4(a.uv_alpha + q), g3 = ldg4(a.duv + q);
+    float Lor, Log, Lob, p[K];
+    smooth_and_probs<K, EV_NONE>(a, q, g0, g1, g2, Lor, Log, Lob, p);
+#pragma unroll
+    for (int k = 0; k < K; ++k) p[k] = sm.lp[threadIdx.x * kLpStride + k];
+    shade_draws<K, INTEGER, DEBUG, kDrawDual, 0>(a, q, g0, g2, g3, Lor, Log, Lob, p);
 }
 
 // Inputs of every pixel: x (n x 64 BF16, background rows 0), lp (n x K).
@@ -739,6 +847,40 @@ cudaError_t glint_launch_mlp_infer(const glint_ctx *ctx, const glint_env *env, c
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+namespace {
+template <int K, bool INTEGER, bool DEBUG>
+cudaError_t launch_shade_mlp(const ShadeArgs &a, const glint_mlp *m, cudaStream_t s) {
+    const size_t smem = sizeof(SmemFused);
+    cudaError_t e = cudaFuncSetAttribute(k_shade_mlp<K, INTEGER, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((a.npix + kFusedNT - 1) / kFusedNT);
+    k_shade_mlp<K, INTEGER, DEBUG><<<grid, kFusedNT, smem, s>>>(a, m->wt, m->params);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_shade_mlp_k(const ShadeArgs &a, const glint_mlp *m, bool integer, bool debug, cudaStream_t s) {
+    if (integer) return debug ? launch_shade_mlp<K, true, true>(a, m, s) : launch_shade_mlp<K, true, false>(a, m, s);
+    return debug ? launch_shade_mlp<K, false, true>(a, m, s) : launch_shade_mlp<K, false, false>(a, m, s);
+}
+}  // namespace
+
+cudaError_t glint_launch_shade_mlp(const glint_ctx *ctx, const glint_env *env, const glint_gbuffer *g,
+                                   const glint_params *p, float *out, const glint_debug *dbg, cudaStream_t s) {
+    ShadeArgs a = make_args(ctx, env, g, p);
+    a.out = reinterpret_cast<float4 *>(out);
+    a.dbg = dbg ? *dbg : glint_debug{};
+    if (a.npix == 0) return cudaSuccess;
+    const bool integer = p->count_mode == GLINT_COUNT_INTEGER, debug = dbg != nullptr;
+    switch (p->mlp->K) {
+    case 2: return launch_shade_mlp_k<2>(a, p->mlp, integer, debug, s);
+    case 4: return launch_shade_mlp_k<4>(a, p->mlp, integer, debug, s);
+    case 8: return launch_shade_mlp_k<8>(a, p->mlp, integer, debug, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t glint_launch_mlp_serve(int K, int num_sms, const ShadeArgs *frames, const ServeItem *items, int nitems,

@@ -46,8 +46,9 @@ struct ServeItem {
 // Binomial approximation at the tree nodes (glint_draw).
 constexpr int kDrawDual = 0, kDrawSingle = 1, kDrawSingleOld = 2, kDrawWang = 3;
 
-// Source of the reflection probabilities p_k.
-constexpr int EV_E1 = 0, EV_E2 = 1, EV_GIVEN = 2;
+// Source of the reflection probabilities p_k (EV_NONE: smooth radiance only,
+// p left to the caller).
+constexpr int EV_E1 = 0, EV_E2 = 1, EV_GIVEN = 2, EV_NONE = 3;
 
 // E2: reflection probabilities of an anisotropic GGX footprint by quadrature
 // (Eq. probhk).  Points of the projected-area slope distribution in
@@ -268,6 +269,7 @@ __device__ __forceinline__ void smooth_and_probs(const ShadeArgs &a, long q, flo
     } else if (EV == EV_GIVEN) {
 #pragma unroll
         for (int k = 0; k < K; ++k) p[k] = __ldg(a.pk_in + q * K + k);
+    } else if (EV == EV_NONE) {
     } else {
         p[0] = tab.y + tab.x * ch[3];
 #pragma unroll

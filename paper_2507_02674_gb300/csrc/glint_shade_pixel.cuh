@@ -254,6 +254,10 @@ __device__ __forceinline__ void footprint_cell(float4 g3, float area, int l0, fl
     }
 }
 
+template <int K, bool INTEGER, bool DEBUG, int DRAW, int GRID>
+__device__ __forceinline__ void shade_draws(const ShadeArgs &a, long q, const float4 &g0, const float4 &g2,
+                                            const float4 &g3, float Lor, float Log, float Lob, const float *p);
+
 // Steps 1-5 for pixel q of the frame described by a.  DRAW selects the binomial
 // approximation at the tree nodes: dual-gated (the paper's), single-gated
 // (Eq. gated), the older single-gated form (Eq. oldgated), or the Wang 2020
@@ -287,6 +291,15 @@ __device__ __forceinline__ void shade_pixel(const ShadeArgs &a, long q) {
     float Lor, Log, Lob;
     float p[K];
     smooth_and_probs<K, EV>(a, q, g0, g1, g2, Lor, Log, Lob, p);
+    shade_draws<K, INTEGER, DEBUG, DRAW, GRID>(a, q, g0, g2, g3, Lor, Log, Lob, p);
+}
+
+// Steps 2-5 for foreground pixel q given its smooth radiance (Lor, Log, Lob)
+// and reflection probabilities p.
+template <int K, bool INTEGER, bool DEBUG, int DRAW, int GRID>
+__device__ __forceinline__ void shade_draws(const ShadeArgs &a, long q, const float4 &g0, const float4 &g2,
+                                            const float4 &g3, float Lor, float Log, float Lob, const float *p) {
+    constexpr int NS = GRID ? 12 : 6;  // grid samples per pixel
 
     // ---- 2. footprint, microfacet count, grid level
     const float area = footprint_area(g3.x, g3.y, g3.z, g3.w);

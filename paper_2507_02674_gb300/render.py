@@ -48,8 +48,6 @@ class Frame:
               grid: int = glint.GRID_ISOTROPIC):
         if out is None:
             out = torch.empty(width * height, 4, device=planes[0].device)
-        if evaluator == glint.EVAL_MLP and p_scratch is None:
-            p_scratch = torch.empty(width * height, self.cfg.K, device=planes[0].device)
         glint.shade(self.ctx, self.env, planes, width, height, out, seed, count_mode, debug, stream, tangent,
                     evaluator, e2_samples, mlp, p_scratch, draw, gamma, grid)
         return out

@@ -255,9 +255,10 @@ def test_shade_with_given_probabilities(gl, orc):
 
 def test_mlp_paths_agree(gl):
     """Fused inference = glint_mlp_features then glint_mlp_forward; the MLP
-    evaluator = fused inference into the scratch buffer then shading with those
-    p_k (both bit for bit); glint_reflect_probs agrees with the debug p_k of E1
-    and E2 shading to FP32 rounding."""
+    evaluator (inputs, network and draws in one kernel, p_k kept on chip) =
+    shading with the p_k of glint_mlp_infer (both bit for bit);
+    glint_reflect_probs agrees with the debug p_k of E1 and E2 shading to FP32
+    rounding."""
     glint, render, ctx, torch = gl
     K = 8
     mp = MethodParams(K=K, Wo=128, seed=3)
@@ -280,17 +281,20 @@ def test_mlp_paths_agree(gl):
     fg = torch.from_numpy(gb.rows16()[:, 3] > 0).cuda()
     torch.cuda.synchronize()
     assert torch.equal(p_inf[fg], p_two[fg]) and torch.all(p_inf[~fg] == 0)
-    scratch = torch.zeros(n, K, device="cuda")
     dbg = glint.debug_buffers(n, K)
     img = fr.shade(planes, gb.width, gb.height, seed=mp.seed, debug=dbg, tangent=tan, evaluator=glint.EVAL_MLP,
-                   mlp=net, p_scratch=scratch)
-    assert ctx.last_launches() == 2
-    img2 = fr.shade(planes, gb.width, gb.height, seed=mp.seed, evaluator=glint.EVAL_GIVEN, p_scratch=p_inf)
+                   mlp=net)
+    assert ctx.last_launches() == 1
+    dbg2 = glint.debug_buffers(n, K)
+    img2 = fr.shade(planes, gb.width, gb.height, seed=mp.seed, debug=dbg2, evaluator=glint.EVAL_GIVEN, p_scratch=p_inf)
+    img3 = fr.shade(planes, gb.width, gb.height, seed=mp.seed, tangent=tan, evaluator=glint.EVAL_MLP, mlp=net)
     p_probs = fr.probs(planes, gb.width, gb.height, evaluator=glint.EVAL_MLP, tangent=tan, mlp=net)
     torch.cuda.synchronize()
-    assert torch.equal(scratch, p_inf) and torch.equal(p_probs, p_inf)
-    assert torch.equal(img, img2)
+    assert torch.equal(p_probs, p_inf)
+    assert torch.equal(img, img2) and torch.equal(img3, img2)
     assert torch.equal(dbg["p"][fg], p_inf[fg])
+    for k in dbg:
+        assert torch.equal(dbg[k], dbg2[k]), k
     for ev in (glint.EVAL_E1, glint.EVAL_E2):
         d = glint.debug_buffers(n, K)
         fr.shade(planes, gb.width, gb.height, seed=mp.seed, debug=d, tangent=tan, evaluator=ev)

@@ -315,9 +315,7 @@ def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed
     steps = args.surrogate_steps
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for i in range(steps):
-        lr = max(SURROGATE_LR * 0.5 * (1 + math.cos(math.pi * i / steps)), 1e-5)
-        net.train_step(X, L, Y, i * SURROGATE_BATCH, SURROGATE_BATCH, lr, stream=stream)
+    net.train(X, L, Y, 0, SURROGATE_BATCH, steps, SURROGATE_LR, 1e-5, stream=stream)
     b.record(stream)
     final_loss = net.train_step(X, L, Y, 0, SURROGATE_BATCH, 0.0, want_loss=True, stream=stream)
     torch.cuda.synchronize(dev)

@@ -425,6 +425,17 @@ glint_status glint_mlp_forward(const glint_mlp *mlp, const uint16_t *x, const fl
 glint_status glint_mlp_train_step(glint_mlp *mlp, const uint16_t *x, const float *lp, const float *targets,
                                   long n_total, long first, long batch, float lr, float *loss_out, void *stream);
 
+/* `steps` Adam steps, enqueued without returning to the caller in between:
+ * step i trains on samples first + i*batch, ... (indices modulo n_total) with
+ * learning rate max(lr_max * (1 + cos(pi i / steps)) / 2, lr_min) (a cosine
+ * schedule), exactly as the same sequence of glint_mlp_train_step calls would
+ * (same kernels, same order: the results are equal bit for bit).  No counterpart in the
+ * paper (the surrogate is this library's).  0 < lr_min <= lr_max < 1; x, lp,
+ * targets as glint_mlp_train_step.  Enqueued on `stream`; two launches per
+ * step. */
+glint_status glint_mlp_train(glint_mlp *mlp, const uint16_t *x, const float *lp, const float *targets, long n_total,
+                             long first, long batch, long steps, float lr_max, float lr_min, void *stream);
+
 /* p_out (device, width*height*K floats) = the network's p_k of every pixel of
  * `gbuf` under `env` (inputs computed on the fly, one persistent launch);
  * background pixels get 0.  The network's K must equal the environment's.

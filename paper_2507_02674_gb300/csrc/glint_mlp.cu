@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -83,12 +84,26 @@ __device__ __forceinline__ uint32_t wd(const __nv_bfloat16 *m, int r, int w) {
     return reinterpret_cast<const uint32_t *>(m)[word_at(r, w)];
 }
 
-// Copy a row-major [rows][64] BF16 matrix from global memory into the
-// swizzled layout.
-__device__ __forceinline__ void copy_swz(__nv_bfloat16 *dst, const __nv_bfloat16 *src, int rows) {
-    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
-    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
-    for (int i = threadIdx.x; i < rows * 32; i += blockDim.x) d32[word_at(i >> 5, i & 31)] = s32[i];
+// Copy a row-major [ROWS][64] BF16 matrix from global memory into the
+// swizzled layout, 16 bytes a thread at a time, for blocks of NT threads: all
+// of a thread's loads are issued before its stores, so their latencies overlap
+// instead of adding up.
+template <int ROWS, int NT>
+__device__ __forceinline__ void copy_swz(__nv_bfloat16 *dst, const __nv_bfloat16 *src) {
+    constexpr int kChunks = ROWS * 8, kPer = (kChunks + NT - 1) / NT;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    uint4 v[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int i = j * NT + (int)threadIdx.x;
+        if (i < kChunks) v[j] = __ldg(s4 + i);
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int i = j * NT + (int)threadIdx.x;
+        if (i < kChunks) d4[(i >> 3) * 8 + ((i & 7) ^ ((i >> 3) & 7))] = v[j];
+    }
 }
 
 struct SmemW {
@@ -99,15 +114,18 @@ struct SmemWB {
     __nv_bfloat16 w2[kHid * kHid], w3[kHid * kOutPad];  // [in][out] (backward)
 };
 
+template <int NT>
 __device__ void load_weights(SmemW &s, const __nv_bfloat16 *wt, const float *params) {
-    copy_swz(s.w1t, wt, kHid);
-    copy_swz(s.w2t, wt + kHid * kIn, kHid);
-    copy_swz(s.w3t, wt + kHid * kIn + kHid * kHid, kOutPad);
-    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
-        s.b1[i] = params[kOffB1 + i];
-        s.b2[i] = params[kOffB2 + i];
+    copy_swz<kHid, NT>(s.w1t, wt);
+    copy_swz<kHid, NT>(s.w2t, wt + kHid * kIn);
+    copy_swz<kOutPad, NT>(s.w3t, wt + kHid * kIn + kHid * kHid);
+    const int i = threadIdx.x;
+    if (i < kHid) {
+        s.b1[i] = __ldg(params + kOffB1 + i);
+        s.b2[i] = __ldg(params + kOffB2 + i);
+    } else if (i < kHid + kOutPad) {
+        s.b3[i - kHid] = __ldg(params + kOffB3 + i - kHid);
     }
-    for (int i = threadIdx.x; i < kOutPad; i += blockDim.x) s.b3[i] = params[kOffB3 + i];
 }
 
 // One layer for a warp's 16-row tile: c[j] = bias + A (16 x 64) W^T[j-th 8 columns].
@@ -292,7 +310,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_forward(const uint4 *__restrict__ x
                                                      int K, const __nv_bfloat16 *__restrict__ wt,
                                                      const float *__restrict__ params, float *__restrict__ p_out) {
     __shared__ SmemInfer sm;
-    load_weights(sm.w, wt, params);
+    load_weights<kNT>(sm.w, wt, params);
     const long ntiles = (n + kNT - 1) / kNT;
 #pragma unroll 1
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -323,7 +341,7 @@ template <int K>
 __global__ void __launch_bounds__(kNT, 4) k_mlp_infer(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
                                                    const float *__restrict__ params, float *__restrict__ p_out) {
     __shared__ SmemInfer sm;
-    load_weights(sm.w, wt, params);
+    load_weights<kNT>(sm.w, wt, params);
     const long ntiles = (a.npix + kNT - 1) / kNT;
 #pragma unroll 1
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(kNT, 4) k_mlp_serve(const ShadeArgs *__restric
         __syncthreads();
         if (sa.mlp_wt != held) {
             held = sa.mlp_wt;
-            load_weights(sm.w, reinterpret_cast<const __nv_bfloat16 *>(sa.mlp_wt), sa.mlp_params);
+            load_weights<kNT>(sm.w, reinterpret_cast<const __nv_bfloat16 *>(sa.mlp_wt), sa.mlp_params);
         }
         const long end = item.first + item.count;
 #pragma unroll 1
@@ -437,7 +455,7 @@ __global__ void __launch_bounds__(kFusedNT, 3) k_shade_mlp(ShadeArgs a, const __
                                                           const float *__restrict__ params) {
     extern __shared__ __align__(16) unsigned char fused_smem[];
     SmemFused &sm = *reinterpret_cast<SmemFused *>(fused_smem);
-    load_weights(sm.w, wt, params);
+    load_weights<kFusedNT>(sm.w, wt, params);
     const long q = (long)blockIdx.x * kFusedNT + threadIdx.x;
     float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f);
     bool fg = false;
@@ -517,11 +535,43 @@ __global__ void __launch_bounds__(kNT) k_mlp_features(ShadeArgs a, uint4 *__rest
 }
 
 // ------------------------------------------------------------------ training
-// Forward and backward over chunks of 128 samples.  Block b handles chunks
+// Forward and backward over chunks of kChunk samples.  Block b handles chunks
 // b, b + G, b + 2G, ... (G = gridDim.x) of the batch and accumulates its
 // gradient (each sample's loss weighted by 1/batch) in partial[b][kP], always
 // in the same order, so the result does not depend on scheduling; its summed
-// cross-entropy goes to loss[b].
+// cross-entropy goes to loss[b].  A chunk of 32 samples gives a batch of 8192
+// 256 blocks, so every SM has work; the 16-row tiles of the chunk go to the
+// warps in turn.
+constexpr int kChunk = 32;
+static_assert(kChunk * 8 % 128 == 0, "whole 16-byte pieces of inputs per thread");
+
+// Fragments of the transposed operands of the weight-gradient products
+// (ldmatrix .trans from row-major [samples][cols] tiles): the 16 x 16 A
+// fragment of act^T (rows = columns m0.., k = samples k0..) from a swizzled
+// [rows][64] BF16 tile, and the 16 x 8 B fragments of two adjacent n-tiles
+// (n0.., n0 + 8..) of a [rows][ld] tile (ld = 64 swizzled or 16 plain).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t r[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ uint32_t row_chunk_addr(const __nv_bfloat16 *m, int ld, int row, int chunk) {
+    const int c = ld == 64 ? (chunk ^ (row & 7)) : chunk;  // 16-byte chunk within the row
+    return smem_u32(m + row * ld + c * 8);
+}
+__device__ __forceinline__ void frag_at(const __nv_bfloat16 *act, int k0, int m0, uint32_t a[4]) {
+    const int L = threadIdx.x & 31;
+    ldsm_x4_trans(a, row_chunk_addr(act, 64, k0 + (L & 7) + ((L >> 4) << 3), (m0 >> 3) + ((L >> 3) & 1)));
+}
+__device__ __forceinline__ void frag_b2(const __nv_bfloat16 *dz, int ld, int k0, int n0, uint32_t b[4]) {
+    // matrices: (k0.., n0), (k0 + 8.., n0), (k0.., n0 + 8), (k0 + 8.., n0 + 8)
+    const int L = threadIdx.x & 31;
+    ldsm_x4_trans(b, row_chunk_addr(dz, ld, k0 + (L & 7) + (((L >> 3) & 1) << 3), (n0 >> 3) + (L >> 4)));
+}
+
 template <int NT>
 __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, const float *__restrict__ lpg,
                                                   const float *__restrict__ targets, long n_total, long first,
@@ -529,90 +579,108 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
                                                   const __nv_bfloat16 *__restrict__ wb,
                                                   const float *__restrict__ params, float *__restrict__ partial,
                                                   float *__restrict__ loss) {
+    constexpr int CH = kChunk, MT = CH / 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemW &sw = *reinterpret_cast<SmemW *>(smem_raw);
     SmemWB &sb = *reinterpret_cast<SmemWB *>(smem_raw + sizeof(SmemW));
     __nv_bfloat16 *xs = reinterpret_cast<__nv_bfloat16 *>(smem_raw + sizeof(SmemW) + sizeof(SmemWB));
-    __nv_bfloat16 *h1 = xs + kNT * 64;
-    __nv_bfloat16 *h2 = h1 + kNT * 64;     // H2, later dZ1
-    __nv_bfloat16 *dz = h2 + kNT * 64;     // dZ2
-    __nv_bfloat16 *dz3 = dz + kNT * 64;    // [kNT][16]
-    float *red = reinterpret_cast<float *>(dz3 + kNT * 16);  // kNT floats
-    float *lps = red + kNT;                                   // [kNT][kLpStride] log-priors
+    __nv_bfloat16 *h1 = xs + CH * 64;
+    __nv_bfloat16 *h2 = h1 + CH * 64;     // H2, later dZ1
+    __nv_bfloat16 *dz = h2 + CH * 64;     // dZ2
+    __nv_bfloat16 *dz3 = dz + CH * 64;    // [CH][16]
+    float *red = reinterpret_cast<float *>(dz3 + CH * 16);  // kNT floats
+    float *lps = red + kNT;                                  // [CH][kLpStride] log-priors
+    float *ys = lps + CH * kLpStride;                        // [CH][16] targets
 
-    load_weights(sw, wt, params);
-    copy_swz(sb.w2, wb, kHid);
-    for (int i = threadIdx.x; i < kHid * kOutPad; i += kNT) sb.w3[i] = wb[kHid * kHid + i];
+    load_weights<kNT>(sw, wt, params);
+    copy_swz<kHid, kNT>(sb.w2, wb);
+    {  // W3 [in][out] unswizzled: 64 rows of 16 BF16, 2 chunks of 16 bytes each
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(wb + kHid * kHid);
+        reinterpret_cast<uint4 *>(sb.w3)[threadIdx.x] = __ldg(s4 + threadIdx.x);
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float invB = 1.f / (float)batch;
-    const long nchunks = (batch + kNT - 1) / kNT;
+    const long nchunks = (batch + CH - 1) / CH;
     float *part = partial + (size_t)blockIdx.x * kP;
     float lsum = 0.f;
 
     // dst (+)= A^T dZ over the chunk's samples: M = inputs (warp w owns rows
-    // [16 w, 16 w + 16)), N = outputs, K = samples
-    auto grad_w = [&](const __nv_bfloat16 *act, const __nv_bfloat16 *dzm, int ldz, int ntiles, float *dst, int ldo,
-                      bool acc) {
+    // [16 w, 16 w + 16)), N = outputs (ntiles of 8), K = samples
+    auto grad_w = [&](const __nv_bfloat16 *act, const __nv_bfloat16 *dzm, int ldz, float *dst, int ldo, bool acc,
+                      auto ntiles_c) {
+        constexpr int NJ = decltype(ntiles_c)::value;
         const int m0 = warp * 16;
-#pragma unroll 1
-        for (int j = 0; j < ntiles; ++j) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-            for (int ks = 0; ks < kNT / 16; ++ks) {
-                const int k0 = ks * 16 + 2 * t;
-                uint32_t a[4];
-                a[0] = pair16(el(act, k0, m0 + g), el(act, k0 + 1, m0 + g));
-                a[1] = pair16(el(act, k0, m0 + g + 8), el(act, k0 + 1, m0 + g + 8));
-                a[2] = pair16(el(act, k0 + 8, m0 + g), el(act, k0 + 9, m0 + g));
-                a[3] = pair16(el(act, k0 + 8, m0 + g + 8), el(act, k0 + 9, m0 + g + 8));
-                uint32_t b0, b1;
-                if (ldz == 64) {  // swizzled [rows][64]
-                    b0 = pair16(el(dzm, k0, j * 8 + g), el(dzm, k0 + 1, j * 8 + g));
-                    b1 = pair16(el(dzm, k0 + 8, j * 8 + g), el(dzm, k0 + 9, j * 8 + g));
-                } else {
-                    b0 = pair16(dzm + (k0) * ldz + j * 8 + g, dzm + (k0 + 1) * ldz + j * 8 + g);
-                    b1 = pair16(dzm + (k0 + 8) * ldz + j * 8 + g, dzm + (k0 + 9) * ldz + j * 8 + g);
-                }
-                mma16816(c, a, b0, b1);
+        float c[NJ][4];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < MT; ++ks) {
+            uint32_t a[4];
+            frag_at(act, ks * 16, m0, a);
+#pragma unroll
+            for (int j = 0; j < NJ; j += 2) {
+                uint32_t b[4];
+                frag_b2(dzm, ldz, ks * 16, j * 8, b);
+                mma16816(c[j], a, b[0], b[1]);
+                mma16816(c[j + 1], a, b[2], b[3]);
             }
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
             const int col = j * 8 + 2 * t;
             float *d0 = dst + (m0 + g) * ldo + col, *d1 = dst + (m0 + g + 8) * ldo + col;
-            if (acc) { c[0] += d0[0]; c[1] += d0[1]; c[2] += d1[0]; c[3] += d1[1]; }
-            d0[0] = c[0]; d0[1] = c[1]; d1[0] = c[2]; d1[1] = c[3];
+            float v0 = c[j][0], v1 = c[j][1], v2 = c[j][2], v3 = c[j][3];
+            if (acc) { v0 += d0[0]; v1 += d0[1]; v2 += d1[0]; v3 += d1[1]; }
+            d0[0] = v0; d0[1] = v1; d1[0] = v2; d1[1] = v3;
         }
     };
-    // column sums of a [kNT][ld] BF16 matrix into dst (+)= (one thread per column)
+    // column sums of a [CH][ld] BF16 matrix into dst (+)= (one thread per column)
     auto col_sum = [&](const __nv_bfloat16 *m, int ld, int col, float *dst, bool acc) {
         float s = 0.f;
-        for (int r = 0; r < kNT; ++r) s += __bfloat162float(ld == 64 ? *el(m, r, col) : m[r * ld + col]);
+#pragma unroll 8
+        for (int r = 0; r < CH; ++r) s += __bfloat162float(ld == 64 ? *el(m, r, col) : m[r * ld + col]);
         *dst = acc ? *dst + s : s;
     };
 
 #pragma unroll 1
     for (long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const bool acc = chunk != (long)blockIdx.x;
-        const long base = first + chunk * kNT;  // samples [base, base + kNT) of the data set, wrapping
+        const long base = first + chunk * CH;  // samples [base, base + CH) of the data set, wrapping
         const long nb = first + batch;
         {
             uint4 *xs4 = reinterpret_cast<uint4 *>(xs);
+            constexpr int kXPer = CH * 8 / kNT;  // 16-byte pieces of the chunk's inputs per thread
+            uint4 xv[kXPer];
 #pragma unroll
-            for (int it = 0; it < 8; ++it) {
-                const int idx = it * kNT + threadIdx.x;
-                const int r = idx >> 3, q = idx & 7;
+            for (int it = 0; it < kXPer; ++it) {
+                const int idx = it * kNT + threadIdx.x, r = idx >> 3, q = idx & 7;
                 const long i = base + r;
-                xs4[r * 8 + (q ^ (r & 7))] = (i < nb) ? __ldg(xg + (i % n_total) * 8 + q) : make_uint4(0u, 0u, 0u, 0u);
+                xv[it] = (i < nb) ? __ldg(xg + (i % n_total) * 8 + q) : make_uint4(0u, 0u, 0u, 0u);
             }
-            for (int idx = threadIdx.x; idx < kNT * kOutPad; idx += kNT) {
+#pragma unroll
+            for (int it = 0; it < kXPer; ++it) {
+                const int idx = it * kNT + threadIdx.x, r = idx >> 3, q = idx & 7;
+                xs4[r * 8 + (q ^ (r & 7))] = xv[it];
+            }
+#pragma unroll
+            for (int it = 0; it < (CH * kOutPad + kNT - 1) / kNT; ++it) {
+                const int idx = it * kNT + threadIdx.x;
                 const int r = idx / kOutPad, k = idx % kOutPad;
                 const long i = base + r;
-                lps[r * kLpStride + k] = (i < nb && k < K) ? __ldg(lpg + (i % n_total) * K + k) : 0.f;
+                const bool ok = idx < CH * kOutPad && i < nb && k < K;
+                const long src = (i % n_total) * K + k;
+                const float lv = ok ? __ldg(lpg + src) : 0.f, yv = ok ? __ldg(targets + src) : 0.f;
+                if (idx < CH * kOutPad) {
+                    lps[r * kLpStride + k] = lv;
+                    ys[r * 16 + k] = yv;
+                }
             }
         }
         __syncthreads();
         // forward, and dZ3 = (softmax * sum(y) - y) / batch
 #pragma unroll 1
-        for (int mt = 0; mt < 2; ++mt) {
-            const int row0 = warp * 32 + mt * 16;
+        for (int mt = warp; mt < MT; mt += kNT / 32) {
+            const int row0 = mt * 16;
             uint32_t a[4][4];
             float c[8][4];
             load_a(xs, row0, a);
@@ -630,14 +698,13 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
                 const int r = row0 + g + 8 * h;
                 const long i = base + r;
                 const bool live = i < nb;
-                const long s = live ? i % n_total : 0;
                 float y[2][2], ysum = 0.f;
 #pragma unroll
                 for (int j = 0; j < 2; ++j)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int col = j * 8 + 2 * t + e;
-                        y[j][e] = (live && col < K) ? __ldg(targets + s * K + col) : 0.f;
+                        y[j][e] = ys[r * 16 + col];  // 0 past K and for rows past the batch
                         ysum += y[j][e];
                     }
                 ysum += __shfl_xor_sync(0xffffffffu, ysum, 1);
@@ -660,8 +727,8 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
         __syncthreads();
         // dZ2 = (dZ3 W3^T) * 1[H2 > 0]; W3 [in][out] gives (k, k+1) pairs
 #pragma unroll 1
-        for (int mt = 0; mt < 2; ++mt) {
-            const int row0 = warp * 32 + mt * 16;
+        for (int mt = warp; mt < MT; mt += kNT / 32) {
+            const int row0 = mt * 16;
             uint32_t a[4];
             {
                 const __nv_bfloat16 *r0 = dz3 + (row0 + g) * 16 + 2 * t;
@@ -686,16 +753,16 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
             store_c_bf16(dz, row0, c, false);
         }
         __syncthreads();
-        grad_w(h2, dz3, 16, 2, part + kOffW3, kOutPad, acc);
-        grad_w(h1, dz, 64, 8, part + kOffW2, kHid, acc);
+        grad_w(h2, dz3, 16, part + kOffW3, kOutPad, acc, std::integral_constant<int, 2>{});
+        grad_w(h1, dz, 64, part + kOffW2, kHid, acc, std::integral_constant<int, 8>{});
         if (threadIdx.x < kOutPad) col_sum(dz3, 16, threadIdx.x, part + kOffB3 + threadIdx.x, acc);
         else if (threadIdx.x < kOutPad + kHid)
             col_sum(dz, 64, threadIdx.x - kOutPad, part + kOffB2 + threadIdx.x - kOutPad, acc);
         __syncthreads();
         // dZ1 = (dZ2 W2^T) * 1[H1 > 0], written over H2
 #pragma unroll 1
-        for (int mt = 0; mt < 2; ++mt) {
-            const int row0 = warp * 32 + mt * 16;
+        for (int mt = warp; mt < MT; mt += kNT / 32) {
+            const int row0 = mt * 16;
             uint32_t a[4][4];
             load_a(dz, row0, a);
             float c[8][4];
@@ -718,7 +785,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
             store_c_bf16(h2, row0, c, false);
         }
         __syncthreads();
-        grad_w(xs, h2, 64, 8, part + kOffW1, kHid, acc);
+        grad_w(xs, h2, 64, part + kOffW1, kHid, acc, std::integral_constant<int, 8>{});
         if (threadIdx.x < kHid) col_sum(h2, 64, threadIdx.x, part + kOffB1 + threadIdx.x, acc);
         __syncthreads();  // xs, h1, h2 and dz are rewritten by the next chunk
     }
@@ -731,13 +798,46 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
     }
 }
 
-// Sum the per-block gradients in block order (deterministic) into grad, then
-// (if lr > 0) one Adam step on the FP32 master copy and the BF16 copies.
-__global__ void k_mlp_reduce_adam(const float *__restrict__ partial, int nblk, float *__restrict__ grad,
-                                  float *__restrict__ params, float *__restrict__ m, float *__restrict__ v, int K, float lr,
-                                  float beta1, float beta2, float eps, float bc1, float bc2) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= kP) return;
+// The BF16 copies (forward W^T [out][in], backward W [in][out]) of FP32
+// parameter i (biases have none).
+__device__ __forceinline__ void refresh_one(int i, float w, __nv_bfloat16 *__restrict__ wt,
+                                            __nv_bfloat16 *__restrict__ wb) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(w);
+    if (i >= kOffW1 && i < kOffB1) {
+        const int k = i - kOffW1, in = k / kHid, out = k % kHid;
+        wt[out * kIn + in] = b;
+    } else if (i >= kOffW2 && i < kOffB2) {
+        const int k = i - kOffW2, in = k / kHid, out = k % kHid;
+        wt[kHid * kIn + out * kHid + in] = b;
+        wb[k] = b;
+    } else if (i >= kOffW3 && i < kOffB3) {
+        const int k = i - kOffW3, in = k / kOutPad, out = k % kOutPad;
+        wt[kHid * kIn + kHid * kHid + out * kHid + in] = b;
+        wb[kHid * kHid + k] = b;
+    }
+}
+
+// Sum the per-block gradients into grad in a fixed order (deterministic):
+// a block of 256 threads takes 32 consecutive parameters; warp w sums the
+// partials of blocks w, w + 8, w + 16, ... in that order, and the eight warp
+// sums are added in warp order.  Then (if lr > 0) one Adam step on the FP32
+// master copy and, when wt is not NULL, its BF16 copies.
+constexpr int kRedParams = 32, kRedWarps = 8;
+__global__ void __launch_bounds__(kRedParams * kRedWarps) k_mlp_reduce_adam(
+    const float *__restrict__ partial, int nblk, float *__restrict__ grad, float *__restrict__ params,
+    float *__restrict__ m, float *__restrict__ v, int K, float lr, float beta1, float beta2, float eps, float bc1,
+    float bc2, __nv_bfloat16 *__restrict__ wt, __nv_bfloat16 *__restrict__ wb) {
+    __shared__ float part_sum[kRedWarps][kRedParams];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * kRedParams + lane;
+    float gs = 0.f;
+    if (i < kP) {
+#pragma unroll 4
+        for (int b = warp; b < nblk; b += kRedWarps) gs += partial[(size_t)b * kP + i];
+    }
+    part_sum[warp][lane] = gs;
+    __syncthreads();
+    if (warp != 0 || i >= kP) return;
     // output columns >= K carry no parameters: no gradient, no update
     const bool unused = (i >= kOffW3 && i < kOffB3 && (i - kOffW3) % kOutPad >= K) || (i >= kOffB3 && i - kOffB3 >= K);
     if (unused) {
@@ -745,7 +845,8 @@ __global__ void k_mlp_reduce_adam(const float *__restrict__ partial, int nblk, f
         return;
     }
     float g = 0.f;
-    for (int b = 0; b < nblk; ++b) g += partial[(size_t)b * kP + i];
+#pragma unroll
+    for (int w = 0; w < kRedWarps; ++w) g += part_sum[w][lane];
     grad[i] = g;
     if (!(lr > 0.f)) return;
     const float mi = beta1 * m[i] + (1.f - beta1) * g;
@@ -754,6 +855,7 @@ __global__ void k_mlp_reduce_adam(const float *__restrict__ partial, int nblk, f
     v[i] = vi;
     const float w = params[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
     params[i] = w;
+    if (wt) refresh_one(i, w, wt, wb);
 }
 
 // BF16 copies of the weights in both layouts from the FP32 master copy.
@@ -815,8 +917,8 @@ namespace {
 constexpr int kNW = kIn * kHid + kHid * kHid + kHid * kOutPad;  // weights (no biases)
 
 size_t grad_smem() {
-    return sizeof(SmemW) + sizeof(SmemWB) + sizeof(__nv_bfloat16) * (4 * kNT * 64 + kNT * 16) +
-           sizeof(float) * (kNT + kNT * kLpStride);
+    return sizeof(SmemW) + sizeof(SmemWB) + sizeof(__nv_bfloat16) * (4 * kChunk * 64 + kChunk * 16) +
+           sizeof(float) * (kNT + kChunk * kLpStride + kChunk * 16);
 }
 
 void mlp_free(glint_mlp *g) {
@@ -958,7 +1060,7 @@ glint_status glint_mlp_create(glint_ctx *ctx, int K, long max_batch, uint32_t se
         set_error("glint_mlp_create: a surrogate kernel does not fit an SM");
         st = GLINT_ERR_UNSUPPORTED;
     }
-    const long nchunks_max = (max_batch + kNT - 1) / kNT;
+    const long nchunks_max = (max_batch + kChunk - 1) / kChunk;
     g->max_grid = (int)std::min<long>((long)per_sm * ctx->num_sms, nchunks_max);
     g->infer_grid = std::max(1, std::min(per_sm_inf, per_sm_fwd) * ctx->num_sms);
     auto alloc = [&](void **p, size_t bytes) {
@@ -1085,6 +1187,51 @@ glint_status glint_mlp_forward(const glint_mlp *g, const uint16_t *x, const floa
     return cuda_status(cudaGetLastError(), "glint_mlp_forward");
 }
 
+namespace {
+// One optimisation step (two launches): the per-block gradients, then their
+// sum in block order with the Adam update of the FP32 parameters and of their
+// BF16 copies.  Returns the number of gradient blocks.
+int enqueue_step(glint_mlp *g, const uint16_t *x, const float *lp, const float *targets, long n_total, long first,
+                 long batch, float lr, cudaStream_t s) {
+    const long nchunks = (batch + kChunk - 1) / kChunk;
+    const int grid = (int)std::min<long>(nchunks, g->max_grid);
+    k_mlp_grad<1><<<grid, kNT, grad_smem(), s>>>(reinterpret_cast<const uint4 *>(x), lp, targets, n_total,
+                                                 first % n_total, batch, g->K, g->wt, g->wb, g->params, g->partial,
+                                                 g->loss);
+    const long t = lr > 0.f ? g->step + 1 : std::max(g->step, 1L);
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)t));
+    const float bc2 = (float)(1.0 - std::pow(0.999, (double)t));
+    k_mlp_reduce_adam<<<(kP + kRedParams - 1) / kRedParams, kRedParams * kRedWarps, 0, s>>>(
+        g->partial, grid, g->grad, g->params, g->m, g->v, g->K, lr, 0.9f, 0.999f, 1e-8f, bc1, bc2, g->wt, g->wb);
+    if (lr > 0.f) g->step = t;
+    return grid;
+}
+}  // namespace
+
+glint_status glint_mlp_train(glint_mlp *g, const uint16_t *x, const float *lp, const float *targets, long n_total,
+                             long first, long batch, long steps, float lr_max, float lr_min, void *stream) {
+    set_error("%s", "");
+    if (!g || !x || !lp || !targets) { set_error("glint_mlp_train: NULL argument"); return GLINT_ERR_INVALID_ARG; }
+    if (batch < 1 || batch > g->max_batch || n_total < 1 || first < 0 || steps < 0 || !(lr_max > 0.f) ||
+        !(lr_max < 1.f) || !(lr_min > 0.f) || !(lr_min <= lr_max)) {
+        set_error("glint_mlp_train: batch %ld outside [1, %ld], empty data, first or steps < 0, or not "
+                  "0 < lr_min <= lr_max < 1", batch, g->max_batch);
+        return GLINT_ERR_INVALID_ARG;
+    }
+    if (!aligned(x, 16) || !aligned(lp, 4) || !aligned(targets, 4)) {
+        set_error("glint_mlp_train: x must be 16-byte aligned, lp and targets 4-byte aligned");
+        return GLINT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (long i = 0; i < steps; ++i) {
+        const double cosine = 0.5 * (1.0 + std::cos(3.14159265358979323846 * (double)i / (double)steps));
+        const float lr = (float)std::max((double)lr_max * cosine, (double)lr_min);
+        enqueue_step(g, x, lp, targets, n_total, (first + i * batch) % n_total, batch, lr, s);
+    }
+    g->last_launches = (int)std::min<long>(2 * steps, 1L << 30);
+    return cuda_status(cudaGetLastError(), "glint_mlp_train");
+}
+
 glint_status glint_mlp_train_step(glint_mlp *g, const uint16_t *x, const float *lp, const float *targets,
                                   long n_total, long first, long batch, float lr, float *loss_out, void *stream) {
     set_error("%s", "");
@@ -1099,23 +1246,8 @@ glint_status glint_mlp_train_step(glint_mlp *g, const uint16_t *x, const float *
         return GLINT_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const long nchunks = (batch + kNT - 1) / kNT;
-    const int grid = (int)std::min<long>(nchunks, g->max_grid);
-    k_mlp_grad<1><<<grid, kNT, grad_smem(), s>>>(reinterpret_cast<const uint4 *>(x), lp, targets, n_total,
-                                                 first % n_total, batch, g->K, g->wt, g->wb, g->params, g->partial,
-                                                 g->loss);
-    const long t = lr > 0.f ? g->step + 1 : std::max(g->step, 1L);
-    const float bc1 = (float)(1.0 - std::pow(0.9, (double)t));
-    const float bc2 = (float)(1.0 - std::pow(0.999, (double)t));
-    k_mlp_reduce_adam<<<(kP + 255) / 256, 256, 0, s>>>(g->partial, grid, g->grad, g->params, g->m, g->v, g->K, lr,
-                                                       0.9f, 0.999f, 1e-8f, bc1, bc2);
-    int nl = 2;
-    if (lr > 0.f) {
-        k_mlp_refresh<<<(kNW + 255) / 256, 256, 0, s>>>(g->params, g->wt, g->wb);
-        ++nl;
-        g->step = t;
-    }
-    g->last_launches = nl;
+    const int grid = enqueue_step(g, x, lp, targets, n_total, first, batch, lr, s);
+    g->last_launches = 2;
     glint_status st = cuda_status(cudaGetLastError(), "glint_mlp_train_step");
     if (st != GLINT_OK || !loss_out) return st;
     std::vector<float> l(grid);

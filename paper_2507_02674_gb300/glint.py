@@ -130,6 +130,7 @@ def _load():
     lib.glint_mlp_features.argtypes = [P, P, ctypes.POINTER(GBufferDesc), P, P, P]
     lib.glint_mlp_forward.argtypes = [P, P, P, L, P, P]
     lib.glint_mlp_train_step.argtypes = [P, P, P, P, L, L, L, F, ctypes.POINTER(F), P]
+    lib.glint_mlp_train.argtypes = [P, P, P, P, L, L, L, L, F, F, P]
     lib.glint_mlp_infer.argtypes = [P, P, P, ctypes.POINTER(GBufferDesc), P, P]
     lib.glint_mlp_save.argtypes = [P, ctypes.c_char_p]
     lib.glint_mlp_load.argtypes = [P, ctypes.c_char_p, L, ctypes.POINTER(P)]
@@ -433,6 +434,11 @@ class Mlp:
         _check(lib.glint_mlp_train_step(self.handle, _dptr(x), _dptr(lp), _dptr(targets), x.shape[0], first, batch,
                                         lr, ctypes.byref(loss) if want_loss else None, _stream_handle(stream)))
         return float(loss.value) if want_loss else None
+
+    def train(self, x, lp, targets, first: int, batch: int, steps: int, lr_max: float, lr_min: float, stream=None):
+        """glint_mlp_train: `steps` Adam steps on consecutive batches with a cosine learning-rate schedule."""
+        _check(lib.glint_mlp_train(self.handle, _dptr(x), _dptr(lp), _dptr(targets), x.shape[0], first, batch, steps,
+                                   lr_max, lr_min, _stream_handle(stream)))
 
     def infer(self, env: "Env", planes, width: int, height: int, tangent, out, stream=None):
         """glint_mlp_infer: p_k of every pixel (inputs computed on the fly)."""

@@ -10,6 +10,8 @@ rounding boundary lies within the FP32 error of the filtered maps and
 directions; the network's outputs and gradients lie within the reference's
 error model of an FP32/BF16 evaluation (oracle.mlp.error_bounds), and their
 aggregate difference far below BF16 precision."""
+import math
+
 import numpy as np
 import pytest
 
@@ -226,6 +228,33 @@ def test_mlp_training_is_deterministic_and_resumes(gl, tmp_path):
     assert np.array_equal(pa.view(np.uint32), pd.view(np.uint32))
     assert a.step == b.step == c.step == d.step == 6
     assert not np.array_equal(pa, ck[0])
+
+
+def test_mlp_train_equals_step_by_step(gl):
+    """glint_mlp_train (many Adam steps in one call, cosine schedule) gives the
+    parameters, moments and step count of the same sequence of
+    glint_mlp_train_step calls, bit for bit."""
+    glint, render, ctx, torch = gl
+    K, n, batch, steps = 8, 20000, 4096, 7
+    rng = np.random.default_rng(97)
+    X = np.zeros((n, 64))
+    X[:, :51] = rng.uniform(0, 1, size=(n, 51))
+    x = torch.from_numpy(_bits(X)).cuda()
+    l = torch.from_numpy(np.log(synth.distributions(n, K, seed=98)).astype(np.float32)).cuda()
+    Y = torch.from_numpy(synth.distributions(n, K, seed=99)).cuda()
+    a = glint.Mlp(ctx, K, batch, seed=5)
+    a.train(x, l, Y, 1000, batch, steps, 3e-3, 1e-4)
+    b = glint.Mlp(ctx, K, batch, seed=5)
+    lr_max, lr_min = float(np.float32(3e-3)), float(np.float32(1e-4))  # as the C ABI receives them
+    for i in range(steps):
+        cosine = 0.5 * (1.0 + math.cos(math.pi * i / steps))
+        b.train_step(x, l, Y, (1000 + i * batch) % n, batch, float(np.float32(max(lr_max * cosine, lr_min))))
+    torch.cuda.synchronize()
+    for item in (glint.MLP_PARAMS, glint.MLP_ADAM_M, glint.MLP_ADAM_V, glint.MLP_GRAD):
+        assert np.array_equal(a.export(item).view(np.uint32), b.export(item).view(np.uint32)), item
+    assert a.step == b.step == steps
+    with pytest.raises(glint.GlintError):
+        a.train(x, l, Y, 0, batch, 3, 1e-3, 2e-3)  # lr_min above lr_max
 
 
 def test_shade_with_given_probabilities(gl, orc):

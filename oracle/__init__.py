@@ -411,7 +411,8 @@ def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab:
           tangents=None, e2_S: int = 16, env: "EnvOracle | None" = None, pk_in=None, draw: int = 0,
           gamma: float = 0.0, grid: int = 0) -> ShadeOracle:
     """Per-pixel shading (or_shade).  evaluator 0 = E1, 1 = E2 (needs tangents
-    and env), 2 = the p_k given in pk_in (npix x K)."""
+    and env), 2 = the p_k given in pk_in (npix x K), 3 = anisotropic E1 by
+    multi-tap filtered look-ups (needs tangents)."""
     lib = _load()
     gb16 = np.ascontiguousarray(gb16, dtype=np.float32).reshape(-1, 16)
     n = gb16.shape[0]
@@ -435,6 +436,9 @@ def shade(gb16: np.ndarray, pref: Filtered, s_min: float, s_max: float, lut_tab:
         tangents = np.ascontiguousarray(tangents, dtype=np.float32).reshape(-1, 4)
         mips = env.mips_flat
         H, W = env.ch0.shape[:2]
+    elif evaluator == 3:
+        tangents = np.ascontiguousarray(tangents, dtype=np.float32).reshape(-1, 4)
+        mips, W, H = None, 0, 0
     else:
         tangents, mips, W, H = None, None, 0, 0
     if evaluator == 2:

@@ -328,6 +328,7 @@ def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed
     p_e2 = fr.probs(planes, WIDTH, HEIGHT, evaluator=glint.EVAL_E2, e2_samples=E2_REF_S, tangent=tan, stream=stream)
     p_e2_16 = fr.probs(planes, WIDTH, HEIGHT, evaluator=glint.EVAL_E2, e2_samples=E2_S, tangent=tan, stream=stream)
     p_e1 = fr.probs(planes, WIDTH, HEIGHT, evaluator=glint.EVAL_E1, tangent=tan, stream=stream)
+    p_e1a = fr.probs(planes, WIDTH, HEIGHT, evaluator=glint.EVAL_E1_ANISO, tangent=tan, stream=stream)
     p_nn = net.infer(fr.env, planes, WIDTH, HEIGHT, tan, torch.empty(npix, K, device=dev), stream=stream)
     torch.cuda.synchronize(dev)
     fgm = planes[0][:, 3] > 0
@@ -363,7 +364,13 @@ def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed
         fr.shade(planes, WIDTH, HEIGHT, out=out, seed=seed, stream=stream, tangent=tan, evaluator=glint.EVAL_E2,
                  e2_samples=E2_S)
 
+    def e1a_step():
+        fr.update_env(stream)
+        fr.shade(planes, WIDTH, HEIGHT, out=out, seed=seed, stream=stream, tangent=tan,
+                 evaluator=glint.EVAL_E1_ANISO)
+
     ms_nn = timed(mlp_step, args.steps)
+    ms_e1a = timed(e1a_step, args.steps)
     ms_e2 = timed(e2_step, max(3, min(args.steps, 10)))
     return {
         "path": "env update + glint_shade with the surrogate fused in (per 256-pixel block: inputs, BF16 "
@@ -374,7 +381,11 @@ def surrogate(args, glint, render, ctx, fr, gb, planes, out, stream, flush, seed
         "vs_e2": {"e2_samples": E2_S, "e2_value": round(npix / (float(ms_e2.mean()) / 1e3) / 1e6, 3),
                   "e2_ms_per_step": round(float(ms_e2.mean()), 4),
                   "speedup": round(float(ms_e2.mean() / ms_nn.mean()), 2)},
-        "error_vs_e2_p_k": err(p_nn), "e1_error_vs_e2_p_k": err(p_e1), "e2_s16_error_vs_e2_p_k": err(p_e2_16),
+        "e1_aniso": {"path": "env update + shading with the multi-tap anisotropic E1 (five taps along the lobe)",
+                     "value": round(npix / (float(ms_e1a.mean()) / 1e3) / 1e6, 3),
+                     "ms_per_step": round(float(ms_e1a.mean()), 4)},
+        "error_vs_e2_p_k": err(p_nn), "e1_error_vs_e2_p_k": err(p_e1), "e1_aniso_error_vs_e2_p_k": err(p_e1a),
+        "e2_s16_error_vs_e2_p_k": err(p_e2_16),
         "error_reference": f"E2 with {E2_REF_S} x {E2_REF_S} points (within 0.03% RMSE of 128 x 128), foreground pixels",
         "train": {"samples": int(n_train), "label": f"E2 S={SURROGATE_LABEL_S}", "steps": steps,
                   "batch": SURROGATE_BATCH, "ms": round(train_ms, 1),

@@ -66,7 +66,13 @@ typedef enum glint_evaluator {
     GLINT_EVAL_E1 = 0, /* p_k from the filtered maps and tables (Eq. rtiblndf), isotropic sqrt(a_x a_y) */
     GLINT_EVAL_E2 = 1, /* p_k by per-pixel quadrature of the anisotropic NDF (Eq. probhk) */
     GLINT_EVAL_MLP = 2, /* p_k from a trained glint_mlp surrogate of E2 (no counterpart in the paper) */
-    GLINT_EVAL_GIVEN = 3 /* p_k supplied by the caller in params->p_scratch (width*height*K floats) */
+    GLINT_EVAL_GIVEN = 3, /* p_k supplied by the caller in params->p_scratch (width*height*K floats) */
+    GLINT_EVAL_E1_ANISO = 4 /* E1 with multi-tap look-ups along the anisotropic lobe (the multiple filtered
+                               look-ups the paper's related work and limitations point to for anisotropy):
+                               the lobe of reflected directions as an ellipse with axes J_t a_x, J_b a_y
+                               (J the derivatives of the mirror direction with respect to the slope), the
+                               filtered maps read at the minor axis' roughness at five Gauss-Hermite nodes
+                               along the major axis; needs the tangent plane */
 } glint_evaluator;
 
 typedef enum glint_count_mode {

@@ -406,7 +406,7 @@ static glint_status check_shade_args(const char *who, glint_ctx *ctx, const glin
         return GLINT_ERR_INVALID_ARG;
     }
     if (p->evaluator != GLINT_EVAL_E1 && p->evaluator != GLINT_EVAL_E2 && p->evaluator != GLINT_EVAL_MLP &&
-        p->evaluator != GLINT_EVAL_GIVEN) {
+        p->evaluator != GLINT_EVAL_GIVEN && p->evaluator != GLINT_EVAL_E1_ANISO) {
         set_error("%s: unknown evaluator %d", who, p->evaluator);
         return GLINT_ERR_INVALID_ARG;
     }
@@ -456,8 +456,9 @@ static glint_status check_shade_args(const char *who, glint_ctx *ctx, const glin
             set_error("%s: G-buffer planes must be 16-byte aligned", who);
             return GLINT_ERR_INVALID_ARG;
         }
-        if ((p->evaluator == GLINT_EVAL_E2 || p->evaluator == GLINT_EVAL_MLP) && !g->tangent) {
-            set_error("%s: the E2 and MLP evaluators need the tangent plane", who);
+        if ((p->evaluator == GLINT_EVAL_E2 || p->evaluator == GLINT_EVAL_MLP ||
+             p->evaluator == GLINT_EVAL_E1_ANISO) && !g->tangent) {
+            set_error("%s: the E2, MLP and anisotropic E1 evaluators need the tangent plane", who);
             return GLINT_ERR_INVALID_ARG;
         }
     }

@@ -47,8 +47,9 @@ struct ServeItem {
 constexpr int kDrawDual = 0, kDrawSingle = 1, kDrawSingleOld = 2, kDrawWang = 3;
 
 // Source of the reflection probabilities p_k (EV_NONE: smooth radiance only,
-// p left to the caller).
-constexpr int EV_E1 = 0, EV_E2 = 1, EV_GIVEN = 2, EV_NONE = 3;
+// p left to the caller; EV_E1A: E1 with multi-tap look-ups along an
+// anisotropic lobe).
+constexpr int EV_E1 = 0, EV_E2 = 1, EV_GIVEN = 2, EV_NONE = 3, EV_E1A = 4;
 
 // E2: reflection probabilities of an anisotropic GGX footprint by quadrature
 // (Eq. probhk).  Points of the projected-area slope distribution in
@@ -236,6 +237,10 @@ __device__ __forceinline__ void filtered_channels(const ShadeArgs &a, float th, 
     for (int k = 0; k < K; ++k) ch[3 + k] = w[k];
 }
 
+template <int K>
+__device__ __forceinline__ void e1a_weights(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2, float mu,
+                                            float rx, float ry, float rz, float *W);
+
 // Step 1: smooth radiance (L_o) and the reflection probabilities p_k.
 template <int K, int EV>
 __device__ __forceinline__ void smooth_and_probs(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
@@ -270,6 +275,12 @@ __device__ __forceinline__ void smooth_and_probs(const ShadeArgs &a, long q, flo
 #pragma unroll
         for (int k = 0; k < K; ++k) p[k] = __ldg(a.pk_in + q * K + k);
     } else if (EV == EV_NONE) {
+    } else if (EV == EV_E1A) {
+        float W[K];
+        e1a_weights<K>(a, q, g0, g1, g2, mu_o, rx, ry, rz, W);
+        p[0] = tab.y + tab.x * W[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k) p[k] = tab.x * W[k];
     } else {
         p[0] = tab.y + tab.x * ch[3];
 #pragma unroll
@@ -397,6 +408,52 @@ __device__ __forceinline__ void filtered_weights_only(const ShadeArgs &a, float 
     float ph = atan2f(dz, dx);
     if (ph < 0.f) ph += kTwoPi;
     filtered_w<K>(a, th, ph, r0, r1, ft, W);
+}
+
+// Filtered weights of the anisotropic E1 (multi-tap look-ups): the lobe of
+// reflected directions as an ellipse with axes J_t a_x, J_b a_y, J_t = 2 (-(w_o.t)
+// n - mu_o t) and J_b likewise the derivatives of the mirror direction with
+// respect to the slope (t made orthogonal to n, b = n x t); the filtered
+// weights read at roughness a_l = min(|J_t| a_x, |J_b| a_y) / 2 at the five
+// Gauss-Hermite nodes x_j along the longer axis u, d_j = normalize(w_r +
+// x_j sigma u), sigma^2 = 0.4 (L_max^2 - L_min^2), weighted by the rule's w_j.
+template <int K>
+__device__ __forceinline__ void e1a_weights(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2, float mu,
+                                            float rx, float ry, float rz, float *W) {
+    const float4 tg = ldg4(a.tangent + q);
+    const float tn = tg.x * g1.x + tg.y * g1.y + tg.z * g1.z;
+    float tx = tg.x - tn * g1.x, ty = tg.y - tn * g1.y, tz = tg.z - tn * g1.z;
+    const float tinv = 1.f / sqrtf(tx * tx + ty * ty + tz * tz);
+    tx *= tinv; ty *= tinv; tz *= tinv;
+    const float bx = g1.y * tz - g1.z * ty, by = g1.z * tx - g1.x * tz, bz = g1.x * ty - g1.y * tx;
+    const float ot = g0.x * tx + g0.y * ty + g0.z * tz;
+    const float ob = g0.x * bx + g0.y * by + g0.z * bz;
+    const float jtx = -2.f * (ot * g1.x + mu * tx), jty = -2.f * (ot * g1.y + mu * ty), jtz = -2.f * (ot * g1.z + mu * tz);
+    const float jbx = -2.f * (ob * g1.x + mu * bx), jby = -2.f * (ob * g1.y + mu * by), jbz = -2.f * (ob * g1.z + mu * bz);
+    const float nt = sqrtf(jtx * jtx + jty * jty + jtz * jtz), nb = sqrtf(jbx * jbx + jby * jby + jbz * jbz);
+    const float Lt = nt * g2.z, Lb = nb * g2.w;
+    const bool along_t = Lt >= Lb;
+    const float Lmin = fminf(Lt, Lb), Lmax = fmaxf(Lt, Lb);
+    const float ux = along_t ? jtx / nt : jbx / nb, uy = along_t ? jty / nt : jby / nb,
+                uz = along_t ? jtz / nt : jbz / nb;
+    const float s = sqrtf(fminf(fmaxf(0.5f * Lmin, 1e-4f), 1.f));
+    const float sigma = sqrtf(0.4f * (Lmax * Lmax - Lmin * Lmin));
+    constexpr float kX[5] = {0.f, -1.3556261799742659f, 1.3556261799742659f, -2.8569700138728056f,
+                             2.8569700138728056f};
+    constexpr float kW[5] = {0.53333333333333333f, 0.22207592200561265f, 0.22207592200561265f,
+                             0.011257411327720690f, 0.011257411327720690f};
+#pragma unroll
+    for (int k = 0; k < K; ++k) W[k] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const float o = kX[j] * sigma;
+        const float dx = rx + o * ux, dy = ry + o * uy, dz = rz + o * uz;
+        const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float w[K];
+        filtered_weights_only<K>(a, dx * il, dy * il, dz * il, s, w);
+#pragma unroll
+        for (int k = 0; k < K; ++k) W[k] = fmaf(kW[j], w[k], W[k]);
+    }
 }
 
 // E1's p_k (step 1 of smooth_and_probs without the colour channels), from

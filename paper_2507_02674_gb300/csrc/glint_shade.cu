@@ -91,6 +91,7 @@ template <int K>
 cudaError_t launch_k(const ShadeArgs &args, bool integer, bool debug, int ev, cudaStream_t s) {
     if (ev == EV_E2) launch_ke<K, EV_E2>(args, integer, debug, s);
     else if (ev == EV_GIVEN) launch_ke<K, EV_GIVEN>(args, integer, debug, s);
+    else if (ev == EV_E1A) launch_ke<K, EV_E1A>(args, integer, debug, s);
     else launch_ke<K, EV_E1>(args, integer, debug, s);
     return cudaGetLastError();
 }
@@ -99,6 +100,7 @@ template <int K>
 cudaError_t launch_probs(const ShadeArgs &args, int ev, cudaStream_t s) {
     const unsigned grid = (unsigned)((args.npix + kShadeNT - 1) / kShadeNT);
     if (ev == EV_E2) k_probs<K, EV_E2><<<grid, kShadeNT, 0, s>>>(args);
+    else if (ev == EV_E1A) k_probs<K, EV_E1A><<<grid, kShadeNT, 0, s>>>(args);
     else k_probs<K, EV_E1><<<grid, kShadeNT, 0, s>>>(args);
     return cudaGetLastError();
 }
@@ -121,7 +123,8 @@ cudaError_t glint_launch_shade(const glint_ctx *ctx, const glint_env *env, const
         if (launches) *launches = a.npix ? 1 : 0;
         return glint_launch_shade_variant(a, env->d.K, p->count_mode == GLINT_COUNT_INTEGER, p->draw, p->grid, s);
     }
-    const int ev = pk_in ? EV_GIVEN : (p->evaluator == GLINT_EVAL_E2 ? EV_E2 : EV_E1);
+    const int ev = pk_in ? EV_GIVEN : (p->evaluator == GLINT_EVAL_E2 ? EV_E2
+                                       : p->evaluator == GLINT_EVAL_E1_ANISO ? EV_E1A : EV_E1);
     const bool debug = dbg != nullptr;
     const bool integer = p->count_mode == GLINT_COUNT_INTEGER;
     if (launches) *launches = 0;
@@ -142,7 +145,7 @@ cudaError_t glint_launch_probs(const glint_ctx *ctx, const glint_env *env, const
                                const glint_params *p, float *p_out, cudaStream_t s) {
     ShadeArgs a = make_args(ctx, env, g, p);
     a.p_out = p_out;
-    const int ev = p->evaluator == GLINT_EVAL_E2 ? EV_E2 : EV_E1;
+    const int ev = p->evaluator == GLINT_EVAL_E2 ? EV_E2 : p->evaluator == GLINT_EVAL_E1_ANISO ? EV_E1A : EV_E1;
     if (a.npix == 0) return cudaSuccess;
     switch (env->d.K) {
     case 2: return launch_probs<2>(a, ev, s);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libglint.so")
 GLINT_OK = 0
 FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
-EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN = 0, 1, 2, 3
+EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN, EVAL_E1_ANISO = 0, 1, 2, 3, 4
 MLP_PARAMS, MLP_GRAD, MLP_ADAM_M, MLP_ADAM_V = 0, 1, 2, 3
 ABI_VERSION = 7
 HOST_INPUTS_READY = 1

@@ -240,7 +240,7 @@ def test_mlp_train_equals_step_by_step(gl):
     X = np.zeros((n, 64))
     X[:, :51] = rng.uniform(0, 1, size=(n, 51))
     x = torch.from_numpy(_bits(X)).cuda()
-    l = torch.from_numpy(np.log(synth.distributions(n, K, seed=98)).astype(np.float32)).cuda()
+    l = torch.from_numpy(np.log(np.maximum(synth.distributions(n, K, seed=98), 1e-6)).astype(np.float32)).cuda()
     Y = torch.from_numpy(synth.distributions(n, K, seed=99)).cuda()
     a = glint.Mlp(ctx, K, batch, seed=5)
     a.train(x, l, Y, 1000, batch, steps, 3e-3, 1e-4)

@@ -39,7 +39,7 @@ def _run(gl, env, gb, mp: MethodParams, debug=True, rows=None, evaluator=0, e2_S
     fr = render.Frame(ctx, env, _cfg(glint, mp))
     fr.update_env()
     planes = render.gbuffer_tensors(gb)
-    tangent = render.tangent_tensor(gb) if evaluator == 1 else None
+    tangent = render.tangent_tensor(gb) if evaluator in (1, 4) else None
     npix = gb.width * gb.height
     dbg = glint.debug_buffers(npix, mp.K) if debug else None
     mode = glint.COUNT_INTEGER if mp.integer_mode else glint.COUNT_REAL
@@ -220,6 +220,28 @@ def test_shade_e2_anisotropic(gl, orc, K):
     o = oracle_shade(orc, gb.rows16(), env, mp, evaluator=1, tangents=gb.tangents(), e2_S=16)
     rep = _check(orc, o, res, nonunique=o.e2_flags > 0, tie=e2_tie(orc, K))
     assert rep.nonunique < 0.02 * len(o.np_)
+
+
+@pytest.mark.parametrize("K", [4, 8, 16])
+def test_shade_e1_anisotropic_multitap(gl, orc, K):
+    """E1 with multi-tap look-ups along the anisotropic lobe (five taps at the
+    minor axis' roughness along the major axis of the reflected-lobe
+    ellipse): unstructured pixels with alpha_x != alpha_y and tangents, ragged
+    tail, against the oracle's restatement under E1's tie model; the p_k of
+    glint_reflect_probs equal the shading's."""
+    glint, render, ctx, torch = gl
+    mp = MethodParams(K=K, Wo=128, seed=29)
+    env = synth.env_hdr(seed=6, W=256, H=128)
+    gb = synth.gbuffer_random(2037, seed=51 + K, width=2037)
+    res = _run(gl, env, gb, mp, evaluator=4)
+    o = oracle_shade(orc, gb.rows16(), env, mp, evaluator=3, tangents=gb.tangents())
+    _check(orc, o, res)
+    planes = render.gbuffer_tensors(gb)
+    pr = res["frame"].probs(planes, gb.width, gb.height, evaluator=glint.EVAL_E1_ANISO,
+                            tangent=render.tangent_tensor(gb))
+    torch.cuda.synchronize()
+    fg = res["np"] > 0
+    assert np.allclose(pr.cpu().numpy()[fg], res["p"][fg], rtol=2.0 ** -18, atol=2.0 ** -21)
 
 
 def test_shade_e2_isotropic_sphere_close_to_e1(gl, orc):

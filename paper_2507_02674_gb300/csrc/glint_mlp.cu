@@ -634,12 +634,23 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
             d0[0] = v0; d0[1] = v1; d1[0] = v2; d1[1] = v3;
         }
     };
-    // column sums of a [CH][ld] BF16 matrix into dst (+)= (one thread per column)
-    auto col_sum = [&](const __nv_bfloat16 *m, int ld, int col, float *dst, bool acc) {
+    // column sums of a [CH][ld] BF16 matrix into dst (+)= : thread t sums
+    // column t % ncol over rows of parity t / ncol (ncol * 2 <= kNT threads),
+    // the two halves added in shared memory in a fixed order
+    auto col_sums = [&](const __nv_bfloat16 *m, int ld, int ncol, float *dst, bool acc) {
+        const int col = threadIdx.x % ncol, half = threadIdx.x / ncol;
         float s = 0.f;
-#pragma unroll 8
-        for (int r = 0; r < CH; ++r) s += __bfloat162float(ld == 64 ? *el(m, r, col) : m[r * ld + col]);
-        *dst = acc ? *dst + s : s;
+        if (half < 2) {
+#pragma unroll
+            for (int r = half; r < CH; r += 2) s += __bfloat162float(ld == 64 ? *el(m, r, col) : m[r * ld + col]);
+        }
+        if (half == 1) red[col] = s;
+        __syncthreads();
+        if (half == 0) {
+            s += red[col];
+            dst[col] = acc ? dst[col] + s : s;
+        }
+        __syncthreads();
     };
 
 #pragma unroll 1
@@ -755,10 +766,8 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
         __syncthreads();
         grad_w(h2, dz3, 16, part + kOffW3, kOutPad, acc, std::integral_constant<int, 2>{});
         grad_w(h1, dz, 64, part + kOffW2, kHid, acc, std::integral_constant<int, 8>{});
-        if (threadIdx.x < kOutPad) col_sum(dz3, 16, threadIdx.x, part + kOffB3 + threadIdx.x, acc);
-        else if (threadIdx.x < kOutPad + kHid)
-            col_sum(dz, 64, threadIdx.x - kOutPad, part + kOffB2 + threadIdx.x - kOutPad, acc);
-        __syncthreads();
+        col_sums(dz3, 16, kOutPad, part + kOffB3, acc);
+        col_sums(dz, 64, kHid, part + kOffB2, acc);
         // dZ1 = (dZ2 W2^T) * 1[H1 > 0], written over H2
 #pragma unroll 1
         for (int mt = warp; mt < MT; mt += kNT / 32) {
@@ -786,16 +795,14 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
         }
         __syncthreads();
         grad_w(xs, h2, 64, part + kOffW1, kHid, acc, std::integral_constant<int, 8>{});
-        if (threadIdx.x < kHid) col_sum(h2, 64, threadIdx.x, part + kOffB1 + threadIdx.x, acc);
-        __syncthreads();  // xs, h1, h2 and dz are rewritten by the next chunk
+        col_sums(h2, 64, kHid, part + kOffB1, acc);  // ends with a barrier: xs, h1, h2, dz free
     }
-    red[threadIdx.x] = lsum;
+    // the block's summed cross-entropy: warp sums, then the four in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) red[warp] = lsum;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int r = 0; r < kNT; ++r) s += red[r];
-        loss[blockIdx.x] = s;
-    }
+    if (threadIdx.x == 0) loss[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
 }
 
 // The BF16 copies (forward W^T [out][in], backward W [in][out]) of FP32
@@ -832,8 +839,16 @@ __global__ void __launch_bounds__(kRedParams * kRedWarps) k_mlp_reduce_adam(
     const int i = blockIdx.x * kRedParams + lane;
     float gs = 0.f;
     if (i < kP) {
-#pragma unroll 4
-        for (int b = warp; b < nblk; b += kRedWarps) gs += partial[(size_t)b * kP + i];
+        // partials in batches of 8 loads in flight, summed in block order
+        int b = warp;
+        for (; b + 7 * kRedWarps < nblk; b += 8 * kRedWarps) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = partial[(size_t)(b + u * kRedWarps) * kP + i];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) gs += v[u];
+        }
+        for (; b < nblk; b += kRedWarps) gs += partial[(size_t)b * kP + i];
     }
     part_sum[warp][lane] = gs;
     __syncthreads();

@@ -1,7 +1,9 @@
 // Serving: continuous batching of glint-shaded frames (no counterpart in the
 // paper).  Host runtime: FIFO admission by device memory (first-fit arena over
-// one allocation), G-buffer copies on an upload stream, per-tick work lists of
-// (frame, pixel range) items over all admitted frames, one persistent shading
+// one allocation), G-buffer copies on two upload streams (3840 x 2160-class
+// frames apart from the rest), per-tick work lists of (frame, pixel range)
+// items over the admitted frames whose upload has completed (a tick never
+// makes the compute stream wait on an upload), one persistent shading
 // launch per tick (plus the surrogate's fused inference first for frames on
 // that path), copies back of finished frames on a second copy stream (never
 // queued behind uploads) and their release.
@@ -131,7 +133,7 @@ struct Frame {
     float *out = nullptr;      // device output
     float *p = nullptr;        // device p_k scratch (surrogate path)
     cudaEvent_t uploaded = nullptr, downloaded = nullptr;
-    bool waited = false;       // the compute stream waits on `uploaded`
+    bool ready = false;        // `uploaded` has completed: the frame can be planned
     bool copying_back = false;
     double submit_s = 0, admit_s = 0;
 };
@@ -163,7 +165,8 @@ struct glint_server {
     std::chrono::steady_clock::time_point t0;
     char *pool = nullptr;
     glint_arena *arena = nullptr;
-    cudaStream_t copy = nullptr;  // uploads
+    cudaStream_t copy = nullptr;  // uploads of frames above kLargeFrame pixels
+    cudaStream_t copy_small = nullptr;  // uploads of the others (never queued behind a large frame's)
     cudaStream_t back = nullptr;  // copies back (never queued behind uploads)
     std::vector<EnvEntry> envs;
     std::deque<Frame> queue;
@@ -209,6 +212,12 @@ void retire(glint_server *s) {
     }
 }
 
+// Frames above this many pixels (3840 x 2160 in the serving mix) upload on
+// their own stream, so that a small frame admitted behind one does not wait
+// for its ~530 MB upload.
+constexpr long kLargeFrame = 1920L * 1080L;
+cudaStream_t upload_stream(glint_server *s, const Frame &f) { return f.npix > kLargeFrame ? s->copy : s->copy_small; }
+
 glint_status admit(glint_server *s) {
     while (!s->queue.empty() && (int)s->active.size() < s->d.max_frames) {
         Frame &q = s->queue.front();
@@ -230,7 +239,8 @@ glint_status admit(glint_server *s) {
             dst[i] = reinterpret_cast<float *>(p);
             p += plane;
             if (st == GLINT_OK)
-                st = cuda_status(cudaMemcpyAsync(dst[i], src[i], (size_t)f.npix * 16, cudaMemcpyHostToDevice, s->copy),
+                st = cuda_status(cudaMemcpyAsync(dst[i], src[i], (size_t)f.npix * 16, cudaMemcpyHostToDevice,
+                                                 upload_stream(s, f)),
                                  "glint_server_tick: upload");
         }
         f.out = reinterpret_cast<float *>(p);
@@ -239,7 +249,7 @@ glint_status admit(glint_server *s) {
         f.gb = glint_gbuffer{dst[0], dst[1], dst[2], dst[3], f.req.width, f.req.height, dst[4]};
         if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&f.uploaded, cudaEventDisableTiming), "glint_server_tick");
         if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&f.downloaded, cudaEventDisableTiming), "glint_server_tick");
-        if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.uploaded, s->copy), "glint_server_tick");
+        if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.uploaded, upload_stream(s, f)), "glint_server_tick");
         if (st != GLINT_OK) {
             glint_arena_free(s->arena, off);
             free_frame_events(f);
@@ -332,6 +342,8 @@ glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc 
         if (!s->arena) st = GLINT_ERR_OOM;
     }
     if (st == GLINT_OK) st = cuda_status(cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking), "glint_server_create");
+    if (st == GLINT_OK)
+        st = cuda_status(cudaStreamCreateWithFlags(&s->copy_small, cudaStreamNonBlocking), "glint_server_create");
     if (st == GLINT_OK) st = cuda_status(cudaStreamCreateWithFlags(&s->back, cudaStreamNonBlocking), "glint_server_create");
     s->slots.resize(d.max_inflight_ticks + 1);
     for (auto &sl : s->slots) {
@@ -366,6 +378,7 @@ void glint_server_destroy(glint_server *s) {
         if (sl.done) cudaEventDestroy(sl.done);
     }
     if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->copy_small) cudaStreamDestroy(s->copy_small);
     if (s->back) cudaStreamDestroy(s->back);
     cudaFree(s->pool);
     glint_arena_destroy(s->arena);
@@ -440,10 +453,24 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
     retire(s);
     glint_status st = apply_updates(s, cs);
     if (st == GLINT_OK) st = admit(s);
-    // frames with pixels left, in admission order
+    // frames with pixels left whose upload has completed, in admission order:
+    // the compute stream never waits on an upload, so a frame still being
+    // copied in holds up no other frame's shading
     std::vector<int> idx;
-    for (int i = 0; i < (int)s->active.size(); ++i)
-        if (s->active[i].next < s->active[i].npix) idx.push_back(i);
+    for (int i = 0; i < (int)s->active.size(); ++i) {
+        Frame &f = s->active[i];
+        if (f.next >= f.npix) continue;
+        if (!f.ready) {
+            const cudaError_t q = cudaEventQuery(f.uploaded);
+            if (q == cudaErrorNotReady) {
+                if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();  // a state, not an error
+                continue;
+            }
+            if (q != cudaSuccess) { st = cuda_status(q, "glint_server_tick: upload"); break; }
+            f.ready = true;
+        }
+        idx.push_back(i);
+    }
     int nl = 0;
     if (st == GLINT_OK && !idx.empty()) {
         Slot &sl = s->slots[s->tick_no % s->slots.size()];
@@ -510,10 +537,7 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
                     glint_mlp_weights(s->envs[f.req.env].mlp, &a.mlp_wt, &a.mlp_params);
                 table_of[j] = nframes;
                 sl.h_frames[nframes++] = a;
-                if (!f.waited) {
-                    st = cuda_status(cudaStreamWaitEvent(cs, f.uploaded, 0), "glint_server_tick");
-                    f.waited = true;
-                }
+
             }
             sl.h_items[k] = ServeItem{table_of[j], it_c[k], it_first[k]};
             if (j < n_mlp_frames) ++n_mlp_items;

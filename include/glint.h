@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GLINT_ABI_VERSION 7
+#define GLINT_ABI_VERSION 8
 #define GLINT_MAX_K 16
 
 typedef enum glint_status {
@@ -473,15 +473,19 @@ glint_status glint_mlp_generate(glint_ctx *ctx, const glint_env *env, const glin
  * Serving (no counterpart in the paper): a continuous-batching request loop.
  * Frames of any resolution, each with one of the resident environments (and
  * its surrogate), are submitted from host memory; a tick admits queued frames
- * while their device buffers fit the memory budget (FIFO), copies their
- * G-buffers to the device on a copy stream, and shades a tile of every
- * admitted frame and then up to tick_pixels pixels in admission order, in one
- * persistent launch over a work list of
- * (frame, pixel range) items (plus, for frames on the surrogate path, one
- * fused-inference launch per network first).  Finished frames are copied back
- * on the copy stream and released; glint_server_poll reports them.  A frame's
- * pixels are computed exactly as glint_shade's kernel computes them, whatever
- * else shares its ticks.  One host thread drives a server.
+ * while their device buffers fit the memory budget (FIFO).  A frame whose
+ * buffers all lie in page-locked memory the device addresses is shaded in
+ * place (the kernels read its G-buffer and write its result over the CPU-GPU
+ * link; it holds device memory only for the surrogate's p_k), unless the
+ * server was created with upload = 1; other frames are copied to the device
+ * on copy streams.  A tick shades a tile of every admitted frame whose inputs
+ * are on hand and then up to tick_pixels pixels, frames with the fewest pixels
+ * left first, in one persistent launch over a work list of (frame, pixel
+ * range) items (plus, for frames on the surrogate path, one fused-inference
+ * launch first).  Finished frames are copied back (unless shaded in place)
+ * and released; glint_server_poll reports them.  A frame's pixels are computed
+ * exactly as glint_shade's kernel computes them, whatever else shares its
+ * ticks and wherever its buffers lie.  One host thread drives a server.
  * ------------------------------------------------------------------------- */
 typedef struct glint_server glint_server;
 
@@ -492,11 +496,13 @@ typedef struct glint_server_desc {
                                launched in pieces of 1024 pixels */
     int max_frames;         /* admitted frames at most (0 = 64) */
     int max_inflight_ticks; /* ticks enqueued on the GPU at most; a tick waits for older ones (0 = 2) */
+    int upload;             /* 1: copy every frame into the budget's device memory; 0: shade frames in
+                               page-locked host memory in place */
 } glint_server_desc;
 
 /* A frame.  Planes are HOST memory in glint_gbuffer's layout (page-locked
- * memory lets the copies overlap with shading); tangent is required on the
- * surrogate path.  out_rgba: HOST, width*height float4.  The caller keeps all
+ * memory is shaded in place, or lets the copies overlap with shading); tangent
+ * is required on the surrogate path.  out_rgba: HOST, width*height float4.  The caller keeps all
  * of them alive until glint_server_poll has reported the frame. */
 typedef struct glint_frame_request {
     int env;          /* index from glint_server_add_env */
@@ -513,7 +519,7 @@ typedef struct glint_frame_request {
 } glint_frame_request;
 
 /* A finished frame: its id and host-clock times (seconds since the server's
- * creation) of submission, admission and the completed copy back. */
+ * creation) of submission, admission and completion (its result in out_rgba). */
 typedef struct glint_frame_done {
     long id;
     double submit_s;
@@ -575,8 +581,8 @@ size_t glint_arena_largest_free(const glint_arena *arena);
  * npix[f] pixels planned so far.  Items are ranges of at most tile_pixels
  * pixels ending at multiples of tile_pixels (or the frame's end): first one
  * item for every unfinished frame, so that every admitted frame progresses in
- * every tick, then items in frame order until tick_pixels are planned; at most
- * max_items in all.  Writes the items, advances next[] and returns the item
+ * every tick, then items for the frames with the fewest pixels left (frame
+ * order among equals) until tick_pixels are planned; at most max_items in all.  Writes the items, advances next[] and returns the item
  * count. */
 int glint_plan_tick(long *next, const long *npix, int nframes, long tick_pixels, int tile_pixels, int *item_frame,
                     long *item_first, int *item_count, int max_items);

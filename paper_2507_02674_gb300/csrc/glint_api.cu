@@ -66,6 +66,20 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 using namespace glint;
 
+// Device address of `bytes` bytes of host memory at `p` when all of them lie
+// in one page-locked allocation the current device can address, else NULL.
+const void *glint_host_device_view(const void *p, size_t bytes) {
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const char *last = static_cast<const char *>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    if (b.type != cudaMemoryTypeHost ||
+        static_cast<const char *>(b.devicePointer) != static_cast<const char *>(a.devicePointer) + (bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
 extern "C" {
 
 int glint_abi_version(void) { return GLINT_ABI_VERSION; }
@@ -578,19 +592,6 @@ void glint_hostpipe_destroy(glint_hostpipe *pipe) {
 int glint_hostpipe_last_launches(const glint_hostpipe *pipe) { return pipe ? pipe->last_launches : 0; }
 int glint_hostpipe_last_in_place(const glint_hostpipe *pipe) { return pipe ? pipe->last_in_place : 0; }
 
-// Device address of `bytes` bytes of host memory at `p` when all of them lie
-// in one page-locked allocation the current device can address, else NULL.
-static const void *device_view_of_host(const void *p, size_t bytes) {
-    cudaPointerAttributes a{}, b{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return nullptr; }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-    const char *last = static_cast<const char *>(p) + bytes - 1;
-    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) { cudaGetLastError(); return nullptr; }
-    if (b.type != cudaMemoryTypeHost ||
-        static_cast<const char *>(b.devicePointer) != static_cast<const char *>(a.devicePointer) + (bytes - 1))
-        return nullptr;
-    return a.devicePointer;
-}
 
 glint_status glint_shade_host(glint_hostpipe *pipe, const glint_env *env, const glint_gbuffer *hg,
                               const glint_params *p, float *out_host, int rows_per_band, unsigned flags,
@@ -622,11 +623,11 @@ glint_status glint_shade_host(glint_hostpipe *pipe, const glint_env *env, const 
         bool in_place = true;
         for (int i = 0; i < 5 && in_place; ++i) {
             if (i == 4 && !with_tangent) break;
-            dv[i] = device_view_of_host(src[i], plane_bytes);
+            dv[i] = glint_host_device_view(src[i], plane_bytes);
             in_place = dv[i] != nullptr;
         }
         if (in_place) {
-            dv[5] = device_view_of_host(out_host, plane_bytes);
+            dv[5] = glint_host_device_view(out_host, plane_bytes);
             in_place = dv[5] != nullptr;
         }
         if (in_place) {

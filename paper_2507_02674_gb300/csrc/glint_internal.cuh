@@ -162,8 +162,12 @@ cudaError_t glint_launch_mlp_infer(const glint_ctx *ctx, const glint_env *env, c
                                    const glint_gbuffer *g, float *p, cudaStream_t s);
 int glint_mlp_k(const glint_mlp *m);
 int glint_mlp_device(const glint_mlp *m);
+// Device address of `bytes` bytes of host memory at `p` when all of them lie
+// in one page-locked allocation the current device can address, else NULL.
+const void *glint_host_device_view(const void *p, size_t bytes);
 // Serving launches (glint_serve.cu): the shading kernel and the surrogate's
-// fused inference over a work list; frames/items are device arrays.
+// fused inference over a work list; frames/items are device-addressable arrays
+// (the server passes page-locked host tables).
 namespace glint { struct ShadeArgs; struct ServeItem; }
 cudaError_t glint_launch_serve(int K, bool given, const glint::ShadeArgs *frames, const glint::ServeItem *items,
                                int nitems, int grid, cudaStream_t s);

@@ -1,12 +1,15 @@
 // Serving: continuous batching of glint-shaded frames (no counterpart in the
 // paper).  Host runtime: FIFO admission by device memory (first-fit arena over
-// one allocation), G-buffer copies on two upload streams (3840 x 2160-class
-// frames apart from the rest), per-tick work lists of (frame, pixel range)
-// items over the admitted frames whose upload has completed (a tick never
-// makes the compute stream wait on an upload), one persistent shading
-// launch per tick (plus the surrogate's fused inference first for frames on
-// that path), copies back of finished frames on a second copy stream (never
-// queued behind uploads) and their release.
+// one allocation).  A frame whose buffers are all page-locked is shaded in
+// place: the kernels read its G-buffer from, and write its result to, host
+// memory over the CPU-GPU link, so no frame waits on another's copies; other
+// frames are copied in on two upload streams (3840 x 2160-class frames apart
+// from the rest) and out on a third.  Each tick plans (frame, pixel range)
+// items over the admitted frames whose inputs are on hand (a tile of each,
+// then the frames with the fewest pixels left first) and makes one persistent
+// shading launch over them (plus the surrogate's fused inference first for
+// frames on that path); the tick's tables stay in page-locked memory that the
+// kernels read directly.
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -104,9 +107,18 @@ int glint_plan_tick(long *next, const long *npix, int nframes, long tick_pixels,
     // are not starved by large ones ahead of them ...
     for (int f = 0; f < nframes && n < max_items; ++f)
         if (next[f] < npix[f]) take(f);
-    // ... then the rest of the budget goes to frames in admission order
-    for (int f = 0; f < nframes && n < max_items && planned < tick_pixels; ++f)
+    // ... then the rest of the budget goes to the frames with the fewest
+    // pixels left (admission order among equals): a small frame behind a 4K
+    // one finishes in this tick instead of waiting for the 4K frame's ticks
+    std::vector<int> order;
+    for (int f = 0; f < nframes; ++f)
+        if (next[f] < npix[f]) order.push_back(f);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return npix[a] - next[a] < npix[b] - next[b]; });
+    for (size_t i = 0; i < order.size() && n < max_items && planned < tick_pixels; ++i) {
+        const int f = order[i];
         while (next[f] < npix[f] && n < max_items && planned < tick_pixels) take(f);
+    }
     return n;
 }
 
@@ -133,8 +145,9 @@ struct Frame {
     float *out = nullptr;      // device output
     float *p = nullptr;        // device p_k scratch (surrogate path)
     cudaEvent_t uploaded = nullptr, downloaded = nullptr;
-    bool ready = false;        // `uploaded` has completed: the frame can be planned
-    bool copying_back = false;
+    bool in_place = false;     // shaded where it lies: gb and out address the caller's page-locked buffers
+    bool ready = false;        // `uploaded` has completed (or in place): the frame can be planned
+    bool copying_back = false; // `downloaded` is recorded (after the copy back, or the last tick if in place)
     double submit_s = 0, admit_s = 0;
 };
 
@@ -146,9 +159,12 @@ struct EnvEntry {  // a resident map
     const void *texels = nullptr;  // the latest requested update's texels (device)
 };
 
-struct Slot {  // staging of one tick's frame table and work list
-    ShadeArgs *h_frames = nullptr, *d_frames = nullptr;
-    ServeItem *h_items = nullptr, *d_items = nullptr;
+// One tick's frame table and work list, in page-locked host memory that the
+// kernels read directly (v_* are the device addresses): a table copy would
+// queue on the copy engine behind frame uploads.
+struct Slot {
+    ShadeArgs *h_frames = nullptr, *v_frames = nullptr;
+    ServeItem *h_items = nullptr, *v_items = nullptr;
     cudaEvent_t done = nullptr;
     bool used = false;
 };
@@ -180,11 +196,13 @@ struct glint_server {
 
 namespace {
 
-size_t frame_bytes(const glint_frame_request &r, int K) {
+// Device bytes of a frame: its planes and output unless shaded in place, and
+// the p_k scratch of the surrogate path.
+size_t frame_bytes(const glint_frame_request &r, int K, bool in_place) {
     const size_t n = (size_t)r.width * (size_t)r.height;
     const size_t planes = (r.evaluator == GLINT_EVAL_MLP) ? 5 : 4;
     const size_t pbytes = (r.evaluator == GLINT_EVAL_MLP) ? ((n * K * sizeof(float) + 255) / 256 * 256) : 0;
-    return (planes + 1) * ((n * 16 + 255) / 256 * 256) + pbytes;
+    return (in_place ? 0 : (planes + 1) * ((n * 16 + 255) / 256 * 256)) + pbytes;
 }
 
 void free_frame_events(Frame &f) {
@@ -202,7 +220,7 @@ void retire(glint_server *s) {
         if (q == cudaErrorNotReady && cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
         if (q == cudaSuccess) {
             s->finished.push_back(glint_frame_done{f.id, f.submit_s, f.admit_s, now_s(s->t0)});
-            glint_arena_free(s->arena, f.arena_off);
+            if (f.arena_off >= 0) glint_arena_free(s->arena, f.arena_off);
             free_frame_events(f);
             s->active.erase(s->active.begin() + (long)i);
             s->st.active -= 1;
@@ -222,36 +240,43 @@ glint_status admit(glint_server *s) {
     while (!s->queue.empty() && (int)s->active.size() < s->d.max_frames) {
         Frame &q = s->queue.front();
         if (s->envs[q.req.env].applied < q.env_version) break;  // FIFO: waits for its map's update
-        const size_t bytes = frame_bytes(q.req, s->K);
-        const long long off = glint_arena_alloc(s->arena, bytes);
-        if (off < 0) break;  // FIFO: the head waits until memory frees up
+        const size_t bytes = frame_bytes(q.req, s->K, q.in_place);
+        long long off = -1;
+        if (bytes > 0) {
+            off = glint_arena_alloc(s->arena, bytes);
+            if (off < 0) break;  // FIFO: the head waits until memory frees up
+        }
         Frame f = q;
         s->queue.pop_front();
         f.arena_off = off;
-        f.dev = reinterpret_cast<float *>(s->pool + off);
-        const size_t plane = ((size_t)f.npix * 16 + 255) / 256 * 256;
-        char *p = reinterpret_cast<char *>(f.dev);
-        const float *src[5] = {f.req.view_n0, f.req.normal_f0, f.req.uv_alpha, f.req.duv, f.req.tangent};
-        float *dst[5] = {};
-        const int nplanes = (f.req.evaluator == GLINT_EVAL_MLP) ? 5 : 4;
+        char *p = off >= 0 ? s->pool + off : nullptr;
         glint_status st = GLINT_OK;
-        for (int i = 0; i < nplanes; ++i) {
-            dst[i] = reinterpret_cast<float *>(p);
+        if (f.in_place) {
+            f.ready = true;
+        } else {
+            const size_t plane = ((size_t)f.npix * 16 + 255) / 256 * 256;
+            const float *src[5] = {f.req.view_n0, f.req.normal_f0, f.req.uv_alpha, f.req.duv, f.req.tangent};
+            float *dst[5] = {};
+            const int nplanes = (f.req.evaluator == GLINT_EVAL_MLP) ? 5 : 4;
+            for (int i = 0; i < nplanes; ++i) {
+                dst[i] = reinterpret_cast<float *>(p);
+                p += plane;
+                if (st == GLINT_OK)
+                    st = cuda_status(cudaMemcpyAsync(dst[i], src[i], (size_t)f.npix * 16, cudaMemcpyHostToDevice,
+                                                     upload_stream(s, f)),
+                                     "glint_server_tick: upload");
+            }
+            f.out = reinterpret_cast<float *>(p);
             p += plane;
+            f.gb = glint_gbuffer{dst[0], dst[1], dst[2], dst[3], f.req.width, f.req.height, dst[4]};
             if (st == GLINT_OK)
-                st = cuda_status(cudaMemcpyAsync(dst[i], src[i], (size_t)f.npix * 16, cudaMemcpyHostToDevice,
-                                                 upload_stream(s, f)),
-                                 "glint_server_tick: upload");
+                st = cuda_status(cudaEventCreateWithFlags(&f.uploaded, cudaEventDisableTiming), "glint_server_tick");
+            if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.uploaded, upload_stream(s, f)), "glint_server_tick");
         }
-        f.out = reinterpret_cast<float *>(p);
-        p += plane;
         f.p = (f.req.evaluator == GLINT_EVAL_MLP) ? reinterpret_cast<float *>(p) : nullptr;
-        f.gb = glint_gbuffer{dst[0], dst[1], dst[2], dst[3], f.req.width, f.req.height, dst[4]};
-        if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&f.uploaded, cudaEventDisableTiming), "glint_server_tick");
         if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&f.downloaded, cudaEventDisableTiming), "glint_server_tick");
-        if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.uploaded, upload_stream(s, f)), "glint_server_tick");
         if (st != GLINT_OK) {
-            glint_arena_free(s->arena, off);
+            if (off >= 0) glint_arena_free(s->arena, off);
             free_frame_events(f);
             return st;
         }
@@ -317,9 +342,10 @@ glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc 
     if (d.max_frames == 0) d.max_frames = 64;
     if (d.max_inflight_ticks == 0) d.max_inflight_ticks = 2;
     if (d.memory_budget < (1u << 20) || d.tick_pixels < 128 || d.tile_pixels < 128 || d.tile_pixels % 128 ||
-        d.max_frames < 1 || d.max_frames > 4096 || d.max_inflight_ticks < 1 || d.max_inflight_ticks > 16) {
+        d.max_frames < 1 || d.max_frames > 4096 || d.max_inflight_ticks < 1 || d.max_inflight_ticks > 16 ||
+        (d.upload != 0 && d.upload != 1)) {
         set_error("glint_server_create: memory_budget >= 1 MiB, tick_pixels >= 128, tile_pixels a multiple of 128, "
-                  "max_frames in [1, 4096], max_inflight_ticks in [1, 16]");
+                  "max_frames in [1, 4096], max_inflight_ticks in [1, 16], upload 0 or 1");
         return GLINT_ERR_INVALID_ARG;
     }
     int prev = -1;
@@ -349,9 +375,13 @@ glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc 
     for (auto &sl : s->slots) {
         if (st != GLINT_OK) break;
         st = cuda_status(cudaMallocHost(&sl.h_frames, sizeof(ShadeArgs) * d.max_frames), "glint_server_create");
-        if (st == GLINT_OK) st = cuda_status(cudaMalloc(&sl.d_frames, sizeof(ShadeArgs) * d.max_frames), "glint_server_create");
         if (st == GLINT_OK) st = cuda_status(cudaMallocHost(&sl.h_items, sizeof(ServeItem) * s->max_staged), "glint_server_create");
-        if (st == GLINT_OK) st = cuda_status(cudaMalloc(&sl.d_items, sizeof(ServeItem) * s->max_staged), "glint_server_create");
+        if (st == GLINT_OK)
+            st = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void **>(&sl.v_frames), sl.h_frames, 0),
+                             "glint_server_create");
+        if (st == GLINT_OK)
+            st = cuda_status(cudaHostGetDevicePointer(reinterpret_cast<void **>(&sl.v_items), sl.h_items, 0),
+                             "glint_server_create");
         if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "glint_server_create");
     }
     if (prev >= 0) cudaSetDevice(prev);
@@ -372,9 +402,7 @@ void glint_server_destroy(glint_server *s) {
     for (auto &f : s->active) free_frame_events(f);
     for (auto &sl : s->slots) {
         cudaFreeHost(sl.h_frames);
-        cudaFree(sl.d_frames);
         cudaFreeHost(sl.h_items);
-        cudaFree(sl.d_items);
         if (sl.done) cudaEventDestroy(sl.done);
     }
     if (s->copy) cudaStreamDestroy(s->copy);
@@ -425,16 +453,37 @@ glint_status glint_server_submit(glint_server *s, const glint_frame_request *r, 
         set_error("glint_server_submit: NULL plane or output");
         return GLINT_ERR_INVALID_ARG;
     }
-    const size_t bytes = frame_bytes(*r, s->K);
+    Frame f;
+    f.req = *r;
+    f.npix = (long)r->width * r->height;
+    if (!s->d.upload) {
+        // in place when every buffer is page-locked host memory the device addresses
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != s->device) cudaSetDevice(s->device);
+        const size_t pb = (size_t)f.npix * 16;
+        const float *src[5] = {r->view_n0, r->normal_f0, r->uv_alpha, r->duv, r->tangent};
+        const int nplanes = (r->evaluator == GLINT_EVAL_MLP) ? 5 : 4;
+        const void *dv[5] = {};
+        bool ok = true;
+        for (int i = 0; i < nplanes && ok; ++i) ok = (dv[i] = glint_host_device_view(src[i], pb)) != nullptr;
+        const void *dout = ok ? glint_host_device_view(r->out_rgba, pb) : nullptr;
+        if (dout) {
+            f.in_place = true;
+            f.gb = glint_gbuffer{static_cast<const float *>(dv[0]), static_cast<const float *>(dv[1]),
+                                 static_cast<const float *>(dv[2]), static_cast<const float *>(dv[3]), r->width,
+                                 r->height, static_cast<const float *>(dv[4])};
+            f.out = static_cast<float *>(const_cast<void *>(dout));
+        }
+        if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+    }
+    const size_t bytes = frame_bytes(*r, s->K, f.in_place);
     if (bytes > s->arena->bytes) {
         set_error("glint_server_submit: the frame needs %zu bytes, more than the budget %zu", bytes, s->d.memory_budget);
         return GLINT_ERR_INVALID_ARG;
     }
-    Frame f;
     f.id = s->next_id++;
     f.env_version = s->envs[r->env].requested;
-    f.req = *r;
-    f.npix = (long)r->width * r->height;
     f.submit_s = now_s(s->t0);
     s->queue.push_back(f);
     s->st.queued += 1;
@@ -542,27 +591,21 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
             sl.h_items[k] = ServeItem{table_of[j], it_c[k], it_first[k]};
             if (j < n_mlp_frames) ++n_mlp_items;
         }
-        if (st == GLINT_OK)
-            st = cuda_status(cudaMemcpyAsync(sl.d_frames, sl.h_frames, sizeof(ShadeArgs) * nframes,
-                                             cudaMemcpyHostToDevice, cs), "glint_server_tick: table");
-        if (st == GLINT_OK)
-            st = cuda_status(cudaMemcpyAsync(sl.d_items, sl.h_items, sizeof(ServeItem) * nit_all,
-                                             cudaMemcpyHostToDevice, cs), "glint_server_tick: items");
         // surrogate: one fused-inference launch over its frames' items (grouped by network)
         if (st == GLINT_OK && n_mlp_items > 0) {
-            st = cuda_status(glint_launch_mlp_serve(s->K, s->ctx->num_sms, sl.d_frames, sl.d_items, n_mlp_items, cs),
+            st = cuda_status(glint_launch_mlp_serve(s->K, s->ctx->num_sms, sl.v_frames, sl.v_items, n_mlp_items, cs),
                              "glint_server_tick: inference");
             ++nl;
             if (st == GLINT_OK) {
                 const int grid = std::min(n_mlp_items, s->ctx->num_sms * glint::kShadeMinBlocks);
-                st = cuda_status(glint_launch_serve(s->K, true, sl.d_frames, sl.d_items, n_mlp_items, grid, cs),
+                st = cuda_status(glint_launch_serve(s->K, true, sl.v_frames, sl.v_items, n_mlp_items, grid, cs),
                                  "glint_server_tick: shade");
                 ++nl;
             }
         }
         if (st == GLINT_OK && nit_all > n_mlp_items) {
             const int grid = std::min(nit_all - n_mlp_items, s->ctx->num_sms * glint::kShadeMinBlocks);
-            st = cuda_status(glint_launch_serve(s->K, false, sl.d_frames, sl.d_items + n_mlp_items,
+            st = cuda_status(glint_launch_serve(s->K, false, sl.v_frames, sl.v_items + n_mlp_items,
                                                 nit_all - n_mlp_items, grid, cs), "glint_server_tick: shade");
             ++nl;
         }
@@ -573,11 +616,16 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
             Frame &f = s->active[order[j]];
             f.next = next[j];
             if (f.next == f.npix && !f.copying_back) {
-                st = cuda_status(cudaStreamWaitEvent(s->back, sl.done, 0), "glint_server_tick");
-                if (st == GLINT_OK)
-                    st = cuda_status(cudaMemcpyAsync(f.req.out_rgba, f.out, (size_t)f.npix * 16, cudaMemcpyDeviceToHost,
-                                                     s->back), "glint_server_tick: download");
-                if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.downloaded, s->back), "glint_server_tick");
+                if (f.in_place) {  // this tick's kernels write the result into the caller's buffer
+                    st = cuda_status(cudaEventRecord(f.downloaded, cs), "glint_server_tick");
+                } else {
+                    st = cuda_status(cudaStreamWaitEvent(s->back, sl.done, 0), "glint_server_tick");
+                    if (st == GLINT_OK)
+                        st = cuda_status(cudaMemcpyAsync(f.req.out_rgba, f.out, (size_t)f.npix * 16,
+                                                         cudaMemcpyDeviceToHost, s->back),
+                                         "glint_server_tick: download");
+                    if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.downloaded, s->back), "glint_server_tick");
+                }
                 f.copying_back = true;
             }
         }

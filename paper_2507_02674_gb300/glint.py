@@ -21,7 +21,7 @@ FMT_RGBA32F, FMT_RGBA16F = 0, 1
 COUNT_INTEGER, COUNT_REAL = 0, 1
 EVAL_E1, EVAL_E2, EVAL_MLP, EVAL_GIVEN, EVAL_E1_ANISO = 0, 1, 2, 3, 4
 MLP_PARAMS, MLP_GRAD, MLP_ADAM_M, MLP_ADAM_V = 0, 1, 2, 3
-ABI_VERSION = 7
+ABI_VERSION = 8
 HOST_INPUTS_READY = 1
 HOST_STAGED = 2
 GRID_ISOTROPIC, GRID_ANISOTROPIC = 0, 1
@@ -65,7 +65,7 @@ class Debug(ctypes.Structure):
 
 class ServerDesc(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_size_t), ("tick_pixels", ctypes.c_long), ("tile_pixels", ctypes.c_int),
-                ("max_frames", ctypes.c_int), ("max_inflight_ticks", ctypes.c_int)]
+                ("max_frames", ctypes.c_int), ("max_inflight_ticks", ctypes.c_int), ("upload", ctypes.c_int)]
 
 
 class FrameRequest(ctypes.Structure):
@@ -543,9 +543,9 @@ class Server:
     """glint_server: continuous batching of frames submitted from host memory."""
 
     def __init__(self, ctx: Context, K: int, memory_budget: int, tick_pixels: int = 0, tile_pixels: int = 0,
-                 max_frames: int = 0, max_inflight_ticks: int = 0):
+                 max_frames: int = 0, max_inflight_ticks: int = 0, upload: bool = False):
         self.ctx = ctx
-        self.desc = ServerDesc(memory_budget, tick_pixels, tile_pixels, max_frames, max_inflight_ticks)
+        self.desc = ServerDesc(memory_budget, tick_pixels, tile_pixels, max_frames, max_inflight_ticks, int(upload))
         h = ctypes.c_void_p()
         _check(lib.glint_server_create(ctx.handle, K, ctypes.byref(self.desc), ctypes.byref(h)))
         self.handle = h
@@ -564,7 +564,8 @@ class Server:
 
     def submit(self, env_id: int, planes, width: int, height: int, out, seed: int = 0,
                evaluator: int = EVAL_E1, tangent=None) -> int:
-        """planes, tangent, out: host tensors (pinned for overlapped copies), kept alive until polled."""
+        """planes, tangent, out: host tensors, kept alive until polled (all pinned: shaded in place unless
+        the server uploads; else copied in and out)."""
         r = FrameRequest(env_id, width, height, seed & 0xFFFFFFFF, evaluator, _dptr(planes[0]), _dptr(planes[1]),
                          _dptr(planes[2]), _dptr(planes[3]), _dptr(tangent), _dptr(out))
         fid = ctypes.c_long()

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_host_argument_checks_without_gpu(lib):
     lib.glint_last_error.restype = ctypes.c_char_p
     lib.glint_abi_version.restype = ctypes.c_int
-    assert lib.glint_abi_version() == 7
+    assert lib.glint_abi_version() == 8
     assert lib.glint_ctx_create(0, 0, 0, None) == 1
     assert b"NULL" in lib.glint_last_error()
     assert lib.glint_env_create(None, None, None) == 1

@@ -30,13 +30,15 @@ def gl():
 
 
 class Req:
-    def __init__(self, torch, render, n, width, seed):
+    def __init__(self, torch, render, n, width, seed, pinned=True):
         gb = synth.gbuffer_random(n, seed=seed, width=width)
         self.gb = gb
         self.w, self.h = gb.width, gb.height
-        self.planes = render.gbuffer_tensors(gb, device="cpu", pinned=True)
-        self.tan = torch.from_numpy(gb.tangents()).pin_memory()
-        self.out = torch.zeros(self.w * self.h, 4).pin_memory()
+        self.planes = render.gbuffer_tensors(gb, device="cpu", pinned=pinned)
+        self.tan = torch.from_numpy(gb.tangents())
+        self.out = torch.zeros(self.w * self.h, 4)
+        if pinned:
+            self.tan, self.out = self.tan.pin_memory(), self.out.pin_memory()
 
 
 def _drain(server, torch, limit=100000):
@@ -88,11 +90,43 @@ def test_alone_equals_mix_equals_glint_shade(gl):
         torch.testing.assert_close(r.out, ref, rtol=1e-5, atol=1e-6 * float(ref.abs().max()))
 
 
+def test_in_place_equals_uploaded(gl):
+    """Frames in page-locked memory are shaded in place (no device copy of
+    their planes or output); with the server uploading them, or from pageable
+    memory (always uploaded), every frame comes out bit for bit the same."""
+    glint, render, ctx, torch, frames, net = gl
+    shapes = [(640 * 360, 640, 51), (300 * 200 + 7, 300, 52), (50000, 500, 53)]
+    plan = [(0, 5, glint.EVAL_E1), (1, 6, glint.EVAL_MLP), (1, 7, glint.EVAL_E1)]
+    outs = {}
+    for mode in ("in_place", "upload", "pageable"):
+        reqs = [Req(torch, render, n, w, sd, pinned=(mode != "pageable")) for n, w, sd in shapes]
+        s = glint.Server(ctx, 8, 1 << 30, tick_pixels=100000, tile_pixels=4096, upload=(mode == "upload"))
+        s.add_env(frames[0].env, net)
+        s.add_env(frames[1].env, net)
+        for r, (e, seed, ev) in zip(reqs, plan):
+            s.submit(e, r.planes, r.w, r.h, r.out, seed, ev, r.tan)
+        assert len(_drain(s, torch)) == len(reqs)
+        st = s.stats()
+        npix = [r.w * r.h for r in reqs]
+        pk = -(-npix[1] * 8 * 4 // 256) * 256  # the surrogate frame's p_k scratch
+        planes = sum(5 * -(-n * 16 // 256) * 256 for n in npix) + pk + -(-npix[1] * 16 // 256) * 256
+        if mode == "in_place":
+            assert st["peak_bytes"] == pk  # only the surrogate's p_k lives on the device
+        else:
+            assert st["peak_bytes"] == planes
+        assert st["used_bytes"] == 0
+        outs[mode] = [r.out.clone() for r in reqs]
+        assert all(bool(o.abs().sum() > 0) for o in outs[mode])
+        s.close()
+    for a, b, c in zip(outs["in_place"], outs["upload"], outs["pageable"]):
+        assert torch.equal(a, b) and torch.equal(a, c)
+
+
 def test_admission_by_memory(gl):
     glint, render, ctx, torch, frames, net = gl
     r = [Req(torch, render, 640 * 360, 640, 20 + i) for i in range(5)]
     per_frame = 5 * (640 * 360 * 16)  # 4 planes + output (each 256-byte aligned: exact here)
-    s = glint.Server(ctx, 8, 2 * per_frame + 4096, tick_pixels=1 << 22)
+    s = glint.Server(ctx, 8, 2 * per_frame + 4096, tick_pixels=1 << 22, upload=True)
     e = s.add_env(frames[0].env)
     for i, q in enumerate(r):
         s.submit(e, q.planes, q.w, q.h, q.out, i)

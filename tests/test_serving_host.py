@@ -56,13 +56,16 @@ def test_arena_random_workload_never_overlaps(gl):
 def test_planner_tiles_budget_and_order(gl):
     npix = np.array([640 * 360, 3840 * 2160, 100, 1920 * 1080])
     items, nxt = gl.plan_tick(np.zeros(4), npix, tick_pixels=4 << 20, tile_pixels=16384)
-    # every unfinished frame gets a tile first, then the budget goes in frame order
+    # every unfinished frame gets a tile first, then the budget goes to the
+    # frames with the fewest pixels left: 640x360, then 1080p, then the 4K frame
     assert items[:4, 0].tolist() == [0, 1, 2, 3]
+    rest = items[4:, 0].tolist()
+    assert rest == sorted(rest, key=[0, 2, 3, 1].index)
     for f in range(4):
         it = items[items[:, 0] == f]
         assert it[0, 1] == 0 and np.all(it[1:, 1] == it[:-1, 1] + it[:-1, 2])
         assert np.all(it[:, 1] % 16384 == 0) and np.all(it[:, 2] <= 16384)
-    assert nxt[0] == npix[0] and 0 < nxt[1] < npix[1] and nxt[2] == npix[2] and nxt[3] == 16384
+    assert nxt[0] == npix[0] and 0 < nxt[1] < npix[1] and nxt[2] == npix[2] and nxt[3] == npix[3]
     planned = items[:, 2].sum()
     assert 4 << 20 <= planned < (4 << 20) + 16384
     # later ticks cover every pixel of every frame exactly once

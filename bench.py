@@ -522,29 +522,40 @@ def serving(args, glint, render, ctx, dev, stream):
         eids = [srv.add_env(f.env, n) for f, n in zip(frs, nets)]
         free = {i: list(outs[i]) for i in outs}
         busy = {}
-        lat, wait, npx, misses = [], [], 0, 0
+        lat, wait, npx, misses, miss_ms = [], [], 0, 0, 0.0
         lat_by = {i: [] for i in range(len(SERVE_RES))}
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         k = 0
         done_n = 0
+        max_busy, max_call, max_loop = 0, 0.0, 0.0
+        last = time.perf_counter()
         while done_n < SERVE_REQUESTS:
-            now = time.perf_counter() - t0
+            it0 = time.perf_counter()
+            max_loop = max(max_loop, it0 - last)
+            last = it0
+            now = it0 - t0
             if now > 120.0:
                 raise RuntimeError(f"serving: {SERVE_REQUESTS - done_n} frames unfinished after 120 s")
             while k < SERVE_REQUESTS and arrivals[k] <= now:
                 r = int(res_of[k])
                 w, h, planes, tan = host[r]
-                if not free[r]:  # pool exhausted: a pinned allocation inside the timed loop (counted)
+                if not free[r]:  # pool exhausted: a pinned allocation inside the timed loop (counted, timed)
+                    a = time.perf_counter()
                     free[r].append(torch.empty(w * h, 4).pin_memory())
                     outs[r].append(free[r][-1])
                     misses += 1
+                    miss_ms += (time.perf_counter() - a) * 1e3
                 o = free[r].pop()
                 fid = srv.submit(eids[int(env_of[k])], planes, w, h, o, seed=k, evaluator=evaluator, tangent=tan)
                 busy[fid] = (r, o, w * h)
                 k += 1
+            max_busy = max(max_busy, len(busy))
+            a = time.perf_counter()
             srv.tick(stream)
-            for fid, sub_s, adm_s, done_s in srv.poll():
+            polled = srv.poll()
+            max_call = max(max_call, time.perf_counter() - a)
+            for fid, sub_s, adm_s, done_s in polled:
                 r, o, n = busy.pop(fid)
                 free[r].append(o)
                 lat.append((done_s - sub_s) * 1e3)
@@ -569,7 +580,10 @@ def serving(args, glint, render, ctx, dev, stream):
                 "mean_ms": round(float(lat.mean()), 3), "max_ms": round(float(lat.max()), 3),
                 "mpix_s_offered": round(npx / wall / 1e6, 2), "wall_s": round(wall, 3),
                 "ticks": st["ticks"], "launches": st["launches"], "items": st["items"],
-                "peak_device_bytes": st["peak_bytes"], "output_pool_misses": misses}
+                "peak_device_bytes": st["peak_bytes"], "output_pool_misses": misses,
+                "output_pool_miss_ms": round(miss_ms, 2), "max_in_flight": max_busy,
+                "max_tick_poll_ms": round(max_call * 1e3, 3),
+                "max_loop_ms": round(max_loop * 1e3, 3)}
 
     # outputs: SERVE_POOL pinned buffers per resolution allocated before any
     # timing, so that no frame waits on a pinned allocation (a miss is counted)
@@ -578,15 +592,18 @@ def serving(args, glint, render, ctx, dev, stream):
     run(glint.EVAL_E1)  # warm-up pass (pinned pools, module loads)
     plain = run(glint.EVAL_E1)
     surrogate_ = run(glint.EVAL_MLP)
-    plain_upload = run(glint.EVAL_E1, upload=True)
+    legs = {"plain": plain, "surrogate": surrogate_}
+    if args.serving_upload:
+        legs["plain_upload"] = run(glint.EVAL_E1, upload=True)
     return {"requests": SERVE_REQUESTS, "arrivals": f"Poisson, mean {SERVE_RATE_HZ:.0f}/s, seed {SERVE_SEED}",
             "resolutions": [f"{w}x{h}" for w, h in SERVE_RES], "envs": len(SERVE_ENVS),
             "memory_budget_bytes": SERVE_BUDGET, "tick_pixels": SERVE_TICK,
             "frames": "page-locked host buffers, shaded in place (G-buffer read and result written over the "
-                      "CPU-GPU link); plain_upload: the same frames copied in and out by the copy engines",
+                      "CPU-GPU link)" + ("; plain_upload: the same frames copied in and out by the copy engines"
+                                         if args.serving_upload else ""),
             "latency": "host clock from submission to the frame's result in its host buffer "
                        "(queue: submission to admission; service: admission to result)",
-            "plain": plain, "surrogate": surrogate_, "plain_upload": plain_upload}
+            **legs}
 
 
 def run_ours(args):
@@ -794,6 +811,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-config3", action="store_true")
+    ap.add_argument("--serving-upload", action="store_true",
+                    help="also run the serving mix with every frame copied in and out (the server's upload mode)")
     ap.add_argument("--window-ms", type=float, default=WINDOW_MS,
                     help="length of the clock / percentile window after the timed steps (0: none, for profiling)")
     ap.add_argument("--surrogate-steps", type=int, default=SURROGATE_STEPS,

@@ -476,13 +476,13 @@ glint_status glint_mlp_generate(glint_ctx *ctx, const glint_env *env, const glin
  * while their device buffers fit the memory budget (FIFO).  A frame whose
  * buffers all lie in page-locked memory the device addresses is shaded in
  * place (the kernels read its G-buffer and write its result over the CPU-GPU
- * link; it holds device memory only for the surrogate's p_k), unless the
- * server was created with upload = 1; other frames are copied to the device
- * on copy streams.  A tick shades a tile of every admitted frame whose inputs
- * are on hand and then up to tick_pixels pixels, frames with the fewest pixels
- * left first, in one persistent launch over a work list of (frame, pixel
- * range) items (plus, for frames on the surrogate path, one fused-inference
- * launch first).  Finished frames are copied back (unless shaded in place)
+ * link; it holds no device memory), unless the server was created with
+ * upload = 1; other frames are copied to the device on copy streams.  A tick
+ * shades a tile of every admitted frame whose inputs are on hand and then up
+ * to tick_pixels pixels, frames with the fewest pixels left first, in one
+ * persistent launch over a work list of (frame, pixel range) items (and one
+ * more, of the shading with the network fused in, for frames on the surrogate
+ * path).  Finished frames are copied back (unless shaded in place)
  * and released; glint_server_poll reports them.  A frame's pixels are computed
  * exactly as glint_shade's kernel computes them, whatever else shares its
  * ticks and wherever its buffers lie.  One host thread drives a server.
@@ -497,7 +497,7 @@ typedef struct glint_server_desc {
     int max_frames;         /* admitted frames at most (0 = 64) */
     int max_inflight_ticks; /* ticks enqueued on the GPU at most; a tick waits for older ones (0 = 2) */
     int upload;             /* 1: copy every frame into the budget's device memory; 0: shade frames in
-                               page-locked host memory in place */
+                               page-locked host memory in place (no device memory) */
 } glint_server_desc;
 
 /* A frame.  Planes are HOST memory in glint_gbuffer's layout (page-locked

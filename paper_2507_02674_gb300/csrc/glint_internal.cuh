@@ -165,13 +165,13 @@ int glint_mlp_device(const glint_mlp *m);
 // Device address of `bytes` bytes of host memory at `p` when all of them lie
 // in one page-locked allocation the current device can address, else NULL.
 const void *glint_host_device_view(const void *p, size_t bytes);
-// Serving launches (glint_serve.cu): the shading kernel and the surrogate's
-// fused inference over a work list; frames/items are device-addressable arrays
+// Serving launches: the shading kernel (glint_shade.cu) and the shading with
+// the surrogate fused in (glint_mlp.cu) over a work list; frames/items are device-addressable arrays
 // (the server passes page-locked host tables).
 namespace glint { struct ShadeArgs; struct ServeItem; }
-cudaError_t glint_launch_serve(int K, bool given, const glint::ShadeArgs *frames, const glint::ServeItem *items,
-                               int nitems, int grid, cudaStream_t s);
-cudaError_t glint_launch_mlp_serve(int K, int num_sms, const glint::ShadeArgs *frames, const glint::ServeItem *items,
+cudaError_t glint_launch_serve(int K, const glint::ShadeArgs *frames, const glint::ServeItem *items, int nitems,
+                               int grid, cudaStream_t s);
+cudaError_t glint_launch_serve_mlp(int K, int num_sms, const glint::ShadeArgs *frames, const glint::ServeItem *items,
                                    int nitems, cudaStream_t s);
 void glint_mlp_weights(const glint_mlp *m, const void **wt, const float **params);
 // Shading with a comparison draw (glint_variants.cu).

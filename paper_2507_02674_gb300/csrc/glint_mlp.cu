@@ -362,46 +362,6 @@ __global__ void __launch_bounds__(kNT, 4) k_mlp_infer(ShadeArgs a, const __nv_bf
     }
 }
 
-// Serving: fused inference over a work list of (frame, pixel range) items of
-// frames that may use different networks, writing each frame's p_k to its
-// p_out.  A block reloads the weights when an item's network differs from the
-// one it holds.  Items start at multiples of 128 pixels of their frame.
-template <int K>
-__global__ void __launch_bounds__(kNT, 4) k_mlp_serve(const ShadeArgs *__restrict__ frames,
-                                                   const ServeItem *__restrict__ items, int nitems) {
-    __shared__ SmemInfer sm;
-    __shared__ ShadeArgs sa;
-    const void *held = nullptr;
-#pragma unroll 1
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const ServeItem item = items[it];
-        __syncthreads();
-        if (threadIdx.x == 0) sa = frames[item.frame];
-        __syncthreads();
-        if (sa.mlp_wt != held) {
-            held = sa.mlp_wt;
-            load_weights<kNT>(sm.w, reinterpret_cast<const __nv_bfloat16 *>(sa.mlp_wt), sa.mlp_params);
-        }
-        const long end = item.first + item.count;
-#pragma unroll 1
-        for (long base = item.first; base < end; base += kNT) {
-            const long q = base + threadIdx.x;
-            __syncthreads();  // the previous tile's readers are done
-            SmemRowSink<K> sink{sm, (int)threadIdx.x};
-            bool fg = false;
-            if (q < end) {
-                const float4 g0 = ldg4(sa.view_n0 + q);
-                fg = g0.w > 0.f;
-                if (fg) mlp_features<K>(sa, q, g0, ldg4(sa.normal_f0 + q), ldg4(sa.uv_alpha + q), sink);
-            }
-            if (!fg) sink.zero();
-            sm.fg[threadIdx.x] = fg ? 1 : 0;
-            __syncthreads();
-            net_tile<1>(sm, base, end, K, sa.p_out);
-        }
-    }
-}
-
 // ------------------------------------------------------------------ shading
 // The surrogate fused into the shading: a block of kFusedNT pixels computes
 // their inputs (mlp_features, as k_mlp_infer), the network on the tile (warp w
@@ -450,16 +410,14 @@ struct FusedRowSink {
     }
 };
 
+// One tile of the fused kernel: pixel q of frame `a` (valid: q is one of the
+// tile's pixels) with the block's kFusedNT threads; the weights are in sm.w.
+// Every thread of the block calls it (it synchronises twice).
 template <int K, bool INTEGER, bool DEBUG>
-__global__ void __launch_bounds__(kFusedNT, 3) k_shade_mlp(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
-                                                          const float *__restrict__ params) {
-    extern __shared__ __align__(16) unsigned char fused_smem[];
-    SmemFused &sm = *reinterpret_cast<SmemFused *>(fused_smem);
-    load_weights<kFusedNT>(sm.w, wt, params);
-    const long q = (long)blockIdx.x * kFusedNT + threadIdx.x;
+__device__ __forceinline__ void fused_tile(const ShadeArgs &a, SmemFused &sm, long q, bool valid) {
     float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f);
     bool fg = false;
-    if (q < a.npix) {
+    if (valid) {
         g0 = ldg4(a.view_n0 + q);
         fg = g0.w > 0.f;
     }
@@ -496,7 +454,7 @@ __global__ void __launch_bounds__(kFusedNT, 3) k_shade_mlp(ShadeArgs a, const __
         }
     }
     __syncthreads();
-    if (q >= a.npix) return;
+    if (!valid) return;
     if (!fg) {
         shade_pixel<K, INTEGER, DEBUG, EV_NONE>(a, q);  // background: black, debug outputs 0
         return;
@@ -507,6 +465,53 @@ __global__ void __launch_bounds__(kFusedNT, 3) k_shade_mlp(ShadeArgs a, const __
 #pragma unroll
     for (int k = 0; k < K; ++k) p[k] = sm.lp[threadIdx.x * kLpStride + k];
     shade_draws<K, INTEGER, DEBUG, kDrawDual, 0>(a, q, g0, g2, g3, Lor, Log, Lob, p);
+}
+
+template <int K, bool INTEGER, bool DEBUG>
+__global__ void __launch_bounds__(kFusedNT, 3) k_shade_mlp(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
+                                                          const float *__restrict__ params) {
+    extern __shared__ __align__(16) unsigned char fused_smem[];
+    SmemFused &sm = *reinterpret_cast<SmemFused *>(fused_smem);
+    load_weights<kFusedNT>(sm.w, wt, params);
+    const long q = (long)blockIdx.x * kFusedNT + threadIdx.x;
+    fused_tile<K, INTEGER, DEBUG>(a, sm, q, q < a.npix);
+}
+
+// Serving with the fused surrogate: one launch over a work list of (frame,
+// pixel range) items of frames on the surrogate path.  Block b takes items
+// b, b + G, ...; the frame's arguments are staged in shared memory and the
+// weights reloaded when the item's network differs from the block's last;
+// each item runs in tiles of kFusedNT pixels.  A pixel comes out as
+// k_shade_mlp computes it.
+struct SmemServeFused {
+    SmemFused f;
+    ShadeArgs sa;
+};
+
+template <int K>
+__global__ void __launch_bounds__(kFusedNT, 3) k_serve_mlp(const ShadeArgs *__restrict__ frames,
+                                                          const ServeItem *__restrict__ items, int nitems) {
+    extern __shared__ __align__(16) unsigned char fused_smem[];
+    SmemServeFused &sm = *reinterpret_cast<SmemServeFused *>(fused_smem);
+    const void *held = nullptr;
+#pragma unroll 1
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const ServeItem item = items[it];
+        __syncthreads();  // the previous item's readers of sa, the weights and the tile are done
+        if (threadIdx.x == 0) sm.sa = frames[item.frame];
+        __syncthreads();
+        if (sm.sa.mlp_wt != held) {  // uniform over the block
+            held = sm.sa.mlp_wt;
+            load_weights<kFusedNT>(sm.f.w, reinterpret_cast<const __nv_bfloat16 *>(sm.sa.mlp_wt), sm.sa.mlp_params);
+        }
+        const long end = item.first + item.count;
+#pragma unroll 1
+        for (long base = item.first; base < end; base += kFusedNT) {
+            __syncthreads();  // the previous tile's readers of xs and lp are done
+            const long q = base + threadIdx.x;
+            fused_tile<K, true, false>(sm.sa, sm.f, q, q < end);
+        }
+    }
 }
 
 // Inputs of every pixel: x (n x 64 BF16, background rows 0), lp (n x K).
@@ -1000,26 +1005,33 @@ cudaError_t glint_launch_shade_mlp(const glint_ctx *ctx, const glint_env *env, c
     }
 }
 
-cudaError_t glint_launch_mlp_serve(int K, int num_sms, const ShadeArgs *frames, const ServeItem *items, int nitems,
+namespace {
+template <int K>
+cudaError_t launch_serve_mlp_k(int num_sms, const ShadeArgs *frames, const ServeItem *items, int nitems,
+                               cudaStream_t s) {
+    static int per_sm = 0;  // resident blocks per SM
+    const size_t smem = sizeof(SmemServeFused);
+    if (!per_sm) {
+        cudaError_t e = cudaFuncSetAttribute(k_serve_mlp<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve_mlp<K>, kFusedNT, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = std::max(per_sm, 1);
+    }
+    const int grid = std::min(nitems, per_sm * num_sms);
+    k_serve_mlp<K><<<grid, kFusedNT, smem, s>>>(frames, items, nitems);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t glint_launch_serve_mlp(int K, int num_sms, const ShadeArgs *frames, const ServeItem *items, int nitems,
                                    cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    static int per_sm[3] = {0, 0, 0};  // resident blocks per SM of k_mlp_serve<2, 4, 8>
-    const int ki = K == 2 ? 0 : K == 4 ? 1 : 2;
-    if (!per_sm[ki]) {
-        cudaError_t e = K == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ki], k_mlp_serve<2>, kNT, 0)
-                      : K == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ki], k_mlp_serve<4>, kNT, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ki], k_mlp_serve<8>, kNT, 0);
-        if (e != cudaSuccess) return e;
-        per_sm[ki] = std::max(per_sm[ki], 1);
-    }
-    const int grid = std::min(nitems, per_sm[ki] * num_sms);
     switch (K) {
-    case 2: k_mlp_serve<2><<<grid, kNT, 0, s>>>(frames, items, nitems); break;
-    case 4: k_mlp_serve<4><<<grid, kNT, 0, s>>>(frames, items, nitems); break;
-    case 8: k_mlp_serve<8><<<grid, kNT, 0, s>>>(frames, items, nitems); break;
+    case 2: return launch_serve_mlp_k<2>(num_sms, frames, items, nitems, s);
+    case 4: return launch_serve_mlp_k<4>(num_sms, frames, items, nitems, s);
+    case 8: return launch_serve_mlp_k<8>(num_sms, frames, items, nitems, s);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 void glint_mlp_weights(const glint_mlp *g, const void **wt, const float **params) {

@@ -143,7 +143,6 @@ struct Frame {
     float *dev = nullptr;      // base of the frame's device block
     glint_gbuffer gb{};        // device planes
     float *out = nullptr;      // device output
-    float *p = nullptr;        // device p_k scratch (surrogate path)
     cudaEvent_t uploaded = nullptr, downloaded = nullptr;
     bool in_place = false;     // shaded where it lies: gb and out address the caller's page-locked buffers
     bool ready = false;        // `uploaded` has completed (or in place): the frame can be planned
@@ -196,13 +195,11 @@ struct glint_server {
 
 namespace {
 
-// Device bytes of a frame: its planes and output unless shaded in place, and
-// the p_k scratch of the surrogate path.
-size_t frame_bytes(const glint_frame_request &r, int K, bool in_place) {
+// Device bytes of a frame: its planes and output, none if shaded in place.
+size_t frame_bytes(const glint_frame_request &r, bool in_place) {
     const size_t n = (size_t)r.width * (size_t)r.height;
     const size_t planes = (r.evaluator == GLINT_EVAL_MLP) ? 5 : 4;
-    const size_t pbytes = (r.evaluator == GLINT_EVAL_MLP) ? ((n * K * sizeof(float) + 255) / 256 * 256) : 0;
-    return (in_place ? 0 : (planes + 1) * ((n * 16 + 255) / 256 * 256)) + pbytes;
+    return in_place ? 0 : (planes + 1) * ((n * 16 + 255) / 256 * 256);
 }
 
 void free_frame_events(Frame &f) {
@@ -240,7 +237,7 @@ glint_status admit(glint_server *s) {
     while (!s->queue.empty() && (int)s->active.size() < s->d.max_frames) {
         Frame &q = s->queue.front();
         if (s->envs[q.req.env].applied < q.env_version) break;  // FIFO: waits for its map's update
-        const size_t bytes = frame_bytes(q.req, s->K, q.in_place);
+        const size_t bytes = frame_bytes(q.req, q.in_place);
         long long off = -1;
         if (bytes > 0) {
             off = glint_arena_alloc(s->arena, bytes);
@@ -267,13 +264,11 @@ glint_status admit(glint_server *s) {
                                      "glint_server_tick: upload");
             }
             f.out = reinterpret_cast<float *>(p);
-            p += plane;
             f.gb = glint_gbuffer{dst[0], dst[1], dst[2], dst[3], f.req.width, f.req.height, dst[4]};
             if (st == GLINT_OK)
                 st = cuda_status(cudaEventCreateWithFlags(&f.uploaded, cudaEventDisableTiming), "glint_server_tick");
             if (st == GLINT_OK) st = cuda_status(cudaEventRecord(f.uploaded, upload_stream(s, f)), "glint_server_tick");
         }
-        f.p = (f.req.evaluator == GLINT_EVAL_MLP) ? reinterpret_cast<float *>(p) : nullptr;
         if (st == GLINT_OK) st = cuda_status(cudaEventCreateWithFlags(&f.downloaded, cudaEventDisableTiming), "glint_server_tick");
         if (st != GLINT_OK) {
             if (off >= 0) glint_arena_free(s->arena, off);
@@ -477,7 +472,7 @@ glint_status glint_server_submit(glint_server *s, const glint_frame_request *r, 
         }
         if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
     }
-    const size_t bytes = frame_bytes(*r, s->K, f.in_place);
+    const size_t bytes = frame_bytes(*r, f.in_place);
     if (bytes > s->arena->bytes) {
         set_error("glint_server_submit: the frame needs %zu bytes, more than the budget %zu", bytes, s->d.memory_budget);
         return GLINT_ERR_INVALID_ARG;
@@ -580,8 +575,6 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
                 const glint_env *env = s->envs[f.req.env].env;
                 ShadeArgs a = make_args(s->ctx, env, &f.gb, &prm);
                 a.out = reinterpret_cast<float4 *>(f.out);
-                a.pk_in = f.p;
-                a.p_out = f.p;
                 if (f.req.evaluator == GLINT_EVAL_MLP)
                     glint_mlp_weights(s->envs[f.req.env].mlp, &a.mlp_wt, &a.mlp_params);
                 table_of[j] = nframes;
@@ -591,22 +584,17 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
             sl.h_items[k] = ServeItem{table_of[j], it_c[k], it_first[k]};
             if (j < n_mlp_frames) ++n_mlp_items;
         }
-        // surrogate: one fused-inference launch over its frames' items (grouped by network)
+        // surrogate path: one launch of the shading with the network fused in
+        // over its frames' items (grouped by network), then the plain items
         if (st == GLINT_OK && n_mlp_items > 0) {
-            st = cuda_status(glint_launch_mlp_serve(s->K, s->ctx->num_sms, sl.v_frames, sl.v_items, n_mlp_items, cs),
-                             "glint_server_tick: inference");
+            st = cuda_status(glint_launch_serve_mlp(s->K, s->ctx->num_sms, sl.v_frames, sl.v_items, n_mlp_items, cs),
+                             "glint_server_tick: shade (surrogate)");
             ++nl;
-            if (st == GLINT_OK) {
-                const int grid = std::min(n_mlp_items, s->ctx->num_sms * glint::kShadeMinBlocks);
-                st = cuda_status(glint_launch_serve(s->K, true, sl.v_frames, sl.v_items, n_mlp_items, grid, cs),
-                                 "glint_server_tick: shade");
-                ++nl;
-            }
         }
         if (st == GLINT_OK && nit_all > n_mlp_items) {
             const int grid = std::min(nit_all - n_mlp_items, s->ctx->num_sms * glint::kShadeMinBlocks);
-            st = cuda_status(glint_launch_serve(s->K, false, sl.v_frames, sl.v_items + n_mlp_items,
-                                                nit_all - n_mlp_items, grid, cs), "glint_server_tick: shade");
+            st = cuda_status(glint_launch_serve(s->K, sl.v_frames, sl.v_items + n_mlp_items, nit_all - n_mlp_items,
+                                                grid, cs), "glint_server_tick: shade");
             ++nl;
         }
         if (st == GLINT_OK) st = cuda_status(cudaEventRecord(sl.done, cs), "glint_server_tick");

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kShadeNT, kShadeMinBlocks) k_shade(ShadeArgs a
 // Serving: one launch over a work list of (frame, pixel range) items of many
 // frames (resolutions, maps and seeds may differ; K is shared).  Block b
 // takes items b, b + G, ...; the frame's arguments are staged in shared memory.
-template <int K, int EV>
+template <int K>
 __global__ void __launch_bounds__(kShadeNT, kShadeMinBlocks) k_serve(const ShadeArgs *__restrict__ frames,
                                                        const ServeItem *__restrict__ items, int nitems) {
     __shared__ ShadeArgs sa;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kShadeNT, kShadeMinBlocks) k_serve(const Shade
         __syncthreads();
 #pragma unroll 1
         for (int off = threadIdx.x; off < item.count; off += kShadeNT)
-            shade_pixel<K, true, false, EV>(sa, item.first + off);
+            shade_pixel<K, true, false, EV_E1>(sa, item.first + off);
     }
 }
 
@@ -156,18 +156,14 @@ cudaError_t glint_launch_probs(const glint_ctx *ctx, const glint_env *env, const
     }
 }
 
-cudaError_t glint_launch_serve(int K, bool given, const ShadeArgs *frames, const ServeItem *items, int nitems, int grid,
+cudaError_t glint_launch_serve(int K, const ShadeArgs *frames, const ServeItem *items, int nitems, int grid,
                                cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
     switch (K) {
-    case 2: given ? k_serve<2, EV_GIVEN><<<grid, kShadeNT, 0, s>>>(frames, items, nitems)
-                  : k_serve<2, EV_E1><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
-    case 4: given ? k_serve<4, EV_GIVEN><<<grid, kShadeNT, 0, s>>>(frames, items, nitems)
-                  : k_serve<4, EV_E1><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
-    case 8: given ? k_serve<8, EV_GIVEN><<<grid, kShadeNT, 0, s>>>(frames, items, nitems)
-                  : k_serve<8, EV_E1><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
-    case 16: given ? k_serve<16, EV_GIVEN><<<grid, kShadeNT, 0, s>>>(frames, items, nitems)
-                   : k_serve<16, EV_E1><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
+    case 2: k_serve<2><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
+    case 4: k_serve<4><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
+    case 8: k_serve<8><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
+    case 16: k_serve<16><<<grid, kShadeNT, 0, s>>>(frames, items, nitems); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

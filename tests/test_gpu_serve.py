@@ -1,8 +1,9 @@
 """The serving loop on the GPU: each frame's result is the same alone and in
-a mix of frames of other resolutions, maps, seeds and paths (bit for bit), and
-equals glint_shade's; admission by memory (frames wait for the budget, peak
-use stays within it); continuous batching (a small frame submitted after a
-large one finishes first)."""
+a mix of frames of other resolutions, maps, seeds and paths, and the same as
+glint_shade's (bit for bit); frames shaded in place equal uploaded ones;
+admission by memory (frames wait for the budget, peak use stays within it);
+continuous batching (a small frame submitted after a large one finishes
+first)."""
 import numpy as np
 import pytest
 
@@ -85,14 +86,12 @@ def test_alone_equals_mix_equals_glint_shade(gl):
         planes = [p.cuda() for p in r.planes]
         ref = frames[e].shade(planes, r.w, r.h, seed=seed, evaluator=ev, tangent=r.tan.cuda(),
                               mlp=net if ev == glint.EVAL_MLP else None).cpu()
-        same = float((ref == r.out).all(1).float().mean())
-        print(f"frame {r.w}x{r.h} env {e} path {ev}: equal to glint_shade at {same:.4%} of pixels")
-        torch.testing.assert_close(r.out, ref, rtol=1e-5, atol=1e-6 * float(ref.abs().max()))
+        assert torch.equal(r.out, ref)  # the serving kernels compute each pixel as glint_shade's do
 
 
 def test_in_place_equals_uploaded(gl):
-    """Frames in page-locked memory are shaded in place (no device copy of
-    their planes or output); with the server uploading them, or from pageable
+    """Frames in page-locked memory are shaded in place (no device memory at
+    all, on either path); with the server uploading them, or from pageable
     memory (always uploaded), every frame comes out bit for bit the same."""
     glint, render, ctx, torch, frames, net = gl
     shapes = [(640 * 360, 640, 51), (300 * 200 + 7, 300, 52), (50000, 500, 53)]
@@ -108,12 +107,8 @@ def test_in_place_equals_uploaded(gl):
         assert len(_drain(s, torch)) == len(reqs)
         st = s.stats()
         npix = [r.w * r.h for r in reqs]
-        pk = -(-npix[1] * 8 * 4 // 256) * 256  # the surrogate frame's p_k scratch
-        planes = sum(5 * -(-n * 16 // 256) * 256 for n in npix) + pk + -(-npix[1] * 16 // 256) * 256
-        if mode == "in_place":
-            assert st["peak_bytes"] == pk  # only the surrogate's p_k lives on the device
-        else:
-            assert st["peak_bytes"] == planes
+        planes = sum(5 * -(-n * 16 // 256) * 256 for n in npix) + -(-npix[1] * 16 // 256) * 256  # + tangent
+        assert st["peak_bytes"] == (0 if mode == "in_place" else planes)
         assert st["used_bytes"] == 0
         outs[mode] = [r.out.clone() for r in reqs]
         assert all(bool(o.abs().sum() > 0) for o in outs[mode])

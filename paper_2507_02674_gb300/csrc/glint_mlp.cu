@@ -368,9 +368,11 @@ __global__ void __launch_bounds__(kNT, 4) k_mlp_infer(ShadeArgs a, const __nv_bf
 // on rows [32 w, 32 w + 32)), and the glint draws (shade_draws) with the
 // network's p_k from shared memory -- no per-pixel p_k leaves the chip.  The
 // smooth radiance reads the colour channels of the filtered maps as the
-// shading with given p_k does.  Three blocks of 256 threads per SM: 69 KB of
+// shading with given p_k does.  Two blocks of 256 threads per SM: 69 KB of
 // shared memory each (weights, the input tile, log-priors then p_k in place),
-// 80 registers a thread for the draws.
+// leaving ~90 KB of L1 for the texel gathers of the inputs, and up to 128
+// registers a thread (no spills; three blocks at 80 registers spilled and
+// took 3% longer).
 constexpr int kFusedNT = 256;
 
 struct SmemFused {
@@ -468,7 +470,7 @@ __device__ __forceinline__ void fused_tile(const ShadeArgs &a, SmemFused &sm, lo
 }
 
 template <int K, bool INTEGER, bool DEBUG>
-__global__ void __launch_bounds__(kFusedNT, 3) k_shade_mlp(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
+__global__ void __launch_bounds__(kFusedNT, 2) k_shade_mlp(ShadeArgs a, const __nv_bfloat16 *__restrict__ wt,
                                                           const float *__restrict__ params) {
     extern __shared__ __align__(16) unsigned char fused_smem[];
     SmemFused &sm = *reinterpret_cast<SmemFused *>(fused_smem);
@@ -489,7 +491,7 @@ struct SmemServeFused {
 };
 
 template <int K>
-__global__ void __launch_bounds__(kFusedNT, 3) k_serve_mlp(const ShadeArgs *__restrict__ frames,
+__global__ void __launch_bounds__(kFusedNT, 2) k_serve_mlp(const ShadeArgs *__restrict__ frames,
                                                           const ServeItem *__restrict__ items, int nitems) {
     extern __shared__ __align__(16) unsigned char fused_smem[];
     SmemServeFused &sm = *reinterpret_cast<SmemServeFused *>(fused_smem);

@@ -18,6 +18,10 @@ namespace glint {
 // warps to fill the issue slots (1080p frame, K = 8: 0.378 ms at 8 blocks,
 // 0.342 ms at 6, 0.354 ms at 5, 0.403 ms at 4).
 constexpr int kShadeMinBlocks = 6;
+// K = 16 (15 draws a pixel, 16-entry arrays) spills 232 bytes at 80
+// registers; four blocks (128 registers) cut that to 40 and the 3840 x 2160
+// grazing frame from 1.393 to 1.320 ms (five blocks: 1.398 ms).
+constexpr int shade_min_blocks(int K) { return K >= 16 ? 4 : kShadeMinBlocks; }
 
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kTwoPi = 6.28318530717958647692f;

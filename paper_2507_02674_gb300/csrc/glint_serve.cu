@@ -592,7 +592,7 @@ glint_status glint_server_tick(glint_server *s, void *stream, int *launched) {
             ++nl;
         }
         if (st == GLINT_OK && nit_all > n_mlp_items) {
-            const int grid = std::min(nit_all - n_mlp_items, s->ctx->num_sms * glint::kShadeMinBlocks);
+            const int grid = std::min(nit_all - n_mlp_items, s->ctx->num_sms * glint::shade_min_blocks(s->K));
             st = cuda_status(glint_launch_serve(s->K, sl.v_frames, sl.v_items + n_mlp_items, nit_all - n_mlp_items,
                                                 grid, cs), "glint_server_tick: shade");
             ++nl;

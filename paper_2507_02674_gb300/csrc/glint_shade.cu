@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kShadeNT) k_probs(ShadeArgs a) {
 }
 
 template <int K, bool INTEGER, bool DEBUG, int EV>
-__global__ void __launch_bounds__(kShadeNT, kShadeMinBlocks) k_shade(ShadeArgs a) {
+__global__ void __launch_bounds__(kShadeNT, shade_min_blocks(K)) k_shade(ShadeArgs a) {
     const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
     if (q >= a.npix) return;
     shade_pixel<K, INTEGER, DEBUG, EV>(a, q);
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kShadeNT, kShadeMinBlocks) k_shade(ShadeArgs a
 // frames (resolutions, maps and seeds may differ; K is shared).  Block b
 // takes items b, b + G, ...; the frame's arguments are staged in shared memory.
 template <int K>
-__global__ void __launch_bounds__(kShadeNT, kShadeMinBlocks) k_serve(const ShadeArgs *__restrict__ frames,
+__global__ void __launch_bounds__(kShadeNT, shade_min_blocks(K)) k_serve(const ShadeArgs *__restrict__ frames,
                                                        const ServeItem *__restrict__ items, int nitems) {
     __shared__ ShadeArgs sa;
 #pragma unroll 1

@@ -9,7 +9,7 @@
 namespace {
 
 template <int K, bool INTEGER, int DRAW, int GRID>
-__global__ void __launch_bounds__(kShadeNT, kShadeMinBlocks) k_shade_var(ShadeArgs a) {
+__global__ void __launch_bounds__(kShadeNT, shade_min_blocks(K)) k_shade_var(ShadeArgs a) {
     const long q = (long)blockIdx.x * kShadeNT + threadIdx.x;
     if (q >= a.npix) return;
     shade_pixel<K, INTEGER, true, EV_E1, DRAW, GRID>(a, q);

@@ -353,7 +353,12 @@ __global__ void __launch_bounds__(kNT, 4) k_mlp_infer(ShadeArgs a, const __nv_bf
         if (q < a.npix) {
             const float4 g0 = ldg4(a.view_n0 + q);
             fg = g0.w > 0.f;
-            if (fg) mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), sink);
+            if (fg) {
+                const float4 g1 = ldg4(a.normal_f0 + q), g2 = ldg4(a.uv_alpha + q);
+                float pe[K];
+                e1_probs<K>(a, g0, g1, g2, pe);
+                mlp_features<K>(a, q, g0, g1, g2, pe, sink);
+            }
         }
         if (!fg) sink.zero();
         sm.fg[threadIdx.x] = fg ? 1 : 0;
@@ -367,8 +372,8 @@ __global__ void __launch_bounds__(kNT, 4) k_mlp_infer(ShadeArgs a, const __nv_bf
 // their inputs (mlp_features, as k_mlp_infer), the network on the tile (warp w
 // on rows [32 w, 32 w + 32)), and the glint draws (shade_draws) with the
 // network's p_k from shared memory -- no per-pixel p_k leaves the chip.  The
-// smooth radiance reads the colour channels of the filtered maps as the
-// shading with given p_k does.  Two blocks of 256 threads per SM: 69 KB of
+// smooth radiance comes from the colour channels at E1's taps, in the same
+// pass as E1's p_k (one reflection direction, level pair and table fetch).  Two blocks of 256 threads per SM: 69 KB of
 // shared memory each (weights, the input tile, log-priors then p_k in place),
 // leaving ~90 KB of L1 for the texel gathers of the inputs, and up to 128
 // registers a thread (no spills; three blocks at 80 registers spilled and
@@ -389,8 +394,14 @@ struct FusedRowSink {
     int r;
     __device__ __forceinline__ void group(int i, const float *v) {
         uint32_t *w32 = reinterpret_cast<uint32_t *>(sm.xs);
+        if constexpr (K == 8) {  // groups start at multiples of 8 inputs: one whole 16-byte chunk
+            *reinterpret_cast<uint4 *>(w32 + word_at(r, i / 2)) =
+                make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                           pack_bf16(v[6], v[7]));
+        } else {
 #pragma unroll
-        for (int j = 0; j < K / 2; ++j) w32[word_at(r, i / 2 + j)] = pack_bf16(v[2 * j], v[2 * j + 1]);
+            for (int j = 0; j < K / 2; ++j) w32[word_at(r, i / 2 + j)] = pack_bf16(v[2 * j], v[2 * j + 1]);
+        }
     }
     __device__ __forceinline__ void log_prior(const float *l) {
 #pragma unroll
@@ -424,8 +435,15 @@ __device__ __forceinline__ void fused_tile(const ShadeArgs &a, SmemFused &sm, lo
         fg = g0.w > 0.f;
     }
     FusedRowSink<K> sink{sm, (int)threadIdx.x};
-    if (fg) mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), sink);
-    else sink.zero();
+    float L[3] = {0.f, 0.f, 0.f};  // the smooth radiance, from E1's taps
+    if (fg) {
+        const float4 g1 = ldg4(a.normal_f0 + q), g2 = ldg4(a.uv_alpha + q);
+        float pe[K];
+        e1_probs<K, true>(a, g0, g1, g2, pe, L);
+        mlp_features<K>(a, q, g0, g1, g2, pe, sink);
+    } else {
+        sink.zero();
+    }
     sm.fg[threadIdx.x] = fg ? 1 : 0;
     __syncthreads();
     {
@@ -461,12 +479,11 @@ __device__ __forceinline__ void fused_tile(const ShadeArgs &a, SmemFused &sm, lo
         shade_pixel<K, INTEGER, DEBUG, EV_NONE>(a, q);  // background: black, debug outputs 0
         return;
     }
-    const float4 g1 = ldg4(a.normal_f0 + q), g2 = ldg4(a.uv_alpha + q), g3 = ldg4(a.duv + q);
-    float Lor, Log, Lob, p[K];
-    smooth_and_probs<K, EV_NONE>(a, q, g0, g1, g2, Lor, Log, Lob, p);
+    const float4 g2 = ldg4(a.uv_alpha + q), g3 = ldg4(a.duv + q);
+    float p[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) p[k] = sm.lp[threadIdx.x * kLpStride + k];
-    shade_draws<K, INTEGER, DEBUG, kDrawDual, 0>(a, q, g0, g2, g3, Lor, Log, Lob, p);
+    shade_draws<K, INTEGER, DEBUG, kDrawDual, 0>(a, q, g0, g2, g3, L[0], L[1], L[2], p);
 }
 
 template <int K, bool INTEGER, bool DEBUG>
@@ -526,7 +543,10 @@ __global__ void __launch_bounds__(kNT) k_mlp_features(ShadeArgs a, uint4 *__rest
     const bool fg = g0.w > 0.f;
     if (fg) {
         ArraySink<K> sink{f, l};
-        mlp_features<K>(a, q, g0, ldg4(a.normal_f0 + q), ldg4(a.uv_alpha + q), sink);
+        const float4 g1 = ldg4(a.normal_f0 + q), g2 = ldg4(a.uv_alpha + q);
+        float pe[K];
+        e1_probs<K>(a, g0, g1, g2, pe);
+        mlp_features<K>(a, q, g0, g1, g2, pe, sink);
     } else {
 #pragma unroll
         for (int i = 0; i < kMlpIn; ++i) f[i] = 0.f;

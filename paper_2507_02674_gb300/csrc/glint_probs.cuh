@@ -457,9 +457,13 @@ __device__ __forceinline__ void e1a_weights(const ShadeArgs &a, long q, float4 g
 }
 
 // E1's p_k (step 1 of smooth_and_probs without the colour channels), from
-// the weights-only copy: p_1 = U + V W_1, p_k = V W_k.
-template <int K>
-__device__ __forceinline__ void e1_probs(const ShadeArgs &a, float4 g0, float4 g1, float4 g2, float *p) {
+// the weights-only copy: p_1 = U + V W_1, p_k = V W_k.  With COLOUR, also the
+// smooth radiance L = E_b c of smooth_and_probs from the colour channels at the
+// same taps (one reflection direction, level pair and table fetch for both):
+// the same values as smooth_and_probs computes.
+template <int K, bool COLOUR = false>
+__device__ __forceinline__ void e1_probs(const ShadeArgs &a, float4 g0, float4 g1, float4 g2, float *p,
+                                         float *L = nullptr) {
     const float mu_o = g1.x * g0.x + g1.y * g0.y + g1.z * g0.z;
     const float rx = 2.f * mu_o * g1.x - g0.x;
     const float ry = 2.f * mu_o * g1.y - g0.y;
@@ -480,18 +484,26 @@ __device__ __forceinline__ void e1_probs(const ShadeArgs &a, float4 g0, float4 g
     p[0] = tab.y + tab.x * W[0];
 #pragma unroll
     for (int k = 1; k < K; ++k) p[k] = tab.x * W[k];
+    if constexpr (COLOUR) {
+        constexpr int C4 = (3 + K + 3) / 4;
+        float ch[C4 * 4];
+        filtered_channels<K, C4, false>(a, th_r, ph_r, r0, r1, ft, ch);
+        const float Eb = g1.w * tab.z + tab.w;
+        L[0] = ch[0] * Eb;
+        L[1] = ch[1] * Eb;
+        L[2] = ch[2] * Eb;
+    }
 }
 
-// The surrogate's inputs of foreground pixel q, handed to `sink` as they are
-// computed (so that no caller has to hold all 64 at once): sink.group(i, v)
-// receives inputs i .. i+K (E1's p_k at 0, tap t's weights at K + t K),
-// sink.log_prior(lp) the K log-priors, and sink.tail(i, s) the scalars
-// mu, sqrt a_x, sqrt a_y at 6K .. 6K+3, after which the inputs up to 64 are 0.
+// The surrogate's inputs of foreground pixel q with E1's p_k pe (e1_probs),
+// handed to `sink` as they are computed (so that no caller has to hold all 64
+// at once): sink.group(i, v) receives inputs i .. i+K (E1's p_k at 0, tap t's
+// weights at K + t K), sink.log_prior(lp) the K log-priors, and sink.tail(i,
+// s) the scalars mu, sqrt a_x, sqrt a_y at 6K .. 6K+3, after which the inputs
+// up to 64 are 0.
 template <int K, class Sink>
 __device__ __forceinline__ void mlp_features(const ShadeArgs &a, long q, float4 g0, float4 g1, float4 g2,
-                                             Sink &sink) {
-    float pe[K];
-    e1_probs<K>(a, g0, g1, g2, pe);
+                                             const float *pe, Sink &sink) {
     sink.group(0, pe);
     float lp[K];
 #pragma unroll

@@ -32,23 +32,22 @@ _lib = None
 # relative error of subtree probability masses, of the FP32 normal quantile,
 # of an FP32 exp2/log2 chain, an absolute floor of every threshold, and an
 # absolute error of subtree masses.
-# The absolute mass error of E1, 2^-36: a fuzzy weight 1 - t of a texel whose
-# brightness lies just below a radiance level (Sec. 4, Eq. wkdefpractice) is a
-# small difference of FP32 values, so its rounding (~2^-24 of the bracket)
-# reaches a small filtered weight as an absolute, not relative, error (measured
-# on a GB300: 8.9e-13 on p_k = 1.0e-8 at the 1080p material distributions).
-TIE_DEFAULT = (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -36)
+# The absolute mass error, 2^-23, for every evaluator: a fuzzy weight 1 - t of
+# a texel whose brightness lies just below a radiance level (Sec. 4, Eq.
+# wkdefpractice) is a small difference of FP32 values, so its rounding, up to
+# ~2^-24 of the bracket, is an absolute error; the pyramid, the prefilter and
+# the E2 quadrature average texels (weights summing to one) and p_k = V W_k
+# with V <= 1, so no mass carries more than 2^-24 of it, plus its own
+# roundings: bound 2^-23.  (Measured on a GB300: 1.95e-11 on p_k = 5.6e-8 over
+# every pixel of the 1080p frame for E1; E2, whose FP32 texel coordinates also
+# move mass between neighbouring texels, 5e-10 at K = 8 and 3.7e-8 beyond the
+# relative bound at K = 16, where the sixteen levels sit closer.)
+TIE_DEFAULT = (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -23)
 # The E2 quadrature reads single pyramid texels per point at FP32 texel
 # coordinates (up to ~1.2e-4 texel of error, w_k changing by at most 1 per
-# texel), so a mass carried by a few points moves by ~1e-4 of itself and tiny
-# masses by an absolute ~1e-9 (measured on a GB300: 8.9e-5 relative, 5e-10
-# absolute).  Bounds 2^-12 and 2^-28.
-TIE_E2 = (2.0 ** -12, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -28)
-# At K = 16 the sixteen levels sit closer and more texels change weight
-# sharply between neighbours, so the same FP32 texel-coordinate error moves a
-# small mass by more in absolute terms (measured on a GB300 over 1537 random
-# pixels: 3.7e-8 beyond the relative bound; K = 8: 1.6e-9).  Bound 2^-23.
-TIE_E2_K16 = (2.0 ** -12, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -23)
+# texel), so a mass carried by a few points moves by ~1e-4 of itself
+# (measured on a GB300: 8.9e-5): relative bound 2^-12.
+TIE_E2 = (2.0 ** -12, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -23)
 NV = 6
 
 

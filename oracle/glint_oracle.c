@@ -1151,7 +1151,9 @@ static void tree_single(tree_ctx *t, int node, double *N, double *dN, double Nn,
                 double glo = fmin(fmax(old ? floor(G - tauG) : floor(G - tauG + 0.5), 1.0), Nn);
                 double ghi = fmin(fmax(old ? floor(G + tauG) : floor(G + tauG + 0.5), 1.0), Nn);
                 int interval = (dNn > 0.0) || (ghi - glo > 2.0);
-                double eG = interval ? tauG + 0.5 : 0.0;
+                /* the kernel rounds (or floors) some G' with |G' - G| <= tauG: its count
+                 * lies within tauG + 1/2 of G, so within tauG + 1 of round(G) */
+                double eG = interval ? tauG + 1.0 : 0.0;
                 cnt = push_outcome(list, cnt, gn, Nn - gn, eG, dNn + eG);
                 if (pass == 1 && !interval)
                     for (double g = glo; g <= ghi; g += 1.0) cnt = push_outcome(list, cnt, g, Nn - g, 0.0, 0.0);
@@ -1259,7 +1261,9 @@ static void tree_rec(tree_ctx *t, int node, double *N, double *dN)
         double glo = fmin(fmax(floor(G - tauG + 0.5), 1.0), N2 - 1.0);
         double ghi = fmin(fmax(floor(G + tauG + 0.5), 1.0), N2 - 1.0);
         int interval = (dNn > 0.0) || (ghi - glo > 2.0);
-        double eG = interval ? tauG + 0.5 : 0.0;
+        /* the kernel rounds some G' with |G' - G| <= tauG: its count lies
+         * within tauG + 1/2 of G, so within tauG + 1 of Gn = round(G) */
+        double eG = interval ? tauG + 1.0 : 0.0;
         for (int pass = 0; pass < 2; ++pass) {
             for (int reg = 0; reg < 4; ++reg) {
                 if (pass == 0 ? reg != nominal : !poss[reg]) continue;

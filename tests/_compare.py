@@ -16,7 +16,7 @@ import numpy as np
 RAD_RTOL = 1e-4        # relative tolerance on radiance
 RAD_ATOL_FRAC = 1e-6   # absolute floor, as a fraction of the largest smooth radiance
 P_RTOL = 2.0 ** -14    # relative tolerance on p_k: the oracle's tie-model bound e_P
-P_ATOL = 2.0 ** -36    # absolute floor on p_k: the tie model's absolute mass error of E1
+P_ATOL = 2.0 ** -23    # absolute floor on p_k: the tie model's absolute mass error
 LO_RTOL = 1e-4
 W_ATOL = 2e-6
 

@@ -45,18 +45,13 @@ def oracle_env(orc, env, mp: MethodParams):
     return e, pref
 
 
-def e2_tie(orc, K: int):
-    """Tie model of the E2 kernel: the K = 16 variant has its own absolute floor."""
-    return orc.TIE_E2_K16 if K >= 16 else orc.TIE_E2
-
-
 def oracle_shade(orc, rows16: np.ndarray, env, mp: MethodParams, tie=None, max_cand: int = 64, env_pref=None,
                  evaluator: int = 0, tangents=None, e2_S: int = 16, pk_in=None, draw: int = 0, gamma: float = 0.0,
                  grid: int = 0):
     e, pref = env_pref if env_pref is not None else oracle_env(orc, env, mp)
     lut = oracle_lut(orc, mp)
     return orc.shade(rows16, pref, mp.s_min, mp.s_max, lut, e.levels, mp.seed, mp.integer_mode,
-                     tie=e2_tie(orc, mp.K) if (tie is None and evaluator == 1) else (orc.TIE_DEFAULT if tie is None
+                     tie=orc.TIE_E2 if (tie is None and evaluator == 1) else (orc.TIE_DEFAULT if tie is None
                                                                                       else tie),
                      max_cand=max_cand, evaluator=evaluator,
                      tangents=tangents, e2_S=e2_S, env=e, pk_in=pk_in, draw=draw, gamma=gamma, grid=grid)

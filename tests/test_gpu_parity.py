@@ -12,7 +12,7 @@ import pytest
 
 from paper_2507_02674_gb300 import synth
 from tests._compare import compare_shade
-from tests._pipeline import MethodParams, e2_tie, oracle_env, oracle_lut, oracle_shade
+from tests._pipeline import MethodParams, oracle_env, oracle_lut, oracle_shade
 
 pytestmark = pytest.mark.gpu
 
@@ -218,7 +218,7 @@ def test_shade_e2_anisotropic(gl, orc, K):
     gb = synth.gbuffer_random(1537, seed=31 + K, width=1537)
     res = _run(gl, env, gb, mp, evaluator=1, e2_S=16)
     o = oracle_shade(orc, gb.rows16(), env, mp, evaluator=1, tangents=gb.tangents(), e2_S=16)
-    rep = _check(orc, o, res, nonunique=o.e2_flags > 0, tie=e2_tie(orc, K))
+    rep = _check(orc, o, res, nonunique=o.e2_flags > 0, tie=orc.TIE_E2)
     assert rep.nonunique < 0.02 * len(o.np_)
 
 
@@ -301,24 +301,40 @@ def test_shade_edge_cases(gl, orc):
     assert ctx.last_launches() == 0
 
 
-def test_shade_full_1080p_sampled(gl, orc):
+def test_shade_full_1080p_every_pixel(gl, orc):
     """The 1920 x 1080 frame (plane + 16 spheres, 1024 x 512 RGBA16F map with 4
-    suns, K = 8) in the launch configuration of the benchmark; 2000 sampled pixels
-    against the oracle, plus properties over every pixel."""
+    suns, K = 8) in the launch configuration of the benchmark: every pixel
+    against the oracle (in chunks of 16384 pixels, on all host cores), plus
+    properties over the frame."""
     glint, render, ctx, torch = gl
     mp = MethodParams(K=8, Wo=256, seed=1)
     env = synth.env_hdr(seed=1)
     gb = synth.gbuffer_scene(1920, 1080, seed=1)
-    rng = np.random.default_rng(0)
-    rows = np.sort(rng.choice(gb.npix, 2000, replace=False))
-    res = _run(gl, env, gb, mp, rows=rows)
-    o = oracle_shade(orc, gb.rows16()[rows], env, mp)
-    _check(orc, o, res)
-    # whole frame: finite, non-negative radiance
+    res = _run(gl, env, gb, mp)  # the intermediate outputs, from the debug launch
+    # the radiance under test comes from the benchmark's (non-debug) launch
     out = res["frame"].shade(render.gbuffer_tensors(gb), gb.width, gb.height, seed=mp.seed)
     torch.cuda.synchronize()
-    a = out.cpu().numpy()
-    assert np.all(np.isfinite(a)) and np.all(a[:, :3] >= 0) and np.all(a[:, 3] == 1)
+    b = out.cpu().numpy()
+    assert np.all(b[:, 3] == 1)
+    rgb_debug, res["rgb"] = res["rgb"], b[:, :3].astype(np.float64)
+    env_pref = oracle_env(orc, env, mp)
+    rows16 = gb.rows16()
+    keys = ("p", "np", "vert", "w", "nroot", "counts", "lo", "rgb")
+    unresolved = 0
+    chunk = 16384
+    for c0 in range(0, gb.npix, chunk):
+        sl = slice(c0, min(c0 + chunk, gb.npix))
+        o = oracle_shade(orc, rows16[sl], env, mp, env_pref=env_pref, max_cand=64)
+        rep = _check(orc, o, {k: res[k][sl] for k in keys})
+        unresolved += rep.trees_unresolved
+    print(f"1080p: {gb.npix} pixels compared, {unresolved} of {6 * gb.npix} trees with more than 64 valid "
+          f"outcomes (checked by invariants only)")
+    assert unresolved <= 6 * gb.npix // 1000
+    a = res["rgb"]
+    assert np.all(np.isfinite(a)) and np.all(a >= 0)
+    same = float(np.mean(np.all(a == rgb_debug, axis=1)))
+    print(f"benchmark launch vs debug launch: identical radiance at {same:.4%} of pixels")
+    np.testing.assert_allclose(a, rgb_debug, rtol=1e-6, atol=0)
 
 
 def test_invalid_arguments(gl):
@@ -383,7 +399,7 @@ def test_shade_compressed_weights(gl, orc, wfmt):
     env = synth.env_hdr(seed=6, W=256, H=128)
     gb = synth.gbuffer_random(2500, seed=15, width=2500)
     res = _run(gl, env, gb, mp)
-    tie = (2.0 ** -10, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 0.0) if wfmt == 1 else \
+    tie = (2.0 ** -10, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -23) if wfmt == 1 else \
         (2.0 ** -14, 2.0 ** -20, 2.0 ** -21, 2.0 ** -23, 2.0 ** -15)
     o = oracle_shade(orc, gb.rows16(), env, mp, tie=tie)
     # a stored code one step off (values straddling a rounding boundary) moves

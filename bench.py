@@ -752,6 +752,31 @@ def run_ours(args):
     if not torch.equal(host_out, out.cpu()):
         raise RuntimeError("glint_shade_host's frame differs from glint_shade's")
     pipe.close()
+    # the host link's bandwidth in each direction, measured here with copy-engine
+    # copies of the same pinned buffers (SM loads of page-locked memory reach the
+    # same rate): the end-to-end step cannot beat its bytes at these rates
+    scratch = [torch.empty_like(p) for p in planes]
+    scratch_out = torch.empty_like(out)
+    lev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        for d_, h_ in zip(scratch, host_planes):  # warm-up
+            d_.copy_(h_, non_blocking=True)
+        lev[0].record(stream)
+        for _ in range(3):
+            for d_, h_ in zip(scratch, host_planes):
+                d_.copy_(h_, non_blocking=True)
+        lev[1].record(stream)
+        host_out.copy_(scratch_out, non_blocking=True)  # warm-up
+        lev[2].record(stream)
+        for _ in range(3):
+            host_out.copy_(scratch_out, non_blocking=True)
+        lev[3].record(stream)
+    torch.cuda.synchronize(dev)
+    plane_bytes = sum(p.numel() * 4 for p in host_planes)
+    h2d_gbs = 3 * plane_bytes / (lev[0].elapsed_time(lev[1]) / 1e3) / 1e9
+    d2h_gbs = 3 * d2h / (lev[2].elapsed_time(lev[3]) / 1e3) / 1e9
+    del scratch, scratch_out
+    e2e_floor_ms = max(h2d / (h2d_gbs * 1e9), d2h / (d2h_gbs * 1e9)) * 1e3
     e2e_val = job_throughput(ws, npix, e2e_steps, e2e_ms)
     e2e_serial_val = job_throughput(ws, npix, e2e_steps, e2e_serial_ms)
 
@@ -798,7 +823,13 @@ def run_ours(args):
                     "path": ("glint_env_update + glint_shade_host from pinned host buffers, "
                              + ("in place (the shading kernel reads and writes host memory)" if e2e_in_place
                                 else "staged in bands")),
-                    "frames_in_flight": 2, "serial_value": round(e2e_serial_val, 3)},
+                    "frames_in_flight": 2, "serial_value": round(e2e_serial_val, 3),
+                    "roofline": {"bound": "host link", "h2d_gbs": round(h2d_gbs, 1), "d2h_gbs": round(d2h_gbs, 1),
+                                 "floor_ms": round(e2e_floor_ms, 4), "ms_per_step": round(e2e_ms / e2e_steps, 4),
+                                 "frac": round(e2e_floor_ms / (e2e_ms / e2e_steps), 4),
+                                 "basis": "floor = the step's host-to-device bytes (G-buffer and map texels) at "
+                                          "the measured rate (the output goes the other way at the same time); "
+                                          "rates from copies of the same pinned buffers in this run"}},
             "gpu_launches": launches_per_step * args.steps,
         }
     if rank == 0 and not args.no_config3:

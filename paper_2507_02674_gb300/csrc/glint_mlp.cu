@@ -599,6 +599,17 @@ __device__ __forceinline__ void frag_b2(const __nv_bfloat16 *dz, int ld, int k0,
     ldsm_x4_trans(b, row_chunk_addr(dz, ld, k0 + (L & 7) + (((L >> 3) & 1) << 3), (n0 >> 3) + (L >> 4)));
 }
 
+// Programmatic dependent launch between the training kernels: a kernel's
+// blocks may become resident while the previous kernel of the stream still
+// runs; griddepcontrol.wait (first, before any global read or write) holds
+// them until that kernel has completed and its writes are visible, and
+// launch_dependents lets the next kernel's blocks be scheduled.  Without the
+// launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait_then_release() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int NT>
 __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, const float *__restrict__ lpg,
                                                   const float *__restrict__ targets, long n_total, long first,
@@ -619,6 +630,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
     float *lps = red + kNT;                                  // [CH][kLpStride] log-priors
     float *ys = lps + CH * kLpStride;                        // [CH][16] targets
 
+    pdl_wait_then_release();
     load_weights<kNT>(sw, wt, params);
     copy_swz<kHid, kNT>(sb.w2, wb);
     {  // W3 [in][out] unswizzled: 64 rows of 16 BF16, 2 chunks of 16 bytes each
@@ -862,6 +874,7 @@ __global__ void __launch_bounds__(kRedParams * kRedWarps) k_mlp_reduce_adam(
     float *__restrict__ m, float *__restrict__ v, int K, float lr, float beta1, float beta2, float eps, float bc1,
     float bc2, __nv_bfloat16 *__restrict__ wt, __nv_bfloat16 *__restrict__ wb) {
     __shared__ float part_sum[kRedWarps][kRedParams];
+    pdl_wait_then_release();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.x * kRedParams + lane;
     float gs = 0.f;
@@ -1064,6 +1077,27 @@ void glint_mlp_weights(const glint_mlp *g, const void **wt, const float **params
 int glint_mlp_k(const glint_mlp *g) { return g ? g->K : 0; }
 int glint_mlp_device(const glint_mlp *g) { return g ? g->device : -1; }
 
+namespace {
+// A launch whose blocks may start while the stream's previous kernel runs
+// (the kernel begins with pdl_wait_then_release).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+}  // namespace
+
 extern "C" {
 
 int glint_mlp_param_count(void) { return kP; }
@@ -1239,21 +1273,24 @@ glint_status glint_mlp_forward(const glint_mlp *g, const uint16_t *x, const floa
 namespace {
 // One optimisation step (two launches): the per-block gradients, then their
 // sum in block order with the Adam update of the FP32 parameters and of their
-// BF16 copies.  Returns the number of gradient blocks.
-int enqueue_step(glint_mlp *g, const uint16_t *x, const float *lp, const float *targets, long n_total, long first,
-                 long batch, float lr, cudaStream_t s) {
+// BF16 copies.  *grid_out receives the number of gradient blocks.
+cudaError_t enqueue_step(glint_mlp *g, const uint16_t *x, const float *lp, const float *targets, long n_total,
+                         long first, long batch, float lr, cudaStream_t s, int *grid_out = nullptr) {
     const long nchunks = (batch + kChunk - 1) / kChunk;
     const int grid = (int)std::min<long>(nchunks, g->max_grid);
-    k_mlp_grad<1><<<grid, kNT, grad_smem(), s>>>(reinterpret_cast<const uint4 *>(x), lp, targets, n_total,
-                                                 first % n_total, batch, g->K, g->wt, g->wb, g->params, g->partial,
-                                                 g->loss);
+    if (grid_out) *grid_out = grid;
+    cudaError_t e = launch_pdl(k_mlp_grad<1>, grid, kNT, grad_smem(), s, reinterpret_cast<const uint4 *>(x), lp, targets, n_total,
+               first % n_total, batch, g->K, (const __nv_bfloat16 *)g->wt, (const __nv_bfloat16 *)g->wb,
+               (const float *)g->params, g->partial, g->loss);
     const long t = lr > 0.f ? g->step + 1 : std::max(g->step, 1L);
     const float bc1 = (float)(1.0 - std::pow(0.9, (double)t));
     const float bc2 = (float)(1.0 - std::pow(0.999, (double)t));
-    k_mlp_reduce_adam<<<(kP + kRedParams - 1) / kRedParams, kRedParams * kRedWarps, 0, s>>>(
-        g->partial, grid, g->grad, g->params, g->m, g->v, g->K, lr, 0.9f, 0.999f, 1e-8f, bc1, bc2, g->wt, g->wb);
-    if (lr > 0.f) g->step = t;
-    return grid;
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_mlp_reduce_adam, (kP + kRedParams - 1) / kRedParams, kRedParams * kRedWarps, 0, s,
+                   (const float *)g->partial, grid, g->grad, g->params, g->m, g->v, g->K, lr, 0.9f, 0.999f, 1e-8f,
+                   bc1, bc2, g->wt, g->wb);
+    if (e == cudaSuccess && lr > 0.f) g->step = t;
+    return e;
 }
 }  // namespace
 
@@ -1272,12 +1309,15 @@ glint_status glint_mlp_train(glint_mlp *g, const uint16_t *x, const float *lp, c
         return GLINT_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    for (long i = 0; i < steps; ++i) {
+    cudaError_t e = cudaSuccess;
+    long i = 0;
+    for (; i < steps && e == cudaSuccess; ++i) {
         const double cosine = 0.5 * (1.0 + std::cos(3.14159265358979323846 * (double)i / (double)steps));
         const float lr = (float)std::max((double)lr_max * cosine, (double)lr_min);
-        enqueue_step(g, x, lp, targets, n_total, (first + i * batch) % n_total, batch, lr, s);
+        e = enqueue_step(g, x, lp, targets, n_total, (first + i * batch) % n_total, batch, lr, s);
     }
-    g->last_launches = (int)std::min<long>(2 * steps, 1L << 30);
+    g->last_launches = (int)std::min<long>(2 * i, 1L << 30);
+    if (e != cudaSuccess) return cuda_status(e, "glint_mlp_train");
     return cuda_status(cudaGetLastError(), "glint_mlp_train");
 }
 
@@ -1295,9 +1335,10 @@ glint_status glint_mlp_train_step(glint_mlp *g, const uint16_t *x, const float *
         return GLINT_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const int grid = enqueue_step(g, x, lp, targets, n_total, first, batch, lr, s);
+    int grid = 0;
+    const cudaError_t e = enqueue_step(g, x, lp, targets, n_total, first, batch, lr, s, &grid);
     g->last_launches = 2;
-    glint_status st = cuda_status(cudaGetLastError(), "glint_mlp_train_step");
+    glint_status st = cuda_status(e != cudaSuccess ? e : cudaGetLastError(), "glint_mlp_train_step");
     if (st != GLINT_OK || !loss_out) return st;
     std::vector<float> l(grid);
     st = cuda_status(cudaMemcpyAsync(l.data(), g->loss, sizeof(float) * grid, cudaMemcpyDeviceToHost, s),

@@ -105,7 +105,7 @@ def test_shade_config3_sampled(gl, orc, scene3):
     rng = np.random.default_rng(2)
     big = fg[NP[fg] > 2.0 ** 24]
     order = fg[np.argsort(NP[fg])]
-    rows = np.unique(np.concatenate([rng.choice(fg, 2000, replace=False), rng.choice(big, 300, replace=False),
+    rows = np.unique(np.concatenate([rng.choice(fg, 65536, replace=False), rng.choice(big, 300, replace=False),
                                      order[:150], order[-150:], rng.choice(np.where(bg)[0], 50, replace=False)]))
     sub = _subset(gb, rows)
     dbg = glint.debug_buffers(len(rows), mp.K)
@@ -114,13 +114,27 @@ def test_shade_config3_sampled(gl, orc, scene3):
     rgb = out.cpu().numpy()
     assert np.array_equal(rgb, full[rows])  # the launch configuration changes nothing
 
-    o = oracle_shade(orc, sub.rows16(), env, mp)
     gpu = {k: v.cpu().numpy() for k, v in dbg.items()}
-    rep = compare_shade(orc, o, gpu, rgb[:, :3].astype(np.float64))
-    print(rep.summary())
-    assert rep.ok(), rep.failures[:10]
+    sub16 = sub.rows16()
+    env_pref = oracle_env(orc, env, mp)
+    np_all, pk_all, unresolved = [], [], 0
+    # the oracle in chunks, on all host cores; sixteen levels leave more valid
+    # outcomes per tree within the tie model, so up to 256 are enumerated
+    for c0 in range(0, len(rows), 2048):
+        sl = slice(c0, min(c0 + 2048, len(rows)))
+        o = oracle_shade(orc, sub16[sl], env, mp, env_pref=env_pref, max_cand=256)
+        rep = compare_shade(orc, o, {k: v[sl] for k, v in gpu.items()}, rgb[sl, :3].astype(np.float64))
+        print(rep.summary())
+        assert rep.ok(), rep.failures[:10]
+        np_all.append(o.np_)
+        pk_all.append(o.pk)
+        unresolved += rep.trees_unresolved
+    np_, pk = np.concatenate(np_all), np.concatenate(pk_all)
+    print(f"config 3: {len(rows)} pixels compared, {unresolved} of {6 * len(rows)} trees with more than 256 valid "
+          f"outcomes (checked by invariants only)")
+    assert unresolved <= 6 * len(rows) // 1000
     # the sample reaches the regimes this workload is for
-    assert np.sum(o.np_ > 2.0 ** 24) >= 300
-    assert np.sum(o.np_ >= np.float32(4294967040.0)) >= 1
-    assert np.sum((o.pk > 0) & (o.pk < EPS)) >= 100
-    assert np.sum((o.np_ > 0) & (o.np_ < 1)) >= 100
+    assert np.sum(np_ > 2.0 ** 24) >= 300
+    assert np.sum(np_ >= np.float32(4294967040.0)) >= 1
+    assert np.sum((pk > 0) & (pk < EPS)) >= 100
+    assert np.sum((np_ > 0) & (np_ < 1)) >= 100

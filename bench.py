@@ -282,9 +282,9 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 SURROGATE_TRAIN_SCENES = tuple(range(101, 109))  # scene seeds of the training pixels (the timed frame is seed 1)
-SURROGATE_STEPS, SURROGATE_BATCH, SURROGATE_LR = 96000, 8192, 3e-3
+SURROGATE_STEPS, SURROGATE_BATCH, SURROGATE_LR = 96000, 8192, 5e-3
 # the same data through large batches: the throughput end of the batch/accuracy trade-off
-SURROGATE_BIG_BATCH, SURROGATE_BIG_LR = 65536, 6e-3
+SURROGATE_BIG_BATCH, SURROGATE_BIG_LR = 65536, 1e-2
 SURROGATE_LABEL_S, E2_S, E2_REF_S = 32, 16, 64  # labels; the timed E2 path; the converged integral errors are judged against
 
 

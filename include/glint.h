@@ -367,8 +367,9 @@ glint_status glint_reflect_probs(glint_ctx *ctx, const glint_env *env, const gli
  * Parameters (FP32 master copy, glint_mlp_param_count() floats, in order):
  *   W1 [64 in][64 out], b1 [64], W2 [64][64], b2 [64], W3 [64][16], b3 [16]
  * (columns >= K of W3 and b3 are unused and stay fixed).  Training minimises
- * the mean cross-entropy -sum_k y_k log p_k against target distributions y
- * (e.g. E2's p_k from glint_reflect_probs) with Adam (beta1 0.9, beta2 0.999,
+ * the mean squared error sum_k (p_k - y_k)^2 against target distributions y
+ * (e.g. E2's p_k from glint_reflect_probs; the quantity the surrogate's error
+ * is judged by) with Adam (beta1 0.9, beta2 0.999,
  * eps 1e-8, FP32).  The gradient of a batch is accumulated per resident block
  * in a fixed order and summed over blocks in block order, so a step is
  * deterministic.  Inputs x are stored as BF16 bit patterns (uint16), 64 per
@@ -426,7 +427,7 @@ glint_status glint_mlp_forward(const glint_mlp *mlp, const uint16_t *x, const fl
  * modulo n_total) of the inputs x, lp (as glint_mlp_forward) against
  * `targets` (device, n_total*K floats, each row a distribution).  lr = 0 only
  * computes the gradient (GLINT_MLP_GRAD); 0 < lr < 1 also takes an Adam step.
- * If loss_out is not NULL the batch's mean cross-entropy is written there
+ * If loss_out is not NULL the batch's mean squared error is written there
  * (host) and the call waits for the stream.  Enqueued on `stream`. */
 glint_status glint_mlp_train_step(glint_mlp *mlp, const uint16_t *x, const float *lp, const float *targets,
                                   long n_total, long first, long batch, float lr, float *loss_out, void *stream);

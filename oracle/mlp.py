@@ -8,10 +8,12 @@ NDF mass p_k of Eq. probhk (what the E2 quadrature computes), so its maths has
 no printed reference.  This module is the plain definition of the network
 (inputs from the oracle's or_mlp_features: E1's p_k, filtered weights at five
 taps, mu_o, sqrt a_x, sqrt a_y; logits plus the log-prior log max(p^E1,
-1e-6)), its cross-entropy loss, the loss gradient by backpropagation and one
-Adam step, in float64 numpy.  It is pinned, independently of itself, by
-central finite differences of the loss (exact mode), by closed forms (uniform
-logits give log K; the first Adam step moves every weight by lr sign(g)), and
+1e-6)), its loss (the squared error sum_k (p_k - y_k)^2 of the output
+distribution, the quantity the surrogate's error is judged by), the loss
+gradient by backpropagation and one Adam step, in float64 numpy.  It is
+pinned, independently of itself, by central finite differences of the loss
+(exact mode), by closed forms (uniform logits give p = 1/K; the first Adam
+step moves every weight by lr sign(g)), and
 by the BF16 rounding agreeing with PyTorch's conversion.
 
 Two modes:
@@ -101,12 +103,10 @@ def forward(params, X, K: int, lp=None, exact: bool = False) -> dict:
 
 
 def loss(params, X, Y, K: int, lp=None, exact: bool = True) -> float:
-    """Mean over the batch of the cross-entropy -sum_k y_k log p_k."""
+    """Mean over the batch of the squared error sum_k (p_k - y_k)^2."""
     p = forward(params, X, K, lp, exact)["p"]
     Y = np.asarray(Y, np.float64)
-    with np.errstate(divide="ignore"):
-        lp = np.where(Y > 0, np.log(np.maximum(p, 1e-300)), 0.0)
-    return float(-np.sum(Y * lp) / X.shape[0])
+    return float(np.sum((p - Y) ** 2) / X.shape[0])
 
 
 def gradient(params, X, Y, K: int, lp=None, exact: bool = False) -> tuple[np.ndarray, np.ndarray, float]:
@@ -117,9 +117,11 @@ def gradient(params, X, Y, K: int, lp=None, exact: bool = False) -> tuple[np.nda
     f = forward(params, X, K, lp, exact)
     Y = np.asarray(Y, np.float64)
     B = X.shape[0]
-    ysum = Y.sum(axis=1, keepdims=True)
-    # d loss / d z3 for softmax + cross-entropy: (p sum(y) - y) / B
-    e3 = (f["p"] * ysum - Y) / B
+    # d loss / d z3 through the softmax: with d = p - y and s = sum_k p_k d_k,
+    # dL/dz_k = 2 p_k (d_k - s) / B
+    dd = f["p"] - Y
+    sd = np.sum(f["p"] * dd, axis=1, keepdims=True)
+    e3 = 2.0 * f["p"] * (dd - sd) / B
     d3 = rnd(e3)
     m2 = (f["h2"] > 0).astype(np.float64)
     m1 = (f["h1"] > 0).astype(np.float64)
@@ -138,9 +140,7 @@ def gradient(params, X, Y, K: int, lp=None, exact: bool = False) -> tuple[np.nda
            "W3": np.zeros((N_HID, N_OUT_PAD)), "b3": np.zeros(N_OUT_PAD)}
     mag["W3"][:, :K] = np.abs(f["h2"]).T @ a3
     mag["b3"][:K] = a3.sum(0)
-    with np.errstate(divide="ignore"):
-        lp = np.where(Y > 0, np.log(np.maximum(f["p"], 1e-300)), 0.0)
-    L = float(-np.sum(Y * lp) / B)
+    L = float(np.sum(dd ** 2) / B)
     return pack(g), pack(mag), L
 
 
@@ -183,10 +183,15 @@ def error_bounds(params, X, Y, K: int, lp=None, feat_err=None):
         return dp, None
     Y = np.asarray(Y, np.float64)
     B = X.shape[0]
-    ysum = Y.sum(axis=1, keepdims=True)
-    e3 = (p * ysum - Y) / B
+    dd = p - Y
+    sd = np.sum(p * dd, axis=1, keepdims=True)
+    e3 = 2.0 * p * (dd - sd) / B
     d3 = bf16(e3)
-    de3 = dp * ysum / B + 2.0 ** -22 * (np.abs(p * ysum) + np.abs(Y)) / B
+    # p off by at most dp moves d by dp and s by sum_j (dp_j |d_j| + (p_j + dp_j) dp_j);
+    # the FP32 arithmetic of d, s and the product adds a few units of 2^-24
+    dsd = np.sum(dp * np.abs(dd) + (p + dp) * dp, axis=1, keepdims=True)
+    de3 = (2.0 / B) * (dp * np.abs(dd - sd) + (p + dp) * (dp + dsd)) \
+        + 2.0 ** -21 * (2.0 / B) * p * (np.abs(dd) + np.sum(p * np.abs(dd), axis=1, keepdims=True) + np.abs(Y) + p)
     dd3 = rounding_delta(e3, de3)
     # a ReLU mask may differ where the pre-activation is within reach of 0
     u2 = np.abs(f["z2"]) <= dz2

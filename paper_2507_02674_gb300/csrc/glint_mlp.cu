@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_features(ShadeArgs a, uint4 *__rest
 // b, b + G, b + 2G, ... (G = gridDim.x) of the batch and accumulates its
 // gradient (each sample's loss weighted by 1/batch) in partial[b][kP], always
 // in the same order, so the result does not depend on scheduling; its summed
-// cross-entropy goes to loss[b].  A chunk of 32 samples gives a batch of 8192
+// squared error sum_k (p_k - y_k)^2 goes to loss[b].  A chunk of 32 samples gives a batch of 8192
 // 256 blocks, so every SM has work; the 16-row tiles of the chunk go to the
 // warps in turn.
 constexpr int kChunk = 32;
@@ -745,20 +745,27 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
             softmax_rows<NT>(o, K, lps, row0);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
+                // squared error of p: with d = p - y and s = sum_k p_k d_k (the
+                // row's four lanes), dL/dz_k = 2 p_k (d_k - s) / B
                 const int r = row0 + g + 8 * h;
                 const long i = base + r;
                 const bool live = i < nb;
-                float y[2][2], ysum = 0.f;
+                float dv[2][2], sdot = 0.f;
 #pragma unroll
                 for (int j = 0; j < 2; ++j)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int col = j * 8 + 2 * t + e;
-                        y[j][e] = ys[r * 16 + col];  // 0 past K and for rows past the batch
-                        ysum += y[j][e];
+                        dv[j][e] = 0.f;
+                        if (live && col < K) {
+                            const float pv = o[j < NT ? j : 0][2 * h + e];
+                            dv[j][e] = pv - ys[r * 16 + col];
+                            sdot = fmaf(pv, dv[j][e], sdot);
+                            lsum = fmaf(dv[j][e], dv[j][e], lsum);
+                        }
                     }
-                ysum += __shfl_xor_sync(0xffffffffu, ysum, 1);
-                ysum += __shfl_xor_sync(0xffffffffu, ysum, 2);
+                sdot += __shfl_xor_sync(0xffffffffu, sdot, 1);
+                sdot += __shfl_xor_sync(0xffffffffu, sdot, 2);
 #pragma unroll
                 for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -767,8 +774,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
                         float d = 0.f;
                         if (live && col < K) {
                             const float pv = o[j < NT ? j : 0][2 * h + e];
-                            d = (pv * ysum - y[j][e]) * invB;
-                            if (y[j][e] > 0.f) lsum -= y[j][e] * logf(fmaxf(pv, 1e-30f));
+                            d = 2.f * pv * (dv[j][e] - sdot) * invB;
                         }
                         dz3[r * 16 + col] = __float2bfloat16_rn(d);
                     }
@@ -836,7 +842,7 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
         grad_w(xs, h2, 64, part + kOffW1, kHid, acc, std::integral_constant<int, 8>{});
         col_sums(h2, 64, kHid, part + kOffB1, acc);  // ends with a barrier: xs, h1, h2, dz free
     }
-    // the block's summed cross-entropy: warp sums, then the four in order
+    // the block's summed squared error: warp sums, then the four in order
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
     if (lane == 0) red[warp] = lsum;

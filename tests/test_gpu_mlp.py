@@ -119,7 +119,7 @@ def test_mlp_forward_matches_oracle(gl, orc, K):
 @pytest.mark.parametrize("K,n,first,batch", [(4, 3000, 1700, 2500), (8, 3000, 0, 3000), (2, 1000, 900, 777),
                                              (8, 70000, 5, 65613)])
 def test_mlp_gradient_matches_oracle(gl, K, n, first, batch):
-    """Gradient of the mean cross-entropy over `batch` samples starting at
+    """Gradient of the mean squared error of p over `batch` samples starting at
     `first` (wrapping around the data set), seeded inputs shaped like the
     surrogate's; the largest case runs several 128-sample chunks per
     resident block."""

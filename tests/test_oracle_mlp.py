@@ -1,8 +1,9 @@
 """Pins of the FP64 reference of the p_k surrogate (oracle/mlp.py and the
 oracle's or_mlp_features) to facts outside themselves: PyTorch's bfloat16
-conversion, central finite differences of the loss, closed forms of softmax
-cross-entropy and of the first Adam step, the derivative of the mirror
-direction, and the tap features under constant and two-tone maps.  CPU only."""
+conversion, central finite differences of the loss, closed forms of the
+squared error at uniform and prior outputs and of the first Adam step, the
+derivative of the mirror direction, and the tap features under constant and
+two-tone maps.  CPU only."""
 import numpy as np
 import pytest
 import torch
@@ -78,18 +79,25 @@ def test_gradient_matches_finite_differences(K, normalised):
 
 def test_zero_output_layer_gives_the_prior():
     """With W3 = 0 and b3 = 0 the logits are the log-prior: p = normalised
-    prior; without a prior the loss is log K (uniform p)."""
+    prior; without a prior p is uniform and the squared error of a target
+    distribution y is sum_k y_k^2 - 1/K.  Targets equal to the prior are the
+    loss's minimum: loss 0 and a zero gradient everywhere."""
     K = 8
     X, lp, Y = _data(32, K)
     d = mlp.unpack(synth.mlp_params(K=K).astype(np.float64))
     d["W3"][:] = 0.0
     d["b3"][:] = 0.0
     prm = mlp.pack(d)
-    assert mlp.loss(prm, X, Y, K) == pytest.approx(np.log(K), rel=1e-12)
+    Yn = Y / Y.sum(1, keepdims=True)
+    assert mlp.loss(prm, X, Yn, K) == pytest.approx(np.mean(np.sum(Yn ** 2, 1)) - 1.0 / K, rel=1e-12)
     prior = np.exp(lp) / np.exp(lp).sum(1, keepdims=True)
     np.testing.assert_allclose(mlp.forward(prm, X, K, lp, exact=True)["p"], prior, rtol=1e-12)
-    g, _, _ = mlp.gradient(prm, X, Y, K, lp, exact=True)
-    np.testing.assert_allclose(g[-16:][:K], np.mean(prior - Y, axis=0), atol=1e-15)
+    g, _, L = mlp.gradient(prm, X, prior, K, lp, exact=True)
+    assert L == pytest.approx(0.0, abs=1e-28)
+    assert np.abs(g).max() < 1e-15
+    # away from the minimum the output bias moves p towards y: -g . (y - p) > 0
+    g, _, _ = mlp.gradient(prm, X, Yn, K, lp, exact=True)
+    assert -np.dot(g[-16:][:K], np.mean(Yn - prior, axis=0)) > 0
 
 
 def test_first_adam_step_is_lr_sign():

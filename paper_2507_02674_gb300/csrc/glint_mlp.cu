@@ -630,6 +630,44 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
     float *lps = red + kNT;                                  // [CH][kLpStride] log-priors
     float *ys = lps + CH * kLpStride;                        // [CH][16] targets
 
+    // stage chunk c's inputs, log-priors and targets in shared memory
+    auto stage = [&](long c) {
+        const long base = first + c * CH;  // samples [base, base + CH) of the data set, wrapping
+        const long nb = first + batch;
+        uint4 *xs4 = reinterpret_cast<uint4 *>(xs);
+        constexpr int kXPer = CH * 8 / kNT;  // 16-byte pieces of the chunk's inputs per thread
+        uint4 xv[kXPer];
+#pragma unroll
+        for (int it = 0; it < kXPer; ++it) {
+            const int idx = it * kNT + threadIdx.x, r = idx >> 3, q = idx & 7;
+            const long i = base + r;
+            xv[it] = (i < nb) ? __ldg(xg + (i % n_total) * 8 + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int it = 0; it < kXPer; ++it) {
+            const int idx = it * kNT + threadIdx.x, r = idx >> 3, q = idx & 7;
+            xs4[r * 8 + (q ^ (r & 7))] = xv[it];
+        }
+#pragma unroll
+        for (int it = 0; it < (CH * kOutPad + kNT - 1) / kNT; ++it) {
+            const int idx = it * kNT + threadIdx.x;
+            const int r = idx / kOutPad, k = idx % kOutPad;
+            const long i = base + r;
+            const bool ok = idx < CH * kOutPad && i < nb && k < K;
+            const long src = (i % n_total) * K + k;
+            const float lv = ok ? __ldg(lpg + src) : 0.f, yv = ok ? __ldg(targets + src) : 0.f;
+            if (idx < CH * kOutPad) {
+                lps[r * kLpStride + k] = lv;
+                ys[r * 16 + k] = yv;
+            }
+        }
+    };
+    // The training data are read-only for every kernel of the library, so the
+    // first chunk is staged before the wait on the previous kernel (in a
+    // training run, the previous step's Adam update); a launch whose
+    // predecessor may write them does not use programmatic dependent launch.
+    const long nchunks = (batch + CH - 1) / CH;
+    if ((long)blockIdx.x < nchunks) stage(blockIdx.x);
     pdl_wait_then_release();
     load_weights<kNT>(sw, wt, params);
     copy_swz<kHid, kNT>(sb.w2, wb);
@@ -639,7 +677,6 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const float invB = 1.f / (float)batch;
-    const long nchunks = (batch + CH - 1) / CH;
     float *part = partial + (size_t)blockIdx.x * kP;
     float lsum = 0.f;
 
@@ -697,37 +734,9 @@ __global__ void __launch_bounds__(kNT) k_mlp_grad(const uint4 *__restrict__ xg, 
         const bool acc = chunk != (long)blockIdx.x;
         const long base = first + chunk * CH;  // samples [base, base + CH) of the data set, wrapping
         const long nb = first + batch;
-        {
-            uint4 *xs4 = reinterpret_cast<uint4 *>(xs);
-            constexpr int kXPer = CH * 8 / kNT;  // 16-byte pieces of the chunk's inputs per thread
-            uint4 xv[kXPer];
-#pragma unroll
-            for (int it = 0; it < kXPer; ++it) {
-                const int idx = it * kNT + threadIdx.x, r = idx >> 3, q = idx & 7;
-                const long i = base + r;
-                xv[it] = (i < nb) ? __ldg(xg + (i % n_total) * 8 + q) : make_uint4(0u, 0u, 0u, 0u);
-            }
-#pragma unroll
-            for (int it = 0; it < kXPer; ++it) {
-                const int idx = it * kNT + threadIdx.x, r = idx >> 3, q = idx & 7;
-                xs4[r * 8 + (q ^ (r & 7))] = xv[it];
-            }
-#pragma unroll
-            for (int it = 0; it < (CH * kOutPad + kNT - 1) / kNT; ++it) {
-                const int idx = it * kNT + threadIdx.x;
-                const int r = idx / kOutPad, k = idx % kOutPad;
-                const long i = base + r;
-                const bool ok = idx < CH * kOutPad && i < nb && k < K;
-                const long src = (i % n_total) * K + k;
-                const float lv = ok ? __ldg(lpg + src) : 0.f, yv = ok ? __ldg(targets + src) : 0.f;
-                if (idx < CH * kOutPad) {
-                    lps[r * kLpStride + k] = lv;
-                    ys[r * 16 + k] = yv;
-                }
-            }
-        }
+        if (acc) stage(chunk);  // the block's first chunk was staged before the dependency wait
         __syncthreads();
-        // forward, and dZ3 = (softmax * sum(y) - y) / batch
+        // forward, and dZ3 = 2 p (d - p.d) / batch with d = p - y
 #pragma unroll 1
         for (int mt = warp; mt < MT; mt += kNT / 32) {
             const int row0 = mt * 16;
@@ -1085,10 +1094,10 @@ int glint_mlp_device(const glint_mlp *g) { return g ? g->device : -1; }
 
 namespace {
 // A launch whose blocks may start while the stream's previous kernel runs
-// (the kernel begins with pdl_wait_then_release).
+// (pdl: the kernel waits on it with pdl_wait_then_release), or an ordinary one.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
-                       Args... args) {
+cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, Args... args) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -1098,7 +1107,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, 
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
@@ -1279,20 +1288,24 @@ glint_status glint_mlp_forward(const glint_mlp *g, const uint16_t *x, const floa
 namespace {
 // One optimisation step (two launches): the per-block gradients, then their
 // sum in block order with the Adam update of the FP32 parameters and of their
-// BF16 copies.  *grid_out receives the number of gradient blocks.
+// BF16 copies.  *grid_out receives the number of gradient blocks.  after_step:
+// the stream's previous kernel is this network's Adam update (the gradient
+// kernel may then start during it; it never writes the training data).
 cudaError_t enqueue_step(glint_mlp *g, const uint16_t *x, const float *lp, const float *targets, long n_total,
-                         long first, long batch, float lr, cudaStream_t s, int *grid_out = nullptr) {
+                         long first, long batch, float lr, cudaStream_t s, bool after_step,
+                         int *grid_out = nullptr) {
     const long nchunks = (batch + kChunk - 1) / kChunk;
     const int grid = (int)std::min<long>(nchunks, g->max_grid);
     if (grid_out) *grid_out = grid;
-    cudaError_t e = launch_pdl(k_mlp_grad<1>, grid, kNT, grad_smem(), s, reinterpret_cast<const uint4 *>(x), lp, targets, n_total,
-               first % n_total, batch, g->K, (const __nv_bfloat16 *)g->wt, (const __nv_bfloat16 *)g->wb,
-               (const float *)g->params, g->partial, g->loss);
+    cudaError_t e = launch_pdl(after_step, k_mlp_grad<1>, grid, kNT, grad_smem(), s,
+                               reinterpret_cast<const uint4 *>(x), lp, targets, n_total, first % n_total, batch, g->K,
+                               (const __nv_bfloat16 *)g->wt, (const __nv_bfloat16 *)g->wb, (const float *)g->params,
+                               g->partial, g->loss);
     const long t = lr > 0.f ? g->step + 1 : std::max(g->step, 1L);
     const float bc1 = (float)(1.0 - std::pow(0.9, (double)t));
     const float bc2 = (float)(1.0 - std::pow(0.999, (double)t));
     if (e != cudaSuccess) return e;
-    e = launch_pdl(k_mlp_reduce_adam, (kP + kRedParams - 1) / kRedParams, kRedParams * kRedWarps, 0, s,
+    e = launch_pdl(true, k_mlp_reduce_adam, (kP + kRedParams - 1) / kRedParams, kRedParams * kRedWarps, 0, s,
                    (const float *)g->partial, grid, g->grad, g->params, g->m, g->v, g->K, lr, 0.9f, 0.999f, 1e-8f,
                    bc1, bc2, g->wt, g->wb);
     if (e == cudaSuccess && lr > 0.f) g->step = t;
@@ -1320,7 +1333,7 @@ glint_status glint_mlp_train(glint_mlp *g, const uint16_t *x, const float *lp, c
     for (; i < steps && e == cudaSuccess; ++i) {
         const double cosine = 0.5 * (1.0 + std::cos(3.14159265358979323846 * (double)i / (double)steps));
         const float lr = (float)std::max((double)lr_max * cosine, (double)lr_min);
-        e = enqueue_step(g, x, lp, targets, n_total, (first + i * batch) % n_total, batch, lr, s);
+        e = enqueue_step(g, x, lp, targets, n_total, (first + i * batch) % n_total, batch, lr, s, i > 0);
     }
     g->last_launches = (int)std::min<long>(2 * i, 1L << 30);
     if (e != cudaSuccess) return cuda_status(e, "glint_mlp_train");
@@ -1342,7 +1355,7 @@ glint_status glint_mlp_train_step(glint_mlp *g, const uint16_t *x, const float *
     }
     cudaStream_t s = (cudaStream_t)stream;
     int grid = 0;
-    const cudaError_t e = enqueue_step(g, x, lp, targets, n_total, first, batch, lr, s, &grid);
+    const cudaError_t e = enqueue_step(g, x, lp, targets, n_total, first, batch, lr, s, false, &grid);
     g->last_launches = 2;
     glint_status st = cuda_status(e != cudaSuccess ? e : cudaGetLastError(), "glint_mlp_train_step");
     if (st != GLINT_OK || !loss_out) return st;

@@ -492,7 +492,8 @@ typedef struct glint_server glint_server;
 
 typedef struct glint_server_desc {
     size_t memory_budget;   /* device bytes for admitted frames' buffers (one allocation at creation) */
-    long tick_pixels;       /* pixels shaded per tick at most (0 = 4194304) */
+    long tick_pixels;       /* pixels shaded per tick at most (0 = 2097152: ~0.3 ms of shading in device memory,
+                               ~0.7 ms in place; smaller ticks let small frames finish sooner) */
     int tile_pixels;        /* pixels per planned item, a multiple of 128 (0 = 16384); items are
                                launched in pieces of 1024 pixels */
     int max_frames;         /* admitted frames at most (0 = 64) */

@@ -332,7 +332,7 @@ glint_status glint_server_create(glint_ctx *ctx, int K, const glint_server_desc 
     *out = nullptr;
     if (K != 2 && K != 4 && K != 8 && K != 16) { set_error("glint_server_create: K = %d", K); return GLINT_ERR_INVALID_ARG; }
     glint_server_desc d = *desc;
-    if (d.tick_pixels == 0) d.tick_pixels = 4194304;
+    if (d.tick_pixels == 0) d.tick_pixels = 2097152;
     if (d.tile_pixels == 0) d.tile_pixels = 16384;
     if (d.max_frames == 0) d.max_frames = 64;
     if (d.max_inflight_ticks == 0) d.max_inflight_ticks = 2;
